@@ -1,0 +1,926 @@
+/*
+ * jr_oracle.c -- plain, slow, FP64 CPU oracle for Jump Restore light transport
+ * (Holl, Singh, Seidel, "Jump Restore Light Transport", arXiv 2409.07148).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or call
+ * this file: only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline
+ * leg use it.  It shares no code, header, table or constant generator with the
+ * CUDA library; the two meet only through the seeded scene arrays.
+ *
+ * What it computes, in the paper's order and notation:
+ *   - Alg. 2 (Jump Restore, Section 7.2): holding time t1 ~ Exp(1), killing time
+ *     t2 ~ Exp(k(x)); t1 < t2 -> local move, else regeneration from mu.
+ *   - killing rate for pi-invariant local dynamics and state-independent mu
+ *     (Section 6.2, "killing-rate-simplified"): k = c~ * u / p.
+ *   - local dynamics M^0 = Metropolis-Hastings (Alg. 1, Section 4) with the
+ *     Gaussian small-step kernel zeta (Section 5) and the acceptance function
+ *     of Section 4 ("optimal-acceptance-function"); zeta is symmetric so the
+ *     proposal densities cancel.
+ *   - estimator: normalisation-free tour estimator (Section 6.3),
+ *     (c~/j) * sum_i dt_i * g(x_{i-1}) / p(x_{i-1}), left-rectangle rule of
+ *     Section 7.4 ("approx").
+ *   - the integrand: primary-sample-space (Section 2, Kelemen et al.) path
+ *     contribution of a unidirectional path tracer with emission collected at
+ *     every vertex; p = luminance of the RGB contribution.
+ * Readings where the paper is silent (zeta's scale, luminance weights, path
+ * sampler, RNG stream layout, tie rules) are fixed identically for the CUDA
+ * library and listed in the design notes; they are restated where used below.
+ *
+ * Precision: every quantity is double.  Uniform variates are (r >> 8) * 2^-24,
+ * exactly representable in float and double.
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3", SC'11), written from its published definition.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <unistd.h>
+
+#define ORC_EXPORT __attribute__((visibility("default")))
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (SC'11, Section 3.3): 10 rounds of two 32x32->64 multiplies, */
+/* key schedule by the Weyl constants.                                        */
+/* ------------------------------------------------------------------------- */
+static const uint32_t PHILOX_M4x32_0 = 0xD2511F53u;
+static const uint32_t PHILOX_M4x32_1 = 0xCD9E8D57u;
+static const uint32_t PHILOX_W32_0 = 0x9E3779B9u;
+static const uint32_t PHILOX_W32_1 = 0xBB67AE85u;
+
+ORC_EXPORT void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += PHILOX_W32_0;
+            k1 += PHILOX_W32_1;
+        }
+        uint64_t p0 = (uint64_t)PHILOX_M4x32_0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)PHILOX_M4x32_1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Stream layout (a reading: the paper fixes no RNG).                         *
+ *   key     = (lo32(seed), hi32(seed))                                       *
+ *   counter = (block + 256*tag, chain id, lo32(step), hi32(step))            *
+ * tag 0: one Jump Restore step; block 0 -> (U1, U2, Ua, spare), blocks       *
+ *        1..ceil(D/4) -> D coordinates (Gaussian pairs for the local move or *
+ *        uniforms for regeneration -- the same counters, so the stream never *
+ *        depends on the branch taken).                                       *
+ * tag 1: the initial state of a chain (blocks 1.., step 0).                  *
+ * tag 2: plain path-tracing sample (chain id field = lo32(sample),           *
+ *        step field = hi32(sample)).                                         */
+enum { ORC_TAG_STEP = 0, ORC_TAG_INIT = 1, ORC_TAG_PT = 2 };
+
+static double u01(uint32_t r) { return (double)(r >> 8) * (1.0 / 16777216.0); }
+
+static void draw_block(uint64_t seed, uint32_t tag, uint32_t block, uint32_t chain, uint64_t step, double u[4])
+{
+    uint32_t ctr[4] = { block + 256u * tag, chain, (uint32_t)step, (uint32_t)(step >> 32) };
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t r[4];
+    orc_philox4x32_10(ctr, key, r);
+    for (int i = 0; i < 4; ++i) u[i] = u01(r[i]);
+}
+
+/* D coordinates from blocks 1..ceil((D+1)/4); one extra value is always there *
+ * for odd D so that Gaussian pairs never run short.                          */
+#define ORC_MAX_DIM 64
+static void draw_coords(uint64_t seed, uint32_t tag, uint32_t chain, uint64_t step, int D, double v[ORC_MAX_DIM + 4])
+{
+    int nblk = (D + 3) / 4;
+    if (D % 2 == 1 && 4 * nblk < D + 1) nblk++;
+    for (int b = 0; b < nblk; ++b) draw_block(seed, tag, (uint32_t)(b + 1), chain, step, v + 4 * b);
+}
+
+ORC_EXPORT void orc_draw_uniforms(uint64_t seed, uint32_t tag, uint32_t block, uint32_t chain, uint64_t step, double out[4])
+{
+    draw_block(seed, tag, block, chain, step, out);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Small vector helpers                                                       */
+/* ------------------------------------------------------------------------- */
+typedef struct { double x, y, z; } v3;
+static v3 mk(double x, double y, double z) { v3 r = { x, y, z }; return r; }
+static v3 add(v3 a, v3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+static v3 sub(v3 a, v3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+static v3 scl(v3 a, double s) { return mk(a.x * s, a.y * s, a.z * s); }
+static double dot(v3 a, v3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static v3 cross(v3 a, v3 b) { return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
+static v3 normalize(v3 a) { return scl(a, 1.0 / sqrt(dot(a, a))); }
+
+/* Orthonormal basis around unit n: Duff et al., "Building an Orthonormal     *
+ * Basis, Revisited", JCGT 6(1), 2017.                                        */
+static void onb(v3 n, v3* t, v3* b)
+{
+    double sign = copysign(1.0, n.z);
+    double a = -1.0 / (sign + n.z);
+    double bb = n.x * n.y * a;
+    *t = mk(1.0 + sign * n.x * n.x * a, sign * bb, -sign * n.x);
+    *b = mk(bb, sign + n.y * n.y * a, -n.y);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Scene                                                                      */
+/* ------------------------------------------------------------------------- */
+/* Material record: 12 floats                                                 *
+ *  [0] type (0 Lambertian, 1 modified Phong, 2 smooth dielectric)            *
+ *  [1..3] albedo rho (RGB)  [4..6] emission L_e (RGB, one-sided, emits on    *
+ *  the side the winding normal points to)  [7] Phong exponent  [8] IOR       */
+#define ORC_MAT_FLOATS 12
+enum { ORC_LAMBERT = 0, ORC_PHONG = 1, ORC_DIELECTRIC = 2 };
+
+typedef struct {
+    int type;
+    v3 albedo, emission;
+    double phong_n, ior;
+    int emits;
+} orc_material;
+
+typedef struct {
+    double lo[3], hi[3];
+    int left, right;    /* children, or -1 for a leaf */
+    int first, count;   /* leaf triangle range in the permuted index list */
+} orc_bvh_node;
+
+typedef struct {
+    int n_tris, n_mats;
+    v3* v0; v3* v1; v3* v2;
+    v3* ng;              /* unit geometric normal (e1 x e2) */
+    int* mat;
+    orc_material* mats;
+    v3 cam_o, cam_f, cam_r, cam_u;
+    /* optional median-split BVH (closest hit must equal brute force) */
+    int n_nodes;
+    orc_bvh_node* nodes;
+    int* perm;
+} orc_scene;
+
+ORC_EXPORT orc_scene* orc_scene_create(const float* verts, int n_verts, const uint32_t* tris, int n_tris,
+                                       const uint32_t* tri_mat, const float* mats, int n_mats, const float* camera12)
+{
+    orc_scene* s = (orc_scene*)calloc(1, sizeof(orc_scene));
+    if (!s) return NULL;
+    s->n_tris = n_tris;
+    s->n_mats = n_mats;
+    s->v0 = (v3*)malloc(sizeof(v3) * (size_t)(n_tris > 0 ? n_tris : 1));
+    s->v1 = (v3*)malloc(sizeof(v3) * (size_t)(n_tris > 0 ? n_tris : 1));
+    s->v2 = (v3*)malloc(sizeof(v3) * (size_t)(n_tris > 0 ? n_tris : 1));
+    s->ng = (v3*)malloc(sizeof(v3) * (size_t)(n_tris > 0 ? n_tris : 1));
+    s->mat = (int*)malloc(sizeof(int) * (size_t)(n_tris > 0 ? n_tris : 1));
+    s->mats = (orc_material*)malloc(sizeof(orc_material) * (size_t)(n_mats > 0 ? n_mats : 1));
+    for (int i = 0; i < n_tris; ++i) {
+        const uint32_t* t = tris + 3 * i;
+        if ((int)t[0] >= n_verts || (int)t[1] >= n_verts || (int)t[2] >= n_verts) { free(s); return NULL; }
+        s->v0[i] = mk(verts[3 * t[0]], verts[3 * t[0] + 1], verts[3 * t[0] + 2]);
+        s->v1[i] = mk(verts[3 * t[1]], verts[3 * t[1] + 1], verts[3 * t[1] + 2]);
+        s->v2[i] = mk(verts[3 * t[2]], verts[3 * t[2] + 1], verts[3 * t[2] + 2]);
+        s->ng[i] = normalize(cross(sub(s->v1[i], s->v0[i]), sub(s->v2[i], s->v0[i])));
+        s->mat[i] = (int)tri_mat[i];
+    }
+    for (int m = 0; m < n_mats; ++m) {
+        const float* r = mats + ORC_MAT_FLOATS * m;
+        orc_material* q = &s->mats[m];
+        q->type = (int)r[0];
+        q->albedo = mk(r[1], r[2], r[3]);
+        q->emission = mk(r[4], r[5], r[6]);
+        q->phong_n = r[7];
+        q->ior = r[8];
+        q->emits = (r[4] != 0.0f || r[5] != 0.0f || r[6] != 0.0f);
+    }
+    s->cam_o = mk(camera12[0], camera12[1], camera12[2]);
+    s->cam_f = mk(camera12[3], camera12[4], camera12[5]);
+    s->cam_r = mk(camera12[6], camera12[7], camera12[8]);
+    s->cam_u = mk(camera12[9], camera12[10], camera12[11]);
+    return s;
+}
+
+ORC_EXPORT void orc_scene_destroy(orc_scene* s)
+{
+    if (!s) return;
+    free(s->v0); free(s->v1); free(s->v2); free(s->ng); free(s->mat); free(s->mats);
+    free(s->nodes); free(s->perm);
+    free(s);
+}
+
+/* Moller-Trumbore ray/triangle test (Moller & Trumbore, JGT 1997).  Returns  *
+ * t > 0 of the hit, or +inf.  det == 0 (ray in the triangle's plane) misses. */
+static double mt_intersect(v3 o, v3 d, v3 v0, v3 v1, v3 v2)
+{
+    v3 e1 = sub(v1, v0), e2 = sub(v2, v0);
+    v3 pv = cross(d, e2);
+    double det = dot(e1, pv);
+    if (det == 0.0) return INFINITY;
+    double inv = 1.0 / det;
+    v3 tv = sub(o, v0);
+    double u = dot(tv, pv) * inv;
+    if (u < 0.0 || u > 1.0) return INFINITY;
+    v3 qv = cross(tv, e1);
+    double v = dot(d, qv) * inv;
+    if (v < 0.0 || u + v > 1.0) return INFINITY;
+    double t = dot(e2, qv) * inv;
+    return t > 0.0 ? t : INFINITY;
+}
+
+ORC_EXPORT double orc_intersect_triangle(const double o[3], const double d[3], const double v0[3], const double v1[3],
+                                         const double v2[3])
+{
+    return mt_intersect(mk(o[0], o[1], o[2]), mk(d[0], d[1], d[2]), mk(v0[0], v0[1], v0[2]),
+                        mk(v1[0], v1[1], v1[2]), mk(v2[0], v2[1], v2[2]));
+}
+
+/* Closest hit by brute force: the definition.  Ties on equal t go to the     *
+ * smaller triangle index (strict < over increasing index).                   */
+static int closest_brute(const orc_scene* s, v3 o, v3 d, double* t_out)
+{
+    double best = INFINITY;
+    int id = -1;
+    for (int i = 0; i < s->n_tris; ++i) {
+        double t = mt_intersect(o, d, s->v0[i], s->v1[i], s->v2[i]);
+        if (t < best) { best = t; id = i; }
+    }
+    *t_out = best;
+    return id;
+}
+
+/* --- optional median-split BVH (only an accelerator; pinned to brute force) */
+static int bvh_build_rec(orc_scene* s, int first, int count, int* cap)
+{
+    if (s->n_nodes >= *cap) {
+        *cap *= 2;
+        s->nodes = (orc_bvh_node*)realloc(s->nodes, sizeof(orc_bvh_node) * (size_t)*cap);
+    }
+    int me = s->n_nodes++;
+    orc_bvh_node nd;
+    for (int k = 0; k < 3; ++k) { nd.lo[k] = INFINITY; nd.hi[k] = -INFINITY; }
+    double clo[3] = { INFINITY, INFINITY, INFINITY }, chi[3] = { -INFINITY, -INFINITY, -INFINITY };
+    for (int i = first; i < first + count; ++i) {
+        int t = s->perm[i];
+        v3 p[3] = { s->v0[t], s->v1[t], s->v2[t] };
+        for (int j = 0; j < 3; ++j) {
+            double c[3] = { p[j].x, p[j].y, p[j].z };
+            for (int k = 0; k < 3; ++k) {
+                if (c[k] < nd.lo[k]) nd.lo[k] = c[k];
+                if (c[k] > nd.hi[k]) nd.hi[k] = c[k];
+            }
+        }
+        double cen[3] = { (p[0].x + p[1].x + p[2].x) / 3, (p[0].y + p[1].y + p[2].y) / 3, (p[0].z + p[1].z + p[2].z) / 3 };
+        for (int k = 0; k < 3; ++k) {
+            if (cen[k] < clo[k]) clo[k] = cen[k];
+            if (cen[k] > chi[k]) chi[k] = cen[k];
+        }
+    }
+    /* widen by a relative margin so that a slab test never rejects a box      *
+     * whose triangle the exact test accepts                                  */
+    for (int k = 0; k < 3; ++k) {
+        double m = 1e-9 * (1.0 + fabs(nd.lo[k]) + fabs(nd.hi[k]));
+        nd.lo[k] -= m; nd.hi[k] += m;
+    }
+    nd.left = nd.right = -1;
+    nd.first = first;
+    nd.count = count;
+    int axis = 0;
+    double ext = chi[0] - clo[0];
+    for (int k = 1; k < 3; ++k) if (chi[k] - clo[k] > ext) { ext = chi[k] - clo[k]; axis = k; }
+    if (count > 4 && ext > 0.0) {
+        double mid = 0.5 * (clo[axis] + chi[axis]);
+        int i = first, j = first + count - 1;
+        while (i <= j) {
+            int t = s->perm[i];
+            double c = axis == 0 ? s->v0[t].x + s->v1[t].x + s->v2[t].x
+                     : axis == 1 ? s->v0[t].y + s->v1[t].y + s->v2[t].y
+                                 : s->v0[t].z + s->v1[t].z + s->v2[t].z;
+            if (c / 3 < mid) ++i;
+            else { int tmp = s->perm[i]; s->perm[i] = s->perm[j]; s->perm[j] = tmp; --j; }
+        }
+        int nl = i - first;
+        if (nl == 0 || nl == count) nl = count / 2;
+        s->nodes[me] = nd;
+        int l = bvh_build_rec(s, first, nl, cap);
+        int r = bvh_build_rec(s, first + nl, count - nl, cap);
+        s->nodes[me].left = l;
+        s->nodes[me].right = r;
+        return me;
+    }
+    s->nodes[me] = nd;
+    return me;
+}
+
+ORC_EXPORT int orc_scene_build_bvh(orc_scene* s)
+{
+    free(s->nodes); free(s->perm);
+    s->n_nodes = 0;
+    if (s->n_tris == 0) { s->nodes = NULL; s->perm = NULL; return 0; }
+    int cap = 2 * s->n_tris + 1;
+    s->nodes = (orc_bvh_node*)malloc(sizeof(orc_bvh_node) * (size_t)cap);
+    s->perm = (int*)malloc(sizeof(int) * (size_t)s->n_tris);
+    for (int i = 0; i < s->n_tris; ++i) s->perm[i] = i;
+    bvh_build_rec(s, 0, s->n_tris, &cap);
+    return s->n_nodes;
+}
+
+static int slab_hits(const orc_bvh_node* n, v3 o, v3 inv, double tmax)
+{
+    double oo[3] = { o.x, o.y, o.z }, ii[3] = { inv.x, inv.y, inv.z };
+    double t0 = 0.0, t1 = tmax;
+    for (int k = 0; k < 3; ++k) {
+        double a = (n->lo[k] - oo[k]) * ii[k], b = (n->hi[k] - oo[k]) * ii[k];
+        if (isnan(a) || isnan(b)) { /* origin on a slab plane of a flat axis */
+            if (oo[k] < n->lo[k] || oo[k] > n->hi[k]) return 0;
+            continue;
+        }
+        double lo = a < b ? a : b, hi = a < b ? b : a;
+        if (lo > t0) t0 = lo;
+        if (hi < t1) t1 = hi;
+        if (t0 > t1) return 0;
+    }
+    return 1;
+}
+
+static int closest_bvh(const orc_scene* s, v3 o, v3 d, double* t_out)
+{
+    double best = INFINITY;
+    int id = -1;
+    if (s->n_nodes == 0) { *t_out = best; return -1; }
+    v3 inv = mk(1.0 / d.x, 1.0 / d.y, 1.0 / d.z);
+    int stack[128];
+    int sp = 0;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        const orc_bvh_node* n = &s->nodes[stack[--sp]];
+        if (!slab_hits(n, o, inv, best)) continue;
+        if (n->left < 0) {
+            for (int i = n->first; i < n->first + n->count; ++i) {
+                int t = s->perm[i];
+                double th = mt_intersect(o, d, s->v0[t], s->v1[t], s->v2[t]);
+                if (th < best || (th == best && th < INFINITY && t < id)) { best = th; id = t; }
+            }
+        } else {
+            if (sp + 2 > 128) abort();
+            stack[sp++] = n->right;
+            stack[sp++] = n->left;
+        }
+    }
+    *t_out = best;
+    return id;
+}
+
+static int closest_hit(const orc_scene* s, v3 o, v3 d, double* t)
+{
+    return s->n_nodes > 0 ? closest_bvh(s, o, d, t) : closest_brute(s, o, d, t);
+}
+
+ORC_EXPORT int orc_closest_hit(const orc_scene* s, const double o[3], const double d[3], int use_bvh, double* t)
+{
+    v3 oo = mk(o[0], o[1], o[2]), dd = mk(d[0], d[1], d[2]);
+    return use_bvh ? closest_bvh(s, oo, dd, t) : closest_brute(s, oo, dd, t);
+}
+
+/* ------------------------------------------------------------------------- */
+/* BSDF sampling (the path sampler; the paper renders with pbrt/lmc and does  */
+/* not print one, so this is a reading fixed for both sides).                 */
+/* d: incoming ray direction (unit), ng: unit geometric normal.               */
+/* Returns 0 if the path terminates (zero weight).                            */
+/* ------------------------------------------------------------------------- */
+static double lum(v3 c) { return 0.2126 * c.x + 0.7152 * c.y + 0.0722 * c.z; }
+
+/* Exact unpolarised Fresnel reflectance of a smooth dielectric interface.    */
+static double fresnel_dielectric(double cos_i, double eta_i, double eta_t, double* cos_t_out)
+{
+    double e = eta_i / eta_t;
+    double sin2_t = e * e * (1.0 - cos_i * cos_i);
+    if (sin2_t >= 1.0) { *cos_t_out = 0.0; return 1.0; }
+    double cos_t = sqrt(1.0 - sin2_t);
+    double rs = (eta_i * cos_i - eta_t * cos_t) / (eta_i * cos_i + eta_t * cos_t);
+    double rp = (eta_t * cos_i - eta_i * cos_t) / (eta_t * cos_i + eta_i * cos_t);
+    *cos_t_out = cos_t;
+    return 0.5 * (rs * rs + rp * rp);
+}
+
+ORC_EXPORT double orc_fresnel(double cos_i, double eta_i, double eta_t)
+{
+    double ct;
+    return fresnel_dielectric(cos_i, eta_i, eta_t, &ct);
+}
+
+static int scatter(const orc_material* m, v3 d, v3 ng, double u1, double u2, v3* wi, v3* w)
+{
+    if (m->type == ORC_DIELECTRIC) {
+        double cos_i = -dot(d, ng);
+        double eta_i = 1.0, eta_t = m->ior;
+        v3 nn = ng;
+        if (cos_i < 0.0) { cos_i = -cos_i; eta_i = m->ior; eta_t = 1.0; nn = scl(ng, -1.0); }
+        double cos_t;
+        double R = fresnel_dielectric(cos_i, eta_i, eta_t, &cos_t);
+        if (u1 < R) {
+            *wi = add(d, scl(nn, 2.0 * cos_i));
+        } else {
+            double e = eta_i / eta_t;
+            *wi = add(scl(d, e), scl(nn, e * cos_i - cos_t));
+        }
+        *w = mk(1.0, 1.0, 1.0);
+        return 1;
+    }
+    v3 ns = dot(d, ng) < 0.0 ? ng : scl(ng, -1.0); /* two-sided: face the viewer */
+    if (m->type == ORC_LAMBERT) {
+        /* cosine-weighted hemisphere by Malley's method; weight = albedo */
+        double r = sqrt(u1), phi = 2.0 * M_PI * u2;
+        double lz = sqrt(1.0 - u1 > 0.0 ? 1.0 - u1 : 0.0);
+        v3 t, b;
+        onb(ns, &t, &b);
+        *wi = add(add(scl(t, r * cos(phi)), scl(b, r * sin(phi))), scl(ns, lz));
+        *w = m->albedo;
+        return lum(*w) > 0.0 || w->x > 0.0 || w->y > 0.0 || w->z > 0.0;
+    }
+    /* modified Phong (Lafortune & Willems 1994): sample cos^n lobe about the  *
+     * mirror direction, pdf (n+1)/(2pi) cos^n a; weight = f cos_i / pdf       *
+     * = rho (n+2)/(n+1) cos_i, zero below the surface                         */
+    v3 r = sub(d, scl(ns, 2.0 * dot(d, ns)));
+    double n = m->phong_n;
+    double cos_a = pow(1.0 - u1, 1.0 / (n + 1.0));
+    double sin_a = sqrt(1.0 - cos_a * cos_a > 0.0 ? 1.0 - cos_a * cos_a : 0.0);
+    double phi = 2.0 * M_PI * u2;
+    v3 t, b;
+    onb(r, &t, &b);
+    *wi = add(add(scl(t, sin_a * cos(phi)), scl(b, sin_a * sin(phi))), scl(r, cos_a));
+    double cos_i = dot(*wi, ns);
+    if (cos_i <= 0.0) { *w = mk(0, 0, 0); return 0; }
+    *w = scl(m->albedo, (n + 2.0) / (n + 1.0) * cos_i);
+    return 1;
+}
+
+ORC_EXPORT int orc_scatter(const float* mat12, const double d[3], const double ng[3], double u1, double u2,
+                           double wi_out[3], double w_out[3])
+{
+    orc_material m;
+    m.type = (int)mat12[0];
+    m.albedo = mk(mat12[1], mat12[2], mat12[3]);
+    m.emission = mk(mat12[4], mat12[5], mat12[6]);
+    m.phong_n = mat12[7];
+    m.ior = mat12[8];
+    v3 wi, w;
+    int ok = scatter(&m, mk(d[0], d[1], d[2]), mk(ng[0], ng[1], ng[2]), u1, u2, &wi, &w);
+    wi_out[0] = wi.x; wi_out[1] = wi.y; wi_out[2] = wi.z;
+    w_out[0] = w.x; w_out[1] = w.y; w_out[2] = w.z;
+    return ok;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The integrand: PSS path contribution F(x), x in [0,1)^D, D = 2 + 2*depth.  */
+/* (x0, x1): film point; bounce b uses (x_{2+2b}, x_{3+2b}).  Emission is     */
+/* added at every vertex v1..v_{depth+1}.  Miss -> stop (black background).   */
+/* No Russian roulette, no light sampling.  Returns the number of ray casts.  */
+/* hit_ids (optional, depth+1 entries): triangle hit by each cast, -1 = none. */
+/* ------------------------------------------------------------------------- */
+#define ORC_EPS_OFFSET 1e-4
+
+static int eval_path(const orc_scene* s, int depth, const double* x, v3* F_out, int* hit_ids)
+{
+    v3 F = mk(0, 0, 0), T = mk(1, 1, 1);
+    v3 o = s->cam_o;
+    v3 d = normalize(add(s->cam_f, add(scl(s->cam_r, 2.0 * x[0] - 1.0), scl(s->cam_u, 1.0 - 2.0 * x[1]))));
+    int casts = 0;
+    if (hit_ids) for (int v = 0; v <= depth; ++v) hit_ids[v] = -1;
+    for (int v = 0; v <= depth; ++v) {
+        double t;
+        int id = closest_hit(s, o, d, &t);
+        ++casts;
+        if (hit_ids) hit_ids[v] = id;
+        if (id < 0) break;
+        const orc_material* m = &s->mats[s->mat[id]];
+        v3 ng = s->ng[id];
+        v3 p = add(o, scl(d, t));
+        if (m->emits && -dot(d, ng) > 0.0)
+            F = add(F, mk(T.x * m->emission.x, T.y * m->emission.y, T.z * m->emission.z));
+        if (v == depth) break;
+        v3 wi, w;
+        if (!scatter(m, d, ng, x[2 + 2 * v], x[3 + 2 * v], &wi, &w)) break;
+        T = mk(T.x * w.x, T.y * w.y, T.z * w.z);
+        if (T.x == 0.0 && T.y == 0.0 && T.z == 0.0) break;
+        v3 off = dot(wi, ng) >= 0.0 ? ng : scl(ng, -1.0);
+        double mx = fabs(p.x);
+        if (fabs(p.y) > mx) mx = fabs(p.y);
+        if (fabs(p.z) > mx) mx = fabs(p.z);
+        o = add(p, scl(off, ORC_EPS_OFFSET * (1.0 + mx)));
+        d = wi;
+    }
+    *F_out = F;
+    return casts;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Analytic targets on [0,1)^D for the quadrature pins.                       */
+/*   kind 1: sum of isotropic Gaussian bumps in the first two coordinates,    */
+/*           zero on a band a <= x0 < b; RGB channels modulated so g != p:    */
+/*           F = q * (0.5 + x0, 1, 0.5 + x1) (x1 := 0 when D == 1).           */
+/* params: [n_modes, band_a, band_b, (w, m0, m1, s) * n_modes]                */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int n_modes;
+    double band_a, band_b;
+    double w[16], m0[16], m1[16], sd[16];
+} orc_analytic;
+
+ORC_EXPORT orc_analytic* orc_analytic_create(const double* params)
+{
+    orc_analytic* a = (orc_analytic*)calloc(1, sizeof(orc_analytic));
+    a->n_modes = (int)params[0];
+    if (a->n_modes > 16) a->n_modes = 16;
+    a->band_a = params[1];
+    a->band_b = params[2];
+    for (int i = 0; i < a->n_modes; ++i) {
+        a->w[i] = params[3 + 4 * i];
+        a->m0[i] = params[4 + 4 * i];
+        a->m1[i] = params[5 + 4 * i];
+        a->sd[i] = params[6 + 4 * i];
+    }
+    return a;
+}
+
+ORC_EXPORT void orc_analytic_destroy(orc_analytic* a) { free(a); }
+
+static v3 eval_analytic(const orc_analytic* a, int D, const double* x)
+{
+    double x0 = x[0], x1 = D >= 2 ? x[1] : 0.0;
+    if (x0 >= a->band_a && x0 < a->band_b) return mk(0, 0, 0);
+    double q = 0.0;
+    for (int i = 0; i < a->n_modes; ++i) {
+        double dx = x0 - a->m0[i], dy = D >= 2 ? x1 - a->m1[i] : 0.0;
+        q += a->w[i] * exp(-(dx * dx + dy * dy) / (2.0 * a->sd[i] * a->sd[i]));
+    }
+    return mk(q * (0.5 + x0), q, q * (0.5 + x1));
+}
+
+ORC_EXPORT void orc_analytic_eval(const orc_analytic* a, int D, int n, const double* x, double* F3)
+{
+    for (int i = 0; i < n; ++i) {
+        v3 F = eval_analytic(a, D, x + (size_t)i * D);
+        F3[3 * i] = F.x; F3[3 * i + 1] = F.y; F3[3 * i + 2] = F.z;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Method parameters and the target                                           */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int target_kind;        /* 0 scene path, 1 analytic */
+    const orc_scene* scene;
+    const orc_analytic* analytic;
+    int D, depth;           /* depth only for the scene target (D = 2+2 depth) */
+    int width, height;
+    double c_tilde;         /* c~ of the simplified killing rate (Section 6.2) */
+    double sigma;           /* std of the Gaussian small-step kernel zeta */
+    uint64_t seed;
+    int rao_blackwell;      /* 1: holding time replaced by its mean 1/(1+k) */
+} orc_params;
+
+/* Target density p = luminance of F (all weights > 0: p = 0 iff F = 0).      */
+static void eval_target(const orc_params* P, const double* x, v3* F, double* p, int* hit_ids)
+{
+    if (P->target_kind == 0) eval_path(P->scene, P->depth, x, F, hit_ids);
+    else *F = eval_analytic(P->analytic, P->D, x);
+    *p = lum(*F);
+}
+
+/* Regeneration density u of mu w.r.t. Lebesgue measure on [0,1)^D: the      *
+ * uniform large-step distribution, u = 1 (Section 8: mu is the baseline's    *
+ * large-step distribution).                                                  */
+static double regen_density(const orc_params* P, const double* x) { (void)P; (void)x; return 1.0; }
+
+/* Killing rate, Section 6.2 ("killing-rate-simplified"): k = c~ u / p, with   *
+ * k = +inf where p = 0.                                                       */
+ORC_EXPORT double orc_killing_rate(double p, double u, double c_tilde)
+{
+    return p > 0.0 ? c_tilde * u / p : INFINITY;
+}
+
+/* Metropolis-Hastings acceptance probability, Section 4 ("optimal-          *
+ * acceptance-function") for a symmetric proposal: min(1, p(y)/p(x)) if       *
+ * p(x) > 0, else 1.                                                          */
+ORC_EXPORT double orc_mh_accept_prob(double px, double py)
+{
+    if (!(px > 0.0)) return 1.0;
+    double r = py / px;
+    return r < 1.0 ? r : 1.0;
+}
+
+static void pixel_of(const orc_params* P, const double* x, int* px, int* py)
+{
+    int i = (int)floor(x[0] * P->width);
+    int j = P->D >= 2 ? (int)floor(x[1] * P->height) : 0;
+    if (i >= P->width) i = P->width - 1;
+    if (j >= P->height) j = P->height - 1;
+    if (i < 0) i = 0;
+    if (j < 0) j = 0;
+    *px = i; *py = j;
+}
+
+static double wrap01(double y)
+{
+    double w = y - floor(y);
+    return w >= 1.0 ? 0.0 : w;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Chains                                                                     */
+/* State row per chain (doubles): x[0..D), F.rgb, p, u.                       */
+/* ------------------------------------------------------------------------- */
+ORC_EXPORT int orc_state_stride(int D) { return D + 5; }
+
+static orc_params make_params(int target_kind, const orc_scene* scene, const orc_analytic* an, int D, int depth,
+                              int width, int height, double c_tilde, double sigma, uint64_t seed, int rb)
+{
+    orc_params P;
+    P.target_kind = target_kind;
+    P.scene = scene;
+    P.analytic = an;
+    P.D = D;
+    P.depth = depth;
+    P.width = width;
+    P.height = height;
+    P.c_tilde = c_tilde;
+    P.sigma = sigma;
+    P.seed = seed;
+    P.rao_blackwell = rb;
+    return P;
+}
+
+static void eval_into_state(const orc_params* P, const double* x, double* st)
+{
+    v3 F;
+    double p;
+    for (int d = 0; d < P->D; ++d) st[d] = x[d];
+    eval_target(P, x, &F, &p, NULL);
+    st[P->D] = F.x; st[P->D + 1] = F.y; st[P->D + 2] = F.z;
+    st[P->D + 3] = p;
+    st[P->D + 4] = regen_density(P, x);
+}
+
+/* Initial state of each chain: x0 ~ mu (uniform), tag 1. */
+static void init_chains(const orc_params* P, uint64_t chain_begin, uint64_t n, double* state)
+{
+    int S = P->D + 5;
+    double v[ORC_MAX_DIM + 8];
+    for (uint64_t c = 0; c < n; ++c) {
+        draw_coords(P->seed, ORC_TAG_INIT, (uint32_t)(chain_begin + c), 0, P->D, v);
+        eval_into_state(P, v, state + c * S);
+    }
+}
+
+typedef struct {
+    const orc_params* P;
+    uint64_t chain_begin, c_lo, c_hi;
+    uint64_t step_begin, n_steps;
+    double* state;
+    double* accum;            /* W*H*4: RGB sums and time in the pixel */
+    uint64_t J, accepts, locals;
+    uint8_t* tr_flags;        /* optional [chain][step] */
+    double* tr_dt;
+    int32_t* tr_pix;
+    double* tr_margin;        /* optional: decision margins (t1 - t2, p_y - Ua p_x) */
+} orc_job;
+
+/* One chain advanced n steps by Alg. 2.  Splat (estimator of Section 6.3 with *
+ * the left-rectangle rule of Section 7.4): the state x_{i-1} held for dt_i     *
+ * contributes c~ dt_i (W H) F(x_{i-1}) / p(x_{i-1}) to its pixel; the factor   *
+ * W H is the box filter of a pixel in film coordinates.                        */
+static void run_chain(orc_job* jb, uint64_t c)
+{
+    const orc_params* P = jb->P;
+    int D = P->D, S = D + 5;
+    double* st = jb->state + c * S;
+    uint32_t chain = (uint32_t)(jb->chain_begin + c);
+    double v[ORC_MAX_DIM + 8], y[ORC_MAX_DIM];
+    double WH = (double)P->width * (double)P->height;
+    for (uint64_t i = 0; i < jb->n_steps; ++i) {
+        uint64_t step = jb->step_begin + i;
+        double U[4];
+        draw_block(P->seed, ORC_TAG_STEP, 0, chain, step, U);
+        double p = st[D + 3], u = st[D + 4];
+        /* line "Sample t1 from Exp(1)" and "Sample t2 from Exp(k(x))" */
+        double E1 = -log(1.0 - U[0]);
+        double E2 = -log(1.0 - U[1]);
+        double t1 = E1;
+        double t2 = p > 0.0 ? E2 * p / (P->c_tilde * u) : 0.0; /* Exp(k), k = c~u/p; k = inf -> 0 */
+        int local = t1 < t2;                                    /* tie -> termination branch */
+        double dt = local ? t1 : t2;
+        if (P->rao_blackwell) dt = p > 0.0 ? p / (p + P->c_tilde * u) : 0.0;
+        int pix = -1;
+        if (dt > 0.0 && p > 0.0) {
+            int px, py;
+            pixel_of(P, st, &px, &py);
+            pix = py * P->width + px;
+            double wgt = P->c_tilde * dt * WH / p;
+            double* a = jb->accum + 4 * (size_t)pix;
+            a[0] += wgt * st[D];
+            a[1] += wgt * st[D + 1];
+            a[2] += wgt * st[D + 2];
+            a[3] += dt;
+        }
+        draw_coords(P->seed, ORC_TAG_STEP, chain, step, D, v);
+        int accepted = 0;
+        double margin2 = 0.0;
+        if (local) {
+            /* local state transition: one MH step of M^0 with zeta = N(x, sigma^2) *
+             * wrapped onto the unit torus (symmetric, so alpha = min(1, p(y)/p(x))) */
+            for (int k = 0; k < (D + 1) / 2; ++k) {
+                double R = sqrt(-2.0 * log(1.0 - v[2 * k]));
+                double ang = 2.0 * M_PI * v[2 * k + 1];
+                y[2 * k] = wrap01(st[2 * k] + P->sigma * R * cos(ang));
+                if (2 * k + 1 < D) y[2 * k + 1] = wrap01(st[2 * k + 1] + P->sigma * R * sin(ang));
+            }
+            double cand[ORC_MAX_DIM + 5];
+            eval_into_state(P, y, cand);
+            double py = cand[D + 3];
+            /* U < alpha(x, y)  <=>  Ua * p(x) < p(y)  when p(x) > 0 */
+            accepted = (p > 0.0) ? (U[2] * p < py) : 1;
+            margin2 = py - U[2] * p;
+            if (accepted) memcpy(st, cand, sizeof(double) * (size_t)S);
+            jb->accepts += (uint64_t)accepted;
+            jb->locals += 1;
+        } else {
+            /* global state transition: regenerate from mu (a new tour) */
+            eval_into_state(P, v, st);
+            jb->J += 1;
+        }
+        if (jb->tr_flags) {
+            size_t o = (size_t)c * jb->n_steps + i;
+            jb->tr_flags[o] = (uint8_t)((local ? 0 : 1) | (accepted ? 2 : 0));
+            jb->tr_dt[o] = dt;
+            jb->tr_pix[o] = pix;
+            if (jb->tr_margin) {
+                jb->tr_margin[2 * o] = t1 - t2;
+                jb->tr_margin[2 * o + 1] = margin2;
+            }
+        }
+    }
+}
+
+static void* run_worker(void* arg)
+{
+    orc_job* jb = (orc_job*)arg;
+    for (uint64_t c = jb->c_lo; c < jb->c_hi; ++c) run_chain(jb, c);
+    return NULL;
+}
+
+static int resolve_threads(int n_threads, uint64_t n_items)
+{
+    if (n_threads <= 0) {
+        long n = sysconf(_SC_NPROCESSORS_ONLN);
+        n_threads = n > 0 ? (int)n : 1;
+    }
+    if ((uint64_t)n_threads > n_items) n_threads = (int)(n_items > 0 ? n_items : 1);
+    return n_threads;
+}
+
+/* Public: initialise n chains (state rows). */
+ORC_EXPORT void orc_chains_init(int target_kind, const orc_scene* scene, const orc_analytic* an, int D, int depth,
+                                int width, int height, double c_tilde, double sigma, uint64_t seed,
+                                uint64_t chain_begin, uint64_t n, double* state)
+{
+    orc_params P = make_params(target_kind, scene, an, D, depth, width, height, c_tilde, sigma, seed, 0);
+    init_chains(&P, chain_begin, n, state);
+}
+
+/* Public: advance n chains by n_steps (global step indices step_begin..).     *
+ * accum (W*H*4 doubles) is ADDED to; counters are returned in out3 =          *
+ * (J, accepts, local steps).  Trace arrays are optional ([chain][step]).      */
+ORC_EXPORT int orc_chains_advance(int target_kind, const orc_scene* scene, const orc_analytic* an, int D, int depth,
+                                  int width, int height, double c_tilde, double sigma, uint64_t seed,
+                                  int rao_blackwell, uint64_t chain_begin, uint64_t n, uint64_t step_begin,
+                                  uint64_t n_steps, double* state, double* accum, uint64_t* out3, uint8_t* tr_flags,
+                                  double* tr_dt, int32_t* tr_pix, double* tr_margin, int n_threads)
+{
+    if (D > ORC_MAX_DIM || D < 1) return -1;
+    orc_params P = make_params(target_kind, scene, an, D, depth, width, height, c_tilde, sigma, seed, rao_blackwell);
+    int T = resolve_threads(n_threads, n);
+    orc_job* jobs = (orc_job*)calloc((size_t)T, sizeof(orc_job));
+    pthread_t* th = (pthread_t*)calloc((size_t)T, sizeof(pthread_t));
+    size_t npx = (size_t)width * (size_t)height * 4;
+    for (int t = 0; t < T; ++t) {
+        orc_job* jb = &jobs[t];
+        jb->P = &P;
+        jb->chain_begin = chain_begin;
+        jb->c_lo = n * (uint64_t)t / (uint64_t)T;
+        jb->c_hi = n * (uint64_t)(t + 1) / (uint64_t)T;
+        jb->step_begin = step_begin;
+        jb->n_steps = n_steps;
+        jb->state = state;
+        jb->accum = (double*)calloc(npx, sizeof(double));
+        jb->tr_flags = tr_flags;
+        jb->tr_dt = tr_dt;
+        jb->tr_pix = tr_pix;
+        jb->tr_margin = tr_margin;
+        if (T > 1) pthread_create(&th[t], NULL, run_worker, jb);
+    }
+    if (T == 1) run_worker(&jobs[0]);
+    uint64_t J = 0, A = 0, L = 0;
+    for (int t = 0; t < T; ++t) {
+        if (T > 1) pthread_join(th[t], NULL);
+        for (size_t k = 0; k < npx; ++k) accum[k] += jobs[t].accum[k];
+        free(jobs[t].accum);
+        J += jobs[t].J;
+        A += jobs[t].accepts;
+        L += jobs[t].locals;
+    }
+    out3[0] = J; out3[1] = A; out3[2] = L;
+    free(jobs);
+    free(th);
+    return 0;
+}
+
+/* Public: F, p, u, k for given states (row-major n x D).  hit_ids optional,   *
+ * n x (depth+1).                                                             */
+ORC_EXPORT void orc_eval_states(int target_kind, const orc_scene* scene, const orc_analytic* an, int D, int depth,
+                                double c_tilde, uint64_t n, const double* x, double* F3, double* p, double* u,
+                                double* k, int32_t* hit_ids)
+{
+    orc_params P = make_params(target_kind, scene, an, D, depth, 1, 1, c_tilde, 0.0, 0, 0);
+    for (uint64_t i = 0; i < n; ++i) {
+        const double* xi = x + i * (uint64_t)D;
+        v3 F;
+        double pp;
+        int ids[ORC_MAX_DIM];
+        eval_target(&P, xi, &F, &pp, hit_ids ? ids : NULL);
+        if (hit_ids) for (int v = 0; v <= depth; ++v) hit_ids[i * (uint64_t)(depth + 1) + (uint64_t)v] = ids[v];
+        F3[3 * i] = F.x; F3[3 * i + 1] = F.y; F3[3 * i + 2] = F.z;
+        p[i] = pp;
+        u[i] = regen_density(&P, xi);
+        k[i] = orc_killing_rate(pp, u[i], c_tilde);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Plain Monte Carlo path tracing (the regeneration-only estimator; converged */
+/* references).  Sample s uses tag 2.  accum (W*H*4) gets W H F(x) per sample */
+/* (channel 3 counts samples); the pixel estimate is accum / n_samples.       */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    const orc_params* P;
+    uint64_t s_lo, s_hi;
+    double* accum;
+} orc_pt_job;
+
+static void* pt_worker(void* arg)
+{
+    orc_pt_job* jb = (orc_pt_job*)arg;
+    const orc_params* P = jb->P;
+    double v[ORC_MAX_DIM + 8];
+    double WH = (double)P->width * (double)P->height;
+    for (uint64_t s = jb->s_lo; s < jb->s_hi; ++s) {
+        draw_coords(P->seed, ORC_TAG_PT, (uint32_t)s, s >> 32, P->D, v);
+        v3 F;
+        double p;
+        eval_target(P, v, &F, &p, NULL);
+        int px, py;
+        pixel_of(P, v, &px, &py);
+        double* a = jb->accum + 4 * ((size_t)py * P->width + px);
+        a[0] += WH * F.x; a[1] += WH * F.y; a[2] += WH * F.z; a[3] += 1.0;
+    }
+    return NULL;
+}
+
+ORC_EXPORT void orc_render_pt(int target_kind, const orc_scene* scene, const orc_analytic* an, int D, int depth,
+                              int width, int height, uint64_t seed, uint64_t sample_begin, uint64_t n_samples,
+                              double* accum, int n_threads)
+{
+    orc_params P = make_params(target_kind, scene, an, D, depth, width, height, 1.0, 0.0, seed, 0);
+    int T = resolve_threads(n_threads, n_samples);
+    orc_pt_job* jobs = (orc_pt_job*)calloc((size_t)T, sizeof(orc_pt_job));
+    pthread_t* th = (pthread_t*)calloc((size_t)T, sizeof(pthread_t));
+    size_t npx = (size_t)width * (size_t)height * 4;
+    for (int t = 0; t < T; ++t) {
+        jobs[t].P = &P;
+        jobs[t].s_lo = sample_begin + n_samples * (uint64_t)t / (uint64_t)T;
+        jobs[t].s_hi = sample_begin + n_samples * (uint64_t)(t + 1) / (uint64_t)T;
+        jobs[t].accum = (double*)calloc(npx, sizeof(double));
+        if (T > 1) pthread_create(&th[t], NULL, pt_worker, &jobs[t]);
+    }
+    if (T == 1) pt_worker(&jobs[0]);
+    for (int t = 0; t < T; ++t) {
+        if (T > 1) pthread_join(th[t], NULL);
+        for (size_t k = 0; k < npx; ++k) accum[k] += jobs[t].accum[k];
+        free(jobs[t].accum);
+    }
+    free(jobs);
+    free(th);
+}
+
+ORC_EXPORT int orc_threads_default(void)
+{
+    long n = sysconf(_SC_NPROCESSORS_ONLN);
+    return n > 0 ? (int)n : 1;
+}
