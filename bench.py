@@ -1,0 +1,285 @@
+#!/usr/bin/env python3
+"""Throughput of Jump Restore chains on one GB300 (and N under torchrun).
+
+One bench step = one jr_advance of every chain by `--chain-steps` iterations of
+Alg. 2 (local MH move or regeneration, path construction + BVH traversal,
+killing rate, splat) on the 512x512, depth-8 Cornell-box-with-two-20k-triangle
+spheres workload with 2^20 chains -- i.e. 2^20 x 256 chain steps per bench step.
+
+Prints ONE JSON line (rank 0).  `value` = chain steps/s over all ranks, device
+timed with CUDA events on the launching stream; the L2 is flushed (a 512 MB
+write) between timed launches.  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Restore chain steps/s on 1 GB300; time to relMSE 1e-2, learned vs plain regen"
+UNIT = "chain steps/s"
+# FP32 operations issued per unit of traversal work (counted from the kernel
+# source: a node visit = 12 FMA + 24 min/max + 2 scaled compares for two
+# slab tests; a triangle test = Moller-Trumbore: 2 cross, 4 dot, 1 reciprocal,
+# 3 scaled products, 3 subtractions, 5 compares).
+FLOP_PER_NODE = 50
+FLOP_PER_TRI = 45
+SMS, FP32_LANES = 152, 128
+
+
+def workload(name):
+    from paper_2409_07148_gb300 import scenes
+    if name == "cornell_spheres":
+        sc = scenes.cornell_spheres()
+        return sc, dict(chains=1 << 20, chain_steps=256)
+    if name == "cornell":
+        sc = scenes.cornell()
+        return sc, dict(chains=256, chain_steps=10_000)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.idx = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, n in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip() == "Active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_rate(sc, wl, budget_s=12.0, seed=0):
+    """The FP64 oracle as it stands (its own BVH, all host cores) on a bounded
+    sample: a prefix of the chains, a few chain steps each."""
+    from oracle import oracle as O
+    osc = O.Scene(sc, bvh=sc.n_tris > 64)
+    cores = O.threads_default()
+    n_chains = min(wl["chains"], 1 << 12)
+    steps = 2
+    ch = O.Chains(osc, sc.D, sc.width, sc.height, seed=seed, n_chains=n_chains)
+    t0 = time.perf_counter()
+    ch.advance(steps)
+    dt = time.perf_counter() - t0
+    # grow the sample to about budget_s of CPU work (bounded)
+    total_steps, total_t = n_chains * steps, dt
+    grow = max(1, min(64, int(budget_s / max(dt, 1e-3))))
+    if grow > 1 and dt < budget_s:
+        k = min(grow * steps, 256)
+        t0 = time.perf_counter()
+        ch.advance(k)
+        total_t += time.perf_counter() - t0
+        total_steps += n_chains * k
+    return total_steps / total_t, cores, f"{n_chains} chains x {total_steps // n_chains} chain steps of the same workload"
+
+
+def run_reference(args, sc, wl):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    rates = []
+    cores, sample = None, None
+    for _ in range(args.warmup):
+        cpu_oracle_rate(sc, wl, budget_s=2.0)
+    for _ in range(args.steps):
+        r, cores, sample = cpu_oracle_rate(sc, wl, budget_s=args.ref_budget)
+        rates.append(r)
+    v = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "image": [sc.width, sc.height], "depth": sc.depth,
+                       "n_tris": sc.n_tris, "chains": wl["chains"], "chain_steps_per_step": wl["chain_steps"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cornell_spheres")
+    ap.add_argument("--block", type=int, default=0, help="step-kernel block size (0 = library default)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    sc, wl = workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, sc, wl)
+        return
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    from paper_2409_07148_gb300 import jr
+
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    C, K = wl["chains"], wl["chain_steps"]
+    with torch.cuda.stream(stream):
+        scene = jr.Scene(sc, stream=stream)
+        info = scene.info()
+        ch = jr.Chains(scene, sc.width, sc.height, sc.depth, C, seed=0, chain_offset=rank * C, stream=stream)
+        if args.block:
+            ch.set_block_size(args.block)
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+        for _ in range(args.warmup):
+            ch.advance(K, stream=stream)
+        stream.synchronize()
+        sampler = ClockSampler(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        sampler.start()
+        times = []
+        for _ in range(args.steps):
+            flush.fill_(1)                      # evict the L2 between timed launches
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ch.advance(K, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        st = ch.stats(stream=stream)
+        total = sum(times)
+        if ws > 1:
+            t = torch.tensor([total], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total = float(t.item())
+        steps_done = ws * C * K * args.steps
+        value = steps_done / total
+        # algorithmic work of one launch (instrumented variant on a fresh, identical chain set)
+        wc = jr.Chains(scene, sc.width, sc.height, sc.depth, C, seed=0, chain_offset=rank * C, stream=stream)
+        for _ in range(args.warmup):
+            wc.advance(K, stream=stream)
+        work = wc.advance_counted(K, stream=stream)
+        del wc
+        flop = FLOP_PER_NODE * work["nodes"] + FLOP_PER_TRI * work["tris"]
+        pk, pk_kind = peaks()
+        sm_mhz_peak = float(pk.get("sm_max_mhz", 2070.0))
+        alu_peak = SMS * FP32_LANES * 2 * sm_mhz_peak * 1e6 / 1e12
+        per_launch = total / args.steps / 1.0 if ws == 1 else total / args.steps
+        achieved = flop / 1e12 / (sum(times) / args.steps)
+        # end to end through the C ABI with host buffers: scene upload (BVH built on
+        # the host from the caller's arrays), chain init, advance, image read back
+        e2e_times = []
+        h2d = info["device_bytes"] + sc.verts.nbytes + sc.tris.nbytes + sc.tri_mat.nbytes + sc.mats.nbytes
+        d2h = sc.width * sc.height * 3 * 4
+        for _ in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s2 = jr.Scene(sc, stream=stream)
+            c2 = jr.Chains(s2, sc.width, sc.height, sc.depth, C, seed=1, chain_offset=rank * C, stream=stream)
+            c2.advance(K, stream=stream)
+            img = c2.resolve(stream=stream)
+            e2e_times.append(time.perf_counter() - t0)
+            del c2, s2
+        e2e = {"value": ws * C * K / (sum(e2e_times) / len(e2e_times)), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        r, cores, sample = cpu_oracle_rate(sc, wl)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}_{sc.width}x{sc.height}_depth{sc.depth}", "model": None,
+                   "scene": sc.name, "n_tris": sc.n_tris, "bvh_nodes": info["n_nodes"], "image": [sc.width, sc.height],
+                   "depth": sc.depth, "dim": sc.D, "chains_per_gpu": C, "chain_steps_per_step": K, "seed": 0,
+                   "c_tilde": 1.0, "sigma": 0.01, "regen": "uniform", "global_batch": ws * C, "seq_len": K,
+                   "parallelism": f"chains sharded over {ws} GPU(s)", "l2": "flushed by a 512 MB write between timed launches",
+                   "block": args.block or 128},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz_peak:.0f} MHz ({pk_kind} sm_max_mhz)",
+                     "work_per_launch": work, "flop_per_launch": flop},
+        "mrays_per_s": work["rays"] / (sum(times) / args.steps) / 1e6,
+        "regen_fraction": st["regenerations"] / max(1, st["regenerations"] + st["local_steps"]),
+        "accept_rate": st["accepted"] / max(1, st["local_steps"]),
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

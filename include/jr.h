@@ -1,0 +1,227 @@
+/*
+ * jr.h -- C ABI of the GB300-native Jump Restore light-transport library.
+ *
+ * Method: Holl, Singh, Seidel, "Jump Restore Light Transport" (arXiv 2409.07148).
+ * Many independent Jump Restore chains (Alg. 2, Section 7.2) advance in lockstep
+ * over primary sample space (PSS) x in [0,1)^D, D = 2 + 2 * max_depth:
+ *   - local dynamics: one Metropolis-Hastings step (Alg. 1, Section 4) with a
+ *     Gaussian small-step kernel of standard deviation `sigma` per coordinate,
+ *     wrapped onto the unit torus (symmetric, so alpha = min(1, p(y)/p(x)));
+ *   - global dynamics mu: uniform on [0,1)^D (the large-step distribution,
+ *     Section 8), density u = 1;
+ *   - killing rate k = c~ u / p (Section 6.2, invariant local dynamics and
+ *     state-independent mu), k = +inf where p = 0;
+ *   - target density p = luminance (0.2126, 0.7152, 0.0722) of the RGB path
+ *     contribution F(x) of a unidirectional path tracer;
+ *   - estimator: normalisation-free tour estimator (Section 6.3) with the
+ *     left-rectangle rule of Section 7.4: pixel j = (c~/J) sum_i dt_i W H
+ *     F(x_{i-1}) / p(x_{i-1}) over the steps whose state lies in pixel j, where
+ *     J counts regenerations (completed tours).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns a jr_status; no exception or abort crosses the ABI.
+ *     On error the outputs are left untouched and jr_last_error() returns a
+ *     thread-local message.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that only enqueue device work are asynchronous on that
+ *     stream; calls that return host data synchronise it.
+ *   - Handles are opaque and owned by the library; free them with
+ *     jr_*_destroy.  Host arrays passed in are caller-owned and copied before
+ *     the call returns.  Device pointers passed in are caller-owned and must
+ *     stay valid until the enqueued work completes.
+ *   - Device-side faults of the method (non-finite F, traversal budget
+ *     exhausted) are recorded in a status word read by jr_get_stats.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key =
+ *     (lo32(seed), hi32(seed)) and counter = (block + 256 tag, chain id,
+ *     lo32(step), hi32(step)); tag 0 = a chain step (block 0 gives U1, U2, Ua;
+ *     blocks 1.. give the D coordinates: Gaussian pairs for a local move or
+ *     uniforms for a regeneration), tag 1 = initial state (blocks 1..),
+ *     tag 2 = plain path-tracing sample.  A uniform is (r >> 8) * 2^-24.
+ */
+#ifndef JR_H
+#define JR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    JR_OK = 0,
+    JR_ERR_INVALID_ARG = 1, /* a null pointer, a size out of range, a malformed scene */
+    JR_ERR_CUDA = 2,        /* a CUDA runtime call failed (message has the CUDA error) */
+    JR_ERR_OOM = 3,         /* device or host allocation failed */
+    JR_ERR_WATCHDOG = 4,    /* a device-side iteration budget was exhausted */
+    JR_ERR_NUMERIC = 5,     /* a non-finite value reached the estimator */
+    JR_ERR_STATE = 6        /* the handle is in a state that does not allow the call */
+} jr_status;
+
+#define JR_MATERIAL_FLOATS 12 /* [type, albedo rgb, emission rgb, phong n, ior, 0, 0, 0] */
+#define JR_MAT_LAMBERT 0      /* two-sided Lambertian, cosine-weighted sampling, weight = albedo */
+#define JR_MAT_PHONG 1        /* modified Phong lobe about the mirror direction, weight rho (n+2)/(n+1) cos */
+#define JR_MAT_DIELECTRIC 2   /* smooth dielectric, Fresnel-chosen reflect/refract, weight 1 */
+#define JR_MAX_DEPTH 15       /* D = 2 + 2 * max_depth <= 32 */
+#define JR_FLAG_RAO_BLACKWELL 1u /* splat the conditional mean 1/(1+k) instead of the sampled dt */
+
+/* status-word bits (jr_stats.status_word) */
+#define JR_STATUS_NONFINITE 1u  /* F(x) was NaN/Inf for some state: it was treated as 0 */
+#define JR_STATUS_TRAVERSAL 2u  /* a ray exhausted the BVH node-visit budget: treated as a miss */
+#define JR_STATUS_STACK 4u      /* a traversal stack overflowed: treated as a miss */
+
+typedef struct jr_scene jr_scene;
+typedef struct jr_chains jr_chains;
+
+/* Scene: triangles with per-triangle material, a pinhole camera.  Host
+ * arrays, caller-owned, copied by jr_scene_create.
+ *   verts        n_verts x 3 float (x, y, z)
+ *   tris         n_tris x 3 uint32 vertex indices; winding gives the
+ *                geometric normal (v1 - v0) x (v2 - v0), the emitting side
+ *   tri_material n_tris uint32 indices into materials
+ *   materials    n_materials x JR_MATERIAL_FLOATS float
+ *   camera       origin, forward, right, up (12 floats): film point (x0, x1)
+ *                looks along forward + (2 x0 - 1) right + (1 - 2 x1) up. */
+typedef struct {
+    const float* verts;
+    uint32_t n_verts;
+    const uint32_t* tris;
+    uint32_t n_tris;
+    const uint32_t* tri_material;
+    const float* materials;
+    uint32_t n_materials;
+    float camera[12];
+} jr_scene_desc;
+
+/* Render / chain parameters (Alg. 2 inputs: target via the scene, mu, zeta,
+ * c~; Section 7.2). */
+typedef struct {
+    uint32_t width, height; /* image W x H; pixel (floor(x0 W), floor(x1 H)) */
+    uint32_t max_depth;     /* scattering events per path, 0..JR_MAX_DEPTH */
+    uint32_t flags;         /* JR_FLAG_* */
+    uint64_t n_chains;      /* chains in this set, >= 1 */
+    uint64_t chain_offset;  /* global id of the first chain (disjoint Philox streams) */
+    uint64_t seed;          /* Philox key */
+    float c_tilde;          /* c~ > 0 of the killing rate (the paper uses 1, Section 9) */
+    float sigma;            /* std of the Gaussian small-step kernel zeta, > 0 */
+} jr_params;
+
+typedef struct {
+    uint64_t steps_per_chain; /* Alg. 2 iterations each chain has taken */
+    uint64_t regenerations;   /* J: killings followed by a draw from mu (completed tours) */
+    uint64_t local_steps;     /* iterations that took the local branch */
+    uint64_t accepted;        /* accepted local MH proposals */
+    uint32_t status_word;     /* JR_STATUS_* bits, sticky */
+    uint32_t dim;             /* D */
+} jr_stats;
+
+typedef struct {
+    uint32_t n_tris, n_nodes, bvh_depth, n_materials;
+    uint64_t device_bytes; /* nodes + triangles + materials */
+} jr_scene_info;
+
+/* Upload a scene and build its BVH (binned SAH, host, native code).  The
+ * triangle arrays are copied; the call synchronises `stream` before it
+ * returns.  n_tris may be 0 (every ray misses).  Errors: JR_ERR_INVALID_ARG
+ * (index out of range, unknown material type, n_tris >= 2^27), JR_ERR_OOM,
+ * JR_ERR_CUDA. */
+jr_status jr_scene_create(const jr_scene_desc* desc, void* stream, jr_scene** out);
+jr_status jr_scene_get_info(const jr_scene* scene, jr_scene_info* out);
+void jr_scene_destroy(jr_scene* scene);
+
+/* Create a set of chains (library-owned SoA state, RGBA float framebuffer,
+ * FP64 accumulator, counters) and draw each initial state x0 ~ mu (Alg. 2
+ * "initial state"; tag 1).  Asynchronous on `stream`.  The scene must outlive
+ * the chains.  Errors: JR_ERR_INVALID_ARG (sizes, depth > JR_MAX_DEPTH,
+ * c_tilde <= 0, sigma <= 0, chain ids beyond 2^32), JR_ERR_OOM. */
+jr_status jr_chains_create(const jr_scene* scene, const jr_params* params, void* stream, jr_chains** out);
+void jr_chains_destroy(jr_chains* chains);
+
+/* Advance every chain by n_steps iterations of Alg. 2 (Section 7.2): clocks
+ * t1 ~ Exp(1), t2 ~ Exp(k(x)); splat (dt, x) into the framebuffer; local MH
+ * move if t1 < t2, else regenerate from mu and count a tour.  One persistent
+ * launch; then the FP32 framebuffer is folded into the FP64 accumulator.
+ * Asynchronous.  n_steps = 0 is a no-op.  Errors: JR_ERR_INVALID_ARG. */
+jr_status jr_advance(jr_chains* chains, uint32_t n_steps, void* stream);
+
+/* As jr_advance, and also write one record per (chain, step) into caller
+ * device buffers laid out [chain][step] (n_chains x n_steps):
+ *   flags: bit0 = the regeneration branch was taken, bit1 = a local proposal
+ *          was accepted;  dt: the splatted holding time (0 if nothing was
+ *          splatted);  pix: y*W + x of the splat, or -1.
+ * Any of the three pointers may be NULL. */
+jr_status jr_advance_traced(jr_chains* chains, uint32_t n_steps, uint8_t* flags_dev, float* dt_dev,
+                            int32_t* pix_dev, void* stream);
+
+/* As jr_advance, with the instrumented kernel variant that also counts the
+ * work it does: work_out = {ray casts, BVH node visits, ray/triangle tests}
+ * summed over every chain and step.  The chains advance exactly as with
+ * jr_advance (same Philox streams, same results).  Synchronises `stream`. */
+jr_status jr_advance_counted(jr_chains* chains, uint32_t n_steps, uint64_t work_out[3], void* stream);
+
+/* Threads per block of the step kernel for this chain set: a multiple of 32
+ * in [32, 256] (default 128).  Results do not depend on it. */
+jr_status jr_set_block_size(jr_chains* chains, uint32_t block);
+
+/* Resolve the estimate (Section 6.3): rgb_out[H][W][3] = accumulator / J
+ * (zeros while J = 0).  out_is_device = 1: rgb_out is device memory and the
+ * call is asynchronous; 0: host memory, the call synchronises `stream`. */
+jr_status jr_resolve(jr_chains* chains, float* rgb_out, int out_is_device, void* stream);
+
+/* Raw FP64 accumulator, out[H][W][4] = (sum of c~ dt W H F / p per channel,
+ * sum of dt in the pixel), for batch statistics and shard reductions.  Same
+ * device/host convention as jr_resolve. */
+jr_status jr_get_accumulator(jr_chains* chains, double* out, int out_is_device, void* stream);
+
+/* Counters and status word; synchronises `stream`.  Returns JR_ERR_NUMERIC or
+ * JR_ERR_WATCHDOG (with the stats filled in) if the status word is non-zero. */
+jr_status jr_get_stats(jr_chains* chains, jr_stats* out, void* stream);
+
+/* Chain state in SoA layout: x_out[d][chain] (D x n_chains float) and
+ * fpu_out[j][chain] (5 x n_chains float: F.r, F.g, F.b, p, u).  Host buffers;
+ * synchronises `stream`.  Either pointer may be NULL. */
+jr_status jr_get_state(jr_chains* chains, float* x_out, float* fpu_out, void* stream);
+
+/* Overwrite the chain state (same layout, host buffers; every x in [0,1)).
+ * fpu_in (the cached F, p, u of jr_get_state) may be NULL, in which case F, p
+ * and u are re-evaluated on the device.  A checkpoint restored with
+ * jr_set_state(x, fpu) + jr_set_counters continues bit-identically, because
+ * the Philox counters depend only on (seed, chain id, step index).
+ * Synchronises `stream`. */
+jr_status jr_set_state(jr_chains* chains, const float* x_in, const float* fpu_in, void* stream);
+
+/* Restore the per-set counters and step index of a checkpoint (host values). */
+jr_status jr_set_counters(jr_chains* chains, const jr_stats* in, const double* accumulator_host, void* stream);
+
+/* Evaluate the integrand and the Restore quantities for n given states
+ * (Section 6.2 killing rate; Section 4 target density): device buffers,
+ * x_dev[d][i] (D x n float, SoA) in; F_dev[c][i] (3 x n), p_dev, u_dev,
+ * k_dev (n each; k = +inf where p = 0) out; hit_ids_dev[v][i]
+ * ((max_depth+1) x n int32, -1 = no hit / not cast) optional (NULL).
+ * Uses params->max_depth and c_tilde only.  Asynchronous. */
+jr_status jr_eval_states(const jr_scene* scene, const jr_params* params, const float* x_dev, uint64_t n,
+                         float* F_dev, float* p_dev, float* u_dev, float* k_dev, int32_t* hit_ids_dev,
+                         void* stream);
+
+/* Plain Monte Carlo path tracing (the regeneration-only special case c~ ->
+ * inf of Section 6.3): samples sample_begin .. +n_samples (tag 2), each
+ * adding W H F(x) (and 1 in channel 3) to accum_dev[H][W][4] (device, FP64,
+ * caller-owned, added to).  Pixel estimate = accum / total samples.
+ * Asynchronous. */
+jr_status jr_render_pt(const jr_scene* scene, const jr_params* params, uint64_t sample_begin, uint64_t n_samples,
+                       double* accum_dev, void* stream);
+
+/* Raw Philox4x32-10 blocks for chains chain_begin .. +n at one (tag, block,
+ * step): out_dev[i][4] uint32 (device).  For bit-exact RNG parity tests. */
+jr_status jr_philox(uint64_t seed, uint32_t tag, uint32_t block, uint64_t chain_begin, uint64_t step, uint64_t n,
+                    uint32_t* out_dev, void* stream);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char* jr_last_error(void);
+/* Library version string. */
+const char* jr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JR_H */

@@ -1,0 +1,389 @@
+// Host runtime behind the C ABI of include/jr.h: argument checks, device
+// memory for scenes and chain sets, launch sequencing, error reporting.  No
+// exception or abort crosses the ABI; every failure becomes a jr_status and a
+// thread-local message.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/jr.h"
+#include "jr_internal.h"
+
+using namespace jr;
+
+namespace {
+
+thread_local std::string g_err;
+
+jr_status fail(jr_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+jr_status cuda_fail(cudaError_t e, const char* what) {
+    (void)cudaGetLastError();  // clear a sticky launch error so later calls see a clean slate
+    return fail(e == cudaErrorMemoryAllocation ? JR_ERR_OOM : JR_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+#define JR_CUDA(call, what)                      \
+    do {                                         \
+        cudaError_t e_ = (call);                 \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+template <class T>
+cudaError_t dev_alloc(T** p, size_t count) {
+    return cudaMalloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
+}
+
+}  // namespace
+
+struct jr_scene {
+    BvhNode* nodes = nullptr;
+    TriRecord* tris = nullptr;
+    Material* mats = nullptr;
+    SceneView view{};
+    jr_scene_info info{};
+    ~jr_scene() {
+        cudaFree(nodes);
+        cudaFree(tris);
+        cudaFree(mats);
+    }
+};
+
+struct jr_chains {
+    const jr_scene* scene = nullptr;
+    jr_params params{};
+    ChainView view{};
+    uint64_t steps = 0;
+    int block = 128;
+    ~jr_chains() {
+        cudaFree(view.x);
+        cudaFree(view.fpu);
+        cudaFree(view.fb);
+        cudaFree(view.acc64);
+        cudaFree(view.counters);
+        cudaFree(view.status);
+    }
+};
+
+extern "C" {
+
+const char* jr_last_error(void) { return g_err.c_str(); }
+
+const char* jr_version(void) { return "jr-gb300 0.1 (sm_103a)"; }
+
+jr_status jr_scene_create(const jr_scene_desc* desc, void* stream, jr_scene** out) {
+    if (!desc || !out) return fail(JR_ERR_INVALID_ARG, "jr_scene_create: null argument");
+    if (desc->n_tris > 0 && (!desc->verts || !desc->tris || !desc->tri_material))
+        return fail(JR_ERR_INVALID_ARG, "jr_scene_create: null triangle arrays");
+    if (desc->n_materials == 0 || !desc->materials)
+        return fail(JR_ERR_INVALID_ARG, "jr_scene_create: at least one material is required");
+    for (uint32_t t = 0; t < desc->n_tris; ++t)
+        if (desc->tri_material[t] >= desc->n_materials)
+            return fail(JR_ERR_INVALID_ARG, "jr_scene_create: triangle material index out of range");
+    std::vector<Material> mats(desc->n_materials);
+    for (uint32_t m = 0; m < desc->n_materials; ++m) {
+        const float* r = desc->materials + (size_t)JR_MATERIAL_FLOATS * m;
+        Material& q = mats[m];
+        q.type = (int)r[0];
+        if (r[0] != (float)q.type || q.type < JR_MAT_LAMBERT || q.type > JR_MAT_DIELECTRIC)
+            return fail(JR_ERR_INVALID_ARG, "jr_scene_create: unknown material type");
+        q.albedo = make_float3(r[1], r[2], r[3]);
+        q.emission = make_float3(r[4], r[5], r[6]);
+        q.emits = (r[4] != 0.f || r[5] != 0.f || r[6] != 0.f);
+        q.phong_inv_n1 = 1.0f / (r[7] + 1.0f);
+        q.phong_scale = (r[7] + 2.0f) / (r[7] + 1.0f);
+        q.ior = r[8];
+        q.pad = 0.f;
+        if (q.type == JR_MAT_PHONG && !(r[7] >= 0.f)) return fail(JR_ERR_INVALID_ARG, "jr_scene_create: Phong n < 0");
+        if (q.type == JR_MAT_DIELECTRIC && !(r[8] > 0.f)) return fail(JR_ERR_INVALID_ARG, "jr_scene_create: ior <= 0");
+    }
+    HostBvh bvh;
+    std::string err;
+    try {
+        if (!build_bvh(desc->verts, desc->n_verts, desc->tris, desc->n_tris, desc->tri_material, &bvh, &err))
+            return fail(JR_ERR_INVALID_ARG, "jr_scene_create: " + err);
+    } catch (const std::bad_alloc&) {
+        return fail(JR_ERR_OOM, "jr_scene_create: host allocation failed in the BVH build");
+    }
+    jr_scene* s = new (std::nothrow) jr_scene();
+    if (!s) return fail(JR_ERR_OOM, "jr_scene_create: host allocation failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if ((e = dev_alloc(&s->nodes, bvh.nodes.size())) != cudaSuccess ||
+        (e = dev_alloc(&s->tris, bvh.tris.size())) != cudaSuccess ||
+        (e = dev_alloc(&s->mats, mats.size())) != cudaSuccess ||
+        (e = cudaMemcpyAsync(s->nodes, bvh.nodes.data(), sizeof(BvhNode) * bvh.nodes.size(), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(s->tris, bvh.tris.data(), sizeof(TriRecord) * bvh.tris.size(), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(s->mats, mats.data(), sizeof(Material) * mats.size(), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+        delete s;
+        return cuda_fail(e, "jr_scene_create");
+    }
+    s->view.nodes = s->nodes;
+    s->view.tris = s->tris;
+    s->view.mats = s->mats;
+    s->view.root = bvh.root;
+    s->view.n_nodes = (int)bvh.nodes.size();
+    std::memcpy(s->view.cam, desc->camera, sizeof(float) * 12);
+    s->info.n_tris = desc->n_tris;
+    s->info.n_nodes = (uint32_t)bvh.nodes.size();
+    s->info.bvh_depth = (uint32_t)bvh.depth;
+    s->info.n_materials = desc->n_materials;
+    s->info.device_bytes =
+        sizeof(BvhNode) * bvh.nodes.size() + sizeof(TriRecord) * bvh.tris.size() + sizeof(Material) * mats.size();
+    *out = s;
+    return JR_OK;
+}
+
+jr_status jr_scene_get_info(const jr_scene* scene, jr_scene_info* out) {
+    if (!scene || !out) return fail(JR_ERR_INVALID_ARG, "jr_scene_get_info: null argument");
+    *out = scene->info;
+    return JR_OK;
+}
+
+void jr_scene_destroy(jr_scene* scene) { delete scene; }
+
+static jr_status check_params(const jr_params* p, const char* who) {
+    if (!p) return fail(JR_ERR_INVALID_ARG, std::string(who) + ": null params");
+    if (p->width == 0 || p->height == 0 || (uint64_t)p->width * p->height > (1u << 26))
+        return fail(JR_ERR_INVALID_ARG, std::string(who) + ": image size out of range (1 .. 2^26 pixels)");
+    if (p->max_depth > JR_MAX_DEPTH) return fail(JR_ERR_INVALID_ARG, std::string(who) + ": max_depth > 15");
+    if (!(p->c_tilde > 0.f) || !std::isfinite(p->c_tilde))
+        return fail(JR_ERR_INVALID_ARG, std::string(who) + ": c_tilde must be finite and > 0");
+    if (!(p->sigma > 0.f) || !std::isfinite(p->sigma))
+        return fail(JR_ERR_INVALID_ARG, std::string(who) + ": sigma must be finite and > 0");
+    return JR_OK;
+}
+
+jr_status jr_chains_create(const jr_scene* scene, const jr_params* params, void* stream, jr_chains** out) {
+    if (!scene || !out) return fail(JR_ERR_INVALID_ARG, "jr_chains_create: null argument");
+    jr_status ps = check_params(params, "jr_chains_create");
+    if (ps != JR_OK) return ps;
+    if (params->n_chains == 0) return fail(JR_ERR_INVALID_ARG, "jr_chains_create: n_chains must be >= 1");
+    if (params->chain_offset + params->n_chains > (1ull << 32))
+        return fail(JR_ERR_INVALID_ARG, "jr_chains_create: chain ids must stay below 2^32");
+    jr_chains* c = new (std::nothrow) jr_chains();
+    if (!c) return fail(JR_ERR_OOM, "jr_chains_create: host allocation failed");
+    c->scene = scene;
+    c->params = *params;
+    ChainView& v = c->view;
+    v.n = params->n_chains;
+    v.chain_offset = (uint32_t)params->chain_offset;
+    v.width = params->width;
+    v.height = params->height;
+    v.depth = params->max_depth;
+    v.dim = 2 + 2 * params->max_depth;
+    v.flags = params->flags;
+    v.seed = params->seed;
+    v.c_tilde = params->c_tilde;
+    v.sigma = params->sigma;
+    const size_t npx = (size_t)params->width * params->height;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if ((e = dev_alloc(&v.x, (size_t)v.dim * v.n)) != cudaSuccess || (e = dev_alloc(&v.fpu, 5 * v.n)) != cudaSuccess ||
+        (e = dev_alloc(&v.fb, npx)) != cudaSuccess || (e = dev_alloc(&v.acc64, npx)) != cudaSuccess ||
+        (e = dev_alloc(&v.counters, 4)) != cudaSuccess || (e = dev_alloc(&v.status, 1)) != cudaSuccess ||
+        (e = cudaMemsetAsync(v.fb, 0, sizeof(float4) * npx, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(v.acc64, 0, sizeof(double4_32a) * npx, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(v.counters, 0, sizeof(unsigned long long) * 4, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(v.status, 0, sizeof(unsigned int), st)) != cudaSuccess ||
+        (e = launch_init(scene->view, v, st)) != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "jr_chains_create");
+    }
+    *out = c;
+    return JR_OK;
+}
+
+void jr_chains_destroy(jr_chains* chains) { delete chains; }
+
+static jr_status advance_impl(jr_chains* c, uint32_t n_steps, uint8_t* f, float* dt, int32_t* pix,
+                              unsigned long long* work, void* stream, const char* who) {
+    if (!c) return fail(JR_ERR_INVALID_ARG, std::string(who) + ": null chains");
+    if (n_steps == 0) return JR_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    JR_CUDA(launch_step(c->scene->view, c->view, c->steps, n_steps, f, dt, pix, work, c->block, st), who);
+    JR_CUDA(launch_fold(c->view, st), who);
+    c->steps += n_steps;
+    return JR_OK;
+}
+
+jr_status jr_advance(jr_chains* chains, uint32_t n_steps, void* stream) {
+    return advance_impl(chains, n_steps, nullptr, nullptr, nullptr, nullptr, stream, "jr_advance");
+}
+
+jr_status jr_advance_traced(jr_chains* chains, uint32_t n_steps, uint8_t* flags_dev, float* dt_dev,
+                            int32_t* pix_dev, void* stream) {
+    return advance_impl(chains, n_steps, flags_dev, dt_dev, pix_dev, nullptr, stream, "jr_advance_traced");
+}
+
+jr_status jr_set_block_size(jr_chains* chains, uint32_t block) {
+    if (!chains) return fail(JR_ERR_INVALID_ARG, "jr_set_block_size: null chains");
+    if (block < 32 || block > 256 || block % 32 != 0)
+        return fail(JR_ERR_INVALID_ARG, "jr_set_block_size: block must be a multiple of 32 in [32, 256]");
+    chains->block = (int)block;
+    return JR_OK;
+}
+
+jr_status jr_advance_counted(jr_chains* chains, uint32_t n_steps, uint64_t work_out[3], void* stream) {
+    if (!chains || !work_out) return fail(JR_ERR_INVALID_ARG, "jr_advance_counted: null argument");
+    unsigned long long* w = nullptr;
+    JR_CUDA(dev_alloc(&w, 3), "jr_advance_counted");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(w, 0, 3 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) {
+        cudaFree(w);
+        return cuda_fail(e, "jr_advance_counted");
+    }
+    jr_status s = advance_impl(chains, n_steps, nullptr, nullptr, nullptr, w, stream, "jr_advance_counted");
+    unsigned long long h[3] = {0, 0, 0};
+    if (s == JR_OK) {
+        if ((e = cudaMemcpyAsync(h, w, sizeof(h), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+            cudaFree(w);
+            return cuda_fail(e, "jr_advance_counted");
+        }
+        for (int k = 0; k < 3; ++k) work_out[k] = h[k];
+    }
+    cudaFree(w);
+    return s;
+}
+
+jr_status jr_resolve(jr_chains* c, float* rgb_out, int out_is_device, void* stream) {
+    if (!c || !rgb_out) return fail(JR_ERR_INVALID_ARG, "jr_resolve: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t npx = (size_t)c->view.width * c->view.height;
+    if (out_is_device) {
+        JR_CUDA(launch_resolve(c->view, rgb_out, st), "jr_resolve");
+        return JR_OK;
+    }
+    float* tmp = nullptr;
+    JR_CUDA(dev_alloc(&tmp, 3 * npx), "jr_resolve");
+    cudaError_t e;
+    if ((e = launch_resolve(c->view, tmp, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(rgb_out, tmp, sizeof(float) * 3 * npx, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+        cudaFree(tmp);
+        return cuda_fail(e, "jr_resolve");
+    }
+    cudaFree(tmp);
+    return JR_OK;
+}
+
+jr_status jr_get_accumulator(jr_chains* c, double* out, int out_is_device, void* stream) {
+    if (!c || !out) return fail(JR_ERR_INVALID_ARG, "jr_get_accumulator: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double4_32a) * (size_t)c->view.width * c->view.height;
+    JR_CUDA(cudaMemcpyAsync(out, c->view.acc64, bytes, out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            st),
+            "jr_get_accumulator");
+    if (!out_is_device) JR_CUDA(cudaStreamSynchronize(st), "jr_get_accumulator");
+    return JR_OK;
+}
+
+jr_status jr_get_stats(jr_chains* c, jr_stats* out, void* stream) {
+    if (!c || !out) return fail(JR_ERR_INVALID_ARG, "jr_get_stats: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long cnt[4];
+    unsigned int status = 0;
+    JR_CUDA(cudaMemcpyAsync(cnt, c->view.counters, sizeof(cnt), cudaMemcpyDeviceToHost, st), "jr_get_stats");
+    JR_CUDA(cudaMemcpyAsync(&status, c->view.status, sizeof(status), cudaMemcpyDeviceToHost, st), "jr_get_stats");
+    JR_CUDA(cudaStreamSynchronize(st), "jr_get_stats");
+    out->steps_per_chain = c->steps;
+    out->regenerations = cnt[0];
+    out->local_steps = cnt[1];
+    out->accepted = cnt[2];
+    out->status_word = status;
+    out->dim = c->view.dim;
+    if (status & (JR_STATUS_TRAVERSAL | JR_STATUS_STACK))
+        return fail(JR_ERR_WATCHDOG, "jr_get_stats: a ray exhausted the traversal budget or stack");
+    if (status & JR_STATUS_NONFINITE) return fail(JR_ERR_NUMERIC, "jr_get_stats: non-finite path contribution");
+    return JR_OK;
+}
+
+jr_status jr_get_state(jr_chains* c, float* x_out, float* fpu_out, void* stream) {
+    if (!c) return fail(JR_ERR_INVALID_ARG, "jr_get_state: null chains");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (x_out)
+        JR_CUDA(cudaMemcpyAsync(x_out, c->view.x, sizeof(float) * c->view.dim * c->view.n, cudaMemcpyDeviceToHost, st),
+                "jr_get_state");
+    if (fpu_out)
+        JR_CUDA(cudaMemcpyAsync(fpu_out, c->view.fpu, sizeof(float) * 5 * c->view.n, cudaMemcpyDeviceToHost, st),
+                "jr_get_state");
+    JR_CUDA(cudaStreamSynchronize(st), "jr_get_state");
+    return JR_OK;
+}
+
+jr_status jr_set_state(jr_chains* c, const float* x_in, const float* fpu_in, void* stream) {
+    if (!c || !x_in) return fail(JR_ERR_INVALID_ARG, "jr_set_state: null argument");
+    for (uint64_t k = 0; k < (uint64_t)c->view.dim * c->view.n; ++k)
+        if (!(x_in[k] >= 0.0f && x_in[k] < 1.0f)) return fail(JR_ERR_INVALID_ARG, "jr_set_state: x outside [0,1)");
+    cudaStream_t st = (cudaStream_t)stream;
+    JR_CUDA(cudaMemcpyAsync(c->view.x, x_in, sizeof(float) * c->view.dim * c->view.n, cudaMemcpyHostToDevice, st),
+            "jr_set_state");
+    if (fpu_in)
+        JR_CUDA(cudaMemcpyAsync(c->view.fpu, fpu_in, sizeof(float) * 5 * c->view.n, cudaMemcpyHostToDevice, st),
+                "jr_set_state");
+    else
+        JR_CUDA(launch_reeval(c->scene->view, c->view, st), "jr_set_state");
+    JR_CUDA(cudaStreamSynchronize(st), "jr_set_state");
+    return JR_OK;
+}
+
+jr_status jr_set_counters(jr_chains* c, const jr_stats* in, const double* acc_host, void* stream) {
+    if (!c || !in) return fail(JR_ERR_INVALID_ARG, "jr_set_counters: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long cnt[4] = {in->regenerations, in->local_steps, in->accepted, 0};
+    unsigned int status = in->status_word;
+    JR_CUDA(cudaMemcpyAsync(c->view.counters, cnt, sizeof(cnt), cudaMemcpyHostToDevice, st), "jr_set_counters");
+    JR_CUDA(cudaMemcpyAsync(c->view.status, &status, sizeof(status), cudaMemcpyHostToDevice, st), "jr_set_counters");
+    if (acc_host)
+        JR_CUDA(cudaMemcpyAsync(c->view.acc64, acc_host, sizeof(double4_32a) * (size_t)c->view.width * c->view.height,
+                                cudaMemcpyHostToDevice, st),
+                "jr_set_counters");
+    JR_CUDA(cudaStreamSynchronize(st), "jr_set_counters");
+    c->steps = in->steps_per_chain;
+    return JR_OK;
+}
+
+jr_status jr_eval_states(const jr_scene* scene, const jr_params* params, const float* x_dev, uint64_t n, float* F_dev,
+                         float* p_dev, float* u_dev, float* k_dev, int32_t* hit_ids_dev, void* stream) {
+    if (!scene || !params || (n > 0 && !x_dev)) return fail(JR_ERR_INVALID_ARG, "jr_eval_states: null argument");
+    if (params->max_depth > JR_MAX_DEPTH) return fail(JR_ERR_INVALID_ARG, "jr_eval_states: max_depth > 15");
+    if (!(params->c_tilde > 0.f)) return fail(JR_ERR_INVALID_ARG, "jr_eval_states: c_tilde must be > 0");
+    JR_CUDA(launch_eval_states(scene->view, params->max_depth, params->c_tilde, x_dev, n, F_dev, p_dev, u_dev, k_dev,
+                               hit_ids_dev, (cudaStream_t)stream),
+            "jr_eval_states");
+    return JR_OK;
+}
+
+jr_status jr_render_pt(const jr_scene* scene, const jr_params* params, uint64_t sample_begin, uint64_t n_samples,
+                       double* accum_dev, void* stream) {
+    if (!scene || !params || !accum_dev) return fail(JR_ERR_INVALID_ARG, "jr_render_pt: null argument");
+    if (params->width == 0 || params->height == 0 || params->max_depth > JR_MAX_DEPTH)
+        return fail(JR_ERR_INVALID_ARG, "jr_render_pt: bad image size or depth");
+    JR_CUDA(launch_render_pt(scene->view, params->width, params->height, params->max_depth, params->seed, sample_begin,
+                             n_samples, accum_dev, (cudaStream_t)stream),
+            "jr_render_pt");
+    return JR_OK;
+}
+
+jr_status jr_philox(uint64_t seed, uint32_t tag, uint32_t block, uint64_t chain_begin, uint64_t step, uint64_t n,
+                    uint32_t* out_dev, void* stream) {
+    if (n > 0 && !out_dev) return fail(JR_ERR_INVALID_ARG, "jr_philox: null output");
+    JR_CUDA(launch_philox(seed, tag, block, chain_begin, step, n, out_dev, (cudaStream_t)stream), "jr_philox");
+    return JR_OK;
+}
+
+}  // extern "C"

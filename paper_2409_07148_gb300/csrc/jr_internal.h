@@ -1,0 +1,101 @@
+// Internal layout shared by the host runtime (jr_api.cu, bvh_build.cpp) and the
+// kernels (jr_kernels.cu).  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace jr {
+
+constexpr int kMaxDepth = 15;
+constexpr int kMaxDim = 2 + 2 * kMaxDepth;  // 32
+constexpr int kStackSize = 64;              // traversal stack entries
+constexpr int kMaxBvhDepth = kStackSize - 2;
+constexpr int kLeafMax = 8;                 // triangles per leaf (encoded count-1 in 3 bits)
+constexpr uint32_t kNodeVisitBudget = 1u << 16;  // per ray; exceeding it is a watchdog event
+
+constexpr uint32_t kTagStep = 0, kTagInit = 1, kTagPt = 2;
+
+// BVH node, 64 bytes: both children's boxes, Aila & Laine style.
+//   a = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
+//   b = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
+//   c = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
+//   refs.x/.y = child refs: >= 0 inner node index; < 0 leaf = ~((first << 3) | (count - 1))
+struct __align__(16) BvhNode {
+    float4 a, b, c;
+    int4 refs;
+};
+
+// Triangle in BVH leaf order, 48 bytes: v0 | original id, e1 | material, e2.
+struct __align__(16) TriRecord {
+    float4 v0_id;   // .w = __int_as_float(original index)
+    float4 e1_mat;  // .w = __int_as_float(material index)
+    float4 e2;
+};
+
+// Material, prepared on the host.
+struct __align__(16) Material {
+    int type;
+    int emits;
+    float phong_inv_n1;  // 1 / (n + 1)
+    float phong_scale;   // (n + 2) / (n + 1)
+    float3 albedo;
+    float ior;
+    float3 emission;
+    float pad;
+};
+
+struct SceneView {
+    const BvhNode* nodes;
+    const TriRecord* tris;
+    const Material* mats;
+    int root;       // child ref of the root, or INT32_MIN when the scene is empty
+    int n_nodes;
+    float cam[12];
+};
+
+struct ChainView {
+    float* x;        // [D][n] PSS coordinates
+    float* fpu;      // [5][n] F.r F.g F.b p u
+    float4* fb;      // [H*W] RGB sum + dt, FP32 (folded into acc64 after each advance)
+    double4_32a* acc64;  // [H*W]
+    unsigned long long* counters;  // [0] J, [1] local steps, [2] accepted
+    unsigned int* status;
+    uint64_t n;
+    uint32_t chain_offset;
+    uint32_t width, height, depth, dim;
+    uint32_t flags;
+    uint64_t seed;
+    float c_tilde, sigma;
+};
+
+// Host-side BVH build result.
+struct HostBvh {
+    std::vector<BvhNode> nodes;
+    std::vector<TriRecord> tris;
+    int root = 0;
+    int depth = 0;
+};
+
+// bvh_build.cpp
+bool build_bvh(const float* verts, uint32_t n_verts, const uint32_t* tris, uint32_t n_tris,
+               const uint32_t* tri_mat, HostBvh* out, std::string* err);
+
+// jr_kernels.cu -- launch wrappers; all return the cudaGetLastError() of the launch.
+cudaError_t launch_init(const SceneView& s, const ChainView& c, cudaStream_t st);
+cudaError_t launch_step(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
+                        uint8_t* tr_flags, float* tr_dt, int32_t* tr_pix, unsigned long long* work_out, int block,
+                        cudaStream_t st);
+cudaError_t launch_fold(const ChainView& c, cudaStream_t st);
+cudaError_t launch_resolve(const ChainView& c, float* rgb, cudaStream_t st);
+cudaError_t launch_reeval(const SceneView& s, const ChainView& c, cudaStream_t st);
+cudaError_t launch_eval_states(const SceneView& s, uint32_t depth, float c_tilde, const float* x, uint64_t n,
+                               float* F, float* p, float* u, float* k, int32_t* ids, cudaStream_t st);
+cudaError_t launch_render_pt(const SceneView& s, uint32_t width, uint32_t height, uint32_t depth, uint64_t seed,
+                             uint64_t sample_begin, uint64_t n, double* accum, cudaStream_t st);
+cudaError_t launch_philox(uint64_t seed, uint32_t tag, uint32_t block, uint64_t chain_begin, uint64_t step,
+                          uint64_t n, uint32_t* out, cudaStream_t st);
+
+}  // namespace jr

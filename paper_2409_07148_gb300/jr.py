@@ -1,0 +1,276 @@
+"""Python binding of the C ABI in include/jr.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``_lib/libjr_gb300.so``;
+this module converts numpy arrays and torch tensors to pointers and status
+codes to exceptions.  There is no fallback: if the library is missing the
+import of :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libjr_gb300.so")
+
+JR_OK, JR_ERR_INVALID_ARG, JR_ERR_CUDA, JR_ERR_OOM, JR_ERR_WATCHDOG, JR_ERR_NUMERIC, JR_ERR_STATE = range(7)
+JR_FLAG_RAO_BLACKWELL = 1
+JR_STATUS_NONFINITE, JR_STATUS_TRAVERSAL, JR_STATUS_STACK = 1, 2, 4
+MATERIAL_FLOATS = 12
+MAX_DEPTH = 15
+
+
+class JRError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"jr status {status}: {msg}")
+        self.status = status
+
+
+class SceneDesc(ctypes.Structure):
+    _fields_ = [("verts", ctypes.c_void_p), ("n_verts", ctypes.c_uint32), ("tris", ctypes.c_void_p),
+                ("n_tris", ctypes.c_uint32), ("tri_material", ctypes.c_void_p), ("materials", ctypes.c_void_p),
+                ("n_materials", ctypes.c_uint32), ("camera", ctypes.c_float * 12)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_uint32), ("height", ctypes.c_uint32), ("max_depth", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("n_chains", ctypes.c_uint64), ("chain_offset", ctypes.c_uint64),
+                ("seed", ctypes.c_uint64), ("c_tilde", ctypes.c_float), ("sigma", ctypes.c_float)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("steps_per_chain", ctypes.c_uint64), ("regenerations", ctypes.c_uint64),
+                ("local_steps", ctypes.c_uint64), ("accepted", ctypes.c_uint64), ("status_word", ctypes.c_uint32),
+                ("dim", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class SceneInfo(ctypes.Structure):
+    _fields_ = [("n_tris", ctypes.c_uint32), ("n_nodes", ctypes.c_uint32), ("bvh_depth", ctypes.c_uint32),
+                ("n_materials", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_P, _U32, _U64, _I, _F = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_float
+_SIGS = {
+    "jr_scene_create": [ctypes.POINTER(SceneDesc), _P, ctypes.POINTER(_P)],
+    "jr_scene_get_info": [_P, ctypes.POINTER(SceneInfo)],
+    "jr_scene_destroy": [_P],
+    "jr_chains_create": [_P, ctypes.POINTER(Params), _P, ctypes.POINTER(_P)],
+    "jr_chains_destroy": [_P],
+    "jr_advance": [_P, _U32, _P],
+    "jr_advance_traced": [_P, _U32, _P, _P, _P, _P],
+    "jr_advance_counted": [_P, _U32, _P, _P],
+    "jr_set_block_size": [_P, _U32],
+    "jr_resolve": [_P, _P, _I, _P],
+    "jr_get_accumulator": [_P, _P, _I, _P],
+    "jr_get_stats": [_P, ctypes.POINTER(Stats), _P],
+    "jr_get_state": [_P, _P, _P, _P],
+    "jr_set_state": [_P, _P, _P, _P],
+    "jr_set_counters": [_P, ctypes.POINTER(Stats), _P, _P],
+    "jr_eval_states": [_P, ctypes.POINTER(Params), _P, _U64, _P, _P, _P, _P, _P, _P],
+    "jr_render_pt": [_P, ctypes.POINTER(Params), _U64, _U64, _P, _P],
+    "jr_philox": [_U64, _U32, _U32, _U64, _U64, _U64, _P, _P],
+    "jr_last_error": [],
+    "jr_version": [],
+}
+
+
+def lib():
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library missing at {LIB_PATH}: run paper_2409_07148_gb300.build.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, args in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_char_p if name in ("jr_last_error", "jr_version") else ctypes.c_int
+            L.jr_scene_destroy.restype = None
+            L.jr_chains_destroy.restype = None
+            _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != JR_OK:
+        raise JRError(rc, lib().jr_last_error().decode())
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _hptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_params(width, height, depth, n_chains=1, seed=0, c_tilde=1.0, sigma=0.01, chain_offset=0, flags=0):
+    return Params(int(width), int(height), int(depth), int(flags), int(n_chains), int(chain_offset), int(seed),
+                  float(c_tilde), float(sigma))
+
+
+class Scene:
+    """A scene uploaded to the GPU (BVH built by the library)."""
+
+    def __init__(self, sc, stream=None):
+        self.sc = sc
+        self._keep = [np.ascontiguousarray(sc.verts, np.float32), np.ascontiguousarray(sc.tris, np.uint32),
+                      np.ascontiguousarray(sc.tri_mat, np.uint32), np.ascontiguousarray(sc.mats, np.float32)]
+        v, t, tm, m = self._keep
+        d = SceneDesc(_hptr(v), v.shape[0], _hptr(t), t.shape[0], _hptr(tm), _hptr(m), m.shape[0],
+                      (ctypes.c_float * 12)(*[float(c) for c in sc.camera]))
+        h = ctypes.c_void_p()
+        _check(lib().jr_scene_create(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
+        self.h = h
+
+    def info(self):
+        i = SceneInfo()
+        _check(lib().jr_scene_get_info(self.h, ctypes.byref(i)))
+        return {k: int(getattr(i, k)) for k, _ in i._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().jr_scene_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Chains:
+    """A set of Jump Restore chains on the GPU (state, framebuffer, counters)."""
+
+    def __init__(self, scene: Scene, width, height, depth, n_chains, seed=0, c_tilde=1.0, sigma=0.01,
+                 chain_offset=0, flags=0, stream=None):
+        self.scene = scene
+        self.params = make_params(width, height, depth, n_chains, seed, c_tilde, sigma, chain_offset, flags)
+        self.W, self.H, self.depth, self.n = int(width), int(height), int(depth), int(n_chains)
+        self.D = 2 + 2 * self.depth
+        h = ctypes.c_void_p()
+        _check(lib().jr_chains_create(scene.h, ctypes.byref(self.params), _stream(stream), ctypes.byref(h)))
+        self.h = h
+
+    def advance(self, n_steps, stream=None):
+        _check(lib().jr_advance(self.h, int(n_steps), _stream(stream)))
+
+    def advance_traced(self, n_steps, flags=None, dt=None, pix=None, stream=None):
+        _check(lib().jr_advance_traced(self.h, int(n_steps), _dptr(flags), _dptr(dt), _dptr(pix), _stream(stream)))
+
+    def advance_counted(self, n_steps, stream=None):
+        """Advance and return {rays, nodes, tris} counted by the instrumented kernel."""
+        w = (ctypes.c_uint64 * 3)()
+        _check(lib().jr_advance_counted(self.h, int(n_steps), w, _stream(stream)))
+        return {"rays": int(w[0]), "nodes": int(w[1]), "tris": int(w[2])}
+
+    def set_block_size(self, block):
+        _check(lib().jr_set_block_size(self.h, int(block)))
+
+    def resolve(self, out=None, stream=None):
+        """Into a device tensor (async) if given, else into a new host array."""
+        if out is not None:
+            _check(lib().jr_resolve(self.h, _dptr(out), 1, _stream(stream)))
+            return out
+        img = np.zeros((self.H, self.W, 3), np.float32)
+        _check(lib().jr_resolve(self.h, _hptr(img), 0, _stream(stream)))
+        return img
+
+    def accumulator(self, out=None, stream=None):
+        if out is not None:
+            _check(lib().jr_get_accumulator(self.h, _dptr(out), 1, _stream(stream)))
+            return out
+        a = np.zeros((self.H, self.W, 4), np.float64)
+        _check(lib().jr_get_accumulator(self.h, _hptr(a), 0, _stream(stream)))
+        return a
+
+    def stats(self, stream=None, check=True):
+        s = Stats()
+        rc = lib().jr_get_stats(self.h, ctypes.byref(s), _stream(stream))
+        if check:
+            _check(rc)
+        return s.as_dict()
+
+    def get_state(self, stream=None):
+        x = np.zeros((self.D, self.n), np.float32)
+        fpu = np.zeros((5, self.n), np.float32)
+        _check(lib().jr_get_state(self.h, _hptr(x), _hptr(fpu), _stream(stream)))
+        return x, fpu
+
+    def set_state(self, x, fpu=None, stream=None):
+        x = np.ascontiguousarray(x, np.float32)
+        f = None if fpu is None else np.ascontiguousarray(fpu, np.float32)
+        _check(lib().jr_set_state(self.h, _hptr(x), _hptr(f), _stream(stream)))
+
+    def set_counters(self, stats: dict, accumulator=None, stream=None):
+        s = Stats(*[int(stats[k]) for k, _ in Stats._fields_])
+        a = None if accumulator is None else np.ascontiguousarray(accumulator, np.float64)
+        _check(lib().jr_set_counters(self.h, ctypes.byref(s), _hptr(a), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().jr_chains_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def eval_states(scene: Scene, x, depth, c_tilde=1.0, hit_ids=False, stream=None):
+    """x: CUDA float32 tensor [D, n] (SoA).  Returns F [3, n], p, u, k [n] (and ids)."""
+    import torch
+    n = x.shape[1]
+    dev = x.device
+    F = torch.empty((3, n), dtype=torch.float32, device=dev)
+    p = torch.empty(n, dtype=torch.float32, device=dev)
+    u = torch.empty(n, dtype=torch.float32, device=dev)
+    k = torch.empty(n, dtype=torch.float32, device=dev)
+    ids = torch.empty((depth + 1, n), dtype=torch.int32, device=dev) if hit_ids else None
+    prm = make_params(1, 1, depth, c_tilde=c_tilde)
+    _check(lib().jr_eval_states(scene.h, ctypes.byref(prm), _dptr(x), int(n), _dptr(F), _dptr(p), _dptr(u),
+                                _dptr(k), _dptr(ids), _stream(stream)))
+    return (F, p, u, k, ids) if hit_ids else (F, p, u, k)
+
+
+def render_pt(scene: Scene, width, height, depth, n_samples, seed=0, sample_begin=0, accum=None, stream=None):
+    """Plain Monte Carlo path tracing into a CUDA float64 accum [H, W, 4]."""
+    import torch
+    if accum is None:
+        accum = torch.zeros((height, width, 4), dtype=torch.float64, device="cuda")
+    prm = make_params(width, height, depth, seed=seed)
+    _check(lib().jr_render_pt(scene.h, ctypes.byref(prm), int(sample_begin), int(n_samples), _dptr(accum),
+                              _stream(stream)))
+    return accum
+
+
+def philox(seed, tag, block, chain_begin, step, n, stream=None):
+    import torch
+    out = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+    _check(lib().jr_philox(int(seed), int(tag), int(block), int(chain_begin), int(step), int(n), _dptr(out),
+                           _stream(stream)))
+    return out
+
+
+def version():
+    return lib().jr_version().decode()
