@@ -166,8 +166,14 @@ def main():
     ap.add_argument("--block", type=int, default=0, help="step-kernel block size (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=12.0)
+    ap.add_argument("--chains", type=int, default=0, help="override the chain count (profiling small cases only)")
+    ap.add_argument("--chain-steps", type=int, default=0, help="override chain steps per launch (profiling only)")
     args = ap.parse_args()
     sc, wl = workload(args.workload)
+    if args.chains:
+        wl["chains"] = args.chains
+    if args.chain_steps:
+        wl["chain_steps"] = args.chain_steps
     if args.impl == "reference":
         run_reference(args, sc, wl)
         return

@@ -205,9 +205,9 @@ jr_status jr_eval_states(const jr_scene* scene, const jr_params* params, const f
 
 /* Plain Monte Carlo path tracing (the regeneration-only special case c~ ->
  * inf of Section 6.3): samples sample_begin .. +n_samples (tag 2), each
- * adding W H F(x) (and 1 in channel 3) to accum_dev[H][W][4] (device, FP64,
- * caller-owned, added to).  Pixel estimate = accum / total samples.
- * Asynchronous. */
+ * adding W H F(x) to channels 0..2 of accum_dev[H][W][4] (device, FP64,
+ * caller-owned, added to; channel 3 is not touched).  Pixel estimate =
+ * accum / total samples.  Asynchronous. */
 jr_status jr_render_pt(const jr_scene* scene, const jr_params* params, uint64_t sample_begin, uint64_t n_samples,
                        double* accum_dev, void* stream);
 

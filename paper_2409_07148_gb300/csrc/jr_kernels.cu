@@ -534,7 +534,7 @@ __global__ void render_pt_kernel(SceneView s, uint32_t W, uint32_t H, uint32_t d
     if (F.x != 0.f) atomicAdd(a, WH * F.x);
     if (F.y != 0.f) atomicAdd(a + 1, WH * F.y);
     if (F.z != 0.f) atomicAdd(a + 2, WH * F.z);
-    atomicAdd(a + 3, 1.0);
+    // channel 3 is left to the caller: the sample count is n, known on the host
 }
 
 __global__ void philox_kernel(uint64_t seed, uint32_t tag, uint32_t block, uint64_t chain_begin, uint64_t step,
