@@ -103,6 +103,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def launches_per_advance(mode, chains, chain_steps, depth):
+    """Kernels of ours one jr_advance launches (see jr_advance in include/jr.h)."""
+    wave = mode == "wave" or (mode == "auto" and chains >= (1 << 16))
+    if wave:   # per step: step kernel + one bounce kernel per depth; then a finish launch and the fold
+        return chain_steps * (1 + depth) + 2
+    return 2   # the persistent step kernel and the fold
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -164,6 +172,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cornell_spheres")
     ap.add_argument("--block", type=int, default=0, help="step-kernel block size (0 = library default)")
+    ap.add_argument("--exec", default="auto", choices=["auto", "mega", "wave"], help="execution mode")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--chains", type=int, default=0, help="override the chain count (profiling small cases only)")
@@ -195,6 +204,7 @@ def main():
         ch = jr.Chains(scene, sc.width, sc.height, sc.depth, C, seed=0, chain_offset=rank * C, stream=stream)
         if args.block:
             ch.set_block_size(args.block)
+        ch.set_execution(args.exec)
         flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
         for _ in range(args.warmup):
             ch.advance(K, stream=stream)
@@ -269,7 +279,7 @@ def main():
                    "depth": sc.depth, "dim": sc.D, "chains_per_gpu": C, "chain_steps_per_step": K, "seed": 0,
                    "c_tilde": 1.0, "sigma": 0.01, "regen": "uniform", "global_batch": ws * C, "seq_len": K,
                    "parallelism": f"chains sharded over {ws} GPU(s)", "l2": "flushed by a 512 MB write between timed launches",
-                   "block": args.block or 128},
+                   "block": args.block or 128, "exec": args.exec},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved / alu_peak, "traffic": None,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz_peak:.0f} MHz ({pk_kind} sm_max_mhz)",
@@ -279,7 +289,7 @@ def main():
         "accept_rate": st["accepted"] / max(1, st["local_steps"]),
         "clocks": clocks,
         "e2e": e2e,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": args.steps * launches_per_advance(args.exec, C, K, sc.depth),
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

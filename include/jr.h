@@ -159,9 +159,23 @@ jr_status jr_advance_traced(jr_chains* chains, uint32_t n_steps, uint8_t* flags_
  * jr_advance (same Philox streams, same results).  Synchronises `stream`. */
 jr_status jr_advance_counted(jr_chains* chains, uint32_t n_steps, uint64_t work_out[3], void* stream);
 
-/* Threads per block of the step kernel for this chain set: a multiple of 32
+/* Threads per block of the megakernel for this chain set: a multiple of 32
  * in [32, 256] (default 128).  Results do not depend on it. */
 jr_status jr_set_block_size(jr_chains* chains, uint32_t block);
+
+/* Execution mode of jr_advance for this chain set (jr_advance_traced and
+ * jr_advance_counted always use the megakernel):
+ *   JR_EXEC_MEGAKERNEL  one thread per chain for the whole launch;
+ *   JR_EXEC_WAVEFRONT   one launch per step plus one per bounce, over a queue
+ *                       of live paths (better SIMD use for many chains; its
+ *                       buffers, about (4 D + 58) bytes per chain, are
+ *                       allocated by the first wavefront advance);
+ *   JR_EXEC_AUTO        wavefront from 2^16 chains up, else the megakernel.
+ * Both modes run the same per-chain arithmetic on the same Philox streams. */
+#define JR_EXEC_AUTO 0u
+#define JR_EXEC_MEGAKERNEL 1u
+#define JR_EXEC_WAVEFRONT 2u
+jr_status jr_set_execution(jr_chains* chains, uint32_t mode);
 
 /* Resolve the estimate (Section 6.3): rgb_out[H][W][3] = accumulator / J
  * (zeros while J = 0).  out_is_device = 1: rgb_out is device memory and the

@@ -63,7 +63,14 @@ struct jr_chains {
     ChainView view{};
     uint64_t steps = 0;
     int block = 128;
+    uint32_t exec = JR_EXEC_AUTO;
     ~jr_chains() {
+        cudaFree(view.wf.y);
+        cudaFree(view.wf.par);
+        cudaFree(view.wf.ua);
+        cudaFree(view.wf.path);
+        cudaFree(view.wf.queue);
+        cudaFree(view.wf.qcount);
         cudaFree(view.x);
         cudaFree(view.fpu);
         cudaFree(view.fb);
@@ -208,12 +215,44 @@ jr_status jr_chains_create(const jr_scene* scene, const jr_params* params, void*
 
 void jr_chains_destroy(jr_chains* chains) { delete chains; }
 
+// Wavefront buffers, allocated on the first wavefront advance of a chain set.
+static jr_status ensure_wavefront(jr_chains* c, cudaStream_t st) {
+    WaveView& w = c->view.wf;
+    if (w.y) return JR_OK;
+    const uint64_t n = c->view.n;
+    cudaError_t e;
+    if ((e = dev_alloc(&w.y, (size_t)c->view.dim * n)) != cudaSuccess || (e = dev_alloc(&w.par, n)) != cudaSuccess ||
+        (e = dev_alloc(&w.ua, n)) != cudaSuccess || (e = dev_alloc(&w.path, 3 * n)) != cudaSuccess ||
+        (e = dev_alloc(&w.queue, 2 * n)) != cudaSuccess ||
+        (e = dev_alloc(&w.qcount, 2 * (kMaxDepth + 2))) != cudaSuccess ||
+        (e = cudaMemsetAsync(w.par, 0, n, st)) != cudaSuccess) {
+        cudaFree(w.y);
+        cudaFree(w.par);
+        cudaFree(w.ua);
+        cudaFree(w.path);
+        cudaFree(w.queue);
+        cudaFree(w.qcount);
+        w = WaveView{};
+        return cuda_fail(e, "jr_advance (wavefront buffers)");
+    }
+    return JR_OK;
+}
+
 static jr_status advance_impl(jr_chains* c, uint32_t n_steps, uint8_t* f, float* dt, int32_t* pix,
                               unsigned long long* work, void* stream, const char* who) {
     if (!c) return fail(JR_ERR_INVALID_ARG, std::string(who) + ": null chains");
     if (n_steps == 0) return JR_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    JR_CUDA(launch_step(c->scene->view, c->view, c->steps, n_steps, f, dt, pix, work, c->block, st), who);
+    const bool plain = !f && !dt && !pix && !work;
+    const bool wave = plain && (c->exec == JR_EXEC_WAVEFRONT ||
+                                (c->exec == JR_EXEC_AUTO && c->view.n >= kWavefrontMinChains));
+    if (wave) {
+        jr_status a = ensure_wavefront(c, st);
+        if (a != JR_OK) return a;
+        JR_CUDA(launch_wavefront(c->scene->view, c->view, c->steps, n_steps, st), who);
+    } else {
+        JR_CUDA(launch_step(c->scene->view, c->view, c->steps, n_steps, f, dt, pix, work, c->block, st), who);
+    }
     JR_CUDA(launch_fold(c->view, st), who);
     c->steps += n_steps;
     return JR_OK;
@@ -226,6 +265,13 @@ jr_status jr_advance(jr_chains* chains, uint32_t n_steps, void* stream) {
 jr_status jr_advance_traced(jr_chains* chains, uint32_t n_steps, uint8_t* flags_dev, float* dt_dev,
                             int32_t* pix_dev, void* stream) {
     return advance_impl(chains, n_steps, flags_dev, dt_dev, pix_dev, nullptr, stream, "jr_advance_traced");
+}
+
+jr_status jr_set_execution(jr_chains* chains, uint32_t mode) {
+    if (!chains) return fail(JR_ERR_INVALID_ARG, "jr_set_execution: null chains");
+    if (mode > JR_EXEC_WAVEFRONT) return fail(JR_ERR_INVALID_ARG, "jr_set_execution: unknown mode");
+    chains->exec = mode;
+    return JR_OK;
 }
 
 jr_status jr_set_block_size(jr_chains* chains, uint32_t block) {

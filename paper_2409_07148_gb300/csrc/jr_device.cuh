@@ -1,0 +1,306 @@
+// Device functions shared by the megakernel (jr_kernels.cu) and the
+// wavefront pipeline (jr_wavefront.cu): Philox, vector helpers, BVH
+// traversal, BSDF sampling, the PSS path integrand.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "../../include/jr.h"
+#include "jr_internal.h"
+
+namespace jr {
+namespace {
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw(uint64_t seed, uint32_t tag, uint32_t block, uint32_t chain, uint64_t step) {
+    return philox4x32_10(make_uint4(block + 256u * tag, chain, (uint32_t)step, (uint32_t)(step >> 32)),
+                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// (r >> 8) * 2^-24: exact in float, in [0, 1).
+__device__ __forceinline__ float u01(uint32_t r) { return (float)(r >> 8) * 5.9604644775390625e-8f; }
+
+// ------------------------------------------------------------------ vectors
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 mul(float3 a, float3 b) { return f3(a.x * b.x, a.y * b.y, a.z * b.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 normalize(float3 a) { return a * (1.0f / sqrtf(dot(a, a))); }
+__device__ __forceinline__ float lum(float3 c) { return 0.2126f * c.x + 0.7152f * c.y + 0.0722f * c.z; }
+
+// Orthonormal basis around unit n (Duff et al., JCGT 2017).
+__device__ __forceinline__ void onb(float3 n, float3& t, float3& b) {
+    const float sign = copysignf(1.0f, n.z);
+    const float a = -1.0f / (sign + n.z);
+    const float bb = n.x * n.y * a;
+    t = f3(1.0f + sign * n.x * n.x * a, sign * bb, -sign * n.x);
+    b = f3(bb, sign + n.y * n.y * a, -n.y);
+}
+
+__device__ __forceinline__ float wrap01(float y) {
+    const float w = y - floorf(y);
+    return w >= 1.0f ? 0.0f : w;
+}
+
+// ------------------------------------------------------------------ traversal
+constexpr int kSentinel = INT32_MIN;
+
+// Work counters of the instrumented kernel variant (compiled out otherwise).
+struct Work {
+    uint32_t rays = 0, nodes = 0, tris = 0;
+};
+
+// Closest hit, ties on equal t to the smaller original triangle index.
+// Returns the leaf-order record index or -1; t_out gets the hit distance.
+template <bool kCount>
+__device__ __forceinline__ int closest_hit(const SceneView& s, float3 o, float3 d, float& t_out, unsigned& status,
+                                           Work& work) {
+    if constexpr (kCount) work.rays++;
+    t_out = INFINITY;
+    if (s.root == kSentinel) return -1;
+    const float dx = fabsf(d.x) < 1e-20f ? copysignf(1e-20f, d.x) : d.x;
+    const float dy = fabsf(d.y) < 1e-20f ? copysignf(1e-20f, d.y) : d.y;
+    const float dz = fabsf(d.z) < 1e-20f ? copysignf(1e-20f, d.z) : d.z;
+    const float ix = 1.0f / dx, iy = 1.0f / dy, iz = 1.0f / dz;
+    const float ox = o.x * ix, oy = o.y * iy, oz = o.z * iz;
+    float tb = INFINITY;
+    int best = -1, best_id = INT32_MAX;
+    int stack[kStackSize];
+    int sp = 0;
+    int ref = s.root;
+    uint32_t visits = 0;
+    while (true) {
+        while (ref >= 0) {
+            if (++visits > kNodeVisitBudget) {
+                status |= JR_STATUS_TRAVERSAL;
+                return -1;
+            }
+            if constexpr (kCount) work.nodes++;
+            const BvhNode* n = s.nodes + ref;
+            const float4 a = __ldg(&n->a), b = __ldg(&n->b), c = __ldg(&n->c);
+            const int4 rf = __ldg(&n->refs);
+            const float l0x = fmaf(a.x, ix, -ox), h0x = fmaf(a.y, ix, -ox);
+            const float l0y = fmaf(a.z, iy, -oy), h0y = fmaf(a.w, iy, -oy);
+            const float l0z = fmaf(c.x, iz, -oz), h0z = fmaf(c.y, iz, -oz);
+            const float l1x = fmaf(b.x, ix, -ox), h1x = fmaf(b.y, ix, -ox);
+            const float l1y = fmaf(b.z, iy, -oy), h1y = fmaf(b.w, iy, -oy);
+            const float l1z = fmaf(c.z, iz, -oz), h1z = fmaf(c.w, iz, -oz);
+            const float tn0 = fmaxf(fmaxf(fminf(l0x, h0x), fminf(l0y, h0y)), fmaxf(fminf(l0z, h0z), 0.0f));
+            const float tf0 = fminf(fminf(fmaxf(l0x, h0x), fmaxf(l0y, h0y)), fminf(fmaxf(l0z, h0z), tb));
+            const float tn1 = fmaxf(fmaxf(fminf(l1x, h1x), fminf(l1y, h1y)), fmaxf(fminf(l1z, h1z), 0.0f));
+            const float tf1 = fminf(fminf(fmaxf(l1x, h1x), fmaxf(l1y, h1y)), fminf(fmaxf(l1z, h1z), tb));
+            const bool h0 = tn0 <= tf0 * 1.00000024f;
+            const bool h1 = tn1 <= tf1 * 1.00000024f;
+            if (h0 && h1) {
+                const bool first0 = tn0 <= tn1;
+                if (sp >= kStackSize) {
+                    status |= JR_STATUS_STACK;
+                    return -1;
+                }
+                stack[sp++] = first0 ? rf.y : rf.x;
+                ref = first0 ? rf.x : rf.y;
+            } else if (h0) {
+                ref = rf.x;
+            } else if (h1) {
+                ref = rf.y;
+            } else {
+                ref = sp > 0 ? stack[--sp] : kSentinel;
+            }
+        }
+        if (ref == kSentinel) break;
+        const int enc = ~ref;
+        const int first = enc >> 3, cnt = (enc & 7) + 1;
+        if constexpr (kCount) work.tris += (uint32_t)cnt;
+        for (int k = first; k < first + cnt; ++k) {
+            const TriRecord* tr = s.tris + k;
+            const float4 q0 = __ldg(&tr->v0_id), q1 = __ldg(&tr->e1_mat), q2 = __ldg(&tr->e2);
+            // Moller-Trumbore (JGT 1997), same algebra as the reference definition.
+            const float3 e1 = f3(q1.x, q1.y, q1.z), e2 = f3(q2.x, q2.y, q2.z);
+            const float3 pv = cross(d, e2);
+            const float det = dot(e1, pv);
+            if (det == 0.0f) continue;
+            const float inv = 1.0f / det;
+            const float3 tv = o - f3(q0.x, q0.y, q0.z);
+            const float u = dot(tv, pv) * inv;
+            if (u < 0.0f || u > 1.0f) continue;
+            const float3 qv = cross(tv, e1);
+            const float v = dot(d, qv) * inv;
+            if (v < 0.0f || u + v > 1.0f) continue;
+            const float t = dot(e2, qv) * inv;
+            const int id = __float_as_int(q0.w);
+            if (t > 0.0f && (t < tb || (t == tb && id < best_id))) {
+                tb = t;
+                best = k;
+                best_id = id;
+            }
+        }
+        ref = sp > 0 ? stack[--sp] : kSentinel;
+    }
+    t_out = tb;
+    return best;
+}
+
+// ------------------------------------------------------------------ BSDFs
+// Exact unpolarised Fresnel reflectance of a smooth dielectric interface.
+__device__ __forceinline__ float fresnel(float cos_i, float eta_i, float eta_t, float& cos_t) {
+    const float e = eta_i / eta_t;
+    const float sin2_t = e * e * (1.0f - cos_i * cos_i);
+    if (sin2_t >= 1.0f) {
+        cos_t = 0.0f;
+        return 1.0f;
+    }
+    cos_t = sqrtf(1.0f - sin2_t);
+    const float rs = (eta_i * cos_i - eta_t * cos_t) / (eta_i * cos_i + eta_t * cos_t);
+    const float rp = (eta_t * cos_i - eta_i * cos_t) / (eta_t * cos_i + eta_i * cos_t);
+    return 0.5f * (rs * rs + rp * rp);
+}
+
+// Sample the continuation direction; returns false when the path ends.
+__device__ __forceinline__ bool scatter(const Material& m, float3 d, float3 ng, float u1, float u2, float3& wi,
+                                        float3& w) {
+    if (m.type == JR_MAT_DIELECTRIC) {
+        float cos_i = -dot(d, ng);
+        float eta_i = 1.0f, eta_t = m.ior;
+        float3 nn = ng;
+        if (cos_i < 0.0f) {
+            cos_i = -cos_i;
+            eta_i = m.ior;
+            eta_t = 1.0f;
+            nn = ng * -1.0f;
+        }
+        float cos_t;
+        const float R = fresnel(cos_i, eta_i, eta_t, cos_t);
+        if (u1 < R) {
+            wi = d + nn * (2.0f * cos_i);
+        } else {
+            const float e = eta_i / eta_t;
+            wi = d * e + nn * (e * cos_i - cos_t);
+        }
+        w = f3(1.0f, 1.0f, 1.0f);
+        return true;
+    }
+    const float3 ns = dot(d, ng) < 0.0f ? ng : ng * -1.0f;
+    float3 t, b;
+    if (m.type == JR_MAT_LAMBERT) {
+        // cosine-weighted hemisphere (Malley's method); weight = albedo
+        const float r = sqrtf(u1);
+        float sn, cs;
+        sincospif(2.0f * u2, &sn, &cs);
+        const float lz = sqrtf(fmaxf(1.0f - u1, 0.0f));
+        onb(ns, t, b);
+        wi = t * (r * cs) + b * (r * sn) + ns * lz;
+        w = m.albedo;
+        return m.albedo.x > 0.0f || m.albedo.y > 0.0f || m.albedo.z > 0.0f;
+    }
+    // modified Phong lobe about the mirror direction; weight rho (n+2)/(n+1) cos_i
+    const float3 r = d - ns * (2.0f * dot(d, ns));
+    const float cos_a = powf(1.0f - u1, m.phong_inv_n1);
+    const float sin_a = sqrtf(fmaxf(1.0f - cos_a * cos_a, 0.0f));
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    onb(r, t, b);
+    wi = t * (sin_a * cs) + b * (sin_a * sn) + r * cos_a;
+    const float cos_i = dot(wi, ns);
+    if (cos_i <= 0.0f) return false;
+    w = m.albedo * (m.phong_scale * cos_i);
+    return true;
+}
+
+// ------------------------------------------------------------------ integrand
+// PSS path contribution F(y) (the target of Section 4 is p = lum(F)).  y[d] is
+// read at y[d * ys]: film point (y0, y1), bounce b uses (y_{2+2b}, y_{3+2b}).
+// Emission (one-sided) is collected at every vertex; a miss ends the path.
+// Camera ray through film point (y0, y1).
+__device__ __forceinline__ void camera_ray(const SceneView& s, float y0, float y1, float3& o, float3& d) {
+    const float3 cf = f3(s.cam[3], s.cam[4], s.cam[5]);
+    const float3 cr = f3(s.cam[6], s.cam[7], s.cam[8]);
+    const float3 cu = f3(s.cam[9], s.cam[10], s.cam[11]);
+    o = f3(s.cam[0], s.cam[1], s.cam[2]);
+    d = normalize(cf + cr * (2.0f * y0 - 1.0f) + cu * (1.0f - 2.0f * y1));
+}
+
+// One path vertex: the ray (o, d) hit record k at distance t.  Adds the
+// one-sided emission T * L_e to F, and unless v == depth samples the
+// continuation with (u1, u2) = (y_{2+2v}, y_{3+2v}).  Returns true if the path
+// continues, with (o, d, T) updated to the next ray.
+__device__ __forceinline__ bool shade_vertex(const SceneView& s, int k, float t, int v, int depth, float u1,
+                                             float u2, float3& o, float3& d, float3& T, float3& F) {
+    const TriRecord* tr = s.tris + k;
+    const float4 q1 = __ldg(&tr->e1_mat), q2 = __ldg(&tr->e2);
+    const Material m = s.mats[__float_as_int(q1.w)];
+    const float3 ng = normalize(cross(f3(q1.x, q1.y, q1.z), f3(q2.x, q2.y, q2.z)));
+    const float3 p = o + d * t;
+    if (m.emits && -dot(d, ng) > 0.0f) F = F + mul(T, m.emission);
+    if (v == depth) return false;
+    float3 wi, w;
+    if (!scatter(m, d, ng, u1, u2, wi, w)) return false;
+    T = mul(T, w);
+    if (T.x == 0.0f && T.y == 0.0f && T.z == 0.0f) return false;
+    const float3 off = dot(wi, ng) >= 0.0f ? ng : ng * -1.0f;
+    const float mx = fmaxf(fmaxf(fabsf(p.x), fabsf(p.y)), fabsf(p.z));
+    o = p + off * (1e-4f * (1.0f + mx));
+    d = wi;
+    return true;
+}
+
+__device__ __forceinline__ float3 finite_or_zero(float3 F, unsigned& status) {
+    if (!isfinite(F.x) || !isfinite(F.y) || !isfinite(F.z)) {
+        status |= JR_STATUS_NONFINITE;
+        return f3(0.f, 0.f, 0.f);
+    }
+    return F;
+}
+
+template <bool kCount>
+__device__ __forceinline__ float3 eval_path_w(const SceneView& s, int depth, const float* y, uint32_t ys,
+                                              int32_t* ids, uint64_t id_stride, unsigned& status, Work& work) {
+    float3 F = f3(0.f, 0.f, 0.f), T = f3(1.f, 1.f, 1.f);
+    float3 o, d;
+    camera_ray(s, y[0], y[ys], o, d);
+    if (ids)
+        for (int v = 0; v <= depth; ++v) ids[v * id_stride] = -1;
+    for (int v = 0; v <= depth; ++v) {
+        float t;
+        const int k = closest_hit<kCount>(s, o, d, t, status, work);
+        if (k < 0) break;
+        if (ids) ids[v * id_stride] = __float_as_int(__ldg(&s.tris[k].v0_id.w));
+        const float u1 = v < depth ? y[(2 + 2 * v) * ys] : 0.0f;
+        const float u2 = v < depth ? y[(3 + 2 * v) * ys] : 0.0f;
+        if (!shade_vertex(s, k, t, v, depth, u1, u2, o, d, T, F)) break;
+    }
+    return finite_or_zero(F, status);
+}
+
+__device__ __forceinline__ float3 eval_path(const SceneView& s, int depth, const float* y, uint32_t ys, int32_t* ids,
+                                            uint64_t id_stride, unsigned& status) {
+    Work w;
+    return eval_path_w<false>(s, depth, y, ys, ids, id_stride, status, w);
+}
+
+__device__ __forceinline__ void flush_status(unsigned status, unsigned int* word) {
+    if (status) atomicOr(word, status);
+}
+
+}  // namespace
+}  // namespace jr

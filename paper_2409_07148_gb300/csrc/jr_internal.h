@@ -17,6 +17,7 @@ constexpr int kLeafMax = 8;                 // triangles per leaf (encoded count
 constexpr uint32_t kNodeVisitBudget = 1u << 16;  // per ray; exceeding it is a watchdog event
 
 constexpr uint32_t kTagStep = 0, kTagInit = 1, kTagPt = 2;
+constexpr uint64_t kWavefrontMinChains = 1u << 16;  // JR_EXEC_AUTO picks the wavefront from here up
 
 // BVH node, 64 bytes: both children's boxes, Aila & Laine style.
 //   a = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
@@ -56,6 +57,16 @@ struct SceneView {
     float cam[12];
 };
 
+// Buffers of the wavefront execution mode (allocated on first use).
+struct WaveView {
+    float* y = nullptr;           // [D][n] second state buffer
+    uint8_t* par = nullptr;       // [n] 1: the current state is in y, 0: in x
+    float* ua = nullptr;          // [n] Ua of a local step, -1 for a regeneration step
+    float4* path = nullptr;       // [n][3] live path record (o, d, T, F)
+    uint32_t* queue = nullptr;    // [2][n] live-path queues (ping-pong)
+    unsigned int* qcount = nullptr;  // [2 (kMaxDepth + 2)] queue lengths, then fetch cursors
+};
+
 struct ChainView {
     float* x;        // [D][n] PSS coordinates
     float* fpu;      // [5][n] F.r F.g F.b p u
@@ -69,6 +80,7 @@ struct ChainView {
     uint32_t flags;
     uint64_t seed;
     float c_tilde, sigma;
+    WaveView wf;
 };
 
 // Host-side BVH build result.
@@ -89,6 +101,9 @@ cudaError_t launch_step(const SceneView& s, const ChainView& c, uint64_t step_be
                         uint8_t* tr_flags, float* tr_dt, int32_t* tr_pix, unsigned long long* work_out, int block,
                         cudaStream_t st);
 cudaError_t launch_fold(const ChainView& c, cudaStream_t st);
+// jr_wavefront.cu
+cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
+                             cudaStream_t st);
 cudaError_t launch_resolve(const ChainView& c, float* rgb, cudaStream_t st);
 cudaError_t launch_reeval(const SceneView& s, const ChainView& c, cudaStream_t st);
 cudaError_t launch_eval_states(const SceneView& s, uint32_t depth, float c_tilde, const float* x, uint64_t n,

@@ -1,0 +1,267 @@
+// Wavefront execution of the Jump Restore step (sm_103a).
+//
+// The megakernel (jr_kernels.cu) keeps one chain per thread for a whole
+// launch; its warps idle while their longest path and their longest ray finish.
+// Here a step of Alg. 2 (Section 7.2) is split at the ray boundaries:
+//
+//   step kernel (all chains, converged): finish the previous step (MH
+//     acceptance or regeneration), draw the new step's clocks t1 ~ Exp(1),
+//     t2 ~ Exp(k), k = c~ u / p (Section 6.2), splat (dt, x) (Section 6.3/7.4),
+//     build the candidate y (Gaussian small step or a draw from mu), trace the
+//     camera ray and shade vertex 1; live paths go to a queue.
+//   bounce kernel v = 1..depth (persistent, warps fetch 32 queue entries at a
+//     time): trace one ray per live path, shade it, append survivors to the
+//     next queue with one warp-aggregated atomic.
+//
+// Per-chain arithmetic is the megakernel's, through the same device functions,
+// so both modes give the same chains for the same Philox streams.  The state
+// lives in two buffers (x, y) with a per-chain parity byte, so an accepted
+// move is a flip; the final finish launch copies states back into x.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/jr.h"
+#include "jr_device.cuh"
+#include "jr_internal.h"
+
+namespace jr {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Path record of a live path: (o.xyz, d.x) (d.yz, T.xy) (T.z, F.xyz).
+__device__ __forceinline__ void store_path(float4* path, uint64_t i, float3 o, float3 d, float3 T, float3 F) {
+    path[3 * i] = make_float4(o.x, o.y, o.z, d.x);
+    path[3 * i + 1] = make_float4(d.y, d.z, T.x, T.y);
+    path[3 * i + 2] = make_float4(T.z, F.x, F.y, F.z);
+}
+
+__device__ __forceinline__ void load_path(const float4* path, uint64_t i, float3& o, float3& d, float3& T,
+                                          float3& F) {
+    const float4 a = path[3 * i], b = path[3 * i + 1], c = path[3 * i + 2];
+    o = f3(a.x, a.y, a.z);
+    d = f3(a.w, b.x, b.y);
+    T = f3(b.z, b.w, c.x);
+    F = f3(c.y, c.z, c.w);
+}
+
+// Append chain i to a queue if `live`; one atomic per warp.  All 32 lanes call.
+__device__ __forceinline__ void enqueue(bool live, uint32_t i, uint32_t* q, unsigned int* count) {
+    const unsigned m = __ballot_sync(kFull, live);
+    if (m == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (live) q[base + __popc(m & ((1u << lane) - 1u))] = i;
+}
+
+__device__ __forceinline__ void count_and_flush(uint32_t nJ, uint32_t nL, uint32_t nA, unsigned status,
+                                                const ChainView& c) {
+    nJ = __reduce_add_sync(kFull, nJ);
+    nL = __reduce_add_sync(kFull, nL);
+    nA = __reduce_add_sync(kFull, nA);
+    status = __reduce_or_sync(kFull, status);
+    if ((threadIdx.x & 31) == 0) {
+        if (nJ) atomicAdd(c.counters + 0, (unsigned long long)nJ);
+        if (nL) atomicAdd(c.counters + 1, (unsigned long long)nL);
+        if (nA) atomicAdd(c.counters + 2, (unsigned long long)nA);
+        if (status) atomicOr(c.status, status);
+    }
+}
+
+// finish = 1: complete step `step - 1` of every chain.  begin = 1: start step
+// `step`.  With begin = 0 the launch also moves every state back into x.
+__global__ void __launch_bounds__(128) wf_step_kernel(SceneView s, ChainView c, uint64_t step, int finish,
+                                                      int begin) {
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const bool valid = i < c.n;
+    const int D = (int)c.dim;
+    const uint64_t n = c.n;
+    const WaveView& w = c.wf;
+    uint32_t nJ = 0, nL = 0, nA = 0;
+    unsigned status = 0;
+    bool live = false;
+    if (valid) {
+        uint8_t par = w.par[i];
+        float Fr = c.fpu[0 * n + i], Fg = c.fpu[1 * n + i], Fb = c.fpu[2 * n + i];
+        float p = c.fpu[3 * n + i], u = c.fpu[4 * n + i];
+        if (finish) {
+            const float ua = w.ua[i];
+            const float4 pf = w.path[3 * i + 2];
+            const float3 Fy = finite_or_zero(f3(pf.y, pf.z, pf.w), status);
+            const float py = lum(Fy);
+            bool accept;
+            if (ua >= 0.0f) {  // local branch: MH acceptance, U < min(1, p(y)/p(x))
+                accept = ua * p < py;
+                nL++;
+                nA += accept;
+            } else {           // regeneration: the candidate is the new tour's start
+                accept = true;
+                nJ++;
+            }
+            if (accept) {
+                par ^= 1;
+                Fr = Fy.x;
+                Fg = Fy.y;
+                Fb = Fy.z;
+                p = py;
+                u = 1.0f;
+                c.fpu[0 * n + i] = Fr;
+                c.fpu[1 * n + i] = Fg;
+                c.fpu[2 * n + i] = Fb;
+                c.fpu[3 * n + i] = p;
+                c.fpu[4 * n + i] = u;
+            }
+        }
+        float* cur = par ? w.y : c.x;
+        float* cand = par ? c.x : w.y;
+        if (begin) {
+            const uint32_t chain = c.chain_offset + (uint32_t)i;
+            const uint4 r0 = draw(c.seed, kTagStep, 0, chain, step);
+            const float E1 = -logf(1.0f - u01(r0.x));
+            const float E2 = -logf(1.0f - u01(r0.y));
+            const float Ua = u01(r0.z);
+            const float t2 = p > 0.0f ? E2 * p / (c.c_tilde * u) : 0.0f;
+            const bool local = E1 < t2;
+            float dt = local ? E1 : t2;
+            if (c.flags & JR_FLAG_RAO_BLACKWELL) dt = p > 0.0f ? p / (p + c.c_tilde * u) : 0.0f;
+            const float x0 = cur[i], x1 = cur[n + i];
+            if (dt > 0.0f && p > 0.0f) {
+                uint32_t px = min((uint32_t)((double)x0 * (double)c.width), c.width - 1);
+                uint32_t py = min((uint32_t)((double)x1 * (double)c.height), c.height - 1);
+                const float wgt = c.c_tilde * dt * ((float)c.width * (float)c.height) / p;
+                atomicAdd(c.fb + py * c.width + px, make_float4(wgt * Fr, wgt * Fg, wgt * Fb, dt));
+            }
+            w.ua[i] = local ? Ua : -1.0f;
+            float y0 = 0.f, y1 = 0.f, y2 = 0.f, y3 = 0.f;
+            for (int b = 0; 4 * b < D; ++b) {
+                const uint4 r = draw(c.seed, kTagStep, (uint32_t)(b + 1), chain, step);
+                const uint64_t o0 = (uint64_t)(4 * b) * n + i;
+                float v0, v1, v2 = 0.f, v3 = 0.f;
+                const bool two = 4 * b + 2 < D;
+                if (local) {
+                    float sn, cs;
+                    float R = sqrtf(-2.0f * logf(1.0f - u01(r.x)));
+                    sincospif(2.0f * u01(r.y), &sn, &cs);
+                    v0 = wrap01((b == 0 ? x0 : cur[o0]) + c.sigma * R * cs);
+                    v1 = wrap01((b == 0 ? x1 : cur[o0 + n]) + c.sigma * R * sn);
+                    if (two) {
+                        R = sqrtf(-2.0f * logf(1.0f - u01(r.z)));
+                        sincospif(2.0f * u01(r.w), &sn, &cs);
+                        v2 = wrap01(cur[o0 + 2 * n] + c.sigma * R * cs);
+                        v3 = wrap01(cur[o0 + 3 * n] + c.sigma * R * sn);
+                    }
+                } else {
+                    v0 = u01(r.x);
+                    v1 = u01(r.y);
+                    v2 = u01(r.z);
+                    v3 = u01(r.w);
+                }
+                cand[o0] = v0;
+                cand[o0 + n] = v1;
+                if (two) {
+                    cand[o0 + 2 * n] = v2;
+                    cand[o0 + 3 * n] = v3;
+                }
+                if (b == 0) {
+                    y0 = v0;
+                    y1 = v1;
+                    y2 = v2;
+                    y3 = v3;
+                }
+            }
+            // vertex 1: camera ray
+            float3 o, d, T = f3(1.f, 1.f, 1.f), F = f3(0.f, 0.f, 0.f);
+            camera_ray(s, y0, y1, o, d);
+            float t;
+            Work wk;
+            const int k = closest_hit<false>(s, o, d, t, status, wk);
+            if (k >= 0) live = shade_vertex(s, k, t, 0, (int)c.depth, y2, y3, o, d, T, F);
+            if (live)
+                store_path(w.path, i, o, d, T, F);
+            else
+                w.path[3 * i + 2] = make_float4(0.f, F.x, F.y, F.z);
+        } else if (par) {
+            for (int dd = 0; dd < D; ++dd) c.x[(uint64_t)dd * n + i] = w.y[(uint64_t)dd * n + i];
+            par = 0;
+        }
+        w.par[i] = par;
+    }
+    if (begin) enqueue(live, (uint32_t)i, w.queue, w.qcount + 1);
+    count_and_flush(nJ, nL, nA, status, c);
+}
+
+// Bounce v (>= 1): one ray per live path from queue_in; survivors to queue_out.
+__global__ void __launch_bounds__(128) wf_bounce_kernel(SceneView s, ChainView c, int v) {
+    const WaveView& w = c.wf;
+    const uint32_t* qin = w.queue + (uint64_t)((v - 1) & 1) * c.n;
+    uint32_t* qout = w.queue + (uint64_t)(v & 1) * c.n;
+    const unsigned count = w.qcount[v];
+    unsigned int* fetch = w.qcount + (kMaxDepth + 2) + v;
+    const int lane = threadIdx.x & 31;
+    const uint64_t n = c.n;
+    unsigned status = 0;
+    while (true) {
+        unsigned j0 = 0;
+        if (lane == 0) j0 = atomicAdd(fetch, 32u);
+        j0 = __shfl_sync(kFull, j0, 0);
+        if (j0 >= count) break;
+        const unsigned j = j0 + lane;
+        bool live = false;
+        uint32_t i = 0;
+        if (j < count) {
+            i = qin[j];
+            float3 o, d, T, F;
+            load_path(w.path, i, o, d, T, F);
+            float u1 = 0.f, u2 = 0.f;
+            if (v < (int)c.depth) {
+                const float* cand = w.par[i] ? c.x : w.y;
+                u1 = cand[(uint64_t)(2 + 2 * v) * n + i];
+                u2 = cand[(uint64_t)(3 + 2 * v) * n + i];
+            }
+            float t;
+            Work wk;
+            const int k = closest_hit<false>(s, o, d, t, status, wk);
+            if (k >= 0) live = shade_vertex(s, k, t, v, (int)c.depth, u1, u2, o, d, T, F);
+            if (live)
+                store_path(w.path, i, o, d, T, F);
+            else
+                w.path[3 * i + 2] = make_float4(0.f, F.x, F.y, F.z);
+        }
+        enqueue(live, i, qout, w.qcount + v + 1);
+    }
+    status = __reduce_or_sync(kFull, status);
+    if (lane == 0 && status) atomicOr(c.status, status);
+}
+
+inline unsigned grid_for(uint64_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
+                             cudaStream_t st) {
+    static int bounce_blocks = 0;
+    if (bounce_blocks == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wf_bounce_kernel, 128, 0)) != cudaSuccess)
+            return e;
+        bounce_blocks = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const unsigned G = grid_for(c.n, 128);
+    const size_t qbytes = sizeof(unsigned int) * 2 * (kMaxDepth + 2);
+    for (uint32_t k = 0; k < n_steps; ++k) {
+        cudaError_t e = cudaMemsetAsync(c.wf.qcount, 0, qbytes, st);
+        if (e != cudaSuccess) return e;
+        wf_step_kernel<<<G, 128, 0, st>>>(s, c, step_begin + k, k > 0, 1);
+        for (int v = 1; v <= (int)c.depth; ++v) wf_bounce_kernel<<<bounce_blocks, 128, 0, st>>>(s, c, v);
+    }
+    wf_step_kernel<<<G, 128, 0, st>>>(s, c, step_begin + n_steps, n_steps > 0, 0);
+    return cudaGetLastError();
+}
+
+}  // namespace jr

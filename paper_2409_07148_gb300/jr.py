@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libjr_gb300.so")
 
 JR_OK, JR_ERR_INVALID_ARG, JR_ERR_CUDA, JR_ERR_OOM, JR_ERR_WATCHDOG, JR_ERR_NUMERIC, JR_ERR_STATE = range(7)
 JR_FLAG_RAO_BLACKWELL = 1
+JR_EXEC_AUTO, JR_EXEC_MEGAKERNEL, JR_EXEC_WAVEFRONT = 0, 1, 2
 JR_STATUS_NONFINITE, JR_STATUS_TRAVERSAL, JR_STATUS_STACK = 1, 2, 4
 MATERIAL_FLOATS = 12
 MAX_DEPTH = 15
@@ -69,6 +70,7 @@ _SIGS = {
     "jr_advance_traced": [_P, _U32, _P, _P, _P, _P],
     "jr_advance_counted": [_P, _U32, _P, _P],
     "jr_set_block_size": [_P, _U32],
+    "jr_set_execution": [_P, _U32],
     "jr_resolve": [_P, _P, _I, _P],
     "jr_get_accumulator": [_P, _P, _I, _P],
     "jr_get_stats": [_P, ctypes.POINTER(Stats), _P],
@@ -184,6 +186,11 @@ class Chains:
 
     def set_block_size(self, block):
         _check(lib().jr_set_block_size(self.h, int(block)))
+
+    def set_execution(self, mode):
+        """JR_EXEC_AUTO, JR_EXEC_MEGAKERNEL or JR_EXEC_WAVEFRONT (or 'auto'/'mega'/'wave')."""
+        m = {"auto": 0, "mega": 1, "megakernel": 1, "wave": 2, "wavefront": 2}.get(mode, mode)
+        _check(lib().jr_set_execution(self.h, int(m)))
 
     def resolve(self, out=None, stream=None):
         """Into a device tensor (async) if given, else into a new host array."""

@@ -1,13 +1,18 @@
 """Image-level parity of the GPU Jump Restore estimator (needs a GB300).
 
-* per pixel: the GPU image of the 64x64 depth-3 Cornell workload (256 chains
-  x 10^4 steps per batch, 32 batches with disjoint chain ids) against the
-  oracle's image (16 independent batches), z-scores from batch standard
-  errors: at most 0.1% of pixel-channels beyond 4 sigma;
-* a converged plain path-tracing reference (GPU kernel, itself compared
-  pixel by pixel with the oracle's path tracer) and the GPU Jump Restore
-  image against it: relMSE <= 1e-3 (relMSE = mean (I - R)^2 / (R^2 + 1e-2));
-* the furnace image is flat at the closed form L_e (1 - rho^(d+1)) / (1 - rho).
+Two kinds of comparison:
+
+* paired -- the GPU and the oracle draw identical Philox streams (same seed,
+  same chain / sample ids), so their images agree sample for sample up to
+  FP32 rounding, decision ties and rare FP32-vs-FP64 topology flips;
+* independent -- different seeds, per-pixel Welch t statistics over batches
+  with disjoint chain ids, turned into equal-tail normal scores (so the few
+  batches' degrees of freedom do not inflate the tails); the 4-sigma budget is
+  0.1 % of pixel-channels (Bonferroni-style; ~0.006 % expected).
+
+The converged reference is plain path tracing on the GPU (2^32 samples),
+itself checked against the oracle's path tracer on identical samples.
+relMSE = mean over pixels and channels of (I - R)^2 / (R^2 + 1e-2).
 """
 import numpy as np
 import pytest
@@ -32,6 +37,22 @@ def relmse(img, ref):
     return float(np.mean((img - ref) ** 2 / (ref ** 2 + EPS)))
 
 
+def welch_z(a, b):
+    """Per-pixel Welch t of mean(a) - mean(b) over batches, mapped to the
+    normal score with the same two-sided tail probability."""
+    from scipy import stats
+    na, nb = len(a), len(b)
+    va, vb = a.var(0, ddof=1) / na, b.var(0, ddof=1) / nb
+    d = a.mean(0) - b.mean(0)
+    se2 = va + vb
+    ok = se2 > 0
+    assert np.all(d[~ok] == 0)
+    t = d[ok] / np.sqrt(se2[ok])
+    df = se2[ok] ** 2 / (va[ok] ** 2 / (na - 1) + vb[ok] ** 2 / (nb - 1))
+    p = 2 * stats.t.sf(np.abs(t), df)
+    return np.sign(t) * stats.norm.isf(np.maximum(p, 1e-300) / 2)
+
+
 def _gpu_batches(J, sc, n_batches, chains, steps, seed, first_chain=0):
     import torch
     g = J.Scene(sc)
@@ -50,26 +71,42 @@ def _gpu_batches(J, sc, n_batches, chains, steps, seed, first_chain=0):
     return imgs
 
 
-def _z(a, b):
-    d = a.mean(0) - b.mean(0)
-    se = np.sqrt(a.var(0, ddof=1) / len(a) + b.var(0, ddof=1) / len(b))
+def _oracle_batches(sc, n_batches, chains, steps, seed, first_chain=0):
+    osc = O.Scene(sc)
+    out = []
+    for b in range(n_batches):
+        ch = O.Chains(osc, sc.D, sc.width, sc.height, seed=seed, chain_begin=first_chain + b * chains,
+                      n_chains=chains)
+        ch.advance(steps)
+        out.append(ch.image())
+    return np.array(out)
+
+
+def test_cornell_paired_streams_match_oracle(J):
+    """Identical Philox streams: 16 batches of 256 chains x 2000 steps on both
+    sides.  The image difference per pixel is far below one standard error."""
+    sc = scenes.cornell()
+    g = _gpu_batches(J, sc, 16, 256, 2000, seed=3)
+    o = _oracle_batches(sc, 16, 256, 2000, seed=3)
+    se = np.sqrt(o.var(0, ddof=1) / len(o))
+    d = np.abs(g.mean(0) - o.mean(0))
     ok = se > 0
-    assert np.all(d[~ok] == 0)
-    return d[ok] / se[ok]
+    assert np.all(d[~ok] < 1e-6)
+    r = d[ok] / se[ok]
+    assert np.median(r) < 1e-2          # most pixels: identical trajectories, FP32 rounding only
+    assert np.mean(r > 1.0) < 0.01      # a few pixels touched by a chain that diverged at a tie
+    assert np.max(r) < 4.0
 
 
 def test_cornell_per_pixel_vs_oracle(J):
+    """Independent seeds: 64 GPU batches (each the 256-chain x 10^4-step
+    Cornell workload) vs 32 oracle batches."""
     sc = scenes.cornell()
-    gimgs = _gpu_batches(J, sc, 32, 256, 10_000, seed=0)
-    osc = O.Scene(sc)
-    oimgs = []
-    for b in range(16):
-        ch = O.Chains(osc, sc.D, sc.width, sc.height, seed=1, chain_begin=b * 256, n_chains=256)
-        ch.advance(2500)
-        oimgs.append(ch.image())
-    z = _z(gimgs, np.array(oimgs))
+    g = _gpu_batches(J, sc, 64, 256, 10_000, seed=0)
+    o = _oracle_batches(sc, 32, 256, 2500, seed=1, first_chain=1 << 20)
+    z = welch_z(g, o)
     assert np.mean(np.abs(z) > 4) <= 1e-3, np.sort(np.abs(z))[-10:]
-    assert 0.7 < np.mean(z ** 2) < 1.4
+    assert 0.75 < np.mean(z ** 2) < 1.35, np.mean(z ** 2)
 
 
 @pytest.fixture(scope="module")
@@ -88,34 +125,37 @@ def reference(J):
     return sc, (acc[..., :3] / n).cpu().numpy()
 
 
-def test_plain_path_tracer_matches_oracle(J, reference):
+def test_plain_path_tracer_matches_oracle_paired(J):
+    """Same seed and sample ids on both sides: identical samples, so pixel sums
+    agree to FP32 rounding except for rare topology flips."""
     import torch
-    sc, _ = reference
-    g = J.Scene(sc)
-    gb, ob = [], []
-    osc = O.Scene(sc)
-    for b in range(16):
-        acc = J.render_pt(g, sc.width, sc.height, sc.depth, 1 << 22, seed=5, sample_begin=b << 22)
-        torch.cuda.synchronize()
-        gb.append((acc[..., :3] / (1 << 22)).cpu().numpy())
-        img, _ = O.render_pt(osc, sc.D, sc.width, sc.height, 1 << 20, seed=6, sample_begin=b << 20)
-        ob.append(img)
-    z = _z(np.array(gb), np.array(ob))
-    assert np.mean(np.abs(z) > 4) <= 1e-3
-    assert 0.7 < np.mean(z ** 2) < 1.4
+    sc = scenes.cornell()
+    n = 1 << 22
+    acc = J.render_pt(J.Scene(sc), sc.width, sc.height, sc.depth, n, seed=5)
+    torch.cuda.synchronize()
+    g = (acc[..., :3] / n).cpu().numpy()
+    o, _ = O.render_pt(O.Scene(sc), sc.D, sc.width, sc.height, n, seed=5)
+    nz = o != 0
+    assert np.all(g[~nz] == 0) or np.mean(g[~nz] != 0) < 1e-3
+    rel = np.abs(g - o)[nz] / o[nz]
+    assert np.mean(rel > 1e-4) < 5e-3, np.sort(rel)[-5:]
+    assert relmse(g, o) < 1e-6
 
 
 def test_cornell_relmse_vs_converged_reference(J, reference):
     sc, ref = reference
-    imgs = _gpu_batches(J, sc, 8, 1 << 14, 4000, seed=11, first_chain=1 << 20)
+    imgs = _gpu_batches(J, sc, 32, 4096, 4000, seed=11, first_chain=1 << 22)
     img = imgs.mean(0)
     e = relmse(img, ref)
     assert e <= 1e-3, e
-    # and the batches scatter around the reference as their standard errors say
+    # the batches scatter about the reference as their standard errors say
+    from scipy import stats
     se = imgs.std(0, ddof=1) / np.sqrt(len(imgs))
     ok = se > 0
-    z = (img - ref)[ok] / se[ok]
-    assert np.mean(np.abs(z) > 4.5) <= 2e-3
+    t = (img - ref)[ok] / se[ok]
+    z = np.sign(t) * stats.norm.isf(stats.t.sf(np.abs(t), len(imgs) - 1))
+    assert np.mean(np.abs(z) > 4) <= 1e-3
+    assert 0.7 < np.mean(z ** 2) < 1.5
 
 
 def test_furnace_image_is_flat(J):
