@@ -73,12 +73,19 @@ struct Work {
 
 // Closest hit, ties on equal t to the smaller original triangle index.
 // Returns the leaf-order record index or -1; t_out gets the hit distance.
+//
+// Warp-synchronous while-while traversal (Aila & Laine, HPG 2009): every lane
+// in `mask` must call this together (lanes without a ray pass want = false).
+// Each inner-node round and each leaf round ends in a __any_sync over `mask`,
+// so the lanes reconverge every iteration instead of drifting apart under
+// independent thread scheduling; lanes that reach a leaf wait for the others
+// before the leaves are tested together.
 template <bool kCount>
-__device__ __forceinline__ int closest_hit(const SceneView& s, float3 o, float3 d, float& t_out, unsigned& status,
-                                           Work& work) {
-    if constexpr (kCount) work.rays++;
+__device__ __forceinline__ int closest_hit(const SceneView& s, unsigned mask, bool want, float3 o, float3 d,
+                                           float& t_out, unsigned& status, Work& work) {
     t_out = INFINITY;
-    if (s.root == kSentinel) return -1;
+    bool active = want && s.root != kSentinel;
+    if constexpr (kCount) work.rays += want ? 1u : 0u;
     const float dx = fabsf(d.x) < 1e-20f ? copysignf(1e-20f, d.x) : d.x;
     const float dy = fabsf(d.y) < 1e-20f ? copysignf(1e-20f, d.y) : d.y;
     const float dz = fabsf(d.z) < 1e-20f ? copysignf(1e-20f, d.z) : d.z;
@@ -90,74 +97,89 @@ __device__ __forceinline__ int closest_hit(const SceneView& s, float3 o, float3 
     int sp = 0;
     int ref = s.root;
     uint32_t visits = 0;
-    while (true) {
-        while (ref >= 0) {
-            if (++visits > kNodeVisitBudget) {
-                status |= JR_STATUS_TRAVERSAL;
-                return -1;
-            }
-            if constexpr (kCount) work.nodes++;
-            const BvhNode* n = s.nodes + ref;
-            const float4 a = __ldg(&n->a), b = __ldg(&n->b), c = __ldg(&n->c);
-            const int4 rf = __ldg(&n->refs);
-            const float l0x = fmaf(a.x, ix, -ox), h0x = fmaf(a.y, ix, -ox);
-            const float l0y = fmaf(a.z, iy, -oy), h0y = fmaf(a.w, iy, -oy);
-            const float l0z = fmaf(c.x, iz, -oz), h0z = fmaf(c.y, iz, -oz);
-            const float l1x = fmaf(b.x, ix, -ox), h1x = fmaf(b.y, ix, -ox);
-            const float l1y = fmaf(b.z, iy, -oy), h1y = fmaf(b.w, iy, -oy);
-            const float l1z = fmaf(c.z, iz, -oz), h1z = fmaf(c.w, iz, -oz);
-            const float tn0 = fmaxf(fmaxf(fminf(l0x, h0x), fminf(l0y, h0y)), fmaxf(fminf(l0z, h0z), 0.0f));
-            const float tf0 = fminf(fminf(fmaxf(l0x, h0x), fmaxf(l0y, h0y)), fminf(fmaxf(l0z, h0z), tb));
-            const float tn1 = fmaxf(fmaxf(fminf(l1x, h1x), fminf(l1y, h1y)), fmaxf(fminf(l1z, h1z), 0.0f));
-            const float tf1 = fminf(fminf(fmaxf(l1x, h1x), fmaxf(l1y, h1y)), fminf(fmaxf(l1z, h1z), tb));
-            const bool h0 = tn0 <= tf0 * 1.00000024f;
-            const bool h1 = tn1 <= tf1 * 1.00000024f;
-            if (h0 && h1) {
-                const bool first0 = tn0 <= tn1;
-                if (sp >= kStackSize) {
-                    status |= JR_STATUS_STACK;
-                    return -1;
+    while (__any_sync(mask, active)) {
+        // inner nodes until every active lane holds a leaf (or is done)
+        while (__any_sync(mask, active && ref >= 0)) {
+            if (active && ref >= 0) {
+                if (++visits > kNodeVisitBudget) {
+                    status |= JR_STATUS_TRAVERSAL;
+                    active = false;
+                    best = -1;
+                    tb = INFINITY;
+                    continue;
                 }
-                stack[sp++] = first0 ? rf.y : rf.x;
-                ref = first0 ? rf.x : rf.y;
-            } else if (h0) {
-                ref = rf.x;
-            } else if (h1) {
-                ref = rf.y;
+                if constexpr (kCount) work.nodes++;
+                const BvhNode* n = s.nodes + ref;
+                const float4 a = __ldg(&n->a), b = __ldg(&n->b), c = __ldg(&n->c);
+                const int4 rf = __ldg(&n->refs);
+                const float l0x = fmaf(a.x, ix, -ox), h0x = fmaf(a.y, ix, -ox);
+                const float l0y = fmaf(a.z, iy, -oy), h0y = fmaf(a.w, iy, -oy);
+                const float l0z = fmaf(c.x, iz, -oz), h0z = fmaf(c.y, iz, -oz);
+                const float l1x = fmaf(b.x, ix, -ox), h1x = fmaf(b.y, ix, -ox);
+                const float l1y = fmaf(b.z, iy, -oy), h1y = fmaf(b.w, iy, -oy);
+                const float l1z = fmaf(c.z, iz, -oz), h1z = fmaf(c.w, iz, -oz);
+                const float tn0 = fmaxf(fmaxf(fminf(l0x, h0x), fminf(l0y, h0y)), fmaxf(fminf(l0z, h0z), 0.0f));
+                const float tf0 = fminf(fminf(fmaxf(l0x, h0x), fmaxf(l0y, h0y)), fminf(fmaxf(l0z, h0z), tb));
+                const float tn1 = fmaxf(fmaxf(fminf(l1x, h1x), fminf(l1y, h1y)), fmaxf(fminf(l1z, h1z), 0.0f));
+                const float tf1 = fminf(fminf(fmaxf(l1x, h1x), fmaxf(l1y, h1y)), fminf(fmaxf(l1z, h1z), tb));
+                const bool h0 = tn0 <= tf0 * 1.00000024f;
+                const bool h1 = tn1 <= tf1 * 1.00000024f;
+                if (h0 && h1) {
+                    const bool first0 = tn0 <= tn1;
+                    if (sp >= kStackSize) {
+                        status |= JR_STATUS_STACK;
+                        active = false;
+                        best = -1;
+                        tb = INFINITY;
+                        continue;
+                    }
+                    stack[sp++] = first0 ? rf.y : rf.x;
+                    ref = first0 ? rf.x : rf.y;
+                } else if (h0) {
+                    ref = rf.x;
+                } else if (h1) {
+                    ref = rf.y;
+                } else {
+                    ref = sp > 0 ? stack[--sp] : kSentinel;
+                }
+            }
+        }
+        if (active) {
+            if (ref == kSentinel) {
+                active = false;
             } else {
+                const int enc = ~ref;
+                const int first = enc >> 3, cnt = (enc & 7) + 1;
+                if constexpr (kCount) work.tris += (uint32_t)cnt;
+                for (int k = first; k < first + cnt; ++k) {
+                    const TriRecord* tr = s.tris + k;
+                    const float4 q0 = __ldg(&tr->v0_id), q1 = __ldg(&tr->e1_mat), q2 = __ldg(&tr->e2);
+                    // Moller-Trumbore (JGT 1997)
+                    const float3 e1 = f3(q1.x, q1.y, q1.z), e2 = f3(q2.x, q2.y, q2.z);
+                    const float3 pv = cross(d, e2);
+                    const float det = dot(e1, pv);
+                    if (det == 0.0f) continue;
+                    const float inv = 1.0f / det;
+                    const float3 tv = o - f3(q0.x, q0.y, q0.z);
+                    const float u = dot(tv, pv) * inv;
+                    if (u < 0.0f || u > 1.0f) continue;
+                    const float3 qv = cross(tv, e1);
+                    const float v = dot(d, qv) * inv;
+                    if (v < 0.0f || u + v > 1.0f) continue;
+                    const float t = dot(e2, qv) * inv;
+                    const int id = __float_as_int(q0.w);
+                    if (t > 0.0f && (t < tb || (t == tb && id < best_id))) {
+                        tb = t;
+                        best = k;
+                        best_id = id;
+                    }
+                }
                 ref = sp > 0 ? stack[--sp] : kSentinel;
+                if (ref == kSentinel) active = false;
             }
         }
-        if (ref == kSentinel) break;
-        const int enc = ~ref;
-        const int first = enc >> 3, cnt = (enc & 7) + 1;
-        if constexpr (kCount) work.tris += (uint32_t)cnt;
-        for (int k = first; k < first + cnt; ++k) {
-            const TriRecord* tr = s.tris + k;
-            const float4 q0 = __ldg(&tr->v0_id), q1 = __ldg(&tr->e1_mat), q2 = __ldg(&tr->e2);
-            // Moller-Trumbore (JGT 1997), same algebra as the reference definition.
-            const float3 e1 = f3(q1.x, q1.y, q1.z), e2 = f3(q2.x, q2.y, q2.z);
-            const float3 pv = cross(d, e2);
-            const float det = dot(e1, pv);
-            if (det == 0.0f) continue;
-            const float inv = 1.0f / det;
-            const float3 tv = o - f3(q0.x, q0.y, q0.z);
-            const float u = dot(tv, pv) * inv;
-            if (u < 0.0f || u > 1.0f) continue;
-            const float3 qv = cross(tv, e1);
-            const float v = dot(d, qv) * inv;
-            if (v < 0.0f || u + v > 1.0f) continue;
-            const float t = dot(e2, qv) * inv;
-            const int id = __float_as_int(q0.w);
-            if (t > 0.0f && (t < tb || (t == tb && id < best_id))) {
-                tb = t;
-                best = k;
-                best_id = id;
-            }
-        }
-        ref = sp > 0 ? stack[--sp] : kSentinel;
     }
-    t_out = tb;
+    t_out = best >= 0 ? tb : INFINITY;
     return best;
 }
 
@@ -272,30 +294,41 @@ __device__ __forceinline__ float3 finite_or_zero(float3 F, unsigned& status) {
     return F;
 }
 
+// The integrand for the lanes in `mask` (all of which must call together;
+// lanes with want = false only keep the warp in step).  The bounce loop runs
+// until no lane in the warp has a live path.
 template <bool kCount>
-__device__ __forceinline__ float3 eval_path_w(const SceneView& s, int depth, const float* y, uint32_t ys,
-                                              int32_t* ids, uint64_t id_stride, unsigned& status, Work& work) {
+__device__ __forceinline__ float3 eval_path_w(const SceneView& s, unsigned mask, bool want, int depth, const float* y,
+                                              uint32_t ys, int32_t* ids, uint64_t id_stride, unsigned& status,
+                                              Work& work) {
     float3 F = f3(0.f, 0.f, 0.f), T = f3(1.f, 1.f, 1.f);
-    float3 o, d;
-    camera_ray(s, y[0], y[ys], o, d);
-    if (ids)
+    float3 o = f3(0.f, 0.f, 1.f), d = f3(0.f, 0.f, 1.f);
+    if (want) camera_ray(s, y[0], y[ys], o, d);
+    if (want && ids)
         for (int v = 0; v <= depth; ++v) ids[v * id_stride] = -1;
+    bool alive = want;
     for (int v = 0; v <= depth; ++v) {
+        if (!__any_sync(mask, alive)) break;
         float t;
-        const int k = closest_hit<kCount>(s, o, d, t, status, work);
-        if (k < 0) break;
-        if (ids) ids[v * id_stride] = __float_as_int(__ldg(&s.tris[k].v0_id.w));
-        const float u1 = v < depth ? y[(2 + 2 * v) * ys] : 0.0f;
-        const float u2 = v < depth ? y[(3 + 2 * v) * ys] : 0.0f;
-        if (!shade_vertex(s, k, t, v, depth, u1, u2, o, d, T, F)) break;
+        const int k = closest_hit<kCount>(s, mask, alive, o, d, t, status, work);
+        if (alive) {
+            if (k < 0) {
+                alive = false;
+            } else {
+                if (ids) ids[v * id_stride] = __float_as_int(__ldg(&s.tris[k].v0_id.w));
+                const float u1 = v < depth ? y[(2 + 2 * v) * ys] : 0.0f;
+                const float u2 = v < depth ? y[(3 + 2 * v) * ys] : 0.0f;
+                alive = shade_vertex(s, k, t, v, depth, u1, u2, o, d, T, F);
+            }
+        }
     }
-    return finite_or_zero(F, status);
+    return want ? finite_or_zero(F, status) : F;
 }
 
-__device__ __forceinline__ float3 eval_path(const SceneView& s, int depth, const float* y, uint32_t ys, int32_t* ids,
-                                            uint64_t id_stride, unsigned& status) {
+__device__ __forceinline__ float3 eval_path(const SceneView& s, unsigned mask, bool want, int depth, const float* y,
+                                            uint32_t ys, int32_t* ids, uint64_t id_stride, unsigned& status) {
     Work w;
-    return eval_path_w<false>(s, depth, y, ys, ids, id_stride, status, w);
+    return eval_path_w<false>(s, mask, want, depth, y, ys, ids, id_stride, status, w);
 }
 
 __device__ __forceinline__ void flush_status(unsigned status, unsigned int* word) {

@@ -28,6 +28,7 @@ __global__ void init_kernel(SceneView s, ChainView c) {
     extern __shared__ float sh[];
     const uint32_t B = blockDim.x, tid = threadIdx.x;
     const uint64_t i = blockIdx.x * (uint64_t)B + tid;
+    const unsigned mask = __ballot_sync(0xffffffffu, i < c.n);  // lanes that trace together
     if (i >= c.n) return;
     const int D = (int)c.dim;
     float* y = sh + tid;
@@ -40,7 +41,7 @@ __global__ void init_kernel(SceneView s, ChainView c) {
             if (4 * b + q < D) y[(4 * b + q) * B] = u01(rr[q]);
     }
     unsigned status = 0;
-    const float3 F = eval_path(s, (int)c.depth, y, B, nullptr, 0, status);
+    const float3 F = eval_path(s, mask, true, (int)c.depth, y, B, nullptr, 0, status);
     for (int d = 0; d < D; ++d) c.x[d * c.n + i] = y[d * B];
     c.fpu[0 * c.n + i] = F.x;
     c.fpu[1 * c.n + i] = F.y;
@@ -53,9 +54,10 @@ __global__ void init_kernel(SceneView s, ChainView c) {
 // Re-evaluate F, p, u of the stored states (after jr_set_state).
 __global__ void reeval_kernel(SceneView s, ChainView c) {
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const unsigned mask = __ballot_sync(0xffffffffu, i < c.n);
     if (i >= c.n) return;
     unsigned status = 0;
-    const float3 F = eval_path(s, (int)c.depth, c.x + i, (uint32_t)c.n, nullptr, 0, status);
+    const float3 F = eval_path(s, mask, true, (int)c.depth, c.x + i, (uint32_t)c.n, nullptr, 0, status);
     c.fpu[0 * c.n + i] = F.x;
     c.fpu[1 * c.n + i] = F.y;
     c.fpu[2 * c.n + i] = F.z;
@@ -72,6 +74,7 @@ __global__ void __launch_bounds__(256) step_kernel(SceneView s, ChainView c, uin
     const uint32_t B = blockDim.x, tid = threadIdx.x;
     const uint64_t i = blockIdx.x * (uint64_t)B + tid;
     const bool active = i < c.n;
+    const unsigned mask = __ballot_sync(0xffffffffu, active);  // lanes that trace together
     const int D = (int)c.dim;
     float* buf0 = sh + tid;
     float* buf1 = sh + (size_t)D * B + tid;
@@ -135,7 +138,7 @@ __global__ void __launch_bounds__(256) step_kernel(SceneView s, ChainView c, uin
                     }
                 }
             }
-            const float3 Fy = eval_path_w<kCount>(s, (int)c.depth, cand, B, nullptr, 0, status, work);
+            const float3 Fy = eval_path_w<kCount>(s, mask, true, (int)c.depth, cand, B, nullptr, 0, status, work);
             const float py_ = lum(Fy);
             bool accept;
             if (local) {
@@ -225,9 +228,10 @@ __global__ void resolve_kernel(const double4_32a* acc, const unsigned long long*
 __global__ void eval_states_kernel(SceneView s, uint32_t depth, float c_tilde, const float* x, uint64_t n, float* F,
                                    float* p, float* u, float* k, int32_t* ids, unsigned int* status_word) {
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const unsigned mask = __ballot_sync(0xffffffffu, i < n);
     if (i >= n) return;
     unsigned status = 0;
-    const float3 f = eval_path(s, (int)depth, x + i, (uint32_t)n, ids ? ids + i : nullptr, n, status);
+    const float3 f = eval_path(s, mask, true, (int)depth, x + i, (uint32_t)n, ids ? ids + i : nullptr, n, status);
     const float pp = lum(f);
     const float uu = 1.0f;
     if (F) {
@@ -246,6 +250,7 @@ __global__ void render_pt_kernel(SceneView s, uint32_t W, uint32_t H, uint32_t d
     extern __shared__ float sh[];
     const uint32_t B = blockDim.x, tid = threadIdx.x;
     const uint64_t i = blockIdx.x * (uint64_t)B + tid;
+    const unsigned mask = __ballot_sync(0xffffffffu, i < n);
     if (i >= n) return;
     const int D = 2 + 2 * (int)depth;
     float* y = sh + tid;
@@ -258,7 +263,7 @@ __global__ void render_pt_kernel(SceneView s, uint32_t W, uint32_t H, uint32_t d
             if (4 * b + q < D) y[(4 * b + q) * B] = u01(rr[q]);
     }
     unsigned status = 0;
-    const float3 F = eval_path(s, (int)depth, y, B, nullptr, 0, status);
+    const float3 F = eval_path(s, mask, true, (int)depth, y, B, nullptr, 0, status);
     uint32_t px = min((uint32_t)((double)y[0] * (double)W), W - 1);
     uint32_t py = min((uint32_t)((double)y[B] * (double)H), H - 1);
     const double WH = (double)W * (double)H;

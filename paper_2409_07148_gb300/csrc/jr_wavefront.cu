@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(128) wf_step_kernel(SceneView s, ChainView c, 
                                                       int begin) {
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     const bool valid = i < c.n;
+    const unsigned mask = __ballot_sync(kFull, valid);  // lanes that trace the camera rays together
     const int D = (int)c.dim;
     const uint64_t n = c.n;
     const WaveView& w = c.wf;
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(128) wf_step_kernel(SceneView s, ChainView c, 
             camera_ray(s, y0, y1, o, d);
             float t;
             Work wk;
-            const int k = closest_hit<false>(s, o, d, t, status, wk);
+            const int k = closest_hit<false>(s, mask, true, o, d, t, status, wk);
             if (k >= 0) live = shade_vertex(s, k, t, 0, (int)c.depth, y2, y3, o, d, T, F);
             if (live)
                 store_path(w.path, i, o, d, T, F);
@@ -209,21 +210,24 @@ __global__ void __launch_bounds__(128) wf_bounce_kernel(SceneView s, ChainView c
         j0 = __shfl_sync(kFull, j0, 0);
         if (j0 >= count) break;
         const unsigned j = j0 + lane;
+        const bool has = j < count;
         bool live = false;
         uint32_t i = 0;
-        if (j < count) {
+        float3 o = f3(0.f, 0.f, 0.f), d = f3(0.f, 0.f, 1.f), T = f3(0.f, 0.f, 0.f), F = f3(0.f, 0.f, 0.f);
+        float u1 = 0.f, u2 = 0.f;
+        if (has) {
             i = qin[j];
-            float3 o, d, T, F;
             load_path(w.path, i, o, d, T, F);
-            float u1 = 0.f, u2 = 0.f;
             if (v < (int)c.depth) {
                 const float* cand = w.par[i] ? c.x : w.y;
                 u1 = cand[(uint64_t)(2 + 2 * v) * n + i];
                 u2 = cand[(uint64_t)(3 + 2 * v) * n + i];
             }
-            float t;
-            Work wk;
-            const int k = closest_hit<false>(s, o, d, t, status, wk);
+        }
+        float t;
+        Work wk;
+        const int k = closest_hit<false>(s, kFull, has, o, d, t, status, wk);
+        if (has) {
             if (k >= 0) live = shade_vertex(s, k, t, v, (int)c.depth, u1, u2, o, d, T, F);
             if (live)
                 store_path(w.path, i, o, d, T, F);

@@ -99,11 +99,12 @@ def test_cornell_paired_streams_match_oracle(J):
 
 
 def test_cornell_per_pixel_vs_oracle(J):
-    """Independent seeds: 64 GPU batches (each the 256-chain x 10^4-step
-    Cornell workload) vs 32 oracle batches."""
+    """Independent seeds: 64 GPU batches vs 32 oracle batches, each batch the
+    256-chain x 10^4-step Cornell workload (equal batch shapes keep the
+    batch-mean distributions alike on both sides)."""
     sc = scenes.cornell()
     g = _gpu_batches(J, sc, 64, 256, 10_000, seed=0)
-    o = _oracle_batches(sc, 32, 256, 2500, seed=1, first_chain=1 << 20)
+    o = _oracle_batches(sc, 32, 256, 10_000, seed=1, first_chain=1 << 20)
     z = welch_z(g, o)
     assert np.mean(np.abs(z) > 4) <= 1e-3, np.sort(np.abs(z))[-10:]
     assert 0.75 < np.mean(z ** 2) < 1.35, np.mean(z ** 2)
