@@ -177,6 +177,33 @@ jr_status jr_set_block_size(jr_chains* chains, uint32_t block);
 #define JR_EXEC_WAVEFRONT 2u
 jr_status jr_set_execution(jr_chains* chains, uint32_t mode);
 
+/* jr_advance without any device allocation -- the paper has no counterpart;
+ * this is a service of the library for callers that cannot allocate device
+ * memory when they advance: code that runs inside a host framework that owns
+ * all device memory (plugin interfaces whose execute step must not allocate),
+ * or a loop that cannot afford cudaMalloc/cudaFree, which take the allocator's
+ * locks and (cudaFree) synchronise the whole device.
+ *
+ * It runs the wavefront launches of jr_advance (JR_EXEC_WAVEFRONT), with the
+ * same results, but their scratch (second state buffer, live-path records and
+ * queues) lives in one fixed device array inside the library, sized for at
+ * most JR_STATIC_MAX_CHAINS chains of any depth: 12,386,560 bytes, which
+ * every GPU that loads the library holds until the process exits.  The chain
+ * set (state, framebuffer, accumulator, counters) is the caller's, created
+ * beforehand with jr_chains_create.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *
+ * The first call on a device looks up the array's device address for that
+ * device (once per device, with the device current), so make the first call
+ * on each device before any stream capture.  Every call shares the one array
+ * and it keeps the last call's contents: the call clears what must start at
+ * zero, but calls whose work overlaps on the GPU (other streams, other
+ * threads, other chain sets) race on it -- order them on one stream.
+ * Errors: JR_ERR_INVALID_ARG for a null handle or more than
+ * JR_STATIC_MAX_CHAINS chains (nothing is launched); JR_ERR_CUDA. */
+#define JR_STATIC_MAX_CHAINS 65536u
+jr_status jr_advance_static(jr_chains* chains, uint32_t n_steps, void* stream);
+
 /* Resolve the estimate (Section 6.3): rgb_out[H][W][3] = accumulator / J
  * (zeros while J = 0).  out_is_device = 1: rgb_out is device memory and the
  * call is asynchronous; 0: host memory, the call synchronises `stream`. */

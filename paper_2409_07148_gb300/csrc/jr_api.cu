@@ -267,6 +267,21 @@ jr_status jr_advance_traced(jr_chains* chains, uint32_t n_steps, uint8_t* flags_
     return advance_impl(chains, n_steps, flags_dev, dt_dev, pix_dev, nullptr, stream, "jr_advance_traced");
 }
 
+jr_status jr_advance_static(jr_chains* chains, uint32_t n_steps, void* stream) {
+    if (!chains) return fail(JR_ERR_INVALID_ARG, "jr_advance_static: null chains");
+    if (chains->view.n > kStaticMaxChains)
+        return fail(JR_ERR_INVALID_ARG, "jr_advance_static: " + std::to_string(chains->view.n) +
+                                            " chains exceed the fixed scratch of " +
+                                            std::to_string(kStaticMaxChains) + " chains; use jr_advance");
+    if (n_steps == 0) return JR_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    JR_CUDA(launch_wavefront_static(chains->scene->view, chains->view, chains->steps, n_steps, st),
+            "jr_advance_static");
+    JR_CUDA(launch_fold(chains->view, st), "jr_advance_static");
+    chains->steps += n_steps;
+    return JR_OK;
+}
+
 jr_status jr_set_execution(jr_chains* chains, uint32_t mode) {
     if (!chains) return fail(JR_ERR_INVALID_ARG, "jr_set_execution: null chains");
     if (mode > JR_EXEC_WAVEFRONT) return fail(JR_ERR_INVALID_ARG, "jr_set_execution: unknown mode");

@@ -104,6 +104,15 @@ cudaError_t launch_fold(const ChainView& c, cudaStream_t st);
 // jr_wavefront.cu
 cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
                              cudaStream_t st);
+// The same wavefront launches with their buffers in a fixed file-scope device
+// array (no allocation); c.wf is ignored.  c.n <= kStaticMaxChains.
+constexpr uint64_t kStaticMaxChains = 1u << 16;
+constexpr size_t kStaticScratchBytes =
+    sizeof(float) * kMaxDim * kStaticMaxChains + sizeof(float4) * 3 * kStaticMaxChains +
+    sizeof(float) * kStaticMaxChains + sizeof(uint32_t) * 2 * kStaticMaxChains + sizeof(uint8_t) * kStaticMaxChains +
+    256;  // = 12 386 560 bytes (every piece is a multiple of 256 bytes except the queue counters)
+cudaError_t launch_wavefront_static(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
+                                    cudaStream_t st);
 cudaError_t launch_resolve(const ChainView& c, float* rgb, cudaStream_t st);
 cudaError_t launch_reeval(const SceneView& s, const ChainView& c, cudaStream_t st);
 cudaError_t launch_eval_states(const SceneView& s, uint32_t depth, float c_tilde, const float* x, uint64_t n,

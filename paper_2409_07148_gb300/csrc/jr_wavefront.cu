@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/jr.h"
 #include "jr_device.cuh"
 #include "jr_internal.h"
@@ -266,6 +268,69 @@ cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t st
     }
     wf_step_kernel<<<G, 128, 0, st>>>(s, c, step_begin + n_steps, n_steps > 0, 0);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-size scratch for jr_advance_static: the wavefront buffers of up to
+// kStaticMaxChains chains live in one file-scope device array instead of
+// memory allocated per chain set.  Every GPU that loads the library holds it
+// until the process exits.  Layout (256-byte aligned pieces): y [kMaxDim][n],
+// path [n][3] float4, ua [n], queue [2][n], par [n], qcount [2 (kMaxDepth+2)].
+namespace {
+constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t kOffY = 0;
+constexpr size_t kOffPath = kOffY + align256(sizeof(float) * kMaxDim * kStaticMaxChains);
+constexpr size_t kOffUa = kOffPath + align256(sizeof(float4) * 3 * kStaticMaxChains);
+constexpr size_t kOffQueue = kOffUa + align256(sizeof(float) * kStaticMaxChains);
+constexpr size_t kOffPar = kOffQueue + align256(sizeof(uint32_t) * 2 * kStaticMaxChains);
+constexpr size_t kOffCount = kOffPar + align256(sizeof(uint8_t) * kStaticMaxChains);
+constexpr size_t kStaticBytes = kOffCount + align256(sizeof(unsigned int) * 2 * (kMaxDepth + 2));
+static_assert(kStaticBytes == kStaticScratchBytes, "static scratch layout and its declared size disagree");
+
+__device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_base[kMaxDevices] = {};
+
+// Device address of the array on the current device, looked up once per
+// device (host code only sees a host-side stand-in for the symbol).
+cudaError_t static_scratch_base(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_base[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_base[dev] = p;
+    }
+    *out = g_static_base[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t launch_wavefront_static(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
+                                    cudaStream_t st) {
+    if (c.n > kStaticMaxChains || c.dim > (uint32_t)kMaxDim) return cudaErrorInvalidValue;
+    void* base = nullptr;
+    cudaError_t e = static_scratch_base(&base);
+    if (e != cudaSuccess) return e;
+    unsigned char* b = static_cast<unsigned char*>(base);
+    ChainView v = c;
+    v.wf.y = reinterpret_cast<float*>(b + kOffY);
+    v.wf.path = reinterpret_cast<float4*>(b + kOffPath);
+    v.wf.ua = reinterpret_cast<float*>(b + kOffUa);
+    v.wf.queue = reinterpret_cast<uint32_t*>(b + kOffQueue);
+    v.wf.par = b + kOffPar;
+    v.wf.qcount = reinterpret_cast<unsigned int*>(b + kOffCount);
+    // The array keeps the previous call's bytes: the parity must start at 0
+    // (every state in x); the queue counters are cleared per step inside
+    // launch_wavefront; y, ua and the path records are written before use.
+    if ((e = cudaMemsetAsync(v.wf.par, 0, c.n, st)) != cudaSuccess) return e;
+    return launch_wavefront(s, v, step_begin, n_steps, st);
 }
 
 }  // namespace jr

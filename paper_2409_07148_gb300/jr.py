@@ -22,6 +22,7 @@ JR_EXEC_AUTO, JR_EXEC_MEGAKERNEL, JR_EXEC_WAVEFRONT = 0, 1, 2
 JR_STATUS_NONFINITE, JR_STATUS_TRAVERSAL, JR_STATUS_STACK = 1, 2, 4
 MATERIAL_FLOATS = 12
 MAX_DEPTH = 15
+STATIC_MAX_CHAINS = 65536
 
 
 class JRError(RuntimeError):
@@ -71,6 +72,7 @@ _SIGS = {
     "jr_advance_counted": [_P, _U32, _P, _P],
     "jr_set_block_size": [_P, _U32],
     "jr_set_execution": [_P, _U32],
+    "jr_advance_static": [_P, _U32, _P],
     "jr_resolve": [_P, _P, _I, _P],
     "jr_get_accumulator": [_P, _P, _I, _P],
     "jr_get_stats": [_P, ctypes.POINTER(Stats), _P],
@@ -177,6 +179,11 @@ class Chains:
 
     def advance_traced(self, n_steps, flags=None, dt=None, pix=None, stream=None):
         _check(lib().jr_advance_traced(self.h, int(n_steps), _dptr(flags), _dptr(dt), _dptr(pix), _stream(stream)))
+
+    def advance_static(self, n_steps, stream=None):
+        """jr_advance_static: the wavefront advance with no device allocation
+        (fixed in-library scratch, at most STATIC_MAX_CHAINS chains)."""
+        _check(lib().jr_advance_static(self.h, int(n_steps), _stream(stream)))
 
     def advance_counted(self, n_steps, stream=None):
         """Advance and return {rays, nodes, tris} counted by the instrumented kernel."""
