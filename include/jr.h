@@ -168,7 +168,7 @@ jr_status jr_set_block_size(jr_chains* chains, uint32_t block);
  *   JR_EXEC_MEGAKERNEL  one thread per chain for the whole launch;
  *   JR_EXEC_WAVEFRONT   one launch per step plus one per bounce, over a queue
  *                       of live paths (better SIMD use for many chains; its
- *                       buffers, about (4 D + 58) bytes per chain, are
+ *                       buffers, about (4 D + 66) bytes per chain, are
  *                       allocated by the first wavefront advance);
  *   JR_EXEC_AUTO        wavefront from 2^16 chains up, else the megakernel.
  * Both modes run the same per-chain arithmetic on the same Philox streams. */
@@ -187,7 +187,7 @@ jr_status jr_set_execution(jr_chains* chains, uint32_t mode);
  * It runs the wavefront launches of jr_advance (JR_EXEC_WAVEFRONT), with the
  * same results, but their scratch (second state buffer, live-path records and
  * queues) lives in one fixed device array inside the library, sized for at
- * most JR_STATIC_MAX_CHAINS chains of any depth: 12,386,560 bytes, which
+ * most JR_STATIC_MAX_CHAINS chains of any depth: 12,910,848 bytes, which
  * every GPU that loads the library holds until the process exits.  The chain
  * set (state, framebuffer, accumulator, counters) is the caller's, created
  * beforehand with jr_chains_create.  It calls no cudaMalloc, cudaFree or other

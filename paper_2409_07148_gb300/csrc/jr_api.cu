@@ -69,6 +69,7 @@ struct jr_chains {
         cudaFree(view.wf.par);
         cudaFree(view.wf.ua);
         cudaFree(view.wf.path);
+        cudaFree(view.wf.hit);
         cudaFree(view.wf.queue);
         cudaFree(view.wf.qcount);
         cudaFree(view.x);
@@ -223,6 +224,7 @@ static jr_status ensure_wavefront(jr_chains* c, cudaStream_t st) {
     cudaError_t e;
     if ((e = dev_alloc(&w.y, (size_t)c->view.dim * n)) != cudaSuccess || (e = dev_alloc(&w.par, n)) != cudaSuccess ||
         (e = dev_alloc(&w.ua, n)) != cudaSuccess || (e = dev_alloc(&w.path, 3 * n)) != cudaSuccess ||
+        (e = dev_alloc(&w.hit, n)) != cudaSuccess ||
         (e = dev_alloc(&w.queue, 2 * n)) != cudaSuccess ||
         (e = dev_alloc(&w.qcount, 2 * (kMaxDepth + 2))) != cudaSuccess ||
         (e = cudaMemsetAsync(w.par, 0, n, st)) != cudaSuccess) {
@@ -230,6 +232,7 @@ static jr_status ensure_wavefront(jr_chains* c, cudaStream_t st) {
         cudaFree(w.par);
         cudaFree(w.ua);
         cudaFree(w.path);
+        cudaFree(w.hit);
         cudaFree(w.queue);
         cudaFree(w.qcount);
         w = WaveView{};

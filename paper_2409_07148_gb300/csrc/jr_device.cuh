@@ -71,116 +71,152 @@ struct Work {
     uint32_t rays = 0, nodes = 0, tris = 0;
 };
 
-// Closest hit, ties on equal t to the smaller original triangle index.
-// Returns the leaf-order record index or -1; t_out gets the hit distance.
-//
-// Warp-synchronous while-while traversal (Aila & Laine, HPG 2009): every lane
-// in `mask` must call this together (lanes without a ray pass want = false).
-// Each inner-node round and each leaf round ends in a __any_sync over `mask`,
-// so the lanes reconverge every iteration instead of drifting apart under
-// independent thread scheduling; lanes that reach a leaf wait for the others
-// before the leaves are tested together.
-template <bool kCount>
-__device__ __forceinline__ int closest_hit(const SceneView& s, unsigned mask, bool want, float3 o, float3 d,
-                                           float& t_out, unsigned& status, Work& work) {
-    t_out = INFINITY;
-    bool active = want && s.root != kSentinel;
-    if constexpr (kCount) work.rays += want ? 1u : 0u;
+// Three-input float min/max (PTX min/max with three sources, sm_100+): one
+// instruction where two-input chains take two.
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// A ray prepared for slab tests, plus the resumable state of its traversal.
+// The stack lives with the caller (per-thread local memory).
+struct Trav {
+    float3 o, d;
+    float ix, iy, iz, ox, oy, oz;
+    float tb;          // closest hit so far
+    int best, best_id;  // its leaf-order record and original triangle index
+    int ref, sp;        // node/leaf ref being visited, stack depth
+    uint32_t visits;
+};
+
+__device__ __forceinline__ void trav_begin(const SceneView& s, Trav& r, float3 o, float3 d) {
+    r.o = o;
+    r.d = d;
     const float dx = fabsf(d.x) < 1e-20f ? copysignf(1e-20f, d.x) : d.x;
     const float dy = fabsf(d.y) < 1e-20f ? copysignf(1e-20f, d.y) : d.y;
     const float dz = fabsf(d.z) < 1e-20f ? copysignf(1e-20f, d.z) : d.z;
-    const float ix = 1.0f / dx, iy = 1.0f / dy, iz = 1.0f / dz;
-    const float ox = o.x * ix, oy = o.y * iy, oz = o.z * iz;
-    float tb = INFINITY;
-    int best = -1, best_id = INT32_MAX;
-    int stack[kStackSize];
-    int sp = 0;
-    int ref = s.root;
-    uint32_t visits = 0;
-    while (__any_sync(mask, active)) {
-        // inner nodes until every active lane holds a leaf (or is done)
-        while (__any_sync(mask, active && ref >= 0)) {
-            if (active && ref >= 0) {
-                if (++visits > kNodeVisitBudget) {
-                    status |= JR_STATUS_TRAVERSAL;
-                    active = false;
-                    best = -1;
-                    tb = INFINITY;
-                    continue;
-                }
-                if constexpr (kCount) work.nodes++;
-                const BvhNode* n = s.nodes + ref;
-                const float4 a = __ldg(&n->a), b = __ldg(&n->b), c = __ldg(&n->c);
-                const int4 rf = __ldg(&n->refs);
-                const float l0x = fmaf(a.x, ix, -ox), h0x = fmaf(a.y, ix, -ox);
-                const float l0y = fmaf(a.z, iy, -oy), h0y = fmaf(a.w, iy, -oy);
-                const float l0z = fmaf(c.x, iz, -oz), h0z = fmaf(c.y, iz, -oz);
-                const float l1x = fmaf(b.x, ix, -ox), h1x = fmaf(b.y, ix, -ox);
-                const float l1y = fmaf(b.z, iy, -oy), h1y = fmaf(b.w, iy, -oy);
-                const float l1z = fmaf(c.z, iz, -oz), h1z = fmaf(c.w, iz, -oz);
-                const float tn0 = fmaxf(fmaxf(fminf(l0x, h0x), fminf(l0y, h0y)), fmaxf(fminf(l0z, h0z), 0.0f));
-                const float tf0 = fminf(fminf(fmaxf(l0x, h0x), fmaxf(l0y, h0y)), fminf(fmaxf(l0z, h0z), tb));
-                const float tn1 = fmaxf(fmaxf(fminf(l1x, h1x), fminf(l1y, h1y)), fmaxf(fminf(l1z, h1z), 0.0f));
-                const float tf1 = fminf(fminf(fmaxf(l1x, h1x), fmaxf(l1y, h1y)), fminf(fmaxf(l1z, h1z), tb));
-                const bool h0 = tn0 <= tf0 * 1.00000024f;
-                const bool h1 = tn1 <= tf1 * 1.00000024f;
-                if (h0 && h1) {
-                    const bool first0 = tn0 <= tn1;
-                    if (sp >= kStackSize) {
-                        status |= JR_STATUS_STACK;
-                        active = false;
-                        best = -1;
-                        tb = INFINITY;
-                        continue;
-                    }
-                    stack[sp++] = first0 ? rf.y : rf.x;
-                    ref = first0 ? rf.x : rf.y;
-                } else if (h0) {
-                    ref = rf.x;
-                } else if (h1) {
-                    ref = rf.y;
-                } else {
-                    ref = sp > 0 ? stack[--sp] : kSentinel;
-                }
-            }
+    r.ix = 1.0f / dx;
+    r.iy = 1.0f / dy;
+    r.iz = 1.0f / dz;
+    r.ox = o.x * r.ix;
+    r.oy = o.y * r.iy;
+    r.oz = o.z * r.iz;
+    r.tb = INFINITY;
+    r.best = -1;
+    r.best_id = INT32_MAX;
+    r.ref = s.root;
+    r.sp = 0;
+    r.visits = 0;
+}
+
+// Visit inner node r.ref: slab-test both children against [0, tb], descend to
+// the nearer hit child and push the farther, or pop.  Returns false (and sets
+// a status bit) if the visit budget or the stack ran out: the ray then counts
+// as a miss.
+template <bool kCount>
+__device__ __forceinline__ bool trav_node(const SceneView& s, Trav& r, int* stack, unsigned& status, Work& work) {
+    if (++r.visits > kNodeVisitBudget) {
+        status |= JR_STATUS_TRAVERSAL;
+        return false;
+    }
+    if constexpr (kCount) work.nodes++;
+    const BvhNode* n = s.nodes + r.ref;
+    const float4 a = __ldg(&n->a), b = __ldg(&n->b), c = __ldg(&n->c);
+    const int4 rf = __ldg(&n->refs);
+    const float l0x = fmaf(a.x, r.ix, -r.ox), h0x = fmaf(a.y, r.ix, -r.ox);
+    const float l0y = fmaf(a.z, r.iy, -r.oy), h0y = fmaf(a.w, r.iy, -r.oy);
+    const float l0z = fmaf(c.x, r.iz, -r.oz), h0z = fmaf(c.y, r.iz, -r.oz);
+    const float l1x = fmaf(b.x, r.ix, -r.ox), h1x = fmaf(b.y, r.ix, -r.ox);
+    const float l1y = fmaf(b.z, r.iy, -r.oy), h1y = fmaf(b.w, r.iy, -r.oy);
+    const float l1z = fmaf(c.z, r.iz, -r.oz), h1z = fmaf(c.w, r.iz, -r.oz);
+    const float tn0 = fmax3(fminf(l0x, h0x), fminf(l0y, h0y), fmaxf(fminf(l0z, h0z), 0.0f));
+    const float tf0 = fmin3(fmaxf(l0x, h0x), fmaxf(l0y, h0y), fminf(fmaxf(l0z, h0z), r.tb));
+    const float tn1 = fmax3(fminf(l1x, h1x), fminf(l1y, h1y), fmaxf(fminf(l1z, h1z), 0.0f));
+    const float tf1 = fmin3(fmaxf(l1x, h1x), fmaxf(l1y, h1y), fminf(fmaxf(l1z, h1z), r.tb));
+    const bool h0 = tn0 <= tf0 * 1.00000024f;
+    const bool h1 = tn1 <= tf1 * 1.00000024f;
+    if (h0 && h1) {
+        if (r.sp >= kStackSize) {
+            status |= JR_STATUS_STACK;
+            return false;
         }
-        if (active) {
-            if (ref == kSentinel) {
-                active = false;
-            } else {
-                const int enc = ~ref;
-                const int first = enc >> 3, cnt = (enc & 7) + 1;
-                if constexpr (kCount) work.tris += (uint32_t)cnt;
-                for (int k = first; k < first + cnt; ++k) {
-                    const TriRecord* tr = s.tris + k;
-                    const float4 q0 = __ldg(&tr->v0_id), q1 = __ldg(&tr->e1_mat), q2 = __ldg(&tr->e2);
-                    // Moller-Trumbore (JGT 1997)
-                    const float3 e1 = f3(q1.x, q1.y, q1.z), e2 = f3(q2.x, q2.y, q2.z);
-                    const float3 pv = cross(d, e2);
-                    const float det = dot(e1, pv);
-                    if (det == 0.0f) continue;
-                    const float inv = 1.0f / det;
-                    const float3 tv = o - f3(q0.x, q0.y, q0.z);
-                    const float u = dot(tv, pv) * inv;
-                    if (u < 0.0f || u > 1.0f) continue;
-                    const float3 qv = cross(tv, e1);
-                    const float v = dot(d, qv) * inv;
-                    if (v < 0.0f || u + v > 1.0f) continue;
-                    const float t = dot(e2, qv) * inv;
-                    const int id = __float_as_int(q0.w);
-                    if (t > 0.0f && (t < tb || (t == tb && id < best_id))) {
-                        tb = t;
-                        best = k;
-                        best_id = id;
-                    }
-                }
-                ref = sp > 0 ? stack[--sp] : kSentinel;
-                if (ref == kSentinel) active = false;
-            }
+        const bool first0 = tn0 <= tn1;
+        stack[r.sp++] = first0 ? rf.y : rf.x;
+        r.ref = first0 ? rf.x : rf.y;
+    } else if (h0) {
+        r.ref = rf.x;
+    } else if (h1) {
+        r.ref = rf.y;
+    } else {
+        r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
+    }
+    return true;
+}
+
+// Test the triangles of leaf r.ref (Moller-Trumbore, JGT 1997; ties on equal t
+// to the smaller original index), then pop.  Returns false when the ray is done.
+template <bool kCount>
+__device__ __forceinline__ bool trav_leaf(const SceneView& s, Trav& r, const int* stack, Work& work) {
+    const int enc = ~r.ref;
+    const int first = enc >> 3, cnt = (enc & 7) + 1;
+    if constexpr (kCount) work.tris += (uint32_t)cnt;
+    for (int k = first; k < first + cnt; ++k) {
+        const TriRecord* tr = s.tris + k;
+        const float4 q0 = __ldg(&tr->v0_id), q1 = __ldg(&tr->e1_mat), q2 = __ldg(&tr->e2);
+        const float3 e1 = f3(q1.x, q1.y, q1.z), e2 = f3(q2.x, q2.y, q2.z);
+        const float3 pv = cross(r.d, e2);
+        const float det = dot(e1, pv);
+        if (det == 0.0f) continue;
+        const float inv = 1.0f / det;
+        const float3 tv = r.o - f3(q0.x, q0.y, q0.z);
+        const float u = dot(tv, pv) * inv;
+        if (u < 0.0f || u > 1.0f) continue;
+        const float3 qv = cross(tv, e1);
+        const float v = dot(r.d, qv) * inv;
+        if (v < 0.0f || u + v > 1.0f) continue;
+        const float t = dot(e2, qv) * inv;
+        const int id = __float_as_int(q0.w);
+        if (t > 0.0f && (t < r.tb || (t == r.tb && id < r.best_id))) {
+            r.tb = t;
+            r.best = k;
+            r.best_id = id;
         }
     }
-    t_out = best >= 0 ? tb : INFINITY;
-    return best;
+    r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
+    return r.ref != kSentinel;
+}
+
+// Closest hit for the lanes in `mask`, which must all call together (lanes
+// without a ray pass want = false).  Warp-synchronous while-while traversal
+// (Aila & Laine, HPG 2009): each inner-node round and each leaf round ends in
+// a __any_sync over `mask`, so the lanes reconverge every iteration instead of
+// drifting apart under independent thread scheduling.  Returns the leaf-order
+// record index or -1; t_out gets the hit distance.
+template <bool kCount>
+__device__ __forceinline__ int closest_hit(const SceneView& s, unsigned mask, bool want, float3 o, float3 d,
+                                           float& t_out, unsigned& status, Work& work) {
+    Trav r;
+    trav_begin(s, r, o, d);
+    bool active = want && s.root != kSentinel;
+    if constexpr (kCount) work.rays += want ? 1u : 0u;
+    int stack[kStackSize];
+    while (__any_sync(mask, active)) {
+        while (__any_sync(mask, active && r.ref >= 0)) {
+            if (active && r.ref >= 0 && !trav_node<kCount>(s, r, stack, status, work)) {
+                active = false;
+                r.best = -1;
+            }
+        }
+        if (active) active = r.ref != kSentinel && trav_leaf<kCount>(s, r, stack, work);
+    }
+    t_out = r.best >= 0 ? r.tb : INFINITY;
+    return r.best;
 }
 
 // ------------------------------------------------------------------ BSDFs

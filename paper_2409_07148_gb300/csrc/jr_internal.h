@@ -63,6 +63,7 @@ struct WaveView {
     uint8_t* par = nullptr;       // [n] 1: the current state is in y, 0: in x
     float* ua = nullptr;          // [n] Ua of a local step, -1 for a regeneration step
     float4* path = nullptr;       // [n][3] live path record (o, d, T, F)
+    float2* hit = nullptr;        // [n] closest hit of the path's current ray (t, record index bits)
     uint32_t* queue = nullptr;    // [2][n] live-path queues (ping-pong)
     unsigned int* qcount = nullptr;  // [2 (kMaxDepth + 2)] queue lengths, then fetch cursors
 };
@@ -109,8 +110,8 @@ cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t st
 constexpr uint64_t kStaticMaxChains = 1u << 16;
 constexpr size_t kStaticScratchBytes =
     sizeof(float) * kMaxDim * kStaticMaxChains + sizeof(float4) * 3 * kStaticMaxChains +
-    sizeof(float) * kStaticMaxChains + sizeof(uint32_t) * 2 * kStaticMaxChains + sizeof(uint8_t) * kStaticMaxChains +
-    256;  // = 12 386 560 bytes (every piece is a multiple of 256 bytes except the queue counters)
+    sizeof(float2) * kStaticMaxChains + sizeof(float) * kStaticMaxChains + sizeof(uint32_t) * 2 * kStaticMaxChains +
+    sizeof(uint8_t) * kStaticMaxChains + 256;  // = 12 910 848 bytes (every piece but the counters is a multiple of 256)
 cudaError_t launch_wavefront_static(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
                                     cudaStream_t st);
 cudaError_t launch_resolve(const ChainView& c, float* rgb, cudaStream_t st);

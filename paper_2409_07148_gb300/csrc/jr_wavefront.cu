@@ -6,12 +6,15 @@
 //
 //   step kernel (all chains, converged): finish the previous step (MH
 //     acceptance or regeneration), draw the new step's clocks t1 ~ Exp(1),
-//     t2 ~ Exp(k), k = c~ u / p (Section 6.2), splat (dt, x) (Section 6.3/7.4),
-//     build the candidate y (Gaussian small step or a draw from mu), trace the
-//     camera ray and shade vertex 1; live paths go to a queue.
-//   bounce kernel v = 1..depth (persistent, warps fetch 32 queue entries at a
-//     time): trace one ray per live path, shade it, append survivors to the
-//     next queue with one warp-aggregated atomic.
+//     t2 ~ Exp(k), k = c~ u / p (Section 6.2), splat (dt, x) (Sections 6.3/7.4),
+//     build the candidate y (Gaussian small step or a draw from mu) and its
+//     camera ray; every chain joins the ray queue.
+//   trace kernel, per bounce (persistent warps): closest hit of every queued
+//     ray.  Lanes whose ray is done refill from the queue between warp-
+//     synchronous traversal rounds (dynamic ray fetch, Aila & Laine 2009), so
+//     a warp does not idle for its longest ray.
+//   shade kernel, per bounce (converged): emission, BSDF sample, next ray;
+//     survivors join the next queue with one warp-aggregated atomic.
 //
 // Per-chain arithmetic is the megakernel's, through the same device functions,
 // so both modes give the same chains for the same Philox streams.  The state
@@ -30,6 +33,7 @@ namespace jr {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRefill = 8;  // refill a warp once this many lanes are idle
 
 // Path record of a live path: (o.xyz, d.x) (d.yz, T.xy) (T.z, F.xyz).
 __device__ __forceinline__ void store_path(float4* path, uint64_t i, float3 o, float3 d, float3 T, float3 F) {
@@ -75,17 +79,15 @@ __device__ __forceinline__ void count_and_flush(uint32_t nJ, uint32_t nL, uint32
 
 // finish = 1: complete step `step - 1` of every chain.  begin = 1: start step
 // `step`.  With begin = 0 the launch also moves every state back into x.
-__global__ void __launch_bounds__(128) wf_step_kernel(SceneView s, ChainView c, uint64_t step, int finish,
-                                                      int begin) {
+__global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step, int finish, int begin,
+                                                      SceneView s) {
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     const bool valid = i < c.n;
-    const unsigned mask = __ballot_sync(kFull, valid);  // lanes that trace the camera rays together
     const int D = (int)c.dim;
     const uint64_t n = c.n;
     const WaveView& w = c.wf;
     uint32_t nJ = 0, nL = 0, nA = 0;
     unsigned status = 0;
-    bool live = false;
     if (valid) {
         uint8_t par = w.par[i];
         float Fr = c.fpu[0 * n + i], Fg = c.fpu[1 * n + i], Fb = c.fpu[2 * n + i];
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(128) wf_step_kernel(SceneView s, ChainView c, 
             const float E2 = -logf(1.0f - u01(r0.y));
             const float Ua = u01(r0.z);
             const float t2 = p > 0.0f ? E2 * p / (c.c_tilde * u) : 0.0f;
-            const bool local = E1 < t2;
+            const bool local = E1 < t2;  // a tie goes to the killing branch
             float dt = local ? E1 : t2;
             if (c.flags & JR_FLAG_RAO_BLACKWELL) dt = p > 0.0f ? p / (p + c.c_tilde * u) : 0.0f;
             const float x0 = cur[i], x1 = cur[n + i];
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(128) wf_step_kernel(SceneView s, ChainView c, 
                 atomicAdd(c.fb + py * c.width + px, make_float4(wgt * Fr, wgt * Fg, wgt * Fb, dt));
             }
             w.ua[i] = local ? Ua : -1.0f;
-            float y0 = 0.f, y1 = 0.f, y2 = 0.f, y3 = 0.f;
+            float y0 = 0.f, y1 = 0.f;
             for (int b = 0; 4 * b < D; ++b) {
                 const uint4 r = draw(c.seed, kTagStep, (uint32_t)(b + 1), chain, step);
                 const uint64_t o0 = (uint64_t)(4 * b) * n + i;
@@ -171,75 +173,115 @@ __global__ void __launch_bounds__(128) wf_step_kernel(SceneView s, ChainView c, 
                 if (b == 0) {
                     y0 = v0;
                     y1 = v1;
-                    y2 = v2;
-                    y3 = v3;
                 }
             }
-            // vertex 1: camera ray
-            float3 o, d, T = f3(1.f, 1.f, 1.f), F = f3(0.f, 0.f, 0.f);
+            float3 o, d;
             camera_ray(s, y0, y1, o, d);
-            float t;
-            Work wk;
-            const int k = closest_hit<false>(s, mask, true, o, d, t, status, wk);
-            if (k >= 0) live = shade_vertex(s, k, t, 0, (int)c.depth, y2, y3, o, d, T, F);
-            if (live)
-                store_path(w.path, i, o, d, T, F);
-            else
-                w.path[3 * i + 2] = make_float4(0.f, F.x, F.y, F.z);
+            store_path(w.path, i, o, d, f3(1.f, 1.f, 1.f), f3(0.f, 0.f, 0.f));
         } else if (par) {
             for (int dd = 0; dd < D; ++dd) c.x[(uint64_t)dd * n + i] = w.y[(uint64_t)dd * n + i];
             par = 0;
         }
         w.par[i] = par;
     }
-    if (begin) enqueue(live, (uint32_t)i, w.queue, w.qcount + 1);
+    if (begin) enqueue(valid, (uint32_t)i, w.queue, w.qcount + 0);
     count_and_flush(nJ, nL, nA, status, c);
 }
 
-// Bounce v (>= 1): one ray per live path from queue_in; survivors to queue_out.
-__global__ void __launch_bounds__(128) wf_bounce_kernel(SceneView s, ChainView c, int v) {
+// Closest hit of every queued ray of bounce v -> w.hit[chain] = (t, record).
+// Persistent warps; each lane keeps its own resumable traversal and idle lanes
+// refill from the queue between warp-synchronous traversal rounds.
+__global__ void __launch_bounds__(128) wf_trace_kernel(SceneView s, ChainView c, int v) {
     const WaveView& w = c.wf;
-    const uint32_t* qin = w.queue + (uint64_t)((v - 1) & 1) * c.n;
-    uint32_t* qout = w.queue + (uint64_t)(v & 1) * c.n;
+    const uint32_t* qin = w.queue + (uint64_t)(v & 1) * c.n;
     const unsigned count = w.qcount[v];
     unsigned int* fetch = w.qcount + (kMaxDepth + 2) + v;
     const int lane = threadIdx.x & 31;
-    const uint64_t n = c.n;
+    const unsigned lt = (1u << lane) - 1u;
     unsigned status = 0;
+    Work wk;
+    Trav r;
+    int stack[kStackSize];
+    bool has = false;
+    uint32_t i = 0;
+    bool drained = false;  // warp-uniform: the queue has no entries left
     while (true) {
-        unsigned j0 = 0;
-        if (lane == 0) j0 = atomicAdd(fetch, 32u);
-        j0 = __shfl_sync(kFull, j0, 0);
-        if (j0 >= count) break;
-        const unsigned j = j0 + lane;
-        const bool has = j < count;
-        bool live = false;
-        uint32_t i = 0;
-        float3 o = f3(0.f, 0.f, 0.f), d = f3(0.f, 0.f, 1.f), T = f3(0.f, 0.f, 0.f), F = f3(0.f, 0.f, 0.f);
-        float u1 = 0.f, u2 = 0.f;
-        if (has) {
-            i = qin[j];
-            load_path(w.path, i, o, d, T, F);
-            if (v < (int)c.depth) {
-                const float* cand = w.par[i] ? c.x : w.y;
-                u1 = cand[(uint64_t)(2 + 2 * v) * n + i];
-                u2 = cand[(uint64_t)(3 + 2 * v) * n + i];
+        const unsigned idle = __ballot_sync(kFull, !has);
+        if (!drained && (__popc(idle) >= kRefill || idle == kFull)) {
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(fetch, (unsigned)__popc(idle));
+            base = __shfl_sync(kFull, base, 0);
+            if (base + (unsigned)__popc(idle) >= count) drained = true;
+            if (!has) {
+                const unsigned j = base + __popc(idle & lt);
+                if (j < count) {
+                    i = qin[j];
+                    const float4 a = w.path[3 * (uint64_t)i], b = w.path[3 * (uint64_t)i + 1];
+                    trav_begin(s, r, f3(a.x, a.y, a.z), f3(a.w, b.x, b.y));
+                    has = s.root != kSentinel;
+                    if (!has) w.hit[i] = make_float2(INFINITY, __int_as_float(-1));
+                }
             }
         }
-        float t;
-        Work wk;
-        const int k = closest_hit<false>(s, kFull, has, o, d, t, status, wk);
-        if (has) {
-            if (k >= 0) live = shade_vertex(s, k, t, v, (int)c.depth, u1, u2, o, d, T, F);
-            if (live)
-                store_path(w.path, i, o, d, T, F);
-            else
-                w.path[3 * i + 2] = make_float4(0.f, F.x, F.y, F.z);
+        if (!__any_sync(kFull, has)) {
+            if (drained) break;
+            continue;
         }
-        enqueue(live, i, qout, w.qcount + v + 1);
+        // one while-while round: inner nodes until every lane holds a leaf
+        while (__any_sync(kFull, has && r.ref >= 0)) {
+            if (has && r.ref >= 0 && !trav_node<false>(s, r, stack, status, wk)) {
+                r.best = -1;
+                r.ref = kSentinel;
+            }
+        }
+        if (has) {
+            const bool more = r.ref != kSentinel && trav_leaf<false>(s, r, stack, wk);
+            if (!more) {
+                w.hit[i] = make_float2(r.best >= 0 ? r.tb : INFINITY, __int_as_float(r.best));
+                has = false;
+            }
+        }
     }
     status = __reduce_or_sync(kFull, status);
     if (lane == 0 && status) atomicOr(c.status, status);
+}
+
+// Shade every queued ray of bounce v; survivors to the next queue.
+__global__ void __launch_bounds__(128) wf_shade_kernel(SceneView s, ChainView c, int v) {
+    const WaveView& w = c.wf;
+    const uint32_t* qin = w.queue + (uint64_t)(v & 1) * c.n;
+    uint32_t* qout = w.queue + (uint64_t)((v + 1) & 1) * c.n;
+    const unsigned count = w.qcount[v];
+    const uint64_t n = c.n;
+    const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned warps = (gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (unsigned j0 = warp * 32u; j0 < count; j0 += warps * 32u) {
+        const unsigned j = j0 + lane;
+        bool live = false;
+        uint32_t i = 0;
+        if (j < count) {
+            i = qin[j];
+            const float2 h = w.hit[i];
+            float3 o, d, T, F;
+            load_path(w.path, i, o, d, T, F);
+            const int k = __float_as_int(h.y);
+            if (k >= 0) {
+                float u1 = 0.f, u2 = 0.f;
+                if (v < (int)c.depth) {
+                    const float* cand = w.par[i] ? c.x : w.y;
+                    u1 = cand[(uint64_t)(2 + 2 * v) * n + i];
+                    u2 = cand[(uint64_t)(3 + 2 * v) * n + i];
+                }
+                live = shade_vertex(s, k, h.x, v, (int)c.depth, u1, u2, o, d, T, F);
+            }
+            if (live)
+                store_path(w.path, i, o, d, T, F);
+            else
+                w.path[3 * (uint64_t)i + 2] = make_float4(0.f, F.x, F.y, F.z);
+        }
+        enqueue(live, i, qout, w.qcount + v + 1);
+    }
 }
 
 inline unsigned grid_for(uint64_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
@@ -248,25 +290,31 @@ inline unsigned grid_for(uint64_t n, unsigned b) { return (unsigned)((n + b - 1)
 
 cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
                              cudaStream_t st) {
-    static int bounce_blocks = 0;
-    if (bounce_blocks == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
+    static int trace_blocks = 0, shade_blocks = 0;
+    if (trace_blocks == 0) {
+        int dev = 0, sms = 0, per_sm = 0, per_sm2 = 0;
         cudaError_t e;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wf_bounce_kernel, 128, 0)) != cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wf_trace_kernel, 128, 0)) != cudaSuccess)
             return e;
-        bounce_blocks = sms * (per_sm > 0 ? per_sm : 1);
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, wf_shade_kernel, 128, 0)) != cudaSuccess)
+            return e;
+        trace_blocks = sms * (per_sm > 0 ? per_sm : 1);
+        shade_blocks = sms * (per_sm2 > 0 ? per_sm2 : 1);
     }
     const unsigned G = grid_for(c.n, 128);
     const size_t qbytes = sizeof(unsigned int) * 2 * (kMaxDepth + 2);
     for (uint32_t k = 0; k < n_steps; ++k) {
         cudaError_t e = cudaMemsetAsync(c.wf.qcount, 0, qbytes, st);
         if (e != cudaSuccess) return e;
-        wf_step_kernel<<<G, 128, 0, st>>>(s, c, step_begin + k, k > 0, 1);
-        for (int v = 1; v <= (int)c.depth; ++v) wf_bounce_kernel<<<bounce_blocks, 128, 0, st>>>(s, c, v);
+        wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + k, k > 0, 1, s);
+        for (int v = 0; v <= (int)c.depth; ++v) {
+            wf_trace_kernel<<<trace_blocks, 128, 0, st>>>(s, c, v);
+            wf_shade_kernel<<<shade_blocks, 128, 0, st>>>(s, c, v);
+        }
     }
-    wf_step_kernel<<<G, 128, 0, st>>>(s, c, step_begin + n_steps, n_steps > 0, 0);
+    wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + n_steps, n_steps > 0, 0, s);
     return cudaGetLastError();
 }
 
@@ -275,12 +323,14 @@ cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t st
 // kStaticMaxChains chains live in one file-scope device array instead of
 // memory allocated per chain set.  Every GPU that loads the library holds it
 // until the process exits.  Layout (256-byte aligned pieces): y [kMaxDim][n],
-// path [n][3] float4, ua [n], queue [2][n], par [n], qcount [2 (kMaxDepth+2)].
+// path [n][3] float4, hit [n] float2, ua [n], queue [2][n], par [n],
+// qcount [2 (kMaxDepth+2)].
 namespace {
 constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kOffY = 0;
 constexpr size_t kOffPath = kOffY + align256(sizeof(float) * kMaxDim * kStaticMaxChains);
-constexpr size_t kOffUa = kOffPath + align256(sizeof(float4) * 3 * kStaticMaxChains);
+constexpr size_t kOffHit = kOffPath + align256(sizeof(float4) * 3 * kStaticMaxChains);
+constexpr size_t kOffUa = kOffHit + align256(sizeof(float2) * kStaticMaxChains);
 constexpr size_t kOffQueue = kOffUa + align256(sizeof(float) * kStaticMaxChains);
 constexpr size_t kOffPar = kOffQueue + align256(sizeof(uint32_t) * 2 * kStaticMaxChains);
 constexpr size_t kOffCount = kOffPar + align256(sizeof(uint8_t) * kStaticMaxChains);
@@ -322,13 +372,14 @@ cudaError_t launch_wavefront_static(const SceneView& s, const ChainView& c, uint
     ChainView v = c;
     v.wf.y = reinterpret_cast<float*>(b + kOffY);
     v.wf.path = reinterpret_cast<float4*>(b + kOffPath);
+    v.wf.hit = reinterpret_cast<float2*>(b + kOffHit);
     v.wf.ua = reinterpret_cast<float*>(b + kOffUa);
     v.wf.queue = reinterpret_cast<uint32_t*>(b + kOffQueue);
     v.wf.par = b + kOffPar;
     v.wf.qcount = reinterpret_cast<unsigned int*>(b + kOffCount);
     // The array keeps the previous call's bytes: the parity must start at 0
     // (every state in x); the queue counters are cleared per step inside
-    // launch_wavefront; y, ua and the path records are written before use.
+    // launch_wavefront; y, ua, the path and hit records are written before use.
     if ((e = cudaMemsetAsync(v.wf.par, 0, c.n, st)) != cudaSuccess) return e;
     return launch_wavefront(s, v, step_begin, n_steps, st);
 }
