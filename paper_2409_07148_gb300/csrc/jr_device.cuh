@@ -159,11 +159,11 @@ __device__ __forceinline__ bool trav_node(const SceneView& s, Trav& r, int* stac
     return true;
 }
 
-// Test the triangles of leaf r.ref (Moller-Trumbore, JGT 1997; ties on equal t
-// to the smaller original index), then pop.  Returns false when the ray is done.
+// Test the triangles of leaf `leaf` (Moller-Trumbore, JGT 1997; ties on equal
+// t to the smaller original index) against the ray, updating the closest hit.
 template <bool kCount>
-__device__ __forceinline__ bool trav_leaf(const SceneView& s, Trav& r, const int* stack, Work& work) {
-    const int enc = ~r.ref;
+__device__ __forceinline__ void trav_test_leaf(const SceneView& s, Trav& r, int leaf, Work& work) {
+    const int enc = ~leaf;
     const int first = enc >> 3, cnt = (enc & 7) + 1;
     if constexpr (kCount) work.tris += (uint32_t)cnt;
     for (int k = first; k < first + cnt; ++k) {
@@ -188,6 +188,12 @@ __device__ __forceinline__ bool trav_leaf(const SceneView& s, Trav& r, const int
             r.best_id = id;
         }
     }
+}
+
+// Test the triangles of leaf r.ref, then pop.  Returns false when the ray is done.
+template <bool kCount>
+__device__ __forceinline__ bool trav_leaf(const SceneView& s, Trav& r, const int* stack, Work& work) {
+    trav_test_leaf<kCount>(s, r, r.ref, work);
     r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
     return r.ref != kSentinel;
 }

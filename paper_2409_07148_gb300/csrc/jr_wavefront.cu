@@ -202,7 +202,8 @@ __global__ void __launch_bounds__(128) wf_trace_kernel(SceneView s, ChainView c,
     Work wk;
     Trav r;
     int stack[kStackSize];
-    bool has = false;
+    bool has = false, failed = false;
+    int leaf = kSentinel;  // postponed leaf of this lane's ray, or none
     uint32_t i = 0;
     bool drained = false;  // warp-uniform: the queue has no entries left
     while (true) {
@@ -227,18 +228,35 @@ __global__ void __launch_bounds__(128) wf_trace_kernel(SceneView s, ChainView c,
             if (drained) break;
             continue;
         }
-        // one while-while round: inner nodes until every lane holds a leaf
-        while (__any_sync(kFull, has && r.ref >= 0)) {
-            if (has && r.ref >= 0 && !trav_node<false>(s, r, stack, status, wk)) {
-                r.best = -1;
-                r.ref = kSentinel;
+        // One speculative while-while round (Aila & Laine 2009): a lane that
+        // meets a leaf postpones it and keeps descending inner nodes until
+        // every lane holds a leaf; then the postponed leaves are tested together.
+        if (has && leaf == kSentinel && r.ref < 0 && r.ref != kSentinel) {
+            leaf = r.ref;
+            r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
+        }
+        while (__any_sync(kFull, has && leaf == kSentinel && r.ref >= 0)) {
+            if (has && r.ref >= 0) {
+                if (!trav_node<false>(s, r, stack, status, wk)) {
+                    r.best = -1;
+                    r.ref = kSentinel;
+                    leaf = kSentinel;
+                    failed = true;
+                } else if (leaf == kSentinel && r.ref < 0 && r.ref != kSentinel) {
+                    leaf = r.ref;
+                    r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
+                }
             }
         }
         if (has) {
-            const bool more = r.ref != kSentinel && trav_leaf<false>(s, r, stack, wk);
-            if (!more) {
+            if (leaf != kSentinel) {
+                trav_test_leaf<false>(s, r, leaf, wk);
+                leaf = kSentinel;
+            }
+            if (failed || r.ref == kSentinel) {
                 w.hit[i] = make_float2(r.best >= 0 ? r.tb : INFINITY, __int_as_float(r.best));
                 has = false;
+                failed = false;
             }
         }
     }
