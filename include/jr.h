@@ -257,6 +257,49 @@ jr_status jr_render_pt(const jr_scene* scene, const jr_params* params, uint64_t 
 jr_status jr_philox(uint64_t seed, uint32_t tag, uint32_t block, uint64_t chain_begin, uint64_t step, uint64_t n,
                     uint32_t* out_dev, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many chain sets -- scenes of uneven size, images, depths -- advanced
+ * by ONE persistent launch.  Blocks of the launch take work items (a block of
+ * chains of one set) from a global cursor; items are ordered by estimated cost
+ * (depth + 1) x log2(triangles), longest first.  Every set advances exactly as
+ * jr_advance would advance it on its own (same Philox streams, same
+ * per-chain arithmetic; Alg. 2 of Section 7.2 per chain).  The sets stay owned
+ * by the caller and must outlive the batch; a set may still be advanced,
+ * resolved or inspected on its own between batch advances.
+ */
+typedef struct jr_batch jr_batch;
+
+typedef struct {
+    uint32_t n;                   /* candidates tried */
+    uint32_t block[8];            /* chains per work item (= threads per block) */
+    double ns_per_chain_step[8];  /* measured device time per chain step */
+    uint32_t best_block;          /* the candidate now in use */
+} jr_tune_report;
+
+/* Build a batch over n_sets distinct chain sets (device descriptors, work
+ * items, one set-up launch).  Synchronises `stream`. */
+jr_status jr_batch_create(jr_chains* const* sets, uint32_t n_sets, void* stream, jr_batch** out);
+void jr_batch_destroy(jr_batch* batch);
+
+/* Chains per work item (= threads per block): a multiple of 32 in [32, 256]. */
+jr_status jr_batch_set_block(jr_batch* batch, uint32_t block);
+
+/* Advance every set of the batch by n_steps: one persistent launch plus one
+ * fold launch for all sets.  Asynchronous. */
+jr_status jr_batch_advance(jr_batch* batch, uint32_t n_steps, void* stream);
+
+/* As jr_batch_advance, replayed from a CUDA graph that holds the two launches
+ * (captured on the first call, and again whenever n_steps or the block size
+ * changes).  The step indices live on the device, so every replay continues
+ * the chains.  Asynchronous after the first capture. */
+jr_status jr_batch_advance_graph(jr_batch* batch, uint32_t n_steps, void* stream);
+
+/* Autotuner: time probe_steps chain steps of the whole batch for each work-item
+ * size in {32, 64, 128, 256} (CUDA events on `stream`) and keep the fastest.
+ * The probes are real steps: every set advances by 4 x probe_steps.
+ * Synchronises `stream`. */
+jr_status jr_batch_autotune(jr_batch* batch, uint32_t probe_steps, void* stream, jr_tune_report* out);
+
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char* jr_last_error(void);
 /* Library version string. */

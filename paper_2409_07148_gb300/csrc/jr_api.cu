@@ -4,7 +4,9 @@
 // thread-local message.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -447,6 +449,258 @@ jr_status jr_philox(uint64_t seed, uint32_t tag, uint32_t block, uint64_t chain_
                     uint32_t* out_dev, void* stream) {
     if (n > 0 && !out_dev) return fail(JR_ERR_INVALID_ARG, "jr_philox: null output");
     JR_CUDA(launch_philox(seed, tag, block, chain_begin, step, n, out_dev, (cudaStream_t)stream), "jr_philox");
+    return JR_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: many chain sets (scenes of uneven size, images, depths) advanced by
+// one persistent launch, optionally replayed from a captured CUDA graph.
+struct jr_batch {
+    std::vector<jr_chains*> sets;
+    std::vector<uint64_t> dev_steps;  // the step index each set has on the device side
+    BatchEntry* entries = nullptr;
+    uint64_t* px_off = nullptr;
+    unsigned int* cursor = nullptr;
+    BatchItem* items = nullptr;
+    size_t items_cap = 0;
+    uint32_t n_items = 0;
+    uint32_t max_dim = 0;
+    uint64_t total_px = 0, total_chains = 0;
+    int block = 128;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint32_t graph_steps = 0;
+    int graph_block = 0;
+    ~jr_batch() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaFree(entries);
+        cudaFree(px_off);
+        cudaFree(cursor);
+        cudaFree(items);
+    }
+};
+
+namespace {
+
+// Work items: blocks of `block` chains, most expensive first (a chain step
+// costs about (depth + 1) ray casts of log(triangles) traversal depth).
+jr_status build_items(jr_batch* b, int block, cudaStream_t st) {
+    struct Cand {
+        double cost;
+        BatchItem it;
+    };
+    std::vector<Cand> v;
+    for (uint32_t k = 0; k < b->sets.size(); ++k) {
+        const jr_chains* c = b->sets[k];
+        const double per_chain = (c->view.depth + 1.0) * std::log2(c->scene->info.n_tris + 2.0);
+        for (uint64_t beg = 0; beg < c->view.n; beg += (uint64_t)block) {
+            const uint64_t end = std::min<uint64_t>(beg + block, c->view.n);
+            v.push_back({per_chain * (double)(end - beg), BatchItem{k, (uint32_t)beg, (uint32_t)end}});
+        }
+    }
+    std::stable_sort(v.begin(), v.end(), [](const Cand& a, const Cand& c) { return a.cost > c.cost; });
+    std::vector<BatchItem> h(v.size());
+    for (size_t q = 0; q < v.size(); ++q) h[q] = v[q].it;
+    if (h.size() > b->items_cap) {
+        cudaFree(b->items);
+        b->items = nullptr;
+        b->items_cap = 0;
+        JR_CUDA(dev_alloc(&b->items, h.size()), "jr_batch (work items)");
+        b->items_cap = h.size();
+    }
+    JR_CUDA(cudaMemcpyAsync(b->items, h.data(), sizeof(BatchItem) * h.size(), cudaMemcpyHostToDevice, st),
+            "jr_batch (work items)");
+    JR_CUDA(cudaStreamSynchronize(st), "jr_batch (work items)");
+    b->n_items = (uint32_t)h.size();
+    b->block = block;
+    return JR_OK;
+}
+
+// Bring the device-side step index of every set up to date with its host
+// counter (a set may have been advanced on its own since the last batch).
+jr_status sync_steps(jr_batch* b, cudaStream_t st) {
+    for (size_t k = 0; k < b->sets.size(); ++k) {
+        const uint64_t s = b->sets[k]->steps;
+        if (s != b->dev_steps[k]) {
+            unsigned long long v = s;
+            JR_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(b->entries + k) + offsetof(BatchEntry, step), &v,
+                                    sizeof(v), cudaMemcpyHostToDevice, st),
+                    "jr_batch (step index)");
+            JR_CUDA(cudaStreamSynchronize(st), "jr_batch (step index)");
+            b->dev_steps[k] = s;
+        }
+    }
+    return JR_OK;
+}
+
+void after_launch(jr_batch* b, uint32_t n_steps) {
+    for (size_t k = 0; k < b->sets.size(); ++k) {
+        b->sets[k]->steps += n_steps;
+        b->dev_steps[k] += n_steps;
+    }
+}
+
+jr_status batch_launch(jr_batch* b, uint32_t n_steps, cudaStream_t st, const char* who) {
+    JR_CUDA(launch_batch(b->entries, b->items, b->n_items, b->px_off, (uint32_t)b->sets.size(), b->total_px,
+                         b->cursor, b->max_dim, b->block, n_steps, st),
+            who);
+    return JR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+jr_status jr_batch_create(jr_chains* const* sets, uint32_t n_sets, void* stream, jr_batch** out) {
+    if (!sets || !out || n_sets == 0) return fail(JR_ERR_INVALID_ARG, "jr_batch_create: null argument or no sets");
+    cudaStream_t st = (cudaStream_t)stream;
+    jr_batch* b = new (std::nothrow) jr_batch();
+    if (!b) return fail(JR_ERR_OOM, "jr_batch_create: host allocation failed");
+    std::vector<BatchEntry> h(n_sets);
+    std::vector<uint64_t> off(n_sets + 1, 0);
+    for (uint32_t k = 0; k < n_sets; ++k) {
+        jr_chains* c = sets[k];
+        if (!c) {
+            delete b;
+            return fail(JR_ERR_INVALID_ARG, "jr_batch_create: null chain set");
+        }
+        for (uint32_t q = 0; q < k; ++q)
+            if (sets[q] == c) {
+                delete b;
+                return fail(JR_ERR_INVALID_ARG, "jr_batch_create: a chain set appears twice");
+            }
+        h[k].s = c->scene->view;
+        h[k].c = c->view;
+        h[k].step = c->steps;
+        off[k + 1] = off[k] + (uint64_t)c->view.width * c->view.height;
+        b->max_dim = std::max(b->max_dim, c->view.dim);
+        b->total_chains += c->view.n;
+        b->sets.push_back(c);
+        b->dev_steps.push_back(c->steps);
+    }
+    b->total_px = off[n_sets];
+    cudaError_t e;
+    if ((e = dev_alloc(&b->entries, n_sets)) != cudaSuccess || (e = dev_alloc(&b->px_off, n_sets + 1)) != cudaSuccess ||
+        (e = dev_alloc(&b->cursor, 1)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(b->entries, h.data(), sizeof(BatchEntry) * n_sets, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(b->px_off, off.data(), sizeof(uint64_t) * (n_sets + 1), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaMemsetAsync(b->cursor, 0, sizeof(unsigned int), st)) != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "jr_batch_create");
+    }
+    jr_status r = build_items(b, 128, st);
+    if (r == JR_OK) r = batch_launch(b, 0, st, "jr_batch_create");  // set-up launch: no steps
+    if (r != JR_OK) {
+        delete b;
+        return r;
+    }
+    *out = b;
+    return JR_OK;
+}
+
+void jr_batch_destroy(jr_batch* batch) { delete batch; }
+
+jr_status jr_batch_set_block(jr_batch* b, uint32_t block) {
+    if (!b) return fail(JR_ERR_INVALID_ARG, "jr_batch_set_block: null batch");
+    if (block < 32 || block > 256 || block % 32 != 0)
+        return fail(JR_ERR_INVALID_ARG, "jr_batch_set_block: block must be a multiple of 32 in [32, 256]");
+    return build_items(b, (int)block, nullptr);
+}
+
+jr_status jr_batch_advance(jr_batch* b, uint32_t n_steps, void* stream) {
+    if (!b) return fail(JR_ERR_INVALID_ARG, "jr_batch_advance: null batch");
+    if (n_steps == 0) return JR_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    jr_status r = sync_steps(b, st);
+    if (r == JR_OK) r = batch_launch(b, n_steps, st, "jr_batch_advance");
+    if (r == JR_OK) after_launch(b, n_steps);
+    return r;
+}
+
+jr_status jr_batch_advance_graph(jr_batch* b, uint32_t n_steps, void* stream) {
+    if (!b) return fail(JR_ERR_INVALID_ARG, "jr_batch_advance_graph: null batch");
+    if (n_steps == 0) return JR_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    jr_status r = sync_steps(b, st);
+    if (r != JR_OK) return r;
+    if (!b->exec || b->graph_steps != n_steps || b->graph_block != b->block) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        cudaStream_t cap = nullptr;
+        JR_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "jr_batch_advance_graph");
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t el = launch_batch(b->entries, b->items, b->n_items, b->px_off, (uint32_t)b->sets.size(),
+                                          b->total_px, b->cursor, b->max_dim, b->block, n_steps, cap);
+            e = cudaStreamEndCapture(cap, &b->graph);
+            if (e == cudaSuccess) e = el;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) {
+            if (b->graph) cudaGraphDestroy(b->graph);
+            b->graph = nullptr;
+            b->exec = nullptr;
+            return cuda_fail(e, "jr_batch_advance_graph (capture)");
+        }
+        b->graph_steps = n_steps;
+        b->graph_block = b->block;
+    }
+    JR_CUDA(cudaGraphLaunch(b->exec, st), "jr_batch_advance_graph");
+    after_launch(b, n_steps);
+    return JR_OK;
+}
+
+jr_status jr_batch_autotune(jr_batch* b, uint32_t probe_steps, void* stream, jr_tune_report* out) {
+    if (!b || !out || probe_steps == 0) return fail(JR_ERR_INVALID_ARG, "jr_batch_autotune: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t cands[] = {32, 64, 128, 256};
+    jr_tune_report rep{};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    JR_CUDA(cudaEventCreate(&e0), "jr_batch_autotune");
+    JR_CUDA(cudaEventCreate(&e1), "jr_batch_autotune");
+    double best = INFINITY;
+    jr_status r = JR_OK;
+    for (uint32_t q = 0; q < 4 && r == JR_OK; ++q) {
+        r = build_items(b, (int)cands[q], st);
+        if (r == JR_OK) r = sync_steps(b, st);
+        if (r != JR_OK) break;
+        cudaError_t e;
+        if ((e = cudaEventRecord(e0, st)) != cudaSuccess) {
+            r = cuda_fail(e, "jr_batch_autotune");
+            break;
+        }
+        r = batch_launch(b, probe_steps, st, "jr_batch_autotune");
+        if (r != JR_OK) break;
+        after_launch(b, probe_steps);
+        float ms = 0.f;
+        if ((e = cudaEventRecord(e1, st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+            r = cuda_fail(e, "jr_batch_autotune");
+            break;
+        }
+        const double ns = 1e6 * ms / ((double)b->total_chains * probe_steps);
+        rep.block[rep.n] = cands[q];
+        rep.ns_per_chain_step[rep.n] = ns;
+        rep.n++;
+        if (ns < best) {
+            best = ns;
+            rep.best_block = cands[q];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != JR_OK) return r;
+    r = build_items(b, (int)rep.best_block, st);
+    if (r != JR_OK) return r;
+    *out = rep;
     return JR_OK;
 }
 

@@ -84,6 +84,19 @@ struct ChainView {
     WaveView wf;
 };
 
+// A chain set of a batch as the batched kernels see it; `step` is the set's
+// next Philox step index, advanced on the device by every batched launch.
+struct BatchEntry {
+    SceneView s;
+    ChainView c;
+    unsigned long long step;
+};
+
+// One work item of the batched kernel: chains [begin, end) of set `set`.
+struct BatchItem {
+    uint32_t set, begin, end;
+};
+
 // Host-side BVH build result.
 struct HostBvh {
     std::vector<BvhNode> nodes;
@@ -102,6 +115,11 @@ cudaError_t launch_step(const SceneView& s, const ChainView& c, uint64_t step_be
                         uint8_t* tr_flags, float* tr_dt, int32_t* tr_pix, unsigned long long* work_out, int block,
                         cudaStream_t st);
 cudaError_t launch_fold(const ChainView& c, cudaStream_t st);
+// Batched persistent launch + fold over n_sets chain sets (block = chains per
+// work item = threads per block, a multiple of 32 in [32, 256]).
+cudaError_t launch_batch(BatchEntry* entries, const BatchItem* items, uint32_t n_items, const uint64_t* px_off,
+                         uint32_t n_sets, uint64_t total_px, unsigned int* cursor, uint32_t max_dim, int block,
+                         uint32_t n_steps, cudaStream_t st);
 // jr_wavefront.cu
 cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
                              cudaStream_t st);

@@ -15,6 +15,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "../../include/jr.h"
 #include "jr_device.cuh"
 #include "jr_internal.h"
@@ -66,14 +68,14 @@ __global__ void reeval_kernel(SceneView s, ChainView c) {
     flush_status(status, c.status);
 }
 
+// n_steps of Alg. 2 for chain i of set c (thread tid of the block; `active`
+// false for threads without a chain).  Every thread of the block calls it;
+// sh holds [2][D][blockDim] floats.
 template <bool kTrace, bool kCount>
-__global__ void __launch_bounds__(256) step_kernel(SceneView s, ChainView c, uint64_t step_begin, uint32_t n_steps,
-                                                   uint8_t* tr_flags, float* tr_dt, int32_t* tr_pix,
-                                                   unsigned long long* work_out) {
-    extern __shared__ float sh[];
+__device__ __forceinline__ void chain_steps(const SceneView& s, const ChainView& c, uint64_t i, bool active, float* sh,
+                                            uint64_t step_begin, uint32_t n_steps, uint8_t* tr_flags, float* tr_dt,
+                                            int32_t* tr_pix, unsigned long long* work_out) {
     const uint32_t B = blockDim.x, tid = threadIdx.x;
-    const uint64_t i = blockIdx.x * (uint64_t)B + tid;
-    const bool active = i < c.n;
     const unsigned mask = __ballot_sync(0xffffffffu, active);  // lanes that trace together
     const int D = (int)c.dim;
     float* buf0 = sh + tid;
@@ -193,6 +195,67 @@ __global__ void __launch_bounds__(256) step_kernel(SceneView s, ChainView c, uin
         if (nL) atomicAdd(c.counters + 1, (unsigned long long)nL);
         if (nA) atomicAdd(c.counters + 2, (unsigned long long)nA);
         flush_status(status, c.status);
+    }
+}
+
+template <bool kTrace, bool kCount>
+__global__ void __launch_bounds__(256) step_kernel(SceneView s, ChainView c, uint64_t step_begin, uint32_t n_steps,
+                                                   uint8_t* tr_flags, float* tr_dt, int32_t* tr_pix,
+                                                   unsigned long long* work_out) {
+    extern __shared__ float sh[];
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    chain_steps<kTrace, kCount>(s, c, i, i < c.n, sh, step_begin, n_steps, tr_flags, tr_dt, tr_pix, work_out);
+}
+
+// One persistent launch over a batch of chain sets (scenes with different
+// triangle counts, images and depths).  Blocks take work items -- a block of
+// chains of one set -- from a global cursor; the host orders the items by
+// estimated cost, so the longest items start first.  Every item runs all
+// n_steps of Alg. 2 for its chains with the same code as step_kernel.
+__global__ void __launch_bounds__(256) batch_step_kernel(const BatchEntry* entries, const BatchItem* items,
+                                                         uint32_t n_items, unsigned int* cursor, uint32_t n_steps) {
+    extern __shared__ float sh[];
+    __shared__ unsigned int item_s;
+    while (true) {
+        if (threadIdx.x == 0) item_s = atomicAdd(cursor, 1u);
+        __syncthreads();
+        const unsigned it = item_s;
+        __syncthreads();  // every thread has read item_s before it is overwritten
+        if (it >= n_items) break;
+        const BatchItem wi = items[it];
+        const BatchEntry& e = entries[wi.set];  // descriptor fields are read where used
+        const uint64_t i = wi.begin + threadIdx.x;
+        chain_steps<false, false>(e.s, e.c, i, i < wi.end, sh, e.step, n_steps, nullptr, nullptr, nullptr, nullptr);
+        __syncthreads();  // the shared state buffers are reused by the next item
+    }
+}
+
+// Fold every set's framebuffer into its accumulator; advance every set's step
+// index by n_steps; reset the work cursor for the next launch.
+__global__ void batch_fold_kernel(BatchEntry* entries, const uint64_t* px_off, uint32_t n_sets, uint64_t total_px,
+                                  unsigned int* cursor, uint32_t n_steps) {
+    const uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (j == 0) *cursor = 0u;
+    if (j < n_sets) entries[j].step += n_steps;
+    if (j >= total_px) return;
+    uint32_t lo = 0, hi = n_sets;  // the set whose pixel range holds j
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (px_off[mid] <= j) lo = mid;
+        else hi = mid;
+    }
+    const uint64_t p = j - px_off[lo];
+    float4* fb = entries[lo].c.fb;
+    const float4 v = fb[p];
+    if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) {
+        double4_32a* acc = entries[lo].c.acc64;
+        double4_32a a = acc[p];
+        a.x += v.x;
+        a.y += v.y;
+        a.z += v.z;
+        a.w += v.w;
+        acc[p] = a;
+        fb[p] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -329,6 +392,31 @@ cudaError_t launch_step(const SceneView& s, const ChainView& c, uint64_t step_be
 cudaError_t launch_fold(const ChainView& c, cudaStream_t st) {
     const uint32_t n = c.width * c.height;
     fold_kernel<<<grid_for(n, 256), 256, 0, st>>>(c.fb, c.acc64, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch(BatchEntry* entries, const BatchItem* items, uint32_t n_items, const uint64_t* px_off,
+                         uint32_t n_sets, uint64_t total_px, unsigned int* cursor, uint32_t max_dim, int block,
+                         uint32_t n_steps, cudaStream_t st) {
+    static int sms = 0;
+    cudaError_t e;
+    const size_t shm = sizeof(float) * 2 * max_dim * (size_t)block;
+    if (sms == 0) {
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(batch_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(float) * 2 * kMaxDim * 256))) != cudaSuccess)
+            return e;
+    }
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_step_kernel, block, shm)) != cudaSuccess)
+        return e;
+    const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)sms * (per_sm > 0 ? per_sm : 1), n_items);
+    if (n_steps > 0 && n_items > 0)
+        batch_step_kernel<<<grid, block, shm, st>>>(entries, items, n_items, cursor, n_steps);
+    const uint64_t total = total_px > n_sets ? total_px : n_sets;
+    batch_fold_kernel<<<grid_for(total, 256), 256, 0, st>>>(entries, px_off, n_sets, total_px, cursor, n_steps);
     return cudaGetLastError();
 }
 

@@ -82,9 +82,20 @@ _SIGS = {
     "jr_eval_states": [_P, ctypes.POINTER(Params), _P, _U64, _P, _P, _P, _P, _P, _P],
     "jr_render_pt": [_P, ctypes.POINTER(Params), _U64, _U64, _P, _P],
     "jr_philox": [_U64, _U32, _U32, _U64, _U64, _U64, _P, _P],
+    "jr_batch_create": [_P, _U32, _P, ctypes.POINTER(_P)],
+    "jr_batch_destroy": [_P],
+    "jr_batch_set_block": [_P, _U32],
+    "jr_batch_advance": [_P, _U32, _P],
+    "jr_batch_advance_graph": [_P, _U32, _P],
+    "jr_batch_autotune": [_P, _U32, _P, _P],
     "jr_last_error": [],
     "jr_version": [],
 }
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("block", ctypes.c_uint32 * 8), ("ns_per_chain_step", ctypes.c_double * 8),
+                ("best_block", ctypes.c_uint32)]
 
 
 def lib():
@@ -101,6 +112,7 @@ def lib():
                 fn.restype = ctypes.c_char_p if name in ("jr_last_error", "jr_version") else ctypes.c_int
             L.jr_scene_destroy.restype = None
             L.jr_chains_destroy.restype = None
+            L.jr_batch_destroy.restype = None
             _lib = L
     return _lib
 
@@ -242,6 +254,43 @@ class Chains:
     def close(self):
         if getattr(self, "h", None):
             lib().jr_chains_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many chain sets advanced by one persistent launch (optionally a CUDA graph)."""
+
+    def __init__(self, sets, stream=None):
+        self.sets = list(sets)
+        arr = (ctypes.c_void_p * len(self.sets))(*[c.h.value for c in self.sets])
+        h = ctypes.c_void_p()
+        _check(lib().jr_batch_create(arr, len(self.sets), _stream(stream), ctypes.byref(h)))
+        self.h = h
+
+    def set_block(self, block):
+        _check(lib().jr_batch_set_block(self.h, int(block)))
+
+    def advance(self, n_steps, stream=None):
+        _check(lib().jr_batch_advance(self.h, int(n_steps), _stream(stream)))
+
+    def advance_graph(self, n_steps, stream=None):
+        _check(lib().jr_batch_advance_graph(self.h, int(n_steps), _stream(stream)))
+
+    def autotune(self, probe_steps, stream=None):
+        r = TuneReport()
+        _check(lib().jr_batch_autotune(self.h, int(probe_steps), _stream(stream), ctypes.byref(r)))
+        return {"best_block": int(r.best_block),
+                "ns_per_chain_step": {int(r.block[k]): float(r.ns_per_chain_step[k]) for k in range(r.n)}}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().jr_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

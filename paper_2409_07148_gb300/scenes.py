@@ -244,6 +244,79 @@ def glass_furnace(width=16, height=16, depth=6, albedo=0.5) -> SceneArrays:
     return b.build("glass_furnace", cam, width, height, depth)
 
 
+def _subdivided_box(lo, hi, s):
+    """Axis-aligned box with every face split into an s x s grid of quads
+    (12 s^2 triangles), outward winding."""
+    lo, hi = np.asarray(lo, np.float64), np.asarray(hi, np.float64)
+    g = np.linspace(0.0, 1.0, s + 1)
+    verts, tris = [], []
+    for ax in range(3):
+        o1, o2 = [a for a in range(3) if a != ax]
+        for side in (0, 1):
+            U, V = np.meshgrid(g, g, indexing="ij")
+            p = np.zeros((s + 1, s + 1, 3))
+            p[..., ax] = hi[ax] if side else lo[ax]
+            p[..., o1] = lo[o1] + U * (hi[o1] - lo[o1])
+            p[..., o2] = lo[o2] + V * (hi[o2] - lo[o2])
+            base = sum(len(v) for v in verts)
+            verts.append(p.reshape(-1, 3))
+            idx = np.arange((s + 1) * (s + 1)).reshape(s + 1, s + 1) + base
+            a, b, c, d = idx[:-1, :-1], idx[1:, :-1], idx[1:, 1:], idx[:-1, 1:]
+            t = np.concatenate([np.stack([a, b, c], -1).reshape(-1, 3), np.stack([a, c, d], -1).reshape(-1, 3)])
+            # orient outward: normal along +ax on the hi side, -ax on the lo side
+            n = np.zeros(3)
+            n[ax] = 1.0 if side else -1.0
+            v = np.concatenate(verts)
+            nn = np.cross(v[t[:, 1]] - v[t[:, 0]], v[t[:, 2]] - v[t[:, 0]]) @ n
+            t[nn < 0] = t[nn < 0][:, [0, 2, 1]]
+            tris.append(t)
+    return np.concatenate(verts), np.concatenate(tris)
+
+
+def random_boxes(seed, n_tris, width, height, depth) -> SceneArrays:
+    """Seeded procedural interior: a closed room (grey walls, one ceiling
+    light) holding random axis-aligned boxes whose faces are subdivided so the
+    scene has about n_tris triangles; Lambertian and glossy boxes."""
+    rng = np.random.default_rng(seed)
+    b = _Builder()
+    wall = b.add_material(material(LAMBERT, (0.65, 0.65, 0.65)))
+    light = b.add_material(material(LAMBERT, (0.0, 0.0, 0.0), emission=(12.0, 12.0, 12.0)))
+    b.box((0, 0, 0), (1, 1, 1), wall, inward=True)
+    lx, lz = rng.uniform(0.3, 0.7, size=2)
+    b.quad((lx, 0.998, lz), (0.25, 0, 0), (0, 0, 0.25), (0, -1, 0), light)
+    nb = int(rng.integers(6, 25))
+    s = max(1, int(round(np.sqrt(max(n_tris - 14, 12) / (12.0 * nb)))))
+    for _ in range(nb):
+        size = rng.uniform(0.05, 0.3, size=3)
+        lo = rng.uniform(0.02, 0.98 - size)
+        lo[1] = rng.uniform(0.0, 0.6)
+        hi = np.minimum(lo + size, 0.97)
+        if rng.random() < 0.3:
+            m = b.add_material(material(PHONG, tuple(rng.uniform(0.4, 0.9, 3)), phong_n=float(rng.uniform(10, 100))))
+        else:
+            m = b.add_material(material(LAMBERT, tuple(rng.uniform(0.2, 0.85, 3))))
+        v, t = _subdivided_box(lo, hi, s)
+        b.mesh(v, t, m)
+    cam = pinhole((0.5, 0.45, 0.97), (0.5, 0.4, 0.0), (0, 1, 0), 0.75, width / height)
+    return b.build(f"random_boxes_{seed}", cam, width, height, depth)
+
+
+def batched_workload(seed=0, n_scenes=64):
+    """The 64-scene batch: triangle count log-uniform in [1k, 200k], image side
+    log-uniform in [128, 1024] rounded to a multiple of 16, depth uniform in
+    {4..10}.  Returns a list of SceneArrays (one chain per pixel is the
+    intended chain count)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_scenes):
+        n_tris = int(np.exp(rng.uniform(np.log(1e3), np.log(2e5))))
+        side = int(np.exp(rng.uniform(np.log(128), np.log(1024))))
+        side = max(128, min(1024, 16 * int(round(side / 16))))
+        depth = int(rng.integers(4, 11))
+        out.append(random_boxes(seed * 1000 + k, n_tris, side, side, depth))
+    return out
+
+
 def by_name(name: str, **kw) -> SceneArrays:
     return {"cornell": cornell, "cornell_spheres": cornell_spheres, "furnace": furnace, "empty": empty,
-            "glass_furnace": glass_furnace}[name](**kw)
+            "glass_furnace": glass_furnace, "random_boxes": random_boxes}[name](**kw)

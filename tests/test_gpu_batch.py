@@ -1,0 +1,94 @@
+"""Batched advance (one persistent launch over many chain sets, optionally
+replayed from a CUDA graph, with the autotuner) against per-set advances
+through the C ABI (needs a GB300)."""
+import numpy as np
+import pytest
+
+from paper_2409_07148_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def J():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2409_07148_gb300 import jr
+    jr.lib()
+    return jr
+
+
+SETS = [("cornell", dict(width=16, height=16), 100, 1),
+        ("cornell_spheres", dict(width=32, height=24, depth=5, n_lon=30, n_lat=16), 513, 2),
+        ("glass_furnace", {}, 1000, 3),
+        ("random_boxes", dict(seed=4, n_tris=2500, width=48, height=48, depth=6), 2047, 4),
+        ("furnace", dict(depth=0), 64, 5),
+        ("random_boxes", dict(seed=9, n_tris=9000, width=40, height=40, depth=9), 33, 6)]
+
+
+def _make(J, sets=SETS):
+    out = []
+    for name, kw, n, seed in sets:
+        sc = scenes.by_name(name, **kw)
+        g = J.Scene(sc)
+        out.append((sc, g, J.Chains(g, sc.width, sc.height, sc.depth, n, seed=seed, sigma=0.03)))
+    return out
+
+
+def _compare(a, b):
+    (xa, fa), (xb, fb) = a.get_state(), b.get_state()
+    same = np.all(xa == xb, axis=0)
+    assert np.mean(same) >= 0.999
+    assert np.allclose(fa[:, same], fb[:, same], rtol=1e-5, atol=0)
+    sa, sb = a.stats(), b.stats()
+    for k in ("steps_per_chain", "regenerations", "local_steps", "accepted", "status_word"):
+        assert abs(sa[k] - sb[k]) <= int(1e-3 * a.n * sa["steps_per_chain"]) + 1, (k, sa[k], sb[k])
+    ia, ib = a.accumulator(), b.accumulator()
+    assert np.allclose(ia, ib, rtol=1e-4, atol=1e-6 * max(np.abs(ia).max(), 1e-30))
+
+
+def test_batch_equals_individual_advances(J):
+    ref = _make(J)
+    bat = _make(J)
+    for _, _, c in ref:
+        c.set_execution("mega")
+        c.advance(17)
+    b = J.Batch([c for _, _, c in bat])
+    b.set_block(64)
+    b.advance(5)
+    b.advance_graph(6)
+    b.advance_graph(6)   # a replay continues the chains
+    for (_, _, r), (_, _, c) in zip(ref, bat):
+        _compare(r, c)
+
+
+def test_autotune_and_interleaved_individual_advance(J):
+    ref = _make(J)
+    bat = _make(J)
+    for _, _, c in ref:
+        c.set_execution("mega")
+        c.advance(4 * 2 + 3 + 2)
+    b = J.Batch([c for _, _, c in bat])
+    rep = b.autotune(2)                     # 4 candidates x 2 real steps
+    assert rep["best_block"] in (32, 64, 128, 256) and len(rep["ns_per_chain_step"]) == 4
+    assert all(v > 0 for v in rep["ns_per_chain_step"].values())
+    bat[2][2].advance(3)                    # one set moves on its own ...
+    for k, (_, _, c) in enumerate(bat):     # ... the others catch up individually
+        if k != 2:
+            c.advance(3)
+    b.advance_graph(2)                      # the batch picks up every set's step index
+    for (_, _, r), (_, _, c) in zip(ref, bat):
+        _compare(r, c)
+
+
+def test_batch_images_are_estimates(J):
+    """Resolved images of a batched run are finite and non-negative and the
+    counters add up (regenerations + local steps = chains x steps)."""
+    bat = _make(J)
+    b = J.Batch([c for _, _, c in bat])
+    b.advance_graph(20)
+    for sc, _, c in bat:
+        img = c.resolve()
+        st = c.stats()
+        assert np.all(np.isfinite(img)) and np.all(img >= 0)
+        assert st["regenerations"] + st["local_steps"] == c.n * 20
