@@ -110,6 +110,13 @@ ORC_EXPORT void orc_draw_uniforms(uint64_t seed, uint32_t tag, uint32_t block, u
     draw_block(seed, tag, block, chain, step, out);
 }
 
+/* The same block for chains chain_begin .. +n (out: n x 4). */
+ORC_EXPORT void orc_draw_uniforms_many(uint64_t seed, uint32_t tag, uint32_t block, uint32_t chain_begin, uint64_t n,
+                                       uint64_t step, double* out)
+{
+    for (uint64_t i = 0; i < n; ++i) draw_block(seed, tag, block, (uint32_t)(chain_begin + i), step, out + 4 * i);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Small vector helpers                                                       */
 /* ------------------------------------------------------------------------- */

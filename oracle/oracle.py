@@ -54,6 +54,7 @@ def lib():
             P, D, U64, I, U32 = ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32
             L.orc_philox4x32_10.argtypes = [P, P, P]
             L.orc_draw_uniforms.argtypes = [U64, U32, U32, U32, U64, P]
+            L.orc_draw_uniforms_many.argtypes = [U64, U32, U32, U32, U64, U64, P]
             L.orc_scene_create.argtypes = [P, I, P, I, P, P, I, P]
             L.orc_scene_create.restype = P
             L.orc_scene_destroy.argtypes = [P]
@@ -104,6 +105,13 @@ def philox4x32_10(ctr, key):
 def draw_uniforms(seed, tag, block, chain, step):
     o = np.zeros(4, dtype=np.float64)
     lib().orc_draw_uniforms(seed, tag, block, chain, step, _ptr(o))
+    return o
+
+
+def draw_uniforms_many(seed, tag, block, chain_begin, n, step):
+    """Philox block `block` of chains chain_begin .. +n at one step: [n, 4] uniforms."""
+    o = np.zeros((int(n), 4), dtype=np.float64)
+    lib().orc_draw_uniforms_many(int(seed), int(tag), int(block), int(chain_begin), int(n), int(step), _ptr(o))
     return o
 
 
