@@ -300,6 +300,54 @@ jr_status jr_batch_advance_graph(jr_batch* batch, uint32_t n_steps, void* stream
  * Synchronises `stream`. */
 jr_status jr_batch_autotune(jr_batch* batch, uint32_t probe_steps, void* stream, jr_tune_report* out);
 
+/* ---------------------------------------------------------------------------
+ * Learned regeneration (not in the paper; the library's addition).  A chain set
+ * may regenerate from the mixture mu = beta mu_flow + (1 - beta) uniform, whose
+ * density u = beta q + (1 - beta) enters the killing rate k = c~ u / p of
+ * Section 6.2 exactly: q is the change-of-variables density of a normalizing
+ * flow on [0,1)^D.  The flow: JR_FLOW_LAYERS coupling layers; layer l
+ * conditions on x[perm[l][0 .. D/2)] and maps each x[perm[l][D/2 + j]] through
+ * a piecewise-linear CDF of JR_FLOW_BINS bins (Mueller et al., "Neural
+ * Importance Sampling", 2019) with bin masses Q = (1 - 1e-3) softmax(o) +
+ * 1e-3 / JR_FLOW_BINS from an MLP o = W3 relu(W2 relu(W1 x_A + b1) + b2) + b3
+ * (hidden width JR_FLOW_HIDDEN; bf16 tensor-core operands, FP32 accumulation).
+ *
+ * Parameter layout (float32, JR_FLOW_LAYERS consecutive layers of
+ * S = 64*16 + 64 + 64*64 + 64 + (D/2)*16*64 + (D/2)*16 floats): W1 [64][16]
+ * (columns >= D/2 zero), b1 [64], W2 [64][64], b2 [64], W3 [(D/2)*16][64]
+ * (row j*16 + b: bin b of transformed coordinate j), b3 [(D/2)*16].
+ * perm: int32 [JR_FLOW_LAYERS][D], each row a permutation of 0..D-1.
+ */
+#define JR_FLOW_LAYERS 6
+#define JR_FLOW_HIDDEN 64
+#define JR_FLOW_BINS 16
+typedef struct jr_flow jr_flow;
+
+/* Floats of the parameter array for dimension `dim` (0 if dim is not even in
+ * 2..32). */
+uint64_t jr_flow_param_count(uint32_t dim);
+
+/* Create a flow from host arrays (copied); synchronises `stream`. */
+jr_status jr_flow_create(uint32_t dim, const int32_t* perm, const float* params, void* stream, jr_flow** out);
+void jr_flow_destroy(jr_flow* flow);
+/* Replace / read the FP32 parameters (host arrays, the layout above). */
+jr_status jr_flow_set_params(jr_flow* flow, const float* params, void* stream);
+jr_status jr_flow_get_params(jr_flow* flow, float* params, void* stream);
+
+/* log q(x) for n rows of x_dev [D][n] (device, SoA) into lq_dev [n].  Async. */
+jr_status jr_flow_log_density(jr_flow* flow, const float* x_dev, uint64_t n, float* lq_dev, void* stream);
+/* In place: rows z of xz_dev [D][n] in [0,1)^D become x = T^{-1}(z); lq_dev
+ * [n] gets log q(x).  Async. */
+jr_status jr_flow_sample(jr_flow* flow, float* xz_dev, uint64_t n, float* lq_dev, void* stream);
+
+/* Attach a flow (or detach with flow = NULL) with mixture weight beta in
+ * [0, 1), and restart every chain from the new mu: each chain starts a new tour
+ * (Philox tag 3, keyed by the restart count; the restarts are not counted as
+ * regenerations, and each chain's unfinished tour is left as at the end of a
+ * run).  The flow must outlive its use; chains with a flow advance in the
+ * wavefront mode (jr_advance only).  Asynchronous. */
+jr_status jr_chains_set_flow(jr_chains* chains, const jr_flow* flow, float beta, void* stream);
+
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char* jr_last_error(void);
 /* Library version string. */

@@ -66,12 +66,15 @@ struct jr_chains {
     uint64_t steps = 0;
     int block = 128;
     uint32_t exec = JR_EXEC_AUTO;
+    uint64_t epochs = 0;  // restarts from a new regeneration distribution (Philox tag 3 key)
     ~jr_chains() {
         cudaFree(view.wf.y);
         cudaFree(view.wf.par);
         cudaFree(view.wf.ua);
         cudaFree(view.wf.path);
         cudaFree(view.wf.hit);
+        cudaFree(view.wf.uy);
+        cudaFree(view.wf.fq);
         cudaFree(view.wf.queue);
         cudaFree(view.wf.qcount);
         cudaFree(view.x);
@@ -228,7 +231,8 @@ static jr_status ensure_wavefront(jr_chains* c, cudaStream_t st) {
         (e = dev_alloc(&w.ua, n)) != cudaSuccess || (e = dev_alloc(&w.path, 3 * n)) != cudaSuccess ||
         (e = dev_alloc(&w.hit, n)) != cudaSuccess ||
         (e = dev_alloc(&w.queue, 2 * n)) != cudaSuccess ||
-        (e = dev_alloc(&w.qcount, 2 * (kMaxDepth + 2))) != cudaSuccess ||
+        (e = dev_alloc(&w.qcount, kQCount)) != cudaSuccess || (e = dev_alloc(&w.uy, n)) != cudaSuccess ||
+        (e = dev_alloc(&w.fq, 2 * n)) != cudaSuccess ||
         (e = cudaMemsetAsync(w.par, 0, n, st)) != cudaSuccess) {
         cudaFree(w.y);
         cudaFree(w.par);
@@ -237,6 +241,8 @@ static jr_status ensure_wavefront(jr_chains* c, cudaStream_t st) {
         cudaFree(w.hit);
         cudaFree(w.queue);
         cudaFree(w.qcount);
+        cudaFree(w.uy);
+        cudaFree(w.fq);
         w = WaveView{};
         return cuda_fail(e, "jr_advance (wavefront buffers)");
     }
@@ -249,7 +255,10 @@ static jr_status advance_impl(jr_chains* c, uint32_t n_steps, uint8_t* f, float*
     if (n_steps == 0) return JR_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const bool plain = !f && !dt && !pix && !work;
-    const bool wave = plain && (c->exec == JR_EXEC_WAVEFRONT ||
+    const bool has_flow = c->view.flow.D != 0;
+    if (has_flow && !plain)
+        return fail(JR_ERR_STATE, std::string(who) + ": traced and counted advances do not run with a flow attached");
+    const bool wave = plain && (has_flow || c->exec == JR_EXEC_WAVEFRONT ||
                                 (c->exec == JR_EXEC_AUTO && c->view.n >= kWavefrontMinChains));
     if (wave) {
         jr_status a = ensure_wavefront(c, st);
@@ -278,6 +287,8 @@ jr_status jr_advance_static(jr_chains* chains, uint32_t n_steps, void* stream) {
         return fail(JR_ERR_INVALID_ARG, "jr_advance_static: " + std::to_string(chains->view.n) +
                                             " chains exceed the fixed scratch of " +
                                             std::to_string(kStaticMaxChains) + " chains; use jr_advance");
+    if (chains->view.flow.D != 0)
+        return fail(JR_ERR_STATE, "jr_advance_static: chains with a flow attached advance with jr_advance");
     if (n_steps == 0) return JR_OK;
     cudaStream_t st = (cudaStream_t)stream;
     JR_CUDA(launch_wavefront_static(chains->scene->view, chains->view, chains->steps, n_steps, st),
@@ -572,6 +583,10 @@ jr_status jr_batch_create(jr_chains* const* sets, uint32_t n_sets, void* stream,
                 delete b;
                 return fail(JR_ERR_INVALID_ARG, "jr_batch_create: a chain set appears twice");
             }
+        if (c->view.flow.D != 0) {
+            delete b;
+            return fail(JR_ERR_STATE, "jr_batch_create: a chain set with a flow attached cannot join a batch");
+        }
         h[k].s = c->scene->view;
         h[k].c = c->view;
         h[k].step = c->steps;
@@ -701,6 +716,142 @@ jr_status jr_batch_autotune(jr_batch* b, uint32_t probe_steps, void* stream, jr_
     r = build_items(b, (int)rep.best_block, st);
     if (r != JR_OK) return r;
     *out = rep;
+    return JR_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// The learned regeneration flow (jr_flow.cu): parameters, evaluation, and the
+// attachment to a chain set.
+struct jr_flow {
+    uint32_t D = 0, A = 0, AK = 0;
+    uint8_t* perm = nullptr;       // [kFL][D]
+    float* master = nullptr;       // [kFL][S] FP32, the documented layout
+    __nv_bfloat16* wb = nullptr;   // packed bf16 weights
+    float* bias = nullptr;         // packed FP32 biases
+    float* adam_m = nullptr;       // optimiser moments [kFL][S]
+    float* adam_v = nullptr;
+    float* grad = nullptr;         // [kFL][S] gradient accumulator
+    uint64_t adam_t = 0;
+    FlowView view(float beta) const {
+        FlowView f;
+        f.D = D;
+        f.A = A;
+        f.AK = AK;
+        f.perm = perm;
+        f.wb = wb;
+        f.bias = bias;
+        f.beta = beta;
+        return f;
+    }
+    ~jr_flow() {
+        cudaFree(perm);
+        cudaFree(master);
+        cudaFree(wb);
+        cudaFree(bias);
+        cudaFree(adam_m);
+        cudaFree(adam_v);
+        cudaFree(grad);
+    }
+};
+
+extern "C" {
+
+uint64_t jr_flow_param_count(uint32_t dim) {
+    if (dim < 2 || dim > (uint32_t)kMaxDim || dim % 2) return 0;
+    return (uint64_t)kFL * flow_layer_floats(dim);
+}
+
+jr_status jr_flow_create(uint32_t dim, const int32_t* perm, const float* params, void* stream, jr_flow** out) {
+    if (!perm || !params || !out) return fail(JR_ERR_INVALID_ARG, "jr_flow_create: null argument");
+    if (dim < 2 || dim > (uint32_t)kMaxDim || dim % 2)
+        return fail(JR_ERR_INVALID_ARG, "jr_flow_create: dim must be even, 2..32");
+    std::vector<uint8_t> pm((size_t)kFL * dim);
+    for (int l = 0; l < kFL; ++l) {
+        std::vector<int> seen(dim, 0);
+        for (uint32_t d = 0; d < dim; ++d) {
+            const int32_t v = perm[l * dim + d];
+            if (v < 0 || (uint32_t)v >= dim || seen[v]++)
+                return fail(JR_ERR_INVALID_ARG, "jr_flow_create: perm[l] must be a permutation of 0..dim-1");
+            pm[l * dim + d] = (uint8_t)v;
+        }
+    }
+    jr_flow* f = new (std::nothrow) jr_flow();
+    if (!f) return fail(JR_ERR_OOM, "jr_flow_create: host allocation failed");
+    f->D = dim;
+    f->A = dim / 2;
+    f->AK = f->A * kFK;
+    const size_t S = flow_layer_floats(dim), P = (size_t)kFL * S;
+    const size_t nwb = (size_t)kFL * (kFH * kFS1 + kFH * kFS2 + (size_t)f->AK * kFS2);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if ((e = dev_alloc(&f->perm, pm.size())) != cudaSuccess || (e = dev_alloc(&f->master, P)) != cudaSuccess ||
+        (e = dev_alloc(&f->wb, nwb)) != cudaSuccess ||
+        (e = dev_alloc(&f->bias, (size_t)kFL * (2 * kFH + f->AK))) != cudaSuccess ||
+        (e = cudaMemcpyAsync(f->perm, pm.data(), pm.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(f->master, params, sizeof(float) * P, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = launch_flow_pack(f->master, f->wb, f->bias, f->AK, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+        delete f;
+        return cuda_fail(e, "jr_flow_create");
+    }
+    *out = f;
+    return JR_OK;
+}
+
+void jr_flow_destroy(jr_flow* flow) { delete flow; }
+
+jr_status jr_flow_set_params(jr_flow* f, const float* params, void* stream) {
+    if (!f || !params) return fail(JR_ERR_INVALID_ARG, "jr_flow_set_params: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    JR_CUDA(cudaMemcpyAsync(f->master, params, sizeof(float) * kFL * flow_layer_floats(f->D), cudaMemcpyHostToDevice,
+                            st),
+            "jr_flow_set_params");
+    JR_CUDA(launch_flow_pack(f->master, f->wb, f->bias, f->AK, st), "jr_flow_set_params");
+    JR_CUDA(cudaStreamSynchronize(st), "jr_flow_set_params");
+    return JR_OK;
+}
+
+jr_status jr_flow_get_params(jr_flow* f, float* params, void* stream) {
+    if (!f || !params) return fail(JR_ERR_INVALID_ARG, "jr_flow_get_params: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    JR_CUDA(cudaMemcpyAsync(params, f->master, sizeof(float) * kFL * flow_layer_floats(f->D), cudaMemcpyDeviceToHost,
+                            st),
+            "jr_flow_get_params");
+    JR_CUDA(cudaStreamSynchronize(st), "jr_flow_get_params");
+    return JR_OK;
+}
+
+jr_status jr_flow_log_density(jr_flow* f, const float* x_dev, uint64_t n, float* lq_dev, void* stream) {
+    if (!f || (n > 0 && (!x_dev || !lq_dev))) return fail(JR_ERR_INVALID_ARG, "jr_flow_log_density: null argument");
+    if (n >= (1ull << 32)) return fail(JR_ERR_INVALID_ARG, "jr_flow_log_density: n must be below 2^32");
+    JR_CUDA(launch_flow(f->view(0.f), false, nullptr, const_cast<float*>(x_dev), nullptr, nullptr, n, nullptr,
+                        nullptr, (uint32_t)n, nullptr, nullptr, lq_dev, (cudaStream_t)stream),
+            "jr_flow_log_density");
+    return JR_OK;
+}
+
+jr_status jr_flow_sample(jr_flow* f, float* xz_dev, uint64_t n, float* lq_dev, void* stream) {
+    if (!f || (n > 0 && (!xz_dev || !lq_dev))) return fail(JR_ERR_INVALID_ARG, "jr_flow_sample: null argument");
+    if (n >= (1ull << 32)) return fail(JR_ERR_INVALID_ARG, "jr_flow_sample: n must be below 2^32");
+    JR_CUDA(launch_flow(f->view(0.f), true, nullptr, xz_dev, nullptr, nullptr, n, nullptr, nullptr, (uint32_t)n,
+                        nullptr, nullptr, lq_dev, (cudaStream_t)stream),
+            "jr_flow_sample");
+    return JR_OK;
+}
+
+jr_status jr_chains_set_flow(jr_chains* c, const jr_flow* f, float beta, void* stream) {
+    if (!c) return fail(JR_ERR_INVALID_ARG, "jr_chains_set_flow: null chains");
+    if (f && f->D != c->view.dim) return fail(JR_ERR_INVALID_ARG, "jr_chains_set_flow: flow and chain dimensions differ");
+    if (f && !(beta >= 0.f && beta < 1.f))
+        return fail(JR_ERR_INVALID_ARG, "jr_chains_set_flow: beta must be in [0, 1)");
+    cudaStream_t st = (cudaStream_t)stream;
+    jr_status a = ensure_wavefront(c, st);
+    if (a != JR_OK) return a;
+    c->view.flow = f ? f->view(beta) : FlowView{};
+    c->epochs += 1;
+    JR_CUDA(launch_wavefront_restart(c->scene->view, c->view, c->epochs, st), "jr_chains_set_flow");
     return JR_OK;
 }
 

@@ -1,0 +1,358 @@
+// The learned regeneration flow on the tensor cores (sm_103a).
+//
+// Not in the paper: the library's own regeneration distribution
+//   mu = beta mu_flow + (1 - beta) uniform,   u = beta q + (1 - beta),
+// so the killing rate k = c~ u / p (Section 6.2) keeps an exact density.  The
+// flow has L coupling layers on [0,1)^D; layer l conditions on x[perm[l][:A]]
+// (A = D/2) and moves each x[perm[l][A + j]] through a piecewise-linear CDF of
+// K bins whose masses come from an MLP (2 hidden layers of 64, ReLU):
+//   Q_j = (1 - E) softmax(o_j) + E / K,  density factor K Q_j[bin],
+// the piecewise-linear coupling of Mueller et al. ("Neural Importance
+// Sampling", 2019).  The MLP GEMMs run as mma.sync m16n8k16 with bf16
+// operands and FP32 accumulation; everything else is FP32.
+//
+// One CTA of 128 threads works on tiles of 64 rows (4 warps x 16 rows).  Per
+// layer it stages the bf16 weights in shared memory; each warp runs the three
+// GEMMs of its 16 rows; the 64-column chunks of logits go through shared
+// memory to the per-coordinate softmax / bin / CDF step.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/jr.h"
+#include "jr_device.cuh"
+#include "jr_internal.h"
+
+namespace jr {
+namespace {
+
+constexpr int kRows = 64;                 // rows per tile
+constexpr int kXs = 33;                   // row stride of the state tile (floats)
+constexpr int kLs = 65;                   // row stride of the logits chunk (floats)
+
+struct FlowSmem {
+    float x[kRows * kXs];
+    float lq[kRows];
+    float lg[kRows * kLs];
+    float b1[kFH], b2[kFH], b3[kFMaxAK];
+    uint32_t row_idx[kRows];
+    __nv_bfloat16 xa[kRows * kFS1];
+    __nv_bfloat16 h1[kRows * kFS2];
+    __nv_bfloat16 h2[kRows * kFS2];
+    __nv_bfloat16 w1[kFH * kFS1];
+    __nv_bfloat16 w2[kFH * kFS2];
+    __nv_bfloat16 w3[kFMaxAK * kFS2];
+};
+
+__device__ __forceinline__ uint32_t ld_b32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// D[16x8] += A[16x16] (row-major) * B[16x8] (col-major), bf16 in, FP32 accumulate.
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// out[16 x (8 nt)] for this warp's 16 rows: in [rows][kin] (row stride sin) times
+// W^T with W [N][kin] (row stride sw), n-tiles n0 .. n0 + nt.
+template <int kNT>
+__device__ __forceinline__ void warp_gemm(float (&acc)[kNT][4], const __nv_bfloat16* in, int sin, int row0,
+                                          const __nv_bfloat16* W, int sw, int n0, int kin, int nt_valid) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int q = 0; q < kNT; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+    for (int k0 = 0; k0 < kin; k0 += 16) {
+        const __nv_bfloat16* ar = in + (row0 + g) * sin + k0 + 2 * t;
+        const uint32_t a0 = ld_b32(ar), a1 = ld_b32(ar + 8 * sin), a2 = ld_b32(ar + 8), a3 = ld_b32(ar + 8 * sin + 8);
+#pragma unroll
+        for (int q = 0; q < kNT; ++q) {
+            if (q < nt_valid) {
+                const __nv_bfloat16* br = W + (n0 + 8 * q + g) * sw + k0 + 2 * t;
+                mma_bf16(acc[q], a0, a1, a2, a3, ld_b32(br), ld_b32(br + 8));
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ const __nv_bfloat16* layer_w(const FlowView& f, int l) {
+    return f.wb + (size_t)l * (kFH * kFS1 + kFH * kFS2 + (size_t)f.AK * kFS2);
+}
+__device__ __forceinline__ const float* layer_b(const FlowView& f, int l) {
+    return f.bias + (size_t)l * (2 * kFH + f.AK);
+}
+
+// Stage the bf16 weights and FP32 biases of layer l (16-byte copies).
+__device__ __forceinline__ void load_layer(const FlowView& f, int l, FlowSmem& sm) {
+    const __nv_bfloat16* w = layer_w(f, l);
+    const int n1 = kFH * kFS1, n2 = kFH * kFS2, n3 = f.AK * kFS2;
+    const uint4* src = reinterpret_cast<const uint4*>(w);
+    for (int e = threadIdx.x; e < n1 / 8; e += blockDim.x) reinterpret_cast<uint4*>(sm.w1)[e] = src[e];
+    src = reinterpret_cast<const uint4*>(w + n1);
+    for (int e = threadIdx.x; e < n2 / 8; e += blockDim.x) reinterpret_cast<uint4*>(sm.w2)[e] = src[e];
+    src = reinterpret_cast<const uint4*>(w + n1 + n2);
+    for (int e = threadIdx.x; e < n3 / 8; e += blockDim.x) reinterpret_cast<uint4*>(sm.w3)[e] = src[e];
+    const float* b = layer_b(f, l);
+    for (int e = threadIdx.x; e < 2 * kFH + f.AK; e += blockDim.x) {
+        const float v = b[e];
+        if (e < kFH) sm.b1[e] = v;
+        else if (e < 2 * kFH) sm.b2[e - kFH] = v;
+        else sm.b3[e - 2 * kFH] = v;
+    }
+}
+
+// Softmax bin masses of coordinate chunk column c0 (16 logits) of row r.
+__device__ __forceinline__ void bin_masses(const float* lg, float (&Q)[kFK]) {
+    float m = lg[0];
+#pragma unroll
+    for (int k = 1; k < kFK; ++k) m = fmaxf(m, lg[k]);
+    float S = 0.f;
+#pragma unroll
+    for (int k = 0; k < kFK; ++k) {
+        Q[k] = __expf(lg[k] - m);
+        S += Q[k];
+    }
+    const float sc = (1.0f - kFE) / S;
+#pragma unroll
+    for (int k = 0; k < kFK; ++k) Q[k] = Q[k] * sc + kFE / kFK;
+}
+
+// One coupling layer on this CTA's tile (all threads call).
+template <bool kSample>
+__device__ __forceinline__ void coupling_layer(const FlowView& f, int l, FlowSmem& sm) {
+    const int A = (int)f.A, D = (int)f.D;
+    const uint8_t* pm = f.perm + l * D;
+    __syncthreads();
+    load_layer(f, l, sm);
+    for (int e = threadIdx.x; e < kRows * kFAP; e += blockDim.x) {
+        const int r = e / kFAP, c = e % kFAP;
+        sm.xa[r * kFS1 + c] = __float2bfloat16_rn(c < A ? sm.x[r * kXs + pm[c]] : 0.0f);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int row0 = 16 * warp;
+    {   // h1 = relu(W1 xa + b1)
+        float acc[8][4];
+        warp_gemm<8>(acc, sm.xa, kFS1, row0, sm.w1, kFS1, 0, kFAP, 8);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int c = 8 * q + 2 * t;
+            __nv_bfloat16* o0 = sm.h1 + (row0 + g) * kFS2 + c;
+            __nv_bfloat16* o1 = sm.h1 + (row0 + g + 8) * kFS2 + c;
+            o0[0] = __float2bfloat16_rn(fmaxf(acc[q][0] + sm.b1[c], 0.f));
+            o0[1] = __float2bfloat16_rn(fmaxf(acc[q][1] + sm.b1[c + 1], 0.f));
+            o1[0] = __float2bfloat16_rn(fmaxf(acc[q][2] + sm.b1[c], 0.f));
+            o1[1] = __float2bfloat16_rn(fmaxf(acc[q][3] + sm.b1[c + 1], 0.f));
+        }
+    }
+    __syncwarp();
+    {   // h2 = relu(W2 h1 + b2)
+        float acc[8][4];
+        warp_gemm<8>(acc, sm.h1, kFS2, row0, sm.w2, kFS2, 0, kFH, 8);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int c = 8 * q + 2 * t;
+            __nv_bfloat16* o0 = sm.h2 + (row0 + g) * kFS2 + c;
+            __nv_bfloat16* o1 = sm.h2 + (row0 + g + 8) * kFS2 + c;
+            o0[0] = __float2bfloat16_rn(fmaxf(acc[q][0] + sm.b2[c], 0.f));
+            o0[1] = __float2bfloat16_rn(fmaxf(acc[q][1] + sm.b2[c + 1], 0.f));
+            o1[0] = __float2bfloat16_rn(fmaxf(acc[q][2] + sm.b2[c], 0.f));
+            o1[1] = __float2bfloat16_rn(fmaxf(acc[q][3] + sm.b2[c + 1], 0.f));
+        }
+    }
+    __syncwarp();
+    // logits o = W3 h2 + b3, 64 columns (4 coordinates) at a time
+    for (int c0 = 0; c0 < (int)f.AK; c0 += 64) {
+        const int ncol = min(64, (int)f.AK - c0);
+        float acc[8][4];
+        warp_gemm<8>(acc, sm.h2, kFS2, row0, sm.w3, kFS2, c0, kFH, ncol / 8);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (8 * q < ncol) {
+                const int c = 8 * q + 2 * t;
+                float* o0 = sm.lg + (row0 + g) * kLs + c;
+                float* o1 = sm.lg + (row0 + g + 8) * kLs + c;
+                o0[0] = acc[q][0] + sm.b3[c0 + c];
+                o0[1] = acc[q][1] + sm.b3[c0 + c + 1];
+                o1[0] = acc[q][2] + sm.b3[c0 + c];
+                o1[1] = acc[q][3] + sm.b3[c0 + c + 1];
+            }
+        }
+        __syncwarp();
+        // lane -> row row0 + (lane & 15), coordinates 2 (lane >> 4) and + 1 of the chunk
+        const int r = row0 + (lane & 15);
+        float dlq = 0.f;
+        for (int jj = 2 * (lane >> 4); jj < 2 * (lane >> 4) + 2; ++jj) {
+            if (16 * jj >= ncol) break;
+            float Q[kFK];
+            bin_masses(sm.lg + r * kLs + 16 * jj, Q);
+            const int cb = pm[A + c0 / 16 + jj];
+            float* xv = sm.x + r * kXs + cb;
+            if (!kSample) {  // density direction: t -> CDF(t)
+                const float tt = *xv;
+                const int b = min((int)(tt * (float)kFK), kFK - 1);
+                float lo = 0.f, qb = Q[0];
+#pragma unroll
+                for (int k = 0; k < kFK; ++k) {
+                    if (k < b) lo += Q[k];
+                    if (k == b) qb = Q[k];
+                }
+                *xv = lo + (tt * (float)kFK - (float)b) * qb;
+                dlq += __logf((float)kFK * qb);
+            } else {         // sampling direction: c -> CDF^{-1}(c)
+                const float cc = *xv;
+                float cum = 0.f, lo = 0.f, qb = Q[0];
+                int b = 0;
+#pragma unroll
+                for (int k = 0; k < kFK; ++k) {
+                    cum += Q[k];
+                    if (cum <= cc) b = k + 1;
+                }
+                b = min(b, kFK - 1);
+#pragma unroll
+                for (int k = 0; k < kFK; ++k) {
+                    if (k < b) lo += Q[k];
+                    if (k == b) qb = Q[k];
+                }
+                const float xs = ((float)b + (cc - lo) / qb) * (1.0f / (float)kFK);
+                *xv = fminf(fmaxf(xs, 0.0f), 0.99999994f);
+                dlq += __logf((float)kFK * qb);
+            }
+        }
+        dlq += __shfl_down_sync(0xffffffffu, dlq, 16);
+        if (lane < 16) sm.lq[r] += dlq;
+        __syncwarp();
+    }
+}
+
+// Rows: chains idx[j] (or j when idx is null) for j < *count (or n_rows).
+// Row i lives in SoA buffer [D][n] bufA, or -- when par is given -- in bufA if
+// par[i] is 1 and bufB otherwise (the wavefront's candidate buffer).  Density:
+// u_out[i] = beta q + 1 - beta.  Sample: the row is replaced by T^{-1}(row),
+// u_out as above, and the camera ray of the new state goes to path (if given).
+template <bool kSample>
+__global__ void __launch_bounds__(128) flow_kernel(FlowView f, SceneView s, float* bufA, float* bufB,
+                                                   const uint8_t* par, uint64_t n, const uint32_t* idx,
+                                                   const unsigned int* count_dev, uint32_t n_rows, float* u_out,
+                                                   float4* path, float* lq_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FlowSmem& sm = *reinterpret_cast<FlowSmem*>(smem_raw);
+    const uint32_t count = count_dev ? *count_dev : n_rows;
+    const int D = (int)f.D;
+    auto row_buf = [&](uint32_t i) -> float* { return (par && !par[i]) ? bufB : bufA; };
+    for (uint32_t tile = blockIdx.x; tile * kRows < count; tile += gridDim.x) {
+        __syncthreads();
+        for (int r = threadIdx.x; r < kRows; r += blockDim.x) {
+            const uint32_t j = tile * kRows + r;
+            sm.row_idx[r] = j < count ? (idx ? idx[j] : j) : 0xffffffffu;
+            sm.lq[r] = 0.f;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < kRows * D; e += blockDim.x) {
+            const int r = e / D, d = e % D;
+            const uint32_t i = sm.row_idx[r];
+            sm.x[r * kXs + d] = i != 0xffffffffu ? row_buf(i)[(uint64_t)d * n + i] : 0.5f;
+        }
+        if (!kSample)
+            for (int l = 0; l < kFL; ++l) coupling_layer<false>(f, l, sm);
+        else
+            for (int l = kFL - 1; l >= 0; --l) coupling_layer<true>(f, l, sm);
+        __syncthreads();
+        if (kSample)
+            for (int e = threadIdx.x; e < kRows * D; e += blockDim.x) {
+                const int r = e / D, d = e % D;
+                const uint32_t i = sm.row_idx[r];
+                if (i != 0xffffffffu) row_buf(i)[(uint64_t)d * n + i] = sm.x[r * kXs + d];
+            }
+        for (int r = threadIdx.x; r < kRows; r += blockDim.x) {
+            const uint32_t i = sm.row_idx[r];
+            if (i == 0xffffffffu) continue;
+            const float lq = sm.lq[r];
+            if (u_out) u_out[i] = f.beta * __expf(lq) + (1.0f - f.beta);
+            if (lq_out) lq_out[i] = lq;
+            if (kSample && path) {
+                float3 o, d;
+                camera_ray(s, sm.x[r * kXs], sm.x[r * kXs + 1], o, d);
+                path[3 * (uint64_t)i] = make_float4(o.x, o.y, o.z, d.x);
+                path[3 * (uint64_t)i + 1] = make_float4(d.y, d.z, 1.f, 1.f);
+                path[3 * (uint64_t)i + 2] = make_float4(1.f, 0.f, 0.f, 0.f);
+            }
+        }
+    }
+}
+
+// FP32 master parameters (the documented layout: per layer W1 [64][16], b1,
+// W2 [64][64], b2, W3 [AK][64], b3) -> padded bf16 weights + FP32 biases.
+__global__ void pack_kernel(const float* master, __nv_bfloat16* wb, float* bias, uint32_t AK) {
+    const int l = blockIdx.y;
+    const size_t S = (size_t)kFH * kFAP + kFH + kFH * kFH + kFH + (size_t)AK * kFH + AK;
+    const float* m = master + l * S;
+    __nv_bfloat16* w = wb + (size_t)l * (kFH * kFS1 + kFH * kFS2 + (size_t)AK * kFS2);
+    float* b = bias + (size_t)l * (2 * kFH + AK);
+    const uint32_t tot = kFH * kFS1 + kFH * kFS2 + AK * kFS2;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
+        float v = 0.f;
+        if (e < (uint32_t)(kFH * kFS1)) {
+            const uint32_t r = e / kFS1, c = e % kFS1;
+            if (c < (uint32_t)kFAP) v = m[r * kFAP + c];
+        } else if (e < (uint32_t)(kFH * kFS1 + kFH * kFS2)) {
+            const uint32_t q = e - kFH * kFS1, r = q / kFS2, c = q % kFS2;
+            if (c < (uint32_t)kFH) v = m[kFH * kFAP + kFH + r * kFH + c];
+        } else {
+            const uint32_t q = e - kFH * kFS1 - kFH * kFS2, r = q / kFS2, c = q % kFS2;
+            if (c < (uint32_t)kFH) v = m[kFH * kFAP + kFH + kFH * kFH + kFH + r * kFH + c];
+        }
+        w[e] = __float2bfloat16_rn(v);
+    }
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * kFH + AK; e += gridDim.x * blockDim.x) {
+        if (e < (uint32_t)kFH) b[e] = m[kFH * kFAP + e];
+        else if (e < (uint32_t)(2 * kFH)) b[e] = m[kFH * kFAP + kFH + kFH * kFH + (e - kFH)];
+        else b[e] = m[kFH * kFAP + kFH + kFH * kFH + kFH + (size_t)AK * kFH + (e - 2 * kFH)];
+    }
+}
+
+}  // namespace
+
+size_t flow_smem_bytes() { return sizeof(FlowSmem); }
+
+cudaError_t launch_flow_pack(const float* master, __nv_bfloat16* wb, float* bias, uint32_t AK, cudaStream_t st) {
+    pack_kernel<<<dim3(16, kFL), 256, 0, st>>>(master, wb, bias, AK);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flow(const FlowView& f, bool sample, const SceneView* s, float* bufA, float* bufB,
+                        const uint8_t* par, uint64_t n, const uint32_t* idx, const unsigned int* count_dev,
+                        uint32_t n_rows, float* u_out, float4* path, float* lq_out, cudaStream_t st) {
+    static int grid = 0;
+    const size_t shm = sizeof(FlowSmem);
+    if (grid == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaError_t e;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(flow_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)) !=
+                cudaSuccess ||
+            (e = cudaFuncSetAttribute(flow_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)) !=
+                cudaSuccess)
+            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, flow_kernel<false>, 128, shm)) != cudaSuccess)
+            return e;
+        grid = sms * (per > 0 ? per : 1);
+    }
+    SceneView sv{};
+    if (s) sv = *s;
+    unsigned g = (unsigned)grid;
+    if (!count_dev) g = (unsigned)std::min<uint64_t>(g, (n_rows + kRows - 1) / kRows);
+    if (g == 0) return cudaSuccess;
+    if (sample)
+        flow_kernel<true><<<g, 128, shm, st>>>(f, sv, bufA, bufB, par, n, idx, count_dev, n_rows, u_out, path,
+                                               lq_out);
+    else
+        flow_kernel<false><<<g, 128, shm, st>>>(f, sv, bufA, bufB, par, n, idx, count_dev, n_rows, u_out, path,
+                                                lq_out);
+    return cudaGetLastError();
+}
+
+}  // namespace jr

@@ -1,6 +1,7 @@
 // Internal layout shared by the host runtime (jr_api.cu, bvh_build.cpp) and the
 // kernels (jr_kernels.cu).  Not part of the C ABI.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -16,7 +17,7 @@ constexpr int kMaxBvhDepth = kStackSize - 2;
 constexpr int kLeafMax = 8;                 // triangles per leaf (encoded count-1 in 3 bits)
 constexpr uint32_t kNodeVisitBudget = 1u << 16;  // per ray; exceeding it is a watchdog event
 
-constexpr uint32_t kTagStep = 0, kTagInit = 1, kTagPt = 2;
+constexpr uint32_t kTagStep = 0, kTagInit = 1, kTagPt = 2, kTagRestart = 3;
 constexpr uint64_t kWavefrontMinChains = 1u << 16;  // JR_EXEC_AUTO picks the wavefront from here up
 
 // BVH node, 64 bytes: both children's boxes, Aila & Laine style.
@@ -57,6 +58,20 @@ struct SceneView {
     float cam[12];
 };
 
+// The regeneration flow (jr_flow.cu): L coupling layers, MLP of 2 x 64 hidden
+// units, K bins, conditioner width padded to kFAP; bf16 weight rows padded to
+// strides kFS1 / kFS2 (conflict-free fragment loads).
+constexpr int kFL = 6, kFH = 64, kFK = 16, kFAP = 16, kFS1 = 24, kFS2 = 72, kFMaxAK = 256;
+constexpr float kFE = 1e-3f;  // bin-mass floor: Q = (1 - E) softmax + E / K
+
+struct FlowView {
+    uint32_t D = 0, A = 0, AK = 0;      // AK = A * K logits per layer
+    const uint8_t* perm = nullptr;      // [kFL][D]
+    const __nv_bfloat16* wb = nullptr;  // per layer: W1 [64][kFS1], W2 [64][kFS2], W3 [AK][kFS2]
+    const float* bias = nullptr;        // per layer: b1 [64], b2 [64], b3 [AK]
+    float beta = 0.f;                   // mu = beta mu_flow + (1 - beta) uniform
+};
+
 // Buffers of the wavefront execution mode (allocated on first use).
 struct WaveView {
     float* y = nullptr;           // [D][n] second state buffer
@@ -65,8 +80,11 @@ struct WaveView {
     float4* path = nullptr;       // [n][3] live path record (o, d, T, F)
     float2* hit = nullptr;        // [n] closest hit of the path's current ray (t, record index bits)
     uint32_t* queue = nullptr;    // [2][n] live-path queues (ping-pong)
-    unsigned int* qcount = nullptr;  // [2 (kMaxDepth + 2)] queue lengths, then fetch cursors
+    unsigned int* qcount = nullptr;  // [kQCount]: queue lengths, fetch cursors, flow queue lengths
+    float* uy = nullptr;          // [n] u of the step's candidate (with a flow)
+    uint32_t* fq = nullptr;       // [2][n] candidates for the flow: density rows, then sampling rows
 };
+constexpr int kQFlowDensity = 2 * (kMaxDepth + 2), kQFlowSample = kQFlowDensity + 1, kQCount = kQFlowSample + 1;
 
 struct ChainView {
     float* x;        // [D][n] PSS coordinates
@@ -82,6 +100,7 @@ struct ChainView {
     uint64_t seed;
     float c_tilde, sigma;
     WaveView wf;
+    FlowView flow;   // flow.D == 0: uniform regeneration (u = 1)
 };
 
 // A chain set of a batch as the batched kernels see it; `step` is the set's
@@ -132,6 +151,24 @@ constexpr size_t kStaticScratchBytes =
     sizeof(uint8_t) * kStaticMaxChains + 256;  // = 12 910 848 bytes (every piece but the counters is a multiple of 256)
 cudaError_t launch_wavefront_static(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
                                     cudaStream_t st);
+// Restart every chain from the current regeneration distribution (new tours;
+// not counted as regenerations).  `epoch` keys the Philox stream (tag 3).
+cudaError_t launch_wavefront_restart(const SceneView& s, const ChainView& c, uint64_t epoch, cudaStream_t st);
+
+// jr_flow.cu: flow rows through the tensor cores.  Density: u_out[i] = beta q
+// + 1 - beta (and lq_out[i] = log q) for rows i of buf [D][n]; sample: buf
+// rows replaced by T^{-1}(buf), the camera ray of the new state written to
+// path (if not null).  Rows are idx[j], j < *count_dev (device) or n_rows.
+cudaError_t launch_flow(const FlowView& f, bool sample, const SceneView* s, float* bufA, float* bufB,
+                        const uint8_t* par, uint64_t n, const uint32_t* idx, const unsigned int* count_dev,
+                        uint32_t n_rows, float* u_out, float4* path, float* lq_out, cudaStream_t st);
+size_t flow_smem_bytes();
+// FP32 master parameters [kFL][S] -> padded bf16 weights and biases.
+cudaError_t launch_flow_pack(const float* master, __nv_bfloat16* wb, float* bias, uint32_t AK, cudaStream_t st);
+inline size_t flow_layer_floats(uint32_t D) {
+    const size_t A = D / 2, AK = A * kFK;
+    return (size_t)kFH * kFAP + kFH + kFH * kFH + kFH + AK * kFH + AK;
+}
 cudaError_t launch_resolve(const ChainView& c, float* rgb, cudaStream_t st);
 cudaError_t launch_reeval(const SceneView& s, const ChainView& c, cudaStream_t st);
 cudaError_t launch_eval_states(const SceneView& s, uint32_t depth, float c_tilde, const float* x, uint64_t n,

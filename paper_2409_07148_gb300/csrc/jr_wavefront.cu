@@ -79,15 +79,23 @@ __device__ __forceinline__ void count_and_flush(uint32_t nJ, uint32_t nL, uint32
 
 // finish = 1: complete step `step - 1` of every chain.  begin = 1: start step
 // `step`.  With begin = 0 the launch also moves every state back into x.
+// restart = 1: the step is a restart of every chain from mu (a new tour that is
+// not a regeneration of Alg. 2: no clocks, no splat, J unchanged); `step` is
+// then the restart epoch and the stream tag is kTagRestart.
+// With a flow attached (c.flow.D > 0), a regeneration draws from the flow when
+// Ub < beta (Ub = fourth value of block 0), else uniformly; the candidates go
+// to the flow queues, whose kernels fill in u(y) (and y for flow draws).
 __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step, int finish, int begin,
-                                                      SceneView s) {
+                                                      SceneView s, int restart) {
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     const bool valid = i < c.n;
     const int D = (int)c.dim;
     const uint64_t n = c.n;
     const WaveView& w = c.wf;
+    const bool has_flow = c.flow.D != 0;
     uint32_t nJ = 0, nL = 0, nA = 0;
     unsigned status = 0;
+    bool to_density = false, to_sample = false;
     if (valid) {
         uint8_t par = w.par[i];
         float Fr = c.fpu[0 * n + i], Fg = c.fpu[1 * n + i], Fb = c.fpu[2 * n + i];
@@ -98,7 +106,9 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
             const float3 Fy = finite_or_zero(f3(pf.y, pf.z, pf.w), status);
             const float py = lum(Fy);
             bool accept;
-            if (ua >= 0.0f) {  // local branch: MH acceptance, U < min(1, p(y)/p(x))
+            if (restart) {     // a restart: the new tour's start, not a regeneration
+                accept = true;
+            } else if (ua >= 0.0f) {  // local branch: MH acceptance, U < min(1, p(y)/p(x))
                 accept = ua * p < py;
                 nL++;
                 nA += accept;
@@ -112,7 +122,7 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
                 Fg = Fy.y;
                 Fb = Fy.z;
                 p = py;
-                u = 1.0f;
+                u = has_flow ? w.uy[i] : 1.0f;
                 c.fpu[0 * n + i] = Fr;
                 c.fpu[1 * n + i] = Fg;
                 c.fpu[2 * n + i] = Fb;
@@ -124,14 +134,19 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
         float* cand = par ? c.x : w.y;
         if (begin) {
             const uint32_t chain = c.chain_offset + (uint32_t)i;
-            const uint4 r0 = draw(c.seed, kTagStep, 0, chain, step);
+            const uint32_t tag = restart ? kTagRestart : kTagStep;
+            const uint4 r0 = draw(c.seed, tag, 0, chain, step);
             const float E1 = -logf(1.0f - u01(r0.x));
             const float E2 = -logf(1.0f - u01(r0.y));
             const float Ua = u01(r0.z);
             const float t2 = p > 0.0f ? E2 * p / (c.c_tilde * u) : 0.0f;
-            const bool local = E1 < t2;  // a tie goes to the killing branch
+            const bool local = !restart && E1 < t2;  // a tie goes to the killing branch
             float dt = local ? E1 : t2;
             if (c.flags & JR_FLAG_RAO_BLACKWELL) dt = p > 0.0f ? p / (p + c.c_tilde * u) : 0.0f;
+            if (restart) dt = 0.0f;
+            const bool use_flow = has_flow && !local && u01(r0.w) < c.flow.beta;
+            to_sample = use_flow;
+            to_density = has_flow && !use_flow;
             const float x0 = cur[i], x1 = cur[n + i];
             if (dt > 0.0f && p > 0.0f) {
                 uint32_t px = min((uint32_t)((double)x0 * (double)c.width), c.width - 1);
@@ -142,7 +157,7 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
             w.ua[i] = local ? Ua : -1.0f;
             float y0 = 0.f, y1 = 0.f;
             for (int b = 0; 4 * b < D; ++b) {
-                const uint4 r = draw(c.seed, kTagStep, (uint32_t)(b + 1), chain, step);
+                const uint4 r = draw(c.seed, tag, (uint32_t)(b + 1), chain, step);
                 const uint64_t o0 = (uint64_t)(4 * b) * n + i;
                 float v0, v1, v2 = 0.f, v3 = 0.f;
                 const bool two = 4 * b + 2 < D;
@@ -175,16 +190,24 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
                     y1 = v1;
                 }
             }
-            float3 o, d;
-            camera_ray(s, y0, y1, o, d);
-            store_path(w.path, i, o, d, f3(1.f, 1.f, 1.f), f3(0.f, 0.f, 0.f));
+            if (!use_flow) {  // a flow draw gets its camera ray from the flow kernel
+                float3 o, d;
+                camera_ray(s, y0, y1, o, d);
+                store_path(w.path, i, o, d, f3(1.f, 1.f, 1.f), f3(0.f, 0.f, 0.f));
+            }
         } else if (par) {
             for (int dd = 0; dd < D; ++dd) c.x[(uint64_t)dd * n + i] = w.y[(uint64_t)dd * n + i];
             par = 0;
         }
         w.par[i] = par;
     }
-    if (begin) enqueue(valid, (uint32_t)i, w.queue, w.qcount + 0);
+    if (begin) {
+        enqueue(valid, (uint32_t)i, w.queue, w.qcount + 0);
+        if (has_flow) {
+            enqueue(to_density, (uint32_t)i, w.fq, w.qcount + kQFlowDensity);
+            enqueue(to_sample, (uint32_t)i, w.fq + n, w.qcount + kQFlowSample);
+        }
+    }
     count_and_flush(nJ, nL, nA, status, c);
 }
 
@@ -304,6 +327,17 @@ __global__ void __launch_bounds__(128) wf_shade_kernel(SceneView s, ChainView c,
 
 inline unsigned grid_for(uint64_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 
+// The flow stage of a step: u(y) of the density rows (local candidates and
+// uniform regenerations); y = T^{-1}(z) and u(y) of the flow draws.  A chain's
+// candidate lives in x when its parity byte is 1, else in y.
+cudaError_t launch_flow_candidates(const SceneView& s, const ChainView& c, cudaStream_t st) {
+    cudaError_t e = launch_flow(c.flow, false, &s, c.x, c.wf.y, c.wf.par, c.n, c.wf.fq, c.wf.qcount + kQFlowDensity,
+                                0, c.wf.uy, nullptr, nullptr, st);
+    if (e != cudaSuccess) return e;
+    return launch_flow(c.flow, true, &s, c.x, c.wf.y, c.wf.par, c.n, c.wf.fq + c.n, c.wf.qcount + kQFlowSample, 0,
+                       c.wf.uy, c.wf.path, nullptr, st);
+}
+
 }  // namespace
 
 cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
@@ -322,17 +356,44 @@ cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t st
         shade_blocks = sms * (per_sm2 > 0 ? per_sm2 : 1);
     }
     const unsigned G = grid_for(c.n, 128);
-    const size_t qbytes = sizeof(unsigned int) * 2 * (kMaxDepth + 2);
+    const bool has_flow = c.flow.D != 0;
+    const size_t qbytes = sizeof(unsigned int) * (has_flow ? kQCount : 2 * (kMaxDepth + 2));
     for (uint32_t k = 0; k < n_steps; ++k) {
         cudaError_t e = cudaMemsetAsync(c.wf.qcount, 0, qbytes, st);
         if (e != cudaSuccess) return e;
-        wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + k, k > 0, 1, s);
+        wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + k, k > 0, 1, s, 0);
+        if (has_flow && (e = launch_flow_candidates(s, c, st)) != cudaSuccess) return e;
         for (int v = 0; v <= (int)c.depth; ++v) {
             wf_trace_kernel<<<trace_blocks, 128, 0, st>>>(s, c, v);
             wf_shade_kernel<<<shade_blocks, 128, 0, st>>>(s, c, v);
         }
     }
-    wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + n_steps, n_steps > 0, 0, s);
+    wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + n_steps, n_steps > 0, 0, s, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wavefront_restart(const SceneView& s, const ChainView& c, uint64_t epoch, cudaStream_t st) {
+    cudaError_t e = launch_wavefront(s, c, 0, 0, st);  // sets up the persistent grid sizes; launches a no-op finish
+    if (e != cudaSuccess) return e;
+    const unsigned G = grid_for(c.n, 128);
+    if ((e = cudaMemsetAsync(c.wf.qcount, 0, sizeof(unsigned int) * kQCount, st)) != cudaSuccess) return e;
+    wf_step_kernel<<<G, 128, 0, st>>>(c, epoch, 0, 1, s, 1);
+    if (c.flow.D != 0 && (e = launch_flow_candidates(s, c, st)) != cudaSuccess) return e;
+    int trace_blocks = 0, shade_blocks = 0;
+    {
+        int dev = 0, sms = 0, p1 = 0, p2 = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, wf_trace_kernel, 128, 0)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, wf_shade_kernel, 128, 0)) != cudaSuccess) return e;
+        trace_blocks = sms * (p1 > 0 ? p1 : 1);
+        shade_blocks = sms * (p2 > 0 ? p2 : 1);
+    }
+    for (int v = 0; v <= (int)c.depth; ++v) {
+        wf_trace_kernel<<<trace_blocks, 128, 0, st>>>(s, c, v);
+        wf_shade_kernel<<<shade_blocks, 128, 0, st>>>(s, c, v);
+    }
+    wf_step_kernel<<<G, 128, 0, st>>>(c, epoch, 1, 0, s, 1);
     return cudaGetLastError();
 }
 

@@ -88,6 +88,14 @@ _SIGS = {
     "jr_batch_advance": [_P, _U32, _P],
     "jr_batch_advance_graph": [_P, _U32, _P],
     "jr_batch_autotune": [_P, _U32, _P, _P],
+    "jr_flow_param_count": [_U32],
+    "jr_flow_create": [_U32, _P, _P, _P, ctypes.POINTER(_P)],
+    "jr_flow_destroy": [_P],
+    "jr_flow_set_params": [_P, _P, _P],
+    "jr_flow_get_params": [_P, _P, _P],
+    "jr_flow_log_density": [_P, _P, _U64, _P, _P],
+    "jr_flow_sample": [_P, _P, _U64, _P, _P],
+    "jr_chains_set_flow": [_P, _P, ctypes.c_float, _P],
     "jr_last_error": [],
     "jr_version": [],
 }
@@ -113,6 +121,8 @@ def lib():
             L.jr_scene_destroy.restype = None
             L.jr_chains_destroy.restype = None
             L.jr_batch_destroy.restype = None
+            L.jr_flow_destroy.restype = None
+            L.jr_flow_param_count.restype = ctypes.c_uint64
             _lib = L
     return _lib
 
@@ -261,6 +271,58 @@ class Chains:
             self.close()
         except Exception:
             pass
+
+
+class Flow:
+    """The learned regeneration flow (parameters in the layout of include/jr.h)."""
+
+    def __init__(self, D, perm, params, stream=None):
+        self.D = int(D)
+        self._perm = np.ascontiguousarray(perm, np.int32)
+        p = np.ascontiguousarray(params, np.float32)
+        assert p.size == lib().jr_flow_param_count(self.D), "parameter count does not match the layout"
+        h = ctypes.c_void_p()
+        _check(lib().jr_flow_create(self.D, _hptr(self._perm), _hptr(p), _stream(stream), ctypes.byref(h)))
+        self.h = h
+
+    def set_params(self, params, stream=None):
+        p = np.ascontiguousarray(params, np.float32)
+        _check(lib().jr_flow_set_params(self.h, _hptr(p), _stream(stream)))
+
+    def get_params(self, stream=None):
+        p = np.zeros(int(lib().jr_flow_param_count(self.D)), np.float32)
+        _check(lib().jr_flow_get_params(self.h, _hptr(p), _stream(stream)))
+        return p
+
+    def log_density(self, x, stream=None):
+        """x: CUDA float32 [D, n] -> log q [n]."""
+        import torch
+        lq = torch.empty(x.shape[1], dtype=torch.float32, device=x.device)
+        _check(lib().jr_flow_log_density(self.h, _dptr(x), int(x.shape[1]), _dptr(lq), _stream(stream)))
+        return lq
+
+    def sample(self, z, stream=None):
+        """z: CUDA float32 [D, n], replaced in place by T^{-1}(z); returns log q [n]."""
+        import torch
+        lq = torch.empty(z.shape[1], dtype=torch.float32, device=z.device)
+        _check(lib().jr_flow_sample(self.h, _dptr(z), int(z.shape[1]), _dptr(lq), _stream(stream)))
+        return lq
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().jr_flow_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def set_flow(chains, flow, beta, stream=None):
+    """Attach `flow` (or None) with mixture weight beta and restart every chain."""
+    _check(lib().jr_chains_set_flow(chains.h, None if flow is None else flow.h, float(beta), _stream(stream)))
 
 
 class Batch:

@@ -1,0 +1,138 @@
+"""The regeneration flow on the GPU (tensor-core MLP) against the FP64 flow
+oracle, and Jump Restore chains with a learned mixture mu (needs a GB300).
+
+Tolerance (derived from the arithmetic): the MLP operands are bf16 on both
+sides, but the GPU accumulates in FP32 and the oracle exactly, so a bf16
+rounding of an activation can land on the other side of a rounding edge
+(relative 2^-9 steps).  Per row |log q_gpu - log q_oracle| <= 2e-3 for 99.5 %
+of rows; the rest are rows where a coordinate sits within rounding of a bin
+edge (the density jumps there).
+"""
+import numpy as np
+import pytest
+
+from oracle import flow as FL
+from oracle import learned as LR
+from oracle import oracle as O
+from paper_2409_07148_gb300 import scenes
+from paper_2409_07148_gb300.flowinit import init_flow_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def J():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2409_07148_gb300 import jr
+    jr.lib()
+    return jr
+
+
+def _flow(D, seed, sd):
+    perm, w = init_flow_params(D, seed)
+    A = D // 2
+    tail = A * 16 * 64 + A * 16
+    w[:, -tail:] = np.random.default_rng(seed + 100).normal(0.0, sd, (w.shape[0], tail)).astype(np.float32)
+    return perm, w
+
+
+@pytest.mark.parametrize("D,n", [(2, 100), (8, 10007), (18, 4096), (22, 5000), (32, 3000)])
+def test_log_density_matches_oracle(J, D, n):
+    import torch
+    perm, w = _flow(D, D, 0.1)
+    f = J.Flow(D, perm, w)
+    x = np.random.default_rng(D).random((n, D)).astype(np.float32)
+    lq = f.log_density(torch.from_numpy(np.ascontiguousarray(x.T)).cuda()).cpu().numpy()
+    lo, _ = FL.log_density(perm, w, x.astype(np.float64))
+    d = np.abs(lq - lo)
+    assert np.mean(d <= 2e-3) >= 0.995, np.sort(d)[-5:]
+    assert np.isfinite(lq).all()
+
+
+@pytest.mark.parametrize("D,n", [(8, 4099), (22, 5000)])
+def test_sampling_matches_oracle_and_inverts(J, D, n):
+    import torch
+    perm, w = _flow(D, D + 1, 0.1)
+    f = J.Flow(D, perm, w)
+    z = np.random.default_rng(D + 7).random((n, D)).astype(np.float32)
+    t = torch.from_numpy(np.ascontiguousarray(z.T)).cuda()
+    lq = f.sample(t).cpu().numpy()
+    x = t.cpu().numpy().T
+    xo, lqo = FL.sample(perm, w, z.astype(np.float64))
+    ok = np.all(np.abs(x - xo) <= 1e-4, axis=1) & (np.abs(lq - lqo) <= 2e-3)
+    assert np.mean(ok) >= 0.995
+    # GPU round trip: the density direction gives back the sampling log-density
+    lq2 = f.log_density(torch.from_numpy(np.ascontiguousarray(x.T)).cuda()).cpu().numpy()
+    assert np.mean(np.abs(lq2 - lq) <= 2e-3) >= 0.995
+
+
+def test_params_round_trip(J):
+    perm, w = _flow(10, 3, 0.2)
+    f = J.Flow(10, perm, w)
+    assert np.array_equal(f.get_params(), w.ravel())
+    w2 = w * 0.5
+    f.set_params(w2)
+    assert np.array_equal(f.get_params(), w2.ravel())
+
+
+def test_chains_with_flow_step_replay(J):
+    """One step of chains with u = beta q + 1 - beta, replayed by the oracle's
+    Alg. 2 with the FP64 flow from the GPU's own state."""
+    sc = scenes.cornell(width=16, height=16, depth=3)
+    perm, w = _flow(sc.D, 5, 0.1)
+    g = J.Scene(sc)
+    f = J.Flow(sc.D, perm, w)
+    ch = J.Chains(g, 16, 16, sc.depth, 512, seed=3, sigma=0.02)
+    J.set_flow(ch, f, 0.6)
+    ch.advance(4)
+    x, fpu = ch.get_state()
+    st = ch.stats()
+    osc = O.Scene(sc)
+    F_of = lambda xx: O.eval_states(osc, xx)[0]
+    oc = LR.LearnedChains(F_of, sc.D, 16, 16, perm, w, beta=0.6, sigma=0.02, seed=3, n_chains=512)
+    oc.x = x.T.astype(np.float64)
+    oc.F = fpu[:3].T.astype(np.float64)
+    oc.p = fpu[3].astype(np.float64)
+    oc.u = fpu[4].astype(np.float64)
+    oc.step = st["steps_per_chain"]
+    # u of the GPU state is the flow's density (up to the tolerance above)
+    u_o = FL.regen_density(perm, w, oc.x, 0.6)
+    assert np.mean(np.abs(fpu[4] - u_o) <= 2e-3 * u_o) >= 0.99
+    oc.advance(1)
+    ch.advance(1)
+    x2, fpu2 = ch.get_state()
+    dx = np.abs(x2.T - oc.x)
+    dx = np.minimum(dx, 1 - dx).max(axis=1)
+    assert np.mean(dx <= 1e-4) >= 0.97       # decisions and flow draws agree except near ties / bin edges
+    same = dx <= 1e-4
+    assert np.mean(np.abs(fpu2[4][same] - oc.u[same]) <= 3e-3 * oc.u[same]) >= 0.98
+
+
+def test_learned_mixture_image_is_unbiased(J):
+    """With a non-trivial flow (beta = 0.7) the Jump Restore image converges to
+    the same pixels as with uniform regeneration (per-pixel z over batches)."""
+    from scipy import stats
+    import torch
+    sc = scenes.cornell(width=32, height=32, depth=3)
+    perm, w = _flow(sc.D, 9, 0.1)
+    g = J.Scene(sc)
+    f = J.Flow(sc.D, perm, w)
+    a, b = [], []
+    for k in range(16):
+        c1 = J.Chains(g, 32, 32, sc.depth, 16384, seed=1, chain_offset=16384 * k)
+        J.set_flow(c1, f, 0.7)
+        c1.advance(300)
+        a.append(c1.resolve())
+        c2 = J.Chains(g, 32, 32, sc.depth, 16384, seed=2, chain_offset=16384 * k)
+        c2.set_execution("wave")
+        c2.advance(300)
+        b.append(c2.resolve())
+        assert c1.stats()["status_word"] == 0
+    a, b = np.array(a, np.float64), np.array(b, np.float64)
+    va, vb = a.var(0, ddof=1) / len(a), b.var(0, ddof=1) / len(b)
+    ok = (va + vb) > 0
+    t = (a.mean(0) - b.mean(0))[ok] / np.sqrt((va + vb)[ok])
+    z = np.sign(t) * stats.norm.isf(stats.t.sf(np.abs(t), 2 * len(a) - 2))
+    assert np.mean(np.abs(z) > 4) <= 2e-3
+    assert 0.6 < np.mean(z ** 2) < 1.6
