@@ -340,13 +340,27 @@ jr_status jr_flow_log_density(jr_flow* flow, const float* x_dev, uint64_t n, flo
  * [n] gets log q(x).  Async. */
 jr_status jr_flow_sample(jr_flow* flow, float* xz_dev, uint64_t n, float* lq_dev, void* stream);
 
+/* Complete every chain's current tour, then start every chain on a new tour.
+ * The estimator of Section 6.3 divides by J, the number of completed tours;
+ * a run stopped after a fixed number of steps leaves one unfinished tour per
+ * chain whose splats are not matched in J (a bias of order chains / J whose
+ * size depends on mu).  Here the chains still inside a tour keep stepping
+ * (regular Alg. 2 steps, counted in the step index) and a kill ends the tour
+ * and the chain, for at most max_steps steps; `remaining` (may be NULL) gets
+ * the chains whose tour is still open after them (0: every tour completed, and
+ * the accumulated image is the completed-tour estimator).  Then each chain
+ * starts a new tour from mu (Philox tag 3, keyed by a restart count; not a
+ * regeneration).  Wavefront mode; synchronises `stream` once per drain step. */
+jr_status jr_complete_tours(jr_chains* chains, uint32_t max_steps, uint64_t* remaining, void* stream);
+
 /* Attach a flow (or detach with flow = NULL) with mixture weight beta in
- * [0, 1), and restart every chain from the new mu: each chain starts a new tour
- * (Philox tag 3, keyed by the restart count; the restarts are not counted as
- * regenerations, and each chain's unfinished tour is left as at the end of a
- * run).  The flow must outlive its use; chains with a flow advance in the
- * wavefront mode (jr_advance only).  Asynchronous. */
-jr_status jr_chains_set_flow(jr_chains* chains, const jr_flow* flow, float beta, void* stream);
+ * [0, 1): first the current tours are completed under the old mu (as in
+ * jr_complete_tours, at most max_drain_steps steps), then every chain starts a
+ * new tour from the new mu.  So no tour mixes two regeneration densities.  The
+ * flow must outlive its use; chains with a flow advance in the wavefront mode
+ * (jr_advance only). */
+jr_status jr_chains_set_flow(jr_chains* chains, const jr_flow* flow, float beta, uint32_t max_drain_steps,
+                             uint64_t* remaining, void* stream);
 
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char* jr_last_error(void);

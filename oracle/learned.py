@@ -19,7 +19,7 @@ from . import flow as FL
 from . import oracle as O
 
 LUM = np.array([0.2126, 0.7152, 0.0722])
-TAG_STEP, TAG_INIT = 0, 1
+TAG_STEP, TAG_INIT, TAG_RESTART = 0, 1, 3
 
 
 def _coords(seed, tag, chain_begin, n, step, D):
@@ -104,3 +104,84 @@ class LearnedChains:
 
     def image(self):
         return self.accum[:, :, :3] / max(self.J, 1)
+
+    def _draw_candidates(self, tag, key, regen_mask, U, v):
+        """Candidates of a regeneration (uniform or flow draw); returns (y, u(y))."""
+        y = v.copy()
+        uy = np.ones(len(v))
+        use_flow = regen_mask & (U[:, 3] < self.beta) & (self.w is not None)
+        if use_flow.any():
+            xf, lq = FL.sample(self.perm, self.w, v[use_flow])
+            y[use_flow] = xf
+            uy[use_flow] = self.beta * np.exp(lq) + (1.0 - self.beta)
+        dens = ~use_flow
+        if dens.any():
+            uy[dens] = self.u_of(y[dens])
+        return y, uy
+
+    def complete_tours(self, max_steps=1 << 20):
+        """Drain, then restart every chain from mu.  Returns the open tours."""
+        remaining = self.drain(max_steps)
+        self.restart()
+        return remaining
+
+    def set_flow(self, perm, w, beta, max_steps=1 << 20):
+        """Complete the tours under the old mu, switch mu, restart."""
+        remaining = self.drain(max_steps)
+        self.perm, self.w, self.beta = perm, w, float(beta)
+        self.restart()
+        return remaining
+
+    def drain(self, max_steps=1 << 20):
+        """Chains inside a tour keep stepping (Alg. 2); a kill ends the tour
+        (J += 1) and the chain.  Returns the chains whose tour was still open
+        after max_steps."""
+        done = np.zeros(self.n, bool)
+        WH = self.W * self.H
+        k = 0
+        while (~done).any() and k < max_steps:
+            s = self.step
+            act = ~done
+            U = O.draw_uniforms_many(self.seed, TAG_STEP, 0, self.cb, self.n, s)
+            E1, E2 = -np.log(1.0 - U[:, 0]), -np.log(1.0 - U[:, 1])
+            t2 = np.where(self.p > 0, E2 * self.p / (self.c * self.u), 0.0)
+            local = (E1 < t2) & act
+            kill = act & ~local
+            dt = np.where(local, E1, t2)
+            ok = act & (dt > 0) & (self.p > 0)
+            px = np.minimum(np.floor(self.x[:, 0] * self.W), self.W - 1).astype(int)
+            py = np.minimum(np.floor(self.x[:, 1] * self.H), self.H - 1).astype(int)
+            wgt = np.where(ok, self.c * dt * WH / np.where(self.p > 0, self.p, 1.0), 0.0)
+            np.add.at(self.accum, (py[ok], px[ok], slice(0, 3)), (wgt[ok, None] * self.F[ok]))
+            np.add.at(self.accum, (py[ok], px[ok], 3), dt[ok])
+            self.J += int(kill.sum())
+            done |= kill
+            if local.any():
+                v = _coords(self.seed, TAG_STEP, self.cb, self.n, s, self.D)
+                R = np.sqrt(-2.0 * np.log(1.0 - v[:, 0::2]))
+                ang = 2.0 * np.pi * v[:, 1::2]
+                st = np.empty_like(self.x)
+                st[:, 0::2] = R * np.cos(ang)
+                st[:, 1::2] = R * np.sin(ang)
+                yl = self.x + self.sigma * st
+                yl = yl - np.floor(yl)
+                yl[yl >= 1.0] = 0.0
+                Fy = self.F_of(yl[local])
+                pyv = Fy @ LUM
+                acc = U[local, 2] * self.p[local] < pyv
+                idx = np.nonzero(local)[0][acc]
+                self.x[idx] = yl[idx]
+                self.F[idx] = Fy[acc]
+                self.p[idx] = pyv[acc]
+                self.u[idx] = self.u_of(yl[idx])
+            self.step += 1
+            k += 1
+        return int((~done).sum())
+
+    def restart(self):
+        """Every chain starts a new tour from mu (tag 3, the restart count)."""
+        self.epochs = getattr(self, "epochs", 0) + 1
+        U = O.draw_uniforms_many(self.seed, TAG_RESTART, 0, self.cb, self.n, self.epochs)
+        v = _coords(self.seed, TAG_RESTART, self.cb, self.n, self.epochs, self.D)
+        y, uy = self._draw_candidates(TAG_RESTART, self.epochs, np.ones(self.n, bool), U, v)
+        self._set(y, uy)

@@ -75,6 +75,7 @@ struct jr_chains {
         cudaFree(view.wf.hit);
         cudaFree(view.wf.uy);
         cudaFree(view.wf.fq);
+        cudaFree(view.wf.done);
         cudaFree(view.wf.queue);
         cudaFree(view.wf.qcount);
         cudaFree(view.x);
@@ -232,8 +233,10 @@ static jr_status ensure_wavefront(jr_chains* c, cudaStream_t st) {
         (e = dev_alloc(&w.hit, n)) != cudaSuccess ||
         (e = dev_alloc(&w.queue, 2 * n)) != cudaSuccess ||
         (e = dev_alloc(&w.qcount, kQCount)) != cudaSuccess || (e = dev_alloc(&w.uy, n)) != cudaSuccess ||
-        (e = dev_alloc(&w.fq, 2 * n)) != cudaSuccess ||
+        (e = dev_alloc(&w.fq, 2 * n)) != cudaSuccess || (e = dev_alloc(&w.done, n)) != cudaSuccess ||
+        (e = cudaMemsetAsync(w.done, 0, n, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(w.par, 0, n, st)) != cudaSuccess) {
+        cudaFree(w.done);
         cudaFree(w.y);
         cudaFree(w.par);
         cudaFree(w.ua);
@@ -841,18 +844,67 @@ jr_status jr_flow_sample(jr_flow* f, float* xz_dev, uint64_t n, float* lq_dev, v
     return JR_OK;
 }
 
-jr_status jr_chains_set_flow(jr_chains* c, const jr_flow* f, float beta, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// Drain: advance only the chains that are inside a tour until every tour has
+// ended (a kill ends the tour and the chain); the steps are regular steps of
+// Alg. 2 for those chains.  Returns the chains still in a tour after
+// max_steps (0 when every tour completed).
+jr_status drain_impl(jr_chains* c, uint32_t max_steps, uint64_t* remaining, cudaStream_t st, const char* who) {
+    jr_status a = ensure_wavefront(c, st);
+    if (a != JR_OK) return a;
+    JR_CUDA(cudaMemsetAsync(c->view.wf.done, 0, c->view.n, st), who);
+    unsigned int active = (unsigned int)std::min<uint64_t>(c->view.n, 0xffffffffu);
+    uint32_t k = 0;
+    while (active > 0 && k < max_steps) {
+        JR_CUDA(launch_wavefront(c->scene->view, c->view, c->steps, 1, st, kModeDrain), who);
+        c->steps += 1;
+        ++k;
+        JR_CUDA(cudaMemcpyAsync(&active, c->view.wf.qcount + kQActive, sizeof(active), cudaMemcpyDeviceToHost, st),
+                who);
+        JR_CUDA(cudaStreamSynchronize(st), who);
+    }
+    JR_CUDA(launch_fold(c->view, st), who);
+    if (remaining) *remaining = active;
+    return JR_OK;
+}
+
+// Restart: every chain starts a new tour from the current mu.
+jr_status restart_impl(jr_chains* c, cudaStream_t st, const char* who) {
+    jr_status a = ensure_wavefront(c, st);
+    if (a != JR_OK) return a;
+    c->epochs += 1;
+    JR_CUDA(launch_wavefront(c->scene->view, c->view, c->epochs, 1, st, kModeRestart), who);
+    return JR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+jr_status jr_complete_tours(jr_chains* c, uint32_t max_steps, uint64_t* remaining, void* stream) {
+    if (!c) return fail(JR_ERR_INVALID_ARG, "jr_complete_tours: null chains");
+    cudaStream_t st = (cudaStream_t)stream;
+    jr_status r = drain_impl(c, max_steps, remaining, st, "jr_complete_tours");
+    if (r == JR_OK) r = restart_impl(c, st, "jr_complete_tours");
+    return r;
+}
+
+jr_status jr_chains_set_flow(jr_chains* c, const jr_flow* f, float beta, uint32_t max_drain_steps,
+                             uint64_t* remaining, void* stream) {
     if (!c) return fail(JR_ERR_INVALID_ARG, "jr_chains_set_flow: null chains");
     if (f && f->D != c->view.dim) return fail(JR_ERR_INVALID_ARG, "jr_chains_set_flow: flow and chain dimensions differ");
     if (f && !(beta >= 0.f && beta < 1.f))
         return fail(JR_ERR_INVALID_ARG, "jr_chains_set_flow: beta must be in [0, 1)");
     cudaStream_t st = (cudaStream_t)stream;
-    jr_status a = ensure_wavefront(c, st);
-    if (a != JR_OK) return a;
+    uint64_t rem = 0;
+    jr_status r = drain_impl(c, max_drain_steps, &rem, st, "jr_chains_set_flow");  // finish the tours of the old mu
+    if (r != JR_OK) return r;
+    if (remaining) *remaining = rem;
     c->view.flow = f ? f->view(beta) : FlowView{};
-    c->epochs += 1;
-    JR_CUDA(launch_wavefront_restart(c->scene->view, c->view, c->epochs, st), "jr_chains_set_flow");
-    return JR_OK;
+    return restart_impl(c, st, "jr_chains_set_flow");
 }
 
 }  // extern "C"

@@ -83,8 +83,14 @@ struct WaveView {
     unsigned int* qcount = nullptr;  // [kQCount]: queue lengths, fetch cursors, flow queue lengths
     float* uy = nullptr;          // [n] u of the step's candidate (with a flow)
     uint32_t* fq = nullptr;       // [2][n] candidates for the flow: density rows, then sampling rows
+    uint8_t* done = nullptr;      // [n] 1: the chain finished its tour during a drain
 };
-constexpr int kQFlowDensity = 2 * (kMaxDepth + 2), kQFlowSample = kQFlowDensity + 1, kQCount = kQFlowSample + 1;
+constexpr int kQFlowDensity = 2 * (kMaxDepth + 2), kQFlowSample = kQFlowDensity + 1, kQActive = kQFlowSample + 1,
+              kQCount = kQActive + 1;
+// Step-kernel modes of the wavefront: a regular step of Alg. 2; a restart of
+// every chain from mu (new tours, not regenerations); a drain step (a kill
+// ends the chain's tour and the chain; no new tours start).
+enum WaveMode { kModeStep = 0, kModeRestart = 1, kModeDrain = 2 };
 
 struct ChainView {
     float* x;        // [D][n] PSS coordinates
@@ -140,8 +146,10 @@ cudaError_t launch_batch(BatchEntry* entries, const BatchItem* items, uint32_t n
                          uint32_t n_sets, uint64_t total_px, unsigned int* cursor, uint32_t max_dim, int block,
                          uint32_t n_steps, cudaStream_t st);
 // jr_wavefront.cu
+// n_steps wavefront steps in `mode` (WaveMode); for kModeRestart step_begin is
+// the restart epoch and n_steps is 1.
 cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
-                             cudaStream_t st);
+                             cudaStream_t st, int mode = kModeStep);
 // The same wavefront launches with their buffers in a fixed file-scope device
 // array (no allocation); c.wf is ignored.  c.n <= kStaticMaxChains.
 constexpr uint64_t kStaticMaxChains = 1u << 16;
@@ -151,9 +159,6 @@ constexpr size_t kStaticScratchBytes =
     sizeof(uint8_t) * kStaticMaxChains + 256;  // = 12 910 848 bytes (every piece but the counters is a multiple of 256)
 cudaError_t launch_wavefront_static(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
                                     cudaStream_t st);
-// Restart every chain from the current regeneration distribution (new tours;
-// not counted as regenerations).  `epoch` keys the Philox stream (tag 3).
-cudaError_t launch_wavefront_restart(const SceneView& s, const ChainView& c, uint64_t epoch, cudaStream_t st);
 
 // jr_flow.cu: flow rows through the tensor cores.  Density: u_out[i] = beta q
 // + 1 - beta (and lq_out[i] = log q) for rows i of buf [D][n]; sample: buf

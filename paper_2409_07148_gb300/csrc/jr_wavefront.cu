@@ -85,22 +85,27 @@ __device__ __forceinline__ void count_and_flush(uint32_t nJ, uint32_t nL, uint32
 // With a flow attached (c.flow.D > 0), a regeneration draws from the flow when
 // Ub < beta (Ub = fourth value of block 0), else uniformly; the candidates go
 // to the flow queues, whose kernels fill in u(y) (and y for flow draws).
+// mode = kModeDrain: a kill ends the chain's tour (counted in J) and the chain
+// (done = 1); done chains do nothing; no regeneration starts a new tour.
+// Chains still in a tour after the step are counted in qcount[kQActive].
 __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step, int finish, int begin,
-                                                      SceneView s, int restart) {
+                                                      SceneView s, int mode) {
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     const bool valid = i < c.n;
     const int D = (int)c.dim;
     const uint64_t n = c.n;
     const WaveView& w = c.wf;
     const bool has_flow = c.flow.D != 0;
+    const bool restart = mode == kModeRestart, drain = mode == kModeDrain;
     uint32_t nJ = 0, nL = 0, nA = 0;
     unsigned status = 0;
-    bool to_density = false, to_sample = false;
+    bool to_density = false, to_sample = false, traced = valid, active = false;
     if (valid) {
         uint8_t par = w.par[i];
         float Fr = c.fpu[0 * n + i], Fg = c.fpu[1 * n + i], Fb = c.fpu[2 * n + i];
         float p = c.fpu[3 * n + i], u = c.fpu[4 * n + i];
-        if (finish) {
+        const bool was_done = drain && w.done[i];
+        if (finish && !(drain && w.ua[i] == -2.0f)) {
             const float ua = w.ua[i];
             const float4 pf = w.path[3 * i + 2];
             const float3 Fy = finite_or_zero(f3(pf.y, pf.z, pf.w), status);
@@ -108,6 +113,7 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
             bool accept;
             if (restart) {     // a restart: the new tour's start, not a regeneration
                 accept = true;
+                w.done[i] = 0;
             } else if (ua >= 0.0f) {  // local branch: MH acceptance, U < min(1, p(y)/p(x))
                 accept = ua * p < py;
                 nL++;
@@ -132,7 +138,10 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
         }
         float* cur = par ? w.y : c.x;
         float* cand = par ? c.x : w.y;
-        if (begin) {
+        if (begin && was_done) {  // finished its tour during this drain
+            w.ua[i] = -2.0f;
+            traced = false;
+        } else if (begin) {
             const uint32_t chain = c.chain_offset + (uint32_t)i;
             const uint32_t tag = restart ? kTagRestart : kTagStep;
             const uint4 r0 = draw(c.seed, tag, 0, chain, step);
@@ -155,8 +164,16 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
                 atomicAdd(c.fb + py * c.width + px, make_float4(wgt * Fr, wgt * Fg, wgt * Fb, dt));
             }
             w.ua[i] = local ? Ua : -1.0f;
+            if (drain && !local) {  // the tour ends here; no new tour in a drain
+                nJ++;
+                w.done[i] = 1;
+                w.ua[i] = -2.0f;
+                traced = false;
+                to_sample = to_density = false;
+            }
+            active = drain && local;
             float y0 = 0.f, y1 = 0.f;
-            for (int b = 0; 4 * b < D; ++b) {
+            for (int b = 0; traced && 4 * b < D; ++b) {
                 const uint4 r = draw(c.seed, tag, (uint32_t)(b + 1), chain, step);
                 const uint64_t o0 = (uint64_t)(4 * b) * n + i;
                 float v0, v1, v2 = 0.f, v3 = 0.f;
@@ -190,7 +207,7 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
                     y1 = v1;
                 }
             }
-            if (!use_flow) {  // a flow draw gets its camera ray from the flow kernel
+            if (traced && !use_flow) {  // a flow draw gets its camera ray from the flow kernel
                 float3 o, d;
                 camera_ray(s, y0, y1, o, d);
                 store_path(w.path, i, o, d, f3(1.f, 1.f, 1.f), f3(0.f, 0.f, 0.f));
@@ -202,10 +219,14 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
         w.par[i] = par;
     }
     if (begin) {
-        enqueue(valid, (uint32_t)i, w.queue, w.qcount + 0);
+        enqueue(traced, (uint32_t)i, w.queue, w.qcount + 0);
         if (has_flow) {
             enqueue(to_density, (uint32_t)i, w.fq, w.qcount + kQFlowDensity);
             enqueue(to_sample, (uint32_t)i, w.fq + n, w.qcount + kQFlowSample);
+        }
+        if (drain) {
+            const unsigned na = __popc(__ballot_sync(kFull, active));
+            if ((threadIdx.x & 31) == 0 && na) atomicAdd(w.qcount + kQActive, na);
         }
     }
     count_and_flush(nJ, nL, nA, status, c);
@@ -341,7 +362,7 @@ cudaError_t launch_flow_candidates(const SceneView& s, const ChainView& c, cudaS
 }  // namespace
 
 cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
-                             cudaStream_t st) {
+                             cudaStream_t st, int mode) {
     static int trace_blocks = 0, shade_blocks = 0;
     if (trace_blocks == 0) {
         int dev = 0, sms = 0, per_sm = 0, per_sm2 = 0;
@@ -357,43 +378,17 @@ cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t st
     }
     const unsigned G = grid_for(c.n, 128);
     const bool has_flow = c.flow.D != 0;
-    const size_t qbytes = sizeof(unsigned int) * (has_flow ? kQCount : 2 * (kMaxDepth + 2));
     for (uint32_t k = 0; k < n_steps; ++k) {
-        cudaError_t e = cudaMemsetAsync(c.wf.qcount, 0, qbytes, st);
+        cudaError_t e = cudaMemsetAsync(c.wf.qcount, 0, sizeof(unsigned int) * kQCount, st);
         if (e != cudaSuccess) return e;
-        wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + k, k > 0, 1, s, 0);
+        wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + k, k > 0, 1, s, mode);
         if (has_flow && (e = launch_flow_candidates(s, c, st)) != cudaSuccess) return e;
         for (int v = 0; v <= (int)c.depth; ++v) {
             wf_trace_kernel<<<trace_blocks, 128, 0, st>>>(s, c, v);
             wf_shade_kernel<<<shade_blocks, 128, 0, st>>>(s, c, v);
         }
     }
-    wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + n_steps, n_steps > 0, 0, s, 0);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_wavefront_restart(const SceneView& s, const ChainView& c, uint64_t epoch, cudaStream_t st) {
-    cudaError_t e = launch_wavefront(s, c, 0, 0, st);  // sets up the persistent grid sizes; launches a no-op finish
-    if (e != cudaSuccess) return e;
-    const unsigned G = grid_for(c.n, 128);
-    if ((e = cudaMemsetAsync(c.wf.qcount, 0, sizeof(unsigned int) * kQCount, st)) != cudaSuccess) return e;
-    wf_step_kernel<<<G, 128, 0, st>>>(c, epoch, 0, 1, s, 1);
-    if (c.flow.D != 0 && (e = launch_flow_candidates(s, c, st)) != cudaSuccess) return e;
-    int trace_blocks = 0, shade_blocks = 0;
-    {
-        int dev = 0, sms = 0, p1 = 0, p2 = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, wf_trace_kernel, 128, 0)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, wf_shade_kernel, 128, 0)) != cudaSuccess) return e;
-        trace_blocks = sms * (p1 > 0 ? p1 : 1);
-        shade_blocks = sms * (p2 > 0 ? p2 : 1);
-    }
-    for (int v = 0; v <= (int)c.depth; ++v) {
-        wf_trace_kernel<<<trace_blocks, 128, 0, st>>>(s, c, v);
-        wf_shade_kernel<<<shade_blocks, 128, 0, st>>>(s, c, v);
-    }
-    wf_step_kernel<<<G, 128, 0, st>>>(c, epoch, 1, 0, s, 1);
+    wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + n_steps, n_steps > 0, 0, s, mode);
     return cudaGetLastError();
 }
 

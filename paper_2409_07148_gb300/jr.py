@@ -95,7 +95,8 @@ _SIGS = {
     "jr_flow_get_params": [_P, _P, _P],
     "jr_flow_log_density": [_P, _P, _U64, _P, _P],
     "jr_flow_sample": [_P, _P, _U64, _P, _P],
-    "jr_chains_set_flow": [_P, _P, ctypes.c_float, _P],
+    "jr_chains_set_flow": [_P, _P, ctypes.c_float, _U32, _P, _P],
+    "jr_complete_tours": [_P, _U32, _P, _P],
     "jr_last_error": [],
     "jr_version": [],
 }
@@ -320,9 +321,22 @@ class Flow:
             pass
 
 
-def set_flow(chains, flow, beta, stream=None):
-    """Attach `flow` (or None) with mixture weight beta and restart every chain."""
-    _check(lib().jr_chains_set_flow(chains.h, None if flow is None else flow.h, float(beta), _stream(stream)))
+def set_flow(chains, flow, beta, max_drain_steps=1 << 20, stream=None):
+    """Complete the current tours, attach `flow` (or None) with mixture weight
+    beta, restart every chain.  Returns the tours left open by the drain."""
+    rem = ctypes.c_uint64(0)
+    _check(lib().jr_chains_set_flow(chains.h, None if flow is None else flow.h, float(beta), int(max_drain_steps),
+                                    ctypes.byref(rem), _stream(stream)))
+    return int(rem.value)
+
+
+def complete_tours(chains, max_steps=1 << 20, stream=None):
+    """Finish every chain's current tour, then start new tours.  Returns the
+    tours still open after max_steps (0: the image is the completed-tour
+    estimator)."""
+    rem = ctypes.c_uint64(0)
+    _check(lib().jr_complete_tours(chains.h, int(max_steps), ctypes.byref(rem), _stream(stream)))
+    return int(rem.value)
 
 
 class Batch:

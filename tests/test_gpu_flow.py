@@ -123,10 +123,12 @@ def test_learned_mixture_image_is_unbiased(J):
         c1 = J.Chains(g, 32, 32, sc.depth, 16384, seed=1, chain_offset=16384 * k)
         J.set_flow(c1, f, 0.7)
         c1.advance(300)
+        assert J.complete_tours(c1) == 0     # no open tour left: the completed-tour estimator
         a.append(c1.resolve())
         c2 = J.Chains(g, 32, 32, sc.depth, 16384, seed=2, chain_offset=16384 * k)
         c2.set_execution("wave")
         c2.advance(300)
+        assert J.complete_tours(c2) == 0
         b.append(c2.resolve())
         assert c1.stats()["status_word"] == 0
     a, b = np.array(a, np.float64), np.array(b, np.float64)
@@ -136,3 +138,33 @@ def test_learned_mixture_image_is_unbiased(J):
     z = np.sign(t) * stats.norm.isf(stats.t.sf(np.abs(t), 2 * len(a) - 2))
     assert np.mean(np.abs(z) > 4) <= 2e-3
     assert 0.6 < np.mean(z ** 2) < 1.6
+
+
+@pytest.mark.parametrize("beta", [0.0, 0.6])
+def test_complete_tours_paired_with_oracle(J, beta):
+    """Identical Philox streams: GPU chains (wavefront, learned mixture or
+    uniform) advanced, drained until every tour ends, and restarted, against
+    the oracle's Alg. 2 doing the same from the same initial states."""
+    sc = scenes.cornell(width=8, height=8, depth=3)
+    perm, w = _flow(sc.D, 13, 0.1)
+    g = J.Scene(sc)
+    ch = J.Chains(g, 8, 8, sc.depth, 2048, seed=4, sigma=0.02)
+    ch.set_execution("wave")
+    osc = O.Scene(sc)
+    F_of = lambda xx: O.eval_states(osc, xx)[0]
+    oc = LR.LearnedChains(F_of, sc.D, 8, 8, beta=0.0, sigma=0.02, seed=4, n_chains=2048)
+    if beta:
+        f = J.Flow(sc.D, perm, w)
+        J.set_flow(ch, f, beta)
+        oc.set_flow(perm, w, beta)
+    ch.advance(6)
+    oc.advance(6)
+    assert J.complete_tours(ch) == 0 and oc.complete_tours() == 0
+    st = ch.stats()
+    assert abs(st["regenerations"] - oc.J) <= 0.01 * oc.J
+    ga, oa = ch.accumulator(), oc.accum
+    rel = np.abs(ga - oa).sum() / np.abs(oa).sum()
+    assert rel < 0.02, rel                 # identical streams; only rare ties and FP32/bf16 differences diverge
+    x, fpu = ch.get_state()                # the restart drew the same new states
+    same = np.all(np.abs(x.T - oc.x) <= 1e-4, axis=1)
+    assert np.mean(same) >= 0.98

@@ -134,3 +134,33 @@ def test_learned_mixture_keeps_the_estimator_exact(beta):
     assert np.abs(z).max() < 4.5
     fr = np.array(fr)
     assert abs(fr.mean() - 1.0 / (p_lambda + 1.0)) < 4 * fr.std(ddof=1) / np.sqrt(len(fr)) + 1e-3
+
+
+def test_completed_tours_remove_the_finite_run_bias():
+    """Short runs (10 steps per chain): stopping at a fixed step leaves one open
+    tour per chain, a bias of order chains / J; completing every tour (drain)
+    gives the pixel means again (quadrature), for uniform and learned mu."""
+    an = O.Analytic([(1.0, 0.3, 0.4, 0.08), (0.5, 0.7, 0.6, 0.1)], (0.45, 0.5))
+    n = 1024
+    g = (np.arange(n) + 0.5) / n
+    X0, X1 = np.meshgrid(g, g)
+    F = an.eval(np.stack([X0.ravel(), X1.ravel()], 1)).reshape(n, n, 3)
+    pix = F.reshape(2, n // 2, 2, n // 2, 3).mean(axis=(1, 3))
+    perm, w = _flow(2, 8, 0.1)
+    for beta in (0.0, 0.7):
+        open_, done_ = [], []
+        for b in range(10):
+            ch = LR.LearnedChains(an.eval, 2, 2, 2, perm, w, beta=beta, c_tilde=0.2, sigma=0.05, seed=21,
+                                  chain_begin=4096 * b, n_chains=4096)
+            if beta:
+                ch.set_flow(perm, w, beta)
+            ch.advance(10)
+            open_.append(ch.image())
+            assert ch.complete_tours() == 0
+            done_.append(ch.image())
+        done_ = np.array(done_)
+        z = (done_.mean(0) - pix) / (done_.std(0, ddof=1) / np.sqrt(len(done_)))
+        assert np.abs(z).max() < 4.5, (beta, z)
+        open_ = np.array(open_)
+        zo = (open_.mean(0) - pix) / (open_.std(0, ddof=1) / np.sqrt(len(open_)))
+        assert np.abs(zo).max() > 4.5     # the open-tour bias is real at this run length
