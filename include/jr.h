@@ -340,6 +340,30 @@ jr_status jr_flow_log_density(jr_flow* flow, const float* x_dev, uint64_t n, flo
  * [n] gets log q(x).  Async. */
 jr_status jr_flow_sample(jr_flow* flow, float* xz_dev, uint64_t n, float* lq_dev, void* stream);
 
+/* Copy perm and parameters of src into dst (same D) on the device. */
+jr_status jr_flow_copy_params(jr_flow* dst, const jr_flow* src, void* stream);
+
+/* Training rows from the chains' current states: x_dev [D][n_chains] (device)
+ * gets the states, w_dev [n_chains] the weights p / (p + c~ u) = E[dt | x],
+ * the expected holding time of Alg. 2, so that the weighted states follow pi
+ * (the states themselves follow the jump chain's law, proportional to
+ * p + c~ u).  Call between advances (the states are then in x).  Async. */
+jr_status jr_chains_snapshot(jr_chains* chains, float* x_dev, float* w_dev, void* stream);
+
+/* Time-weighted maximum likelihood: the loss -sum_r w_r log q(x_r) / sum_r w_r
+ * over rows [off, off + batch) of x_dev [D][n], w_dev [n] (device), and its
+ * gradient w.r.t. the parameters (host, jr_flow_param_count floats, the layout
+ * above).  bf16 roundings pass gradients straight through.  Synchronises. */
+jr_status jr_flow_gradient(jr_flow* flow, const float* x_dev, const float* w_dev, uint64_t n, uint64_t off,
+                           uint32_t batch, float* grad_host, float* loss_host, void* stream);
+
+/* iters Adam steps (lr; beta 0.9 / 0.999) of the same loss on minibatches of
+ * `batch` rows (a multiple of 64) at pseudo-random offsets (seed); the packed
+ * bf16 weights follow every step, so train a flow that no chain set is using.
+ * loss_host (may be NULL) gets the loss of every step.  Synchronises. */
+jr_status jr_flow_train(jr_flow* flow, const float* x_dev, const float* w_dev, uint64_t n, uint32_t iters,
+                        uint32_t batch, float lr, uint64_t seed, float* loss_host, void* stream);
+
 /* Complete every chain's current tour, then start every chain on a new tour.
  * The estimator of Section 6.3 divides by J, the number of completed tours;
  * a run stopped after a fixed number of steps leaves one unfinished tour per

@@ -844,6 +844,95 @@ jr_status jr_flow_sample(jr_flow* f, float* xz_dev, uint64_t n, float* lq_dev, v
     return JR_OK;
 }
 
+jr_status jr_flow_copy_params(jr_flow* dst, const jr_flow* src, void* stream) {
+    if (!dst || !src) return fail(JR_ERR_INVALID_ARG, "jr_flow_copy_params: null argument");
+    if (dst->D != src->D) return fail(JR_ERR_INVALID_ARG, "jr_flow_copy_params: dimensions differ");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t P = (size_t)kFL * flow_layer_floats(src->D);
+    JR_CUDA(cudaMemcpyAsync(dst->perm, src->perm, (size_t)kFL * src->D, cudaMemcpyDeviceToDevice, st),
+            "jr_flow_copy_params");
+    JR_CUDA(cudaMemcpyAsync(dst->master, src->master, sizeof(float) * P, cudaMemcpyDeviceToDevice, st),
+            "jr_flow_copy_params");
+    JR_CUDA(launch_flow_pack(dst->master, dst->wb, dst->bias, dst->AK, st), "jr_flow_copy_params");
+    return JR_OK;
+}
+
+jr_status jr_chains_snapshot(jr_chains* c, float* x_dev, float* w_dev, void* stream) {
+    if (!c || !x_dev || !w_dev) return fail(JR_ERR_INVALID_ARG, "jr_chains_snapshot: null argument");
+    JR_CUDA(launch_snapshot(c->view, x_dev, w_dev, (cudaStream_t)stream), "jr_chains_snapshot");
+    return JR_OK;
+}
+
+jr_status jr_flow_gradient(jr_flow* f, const float* x_dev, const float* w_dev, uint64_t n, uint64_t off,
+                           uint32_t batch, float* grad_host, float* loss_host, void* stream) {
+    if (!f || !x_dev || !w_dev || !grad_host) return fail(JR_ERR_INVALID_ARG, "jr_flow_gradient: null argument");
+    if (batch == 0 || off + batch > n) return fail(JR_ERR_INVALID_ARG, "jr_flow_gradient: rows out of range");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t P = (size_t)kFL * flow_layer_floats(f->D);
+    float* buf = nullptr;  // gradient, then the weight sum and the loss
+    JR_CUDA(dev_alloc(&buf, P + 2), "jr_flow_gradient");
+    cudaError_t e = cudaMemsetAsync(buf, 0, sizeof(float) * (P + 2), st);
+    if (e == cudaSuccess) e = launch_flow_train_step(f->view(0.f), x_dev, w_dev, n, off, batch, buf, buf + P, buf + P + 1, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(grad_host, buf, sizeof(float) * P, cudaMemcpyDeviceToHost, st);
+    float tail[2] = {0.f, 0.f};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tail, buf + P, sizeof(tail), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(e, "jr_flow_gradient");
+    if (loss_host) *loss_host = tail[1];
+    return JR_OK;
+}
+
+jr_status jr_flow_train(jr_flow* f, const float* x_dev, const float* w_dev, uint64_t n, uint32_t iters,
+                        uint32_t batch, float lr, uint64_t seed, float* loss_host, void* stream) {
+    if (!f || !x_dev || !w_dev) return fail(JR_ERR_INVALID_ARG, "jr_flow_train: null argument");
+    if (batch == 0 || batch % 64 != 0 || batch > n)
+        return fail(JR_ERR_INVALID_ARG, "jr_flow_train: batch must be a positive multiple of 64, at most n");
+    if (!(lr > 0.f)) return fail(JR_ERR_INVALID_ARG, "jr_flow_train: lr must be > 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t P = (size_t)kFL * flow_layer_floats(f->D);
+    if (!f->grad) {
+        cudaError_t e;
+        if ((e = dev_alloc(&f->grad, P)) != cudaSuccess || (e = dev_alloc(&f->adam_m, P)) != cudaSuccess ||
+            (e = dev_alloc(&f->adam_v, P)) != cudaSuccess ||
+            (e = cudaMemsetAsync(f->adam_m, 0, sizeof(float) * P, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(f->adam_v, 0, sizeof(float) * P, st)) != cudaSuccess) {
+            cudaFree(f->grad);
+            cudaFree(f->adam_m);
+            cudaFree(f->adam_v);
+            f->grad = f->adam_m = f->adam_v = nullptr;
+            return cuda_fail(e, "jr_flow_train (optimiser state)");
+        }
+    }
+    float* scal = nullptr;  // [iters][2]: minibatch weight sum, loss
+    JR_CUDA(dev_alloc(&scal, 2 * (size_t)std::max<uint32_t>(iters, 1)), "jr_flow_train");
+    cudaError_t e = cudaMemsetAsync(scal, 0, sizeof(float) * 2 * std::max<uint32_t>(iters, 1), st);
+    uint64_t rng = seed * 0x9E3779B97F4A7C15ull + 0xD1B54A32D192ED03ull;
+    for (uint32_t it = 0; it < iters && e == cudaSuccess; ++it) {
+        rng ^= rng >> 30;  // splitmix64 (Steele, Lea, Flood 2014): the minibatch window
+        rng *= 0xBF58476D1CE4E5B9ull;
+        rng ^= rng >> 27;
+        rng *= 0x94D049BB133111EBull;
+        rng ^= rng >> 31;
+        const uint64_t off = rng % (n - batch + 1);
+        if ((e = cudaMemsetAsync(f->grad, 0, sizeof(float) * P, st)) != cudaSuccess) break;
+        if ((e = launch_flow_train_step(f->view(0.f), x_dev, w_dev, n, off, batch, f->grad, scal + 2 * it,
+                                        scal + 2 * it + 1, st)) != cudaSuccess)
+            break;
+        if ((e = launch_adam(f->master, f->grad, f->adam_m, f->adam_v, P, lr, ++f->adam_t, st)) != cudaSuccess) break;
+        if ((e = launch_flow_pack(f->master, f->wb, f->bias, f->AK, st)) != cudaSuccess) break;
+    }
+    std::vector<float> h(2 * (size_t)std::max<uint32_t>(iters, 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), scal, sizeof(float) * h.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(scal);
+    if (e != cudaSuccess) return cuda_fail(e, "jr_flow_train");
+    if (loss_host)
+        for (uint32_t it = 0; it < iters; ++it) loss_host[it] = h[2 * it + 1];
+    return JR_OK;
+}
+
 }  // extern "C"
 
 namespace {

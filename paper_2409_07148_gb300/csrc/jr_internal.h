@@ -170,10 +170,18 @@ cudaError_t launch_flow(const FlowView& f, bool sample, const SceneView* s, floa
 size_t flow_smem_bytes();
 // FP32 master parameters [kFL][S] -> padded bf16 weights and biases.
 cudaError_t launch_flow_pack(const float* master, __nv_bfloat16* wb, float* bias, uint32_t AK, cudaStream_t st);
-inline size_t flow_layer_floats(uint32_t D) {
+__host__ __device__ inline size_t flow_layer_floats(uint32_t D) {
     const size_t A = D / 2, AK = A * kFK;
     return (size_t)kFH * kFAP + kFH + kFH * kFH + kFH + AK * kFH + AK;
 }
+// Training rows from chain states (x [D][n], w = p / (p + c~ u)).
+cudaError_t launch_snapshot(const ChainView& c, float* x_out, float* w_out, cudaStream_t st);
+// One minibatch of the time-weighted maximum-likelihood loss: gradient into
+// grad (added), minibatch weight sum into *wsum (added), loss into *loss (added).
+cudaError_t launch_flow_train_step(const FlowView& f, const float* x, const float* w, uint64_t n, uint64_t off,
+                                   uint32_t batch, float* grad, float* wsum, float* loss, cudaStream_t st);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, uint64_t count, float lr, uint64_t t,
+                        cudaStream_t st);
 cudaError_t launch_resolve(const ChainView& c, float* rgb, cudaStream_t st);
 cudaError_t launch_reeval(const SceneView& s, const ChainView& c, cudaStream_t st);
 cudaError_t launch_eval_states(const SceneView& s, uint32_t depth, float c_tilde, const float* x, uint64_t n,

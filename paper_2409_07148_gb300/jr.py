@@ -97,6 +97,10 @@ _SIGS = {
     "jr_flow_sample": [_P, _P, _U64, _P, _P],
     "jr_chains_set_flow": [_P, _P, ctypes.c_float, _U32, _P, _P],
     "jr_complete_tours": [_P, _U32, _P, _P],
+    "jr_flow_copy_params": [_P, _P, _P],
+    "jr_chains_snapshot": [_P, _P, _P, _P],
+    "jr_flow_gradient": [_P, _P, _P, _U64, _U64, _U32, _P, _P, _P],
+    "jr_flow_train": [_P, _P, _P, _U64, _U32, _U32, ctypes.c_float, _U64, _P, _P],
     "jr_last_error": [],
     "jr_version": [],
 }
@@ -309,6 +313,26 @@ class Flow:
         _check(lib().jr_flow_sample(self.h, _dptr(z), int(z.shape[1]), _dptr(lq), _stream(stream)))
         return lq
 
+    def copy_params_from(self, other, stream=None):
+        _check(lib().jr_flow_copy_params(self.h, other.h, _stream(stream)))
+
+    def gradient(self, x, w, off=0, batch=None, stream=None):
+        """Loss and gradient of rows [off, off + batch) of x [D, n], w [n] (CUDA)."""
+        n = x.shape[1]
+        batch = n - off if batch is None else batch
+        g = np.zeros(int(lib().jr_flow_param_count(self.D)), np.float32)
+        loss = ctypes.c_float(0.0)
+        _check(lib().jr_flow_gradient(self.h, _dptr(x), _dptr(w), int(n), int(off), int(batch), _hptr(g),
+                                      ctypes.byref(loss), _stream(stream)))
+        return float(loss.value), g
+
+    def train(self, x, w, iters, batch, lr=1e-3, seed=0, stream=None):
+        """iters Adam steps on x [D, n], w [n] (CUDA); returns the per-step losses."""
+        losses = np.zeros(max(int(iters), 1), np.float32)
+        _check(lib().jr_flow_train(self.h, _dptr(x), _dptr(w), int(x.shape[1]), int(iters), int(batch), float(lr),
+                                   int(seed), _hptr(losses), _stream(stream)))
+        return losses[:int(iters)]
+
     def close(self):
         if getattr(self, "h", None):
             lib().jr_flow_destroy(self.h)
@@ -328,6 +352,15 @@ def set_flow(chains, flow, beta, max_drain_steps=1 << 20, stream=None):
     _check(lib().jr_chains_set_flow(chains.h, None if flow is None else flow.h, float(beta), int(max_drain_steps),
                                     ctypes.byref(rem), _stream(stream)))
     return int(rem.value)
+
+
+def snapshot(chains, stream=None):
+    """Training rows from the chains' states: (x [D, n], w [n]) CUDA tensors."""
+    import torch
+    x = torch.empty((chains.D, chains.n), dtype=torch.float32, device="cuda")
+    w = torch.empty(chains.n, dtype=torch.float32, device="cuda")
+    _check(lib().jr_chains_snapshot(chains.h, _dptr(x), _dptr(w), _stream(stream)))
+    return x, w
 
 
 def complete_tours(chains, max_steps=1 << 20, stream=None):
