@@ -197,6 +197,95 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def relmse(img, ref, eps=1e-2):
+    """mean over pixels and channels of (I - R)^2 / (R^2 + eps)."""
+    return float(((img - ref) ** 2 / (ref ** 2 + eps)).mean())
+
+
+def run_caustic(args):
+    """Time to relMSE 1e-2 on the slit-caustic scene, learned vs plain
+    regeneration.  Reference: plain path tracing on the GPU (its own noise is
+    estimated from two independent halves and reported).  Each arm runs epochs
+    of `epoch` chain steps; after every epoch the open tours are completed (so
+    the checkpoint image is the completed-tour estimator) and the relMSE is
+    taken off the clock.  The learned arm trains the flow on a snapshot of the
+    chain states (weights p / (p + c~ u)) between epochs and regenerates from
+    mu = beta mu_flow + (1 - beta) uniform in the next epoch."""
+    import torch
+    from paper_2409_07148_gb300 import jr, scenes
+    from paper_2409_07148_gb300.flowinit import init_flow_params
+    side = args.side
+    sc = scenes.caustic_slit(width=side, height=side, depth=10)
+    stream = torch.cuda.Stream()
+    target, tmax, epoch = 1e-2, args.time_limit, args.epoch
+    C = args.chains or (1 << 20)
+    with torch.cuda.stream(stream):
+        g = jr.Scene(sc, stream=stream)
+        # reference: two independent halves of plain path tracing
+        halves = []
+        t0 = time.perf_counter()
+        chunk = 1 << 28
+        n_half = args.ref_samples // 2
+        for h in range(2):
+            acc = torch.zeros((side, side, 4), dtype=torch.float64, device="cuda")
+            for s0 in range(0, n_half, chunk):
+                jr.render_pt(g, side, side, sc.depth, min(chunk, n_half - s0), seed=1000 + h, sample_begin=s0,
+                             accum=acc, stream=stream)
+            halves.append(acc[..., :3] / n_half)
+        stream.synchronize()
+        t_ref = time.perf_counter() - t0
+        ref = 0.5 * (halves[0] + halves[1])
+        ref_noise = relmse(halves[0], halves[1]) / 4.0   # relMSE of the mean of two halves vs truth, roughly
+
+        def run(learned):
+            ch = jr.Chains(g, side, side, sc.depth, C, seed=5 if learned else 6, stream=stream)
+            ch.set_execution("wave")
+            curve = []
+            clock = 0.0
+            trainer = render = None
+            if learned:
+                perm, w = init_flow_params(sc.D, 0)
+                trainer = jr.Flow(sc.D, perm, w, stream=stream)
+                render = [jr.Flow(sc.D, perm, w, stream=stream), jr.Flow(sc.D, perm, w, stream=stream)]
+            e = 0
+            while clock < tmax:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ch.advance(epoch, stream=stream)
+                if learned:
+                    x, wt = jr.snapshot(ch, stream=stream)
+                    trainer.train(x, wt, iters=args.train_iters, batch=8192, lr=args.lr, seed=e, stream=stream)
+                    nxt = render[e % 2]
+                    nxt.copy_params_from(trainer, stream=stream)
+                    jr.set_flow(ch, nxt, args.beta, stream=stream)   # completes the open tours first
+                else:
+                    jr.complete_tours(ch, stream=stream)
+                torch.cuda.synchronize()
+                clock += time.perf_counter() - t0
+                img = torch.zeros((side, side, 3), dtype=torch.float32, device="cuda")
+                ch.resolve(out=img, stream=stream)
+                stream.synchronize()
+                curve.append((clock, relmse(img.double(), ref)))
+                e += 1
+                if curve[-1][1] <= target:
+                    break
+            st = ch.stats(stream=stream, check=False)
+            hit = next((t for t, r in curve if r <= target), None)
+            return {"time_to_target_s": hit, "final_relmse": curve[-1][1], "epochs": len(curve),
+                    "curve": [[round(t, 3), r] for t, r in curve[:: max(1, len(curve) // 40)]],
+                    "chain_steps": int(st["steps_per_chain"]) * C, "status_word": st["status_word"]}
+
+        plain = run(False)
+        learned = run(True)
+    line = {"metric": METRIC, "workload": f"caustic_slit_{side}x{side}_depth10", "unit": "s to relMSE 1e-2",
+            "relmse_eps": 1e-2, "target": target, "time_limit_s": tmax, "chains": C, "epoch_steps": epoch,
+            "reference": {"samples": args.ref_samples, "seconds": round(t_ref, 2), "noise_relmse_est": ref_noise},
+            "plain": plain, "learned": {**learned, "beta": args.beta, "train_iters_per_epoch": args.train_iters,
+                                        "lr": args.lr, "flow": "6 coupling layers, MLP 2x64, 16 bins, bf16/FP32"},
+            "n_tris": sc.n_tris, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, sc, wl):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -232,9 +321,19 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--chains", type=int, default=0, help="override the chain count (profiling small cases only)")
     ap.add_argument("--chain-steps", type=int, default=0, help="override chain steps per launch (profiling only)")
+    ap.add_argument("--side", type=int, default=1024, help="caustic workload: image side")
+    ap.add_argument("--time-limit", type=float, default=60.0, help="caustic workload: seconds per arm")
+    ap.add_argument("--epoch", type=int, default=32, help="caustic workload: chain steps per epoch")
+    ap.add_argument("--ref-samples", type=int, default=1 << 34, help="caustic workload: reference PT samples")
+    ap.add_argument("--train-iters", type=int, default=20)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--beta", type=float, default=0.5)
     args = ap.parse_args()
     if args.workload == "batched64" and args.impl == "ours":
         run_batched(args)
+        return
+    if args.workload == "caustic" and args.impl == "ours":
+        run_caustic(args)
         return
     sc, wl = workload(args.workload)
     if args.chains:

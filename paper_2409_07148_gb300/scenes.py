@@ -317,6 +317,30 @@ def batched_workload(seed=0, n_scenes=64):
     return out
 
 
+def caustic_slit(width=1024, height=1024, depth=10, n_lon=200, n_lat=201, slit=0.02) -> SceneArrays:
+    """A glass UV sphere (IOR 1.5, 2 n_lon (n_lat - 1) = 80k triangles) over a
+    diffuse floor, lit by an area light that shines through a `slit`-wide gap
+    in an opaque occluder: the light reaches the scene only through the slit,
+    and the sphere focuses it into a caustic on the floor."""
+    b = _Builder()
+    floor = b.add_material(material(LAMBERT, (0.8, 0.8, 0.8)))
+    black = b.add_material(material(LAMBERT, (0.0, 0.0, 0.0)))
+    glass = b.add_material(material(DIELECTRIC, (1.0, 1.0, 1.0), ior=1.5))
+    light = b.add_material(material(LAMBERT, (0.0, 0.0, 0.0), emission=(50.0, 50.0, 50.0)))
+    b.quad((0.5, 0.0, 0.5), (3.0, 0, 0), (0, 0, 3.0), (0, 1, 0), floor)
+    b.quad((0.5, 2.0, 0.5), (0.6, 0, 0), (0, 0, 0.6), (0, -1, 0), light)
+    z0, z1 = 0.5 - slit / 2, 0.5 + slit / 2
+    lo_w = z0 - (-0.5)
+    hi_w = 1.5 - z1
+    for sgn in (1, -1):   # the occluder is opaque from both sides
+        b.quad((0.5, 1.4, -0.5 + lo_w / 2), (2.0, 0, 0), (0, 0, lo_w), (0, sgn, 0), black)
+        b.quad((0.5, 1.4, z1 + hi_w / 2), (2.0, 0, 0), (0, 0, hi_w), (0, sgn, 0), black)
+    v, t = uv_sphere((0.5, 0.3, 0.62), 0.25, n_lon, n_lat)
+    b.mesh(v, t, glass)
+    cam = pinhole((0.5, 1.1, 2.3), (0.5, 0.15, 0.55), (0, 1, 0), 0.45, width / height)
+    return b.build("caustic_slit", cam, width, height, depth)
+
+
 def by_name(name: str, **kw) -> SceneArrays:
     return {"cornell": cornell, "cornell_spheres": cornell_spheres, "furnace": furnace, "empty": empty,
-            "glass_furnace": glass_furnace, "random_boxes": random_boxes}[name](**kw)
+            "glass_furnace": glass_furnace, "random_boxes": random_boxes, "caustic_slit": caustic_slit}[name](**kw)
