@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -247,40 +248,85 @@ def run_caustic(args):
                 perm, w = init_flow_params(sc.D, 0)
                 trainer = jr.Flow(sc.D, perm, w, stream=stream)
                 render = [jr.Flow(sc.D, perm, w, stream=stream), jr.Flow(sc.D, perm, w, stream=stream)]
+                buf = jr.ReplayBuffer(sc.D, args.replay)
             e = 0
+            parts = {"advance": 0.0, "train": 0.0, "drain_switch": 0.0}
+            drain_steps = 0
+            diag = []
+            prev = ch.stats(stream=stream)
+
+            def lap(key, t0):
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                parts[key] += t1 - t0
+                return t1
+
             while clock < tmax:
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                ch.advance(epoch, stream=stream)
+                n_ep = min(int(round(epoch * args.epoch_growth ** e)), args.epoch_max)
+                for k in range(0, n_ep, args.snap_every):
+                    ch.advance(min(args.snap_every, n_ep - k), stream=stream)
+                    if learned:
+                        buf.append(ch, stream=stream)
+                t1 = lap("advance", t0)
+                s0 = ch.stats(stream=stream)["steps_per_chain"]
+                t1 = time.perf_counter()
+                loss = None
                 if learned:
-                    x, wt = jr.snapshot(ch, stream=stream)
-                    trainer.train(x, wt, iters=args.train_iters, batch=8192, lr=args.lr, seed=e, stream=stream)
+                    iters = args.train_iters0 if e < args.warm_epochs else args.train_iters
+                    losses = trainer.train_replay(buf, iters, batch=args.batch, lr=args.lr, seed=e, stream=stream)
+                    loss = float(losses[-16:].mean()) if len(losses) else None
                     nxt = render[e % 2]
                     nxt.copy_params_from(trainer, stream=stream)
+                    t1 = lap("train", t1)
                     jr.set_flow(ch, nxt, args.beta, stream=stream)   # completes the open tours first
                 else:
                     jr.complete_tours(ch, stream=stream)
-                torch.cuda.synchronize()
-                clock += time.perf_counter() - t0
+                t2 = lap("drain_switch", t1)
+                clock += t2 - t0
+                cur = ch.stats(stream=stream)
+                drain_steps += cur["steps_per_chain"] - s0
                 img = torch.zeros((side, side, 3), dtype=torch.float32, device="cuda")
                 ch.resolve(out=img, stream=stream)
                 stream.synchronize()
                 curve.append((clock, relmse(img.double(), ref)))
+                dsteps = (cur["steps_per_chain"] - prev["steps_per_chain"]) * C
+                if len(diag) < 24:
+                    diag.append({"epoch": e, "t": round(clock, 3), "relmse": curve[-1][1], "loss": loss,
+                                 "local_frac": (cur["local_steps"] - prev["local_steps"]) / max(dsteps, 1),
+                                 "regen_per_step": (cur["regenerations"] - prev["regenerations"]) / max(dsteps, 1),
+                                 "replay_rows": buf.rows() if learned else None})
+                prev = cur
                 e += 1
                 if curve[-1][1] <= target:
                     break
             st = ch.stats(stream=stream, check=False)
             hit = next((t for t, r in curve if r <= target), None)
-            return {"time_to_target_s": hit, "final_relmse": curve[-1][1], "epochs": len(curve),
+            # log-log interpolation between the checkpoints around the crossing
+            cross = None
+            for (t0_, r0_), (t1_, r1_) in zip(curve, curve[1:]):
+                if r0_ > target >= r1_:
+                    a = (math.log(target) - math.log(r0_)) / (math.log(r1_) - math.log(r0_))
+                    cross = math.exp(math.log(t0_) + a * (math.log(t1_) - math.log(t0_)))
+                    break
+            return {"time_to_target_s": hit, "time_to_target_interp_s": cross, "final_relmse": curve[-1][1],
+                    "epochs": len(curve),
                     "curve": [[round(t, 3), r] for t, r in curve[:: max(1, len(curve) // 40)]],
-                    "chain_steps": int(st["steps_per_chain"]) * C, "status_word": st["status_word"]}
+                    "seconds": {k: round(v, 3) for k, v in parts.items()}, "drain_steps": drain_steps, "diag": diag,
+                    "regenerations": st["regenerations"], "local_steps": st["local_steps"],
+                    "accepted": st["accepted"], "chain_steps": int(st["steps_per_chain"]) * C,
+                    "status_word": st["status_word"]}
 
         plain = run(False)
         learned = run(True)
     line = {"metric": METRIC, "workload": f"caustic_slit_{side}x{side}_depth10", "unit": "s to relMSE 1e-2",
             "relmse_eps": 1e-2, "target": target, "time_limit_s": tmax, "chains": C, "epoch_steps": epoch,
+            "epoch_growth": args.epoch_growth, "epoch_max": args.epoch_max,
             "reference": {"samples": args.ref_samples, "seconds": round(t_ref, 2), "noise_relmse_est": ref_noise},
             "plain": plain, "learned": {**learned, "beta": args.beta, "train_iters_per_epoch": args.train_iters,
+                                        "train_iters_first": args.train_iters0, "warm_epochs": args.warm_epochs,
+                                        "batch": args.batch, "snap_every": args.snap_every, "replay": args.replay,
                                         "lr": args.lr, "flow": "6 coupling layers, MLP 2x64, 16 bins, bf16/FP32"},
             "n_tris": sc.n_tris, "data": "synthetic"}
     print(json.dumps(line), flush=True)
@@ -323,10 +369,17 @@ def main():
     ap.add_argument("--chain-steps", type=int, default=0, help="override chain steps per launch (profiling only)")
     ap.add_argument("--side", type=int, default=1024, help="caustic workload: image side")
     ap.add_argument("--time-limit", type=float, default=60.0, help="caustic workload: seconds per arm")
-    ap.add_argument("--epoch", type=int, default=32, help="caustic workload: chain steps per epoch")
+    ap.add_argument("--epoch", type=int, default=128, help="caustic workload: chain steps of the first epoch")
+    ap.add_argument("--epoch-growth", type=float, default=1.25, help="caustic workload: epoch length factor")
+    ap.add_argument("--epoch-max", type=int, default=1024, help="caustic workload: longest epoch (steps)")
     ap.add_argument("--ref-samples", type=int, default=1 << 34, help="caustic workload: reference PT samples")
-    ap.add_argument("--train-iters", type=int, default=20)
-    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--train-iters", type=int, default=50, help="caustic workload: Adam steps per epoch")
+    ap.add_argument("--train-iters0", type=int, default=400, help="caustic workload: Adam steps in the first epochs")
+    ap.add_argument("--warm-epochs", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=16384, help="caustic workload: training minibatch rows")
+    ap.add_argument("--snap-every", type=int, default=16, help="caustic workload: steps between training snapshots")
+    ap.add_argument("--replay", type=int, default=1 << 20, help="caustic workload: replay ring rows")
+    ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--beta", type=float, default=0.5)
     args = ap.parse_args()
     if args.workload == "batched64" and args.impl == "ours":

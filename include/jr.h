@@ -69,6 +69,7 @@ typedef enum {
 #define JR_STATUS_NONFINITE 1u  /* F(x) was NaN/Inf for some state: it was treated as 0 */
 #define JR_STATUS_TRAVERSAL 2u  /* a ray exhausted the BVH node-visit budget: treated as a miss */
 #define JR_STATUS_STACK 4u      /* a traversal stack overflowed: treated as a miss */
+#define JR_STATUS_FLOW_WAIT 8u  /* a flow kernel's weight copy did not arrive in time: its outputs are invalid */
 
 typedef struct jr_scene jr_scene;
 typedef struct jr_chains jr_chains;
@@ -333,6 +334,10 @@ void jr_flow_destroy(jr_flow* flow);
 /* Replace / read the FP32 parameters (host arrays, the layout above). */
 jr_status jr_flow_set_params(jr_flow* flow, const float* params, void* stream);
 jr_status jr_flow_get_params(jr_flow* flow, float* params, void* stream);
+/* JR_STATUS_* bits (sticky) of the flow's own jr_flow_log_density /
+ * jr_flow_sample launches; launches made for a chain set report to that set's
+ * status word instead.  Synchronises. */
+jr_status jr_flow_get_status(jr_flow* flow, uint32_t* status_out, void* stream);
 
 /* log q(x) for n rows of x_dev [D][n] (device, SoA) into lq_dev [n].  Async. */
 jr_status jr_flow_log_density(jr_flow* flow, const float* x_dev, uint64_t n, float* lq_dev, void* stream);
@@ -350,6 +355,15 @@ jr_status jr_flow_copy_params(jr_flow* dst, const jr_flow* src, void* stream);
  * p + c~ u).  Call between advances (the states are then in x).  Async. */
 jr_status jr_chains_snapshot(jr_chains* chains, float* x_dev, float* w_dev, void* stream);
 
+/* The same rows, keeping only those of weight > 0 (states with p > 0), appended
+ * to a ring buffer of `capacity` rows: x_ring [D][capacity], w_ring [capacity]
+ * (device, caller-owned).  *total_dev (device, caller-owned, start at 0) counts
+ * every row ever appended; row r lands in slot r % capacity, so the buffer
+ * holds min(total, capacity) rows, in slots [0, min(total, capacity)).  The
+ * order of rows within one call is unspecified.  Async. */
+jr_status jr_chains_snapshot_append(jr_chains* chains, float* x_ring, float* w_ring, uint64_t capacity,
+                                    unsigned long long* total_dev, void* stream);
+
 /* Time-weighted maximum likelihood: the loss -sum_r w_r log q(x_r) / sum_r w_r
  * over rows [off, off + batch) of x_dev [D][n], w_dev [n] (device), and its
  * gradient w.r.t. the parameters (host, jr_flow_param_count floats, the layout
@@ -363,6 +377,12 @@ jr_status jr_flow_gradient(jr_flow* flow, const float* x_dev, const float* w_dev
  * loss_host (may be NULL) gets the loss of every step.  Synchronises. */
 jr_status jr_flow_train(jr_flow* flow, const float* x_dev, const float* w_dev, uint64_t n, uint32_t iters,
                         uint32_t batch, float lr, uint64_t seed, float* loss_host, void* stream);
+/* The same on the first n_rows rows of x_dev [D][stride], w_dev [stride] (a
+ * partly filled jr_chains_snapshot_append ring): minibatches are windows of
+ * `batch` rows inside [0, n_rows); batch <= n_rows <= stride.  Synchronises. */
+jr_status jr_flow_train_rows(jr_flow* flow, const float* x_dev, const float* w_dev, uint64_t stride,
+                             uint64_t n_rows, uint32_t iters, uint32_t batch, float lr, uint64_t seed,
+                             float* loss_host, void* stream);
 
 /* Complete every chain's current tour, then start every chain on a new tour.
  * The estimator of Section 6.3 divides by J, the number of completed tours;

@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB_NAME = "libjr_gb300.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["jr_kernels.cu", "jr_wavefront.cu", "jr_flow.cu", "jr_api.cu", "bvh_build.cpp"]
+SOURCES = ["jr_kernels.cu", "jr_wavefront.cu", "jr_flow.cu", "jr_flow_infer.cu", "jr_api.cu", "bvh_build.cpp"]
 HEADERS = ["jr_internal.h", "jr_device.cuh", os.path.join("..", "..", "include", "jr.h")]
 
 

@@ -733,6 +733,8 @@ struct jr_flow {
     float* master = nullptr;       // [kFL][S] FP32, the documented layout
     __nv_bfloat16* wb = nullptr;   // packed bf16 weights
     float* bias = nullptr;         // packed FP32 biases
+    unsigned char* ws = nullptr;   // inference layout
+    unsigned int* status = nullptr;  // JR_STATUS_* bits of the flow's own launches
     float* adam_m = nullptr;       // optimiser moments [kFL][S]
     float* adam_v = nullptr;
     float* grad = nullptr;         // [kFL][S] gradient accumulator
@@ -745,6 +747,7 @@ struct jr_flow {
         f.perm = perm;
         f.wb = wb;
         f.bias = bias;
+        f.ws = ws;
         f.beta = beta;
         return f;
     }
@@ -753,6 +756,8 @@ struct jr_flow {
         cudaFree(master);
         cudaFree(wb);
         cudaFree(bias);
+        cudaFree(ws);
+        cudaFree(status);
         cudaFree(adam_m);
         cudaFree(adam_v);
         cudaFree(grad);
@@ -765,6 +770,15 @@ uint64_t jr_flow_param_count(uint32_t dim) {
     if (dim < 2 || dim > (uint32_t)kMaxDim || dim % 2) return 0;
     return (uint64_t)kFL * flow_layer_floats(dim);
 }
+
+namespace {
+// Both packed copies of the master parameters: the training layout and the
+// inference layout.
+cudaError_t pack_all(jr_flow* f, cudaStream_t st) {
+    cudaError_t e = launch_flow_pack(f->master, f->wb, f->bias, f->AK, st);
+    return e != cudaSuccess ? e : launch_flow_pack_ws(f->master, f->ws, f->AK, st);
+}
+}  // namespace
 
 jr_status jr_flow_create(uint32_t dim, const int32_t* perm, const float* params, void* stream, jr_flow** out) {
     if (!perm || !params || !out) return fail(JR_ERR_INVALID_ARG, "jr_flow_create: null argument");
@@ -792,9 +806,12 @@ jr_status jr_flow_create(uint32_t dim, const int32_t* perm, const float* params,
     if ((e = dev_alloc(&f->perm, pm.size())) != cudaSuccess || (e = dev_alloc(&f->master, P)) != cudaSuccess ||
         (e = dev_alloc(&f->wb, nwb)) != cudaSuccess ||
         (e = dev_alloc(&f->bias, (size_t)kFL * (2 * kFH + f->AK))) != cudaSuccess ||
+        (e = dev_alloc(&f->ws, (size_t)kFL * flow_ws_layer_bytes(f->AK))) != cudaSuccess ||
+        (e = dev_alloc(&f->status, 1)) != cudaSuccess ||
+        (e = cudaMemsetAsync(f->status, 0, sizeof(unsigned int), st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(f->perm, pm.data(), pm.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(f->master, params, sizeof(float) * P, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = launch_flow_pack(f->master, f->wb, f->bias, f->AK, st)) != cudaSuccess ||
+        (e = pack_all(f, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess) {
         delete f;
         return cuda_fail(e, "jr_flow_create");
@@ -811,8 +828,18 @@ jr_status jr_flow_set_params(jr_flow* f, const float* params, void* stream) {
     JR_CUDA(cudaMemcpyAsync(f->master, params, sizeof(float) * kFL * flow_layer_floats(f->D), cudaMemcpyHostToDevice,
                             st),
             "jr_flow_set_params");
-    JR_CUDA(launch_flow_pack(f->master, f->wb, f->bias, f->AK, st), "jr_flow_set_params");
+    JR_CUDA(pack_all(f, st), "jr_flow_set_params");
     JR_CUDA(cudaStreamSynchronize(st), "jr_flow_set_params");
+    return JR_OK;
+}
+
+jr_status jr_flow_get_status(jr_flow* f, uint32_t* status_out, void* stream) {
+    if (!f || !status_out) return fail(JR_ERR_INVALID_ARG, "jr_flow_get_status: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned int v = 0;
+    JR_CUDA(cudaMemcpyAsync(&v, f->status, sizeof(v), cudaMemcpyDeviceToHost, st), "jr_flow_get_status");
+    JR_CUDA(cudaStreamSynchronize(st), "jr_flow_get_status");
+    *status_out = v;
     return JR_OK;
 }
 
@@ -830,7 +857,7 @@ jr_status jr_flow_log_density(jr_flow* f, const float* x_dev, uint64_t n, float*
     if (!f || (n > 0 && (!x_dev || !lq_dev))) return fail(JR_ERR_INVALID_ARG, "jr_flow_log_density: null argument");
     if (n >= (1ull << 32)) return fail(JR_ERR_INVALID_ARG, "jr_flow_log_density: n must be below 2^32");
     JR_CUDA(launch_flow(f->view(0.f), false, nullptr, const_cast<float*>(x_dev), nullptr, nullptr, n, nullptr,
-                        nullptr, (uint32_t)n, nullptr, nullptr, lq_dev, (cudaStream_t)stream),
+                        nullptr, (uint32_t)n, nullptr, nullptr, lq_dev, f->status, (cudaStream_t)stream),
             "jr_flow_log_density");
     return JR_OK;
 }
@@ -839,7 +866,7 @@ jr_status jr_flow_sample(jr_flow* f, float* xz_dev, uint64_t n, float* lq_dev, v
     if (!f || (n > 0 && (!xz_dev || !lq_dev))) return fail(JR_ERR_INVALID_ARG, "jr_flow_sample: null argument");
     if (n >= (1ull << 32)) return fail(JR_ERR_INVALID_ARG, "jr_flow_sample: n must be below 2^32");
     JR_CUDA(launch_flow(f->view(0.f), true, nullptr, xz_dev, nullptr, nullptr, n, nullptr, nullptr, (uint32_t)n,
-                        nullptr, nullptr, lq_dev, (cudaStream_t)stream),
+                        nullptr, nullptr, lq_dev, f->status, (cudaStream_t)stream),
             "jr_flow_sample");
     return JR_OK;
 }
@@ -853,13 +880,22 @@ jr_status jr_flow_copy_params(jr_flow* dst, const jr_flow* src, void* stream) {
             "jr_flow_copy_params");
     JR_CUDA(cudaMemcpyAsync(dst->master, src->master, sizeof(float) * P, cudaMemcpyDeviceToDevice, st),
             "jr_flow_copy_params");
-    JR_CUDA(launch_flow_pack(dst->master, dst->wb, dst->bias, dst->AK, st), "jr_flow_copy_params");
+    JR_CUDA(pack_all(dst, st), "jr_flow_copy_params");
     return JR_OK;
 }
 
 jr_status jr_chains_snapshot(jr_chains* c, float* x_dev, float* w_dev, void* stream) {
     if (!c || !x_dev || !w_dev) return fail(JR_ERR_INVALID_ARG, "jr_chains_snapshot: null argument");
     JR_CUDA(launch_snapshot(c->view, x_dev, w_dev, (cudaStream_t)stream), "jr_chains_snapshot");
+    return JR_OK;
+}
+
+jr_status jr_chains_snapshot_append(jr_chains* c, float* x_ring, float* w_ring, uint64_t capacity,
+                                    unsigned long long* total_dev, void* stream) {
+    if (!c || !x_ring || !w_ring || !total_dev) return fail(JR_ERR_INVALID_ARG, "jr_chains_snapshot_append: null argument");
+    if (capacity == 0) return fail(JR_ERR_INVALID_ARG, "jr_chains_snapshot_append: capacity must be > 0");
+    JR_CUDA(launch_snapshot_append(c->view, x_ring, w_ring, capacity, total_dev, (cudaStream_t)stream),
+            "jr_chains_snapshot_append");
     return JR_OK;
 }
 
@@ -885,9 +921,16 @@ jr_status jr_flow_gradient(jr_flow* f, const float* x_dev, const float* w_dev, u
 
 jr_status jr_flow_train(jr_flow* f, const float* x_dev, const float* w_dev, uint64_t n, uint32_t iters,
                         uint32_t batch, float lr, uint64_t seed, float* loss_host, void* stream) {
+    return jr_flow_train_rows(f, x_dev, w_dev, n, n, iters, batch, lr, seed, loss_host, stream);
+}
+
+jr_status jr_flow_train_rows(jr_flow* f, const float* x_dev, const float* w_dev, uint64_t n, uint64_t n_rows,
+                             uint32_t iters, uint32_t batch, float lr, uint64_t seed, float* loss_host,
+                             void* stream) {
     if (!f || !x_dev || !w_dev) return fail(JR_ERR_INVALID_ARG, "jr_flow_train: null argument");
-    if (batch == 0 || batch % 64 != 0 || batch > n)
-        return fail(JR_ERR_INVALID_ARG, "jr_flow_train: batch must be a positive multiple of 64, at most n");
+    if (n_rows > n) return fail(JR_ERR_INVALID_ARG, "jr_flow_train: n_rows exceeds the row stride");
+    if (batch == 0 || batch % 64 != 0 || batch > n_rows)
+        return fail(JR_ERR_INVALID_ARG, "jr_flow_train: batch must be a positive multiple of 64, at most n_rows");
     if (!(lr > 0.f)) return fail(JR_ERR_INVALID_ARG, "jr_flow_train: lr must be > 0");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t P = (size_t)kFL * flow_layer_floats(f->D);
@@ -914,7 +957,7 @@ jr_status jr_flow_train(jr_flow* f, const float* x_dev, const float* w_dev, uint
         rng ^= rng >> 27;
         rng *= 0x94D049BB133111EBull;
         rng ^= rng >> 31;
-        const uint64_t off = rng % (n - batch + 1);
+        const uint64_t off = rng % (n_rows - batch + 1);
         if ((e = cudaMemsetAsync(f->grad, 0, sizeof(float) * P, st)) != cudaSuccess) break;
         if ((e = launch_flow_train_step(f->view(0.f), x_dev, w_dev, n, off, batch, f->grad, scal + 2 * it,
                                         scal + 2 * it + 1, st)) != cudaSuccess)
@@ -922,6 +965,7 @@ jr_status jr_flow_train(jr_flow* f, const float* x_dev, const float* w_dev, uint
         if ((e = launch_adam(f->master, f->grad, f->adam_m, f->adam_v, P, lr, ++f->adam_t, st)) != cudaSuccess) break;
         if ((e = launch_flow_pack(f->master, f->wb, f->bias, f->AK, st)) != cudaSuccess) break;
     }
+    if (e == cudaSuccess) e = launch_flow_pack_ws(f->master, f->ws, f->AK, st);
     std::vector<float> h(2 * (size_t)std::max<uint32_t>(iters, 1));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h.data(), scal, sizeof(float) * h.size(), cudaMemcpyDeviceToHost, st);
@@ -947,13 +991,28 @@ jr_status drain_impl(jr_chains* c, uint32_t max_steps, uint64_t* remaining, cuda
     JR_CUDA(cudaMemsetAsync(c->view.wf.done, 0, c->view.n, st), who);
     unsigned int active = (unsigned int)std::min<uint64_t>(c->view.n, 0xffffffffu);
     uint32_t k = 0;
+    // Steps are enqueued in groups that grow while tours stay open, so the
+    // host waits rarely.  A step after the last tour has ended is a no-op; the
+    // drain mark (1 + the last step after which a tour was open) gives the
+    // steps the drain really took, as if the host had checked after every step.
+    JR_CUDA(cudaMemsetAsync(c->view.counters + 3, 0, sizeof(unsigned long long), st), who);
+    const uint64_t s0 = c->steps;
+    uint32_t group = 1;
     while (active > 0 && k < max_steps) {
-        JR_CUDA(launch_wavefront(c->scene->view, c->view, c->steps, 1, st, kModeDrain), who);
-        c->steps += 1;
-        ++k;
+        const uint32_t g = std::min(group, max_steps - k);
+        for (uint32_t j = 0; j < g; ++j)
+            JR_CUDA(launch_wavefront(c->scene->view, c->view, s0 + k + j, 1, st, kModeDrain), who);
+        k += g;
         JR_CUDA(cudaMemcpyAsync(&active, c->view.wf.qcount + kQActive, sizeof(active), cudaMemcpyDeviceToHost, st),
                 who);
         JR_CUDA(cudaStreamSynchronize(st), who);
+        group = std::min<uint32_t>(2 * group, 16);
+    }
+    if (k > 0) {
+        unsigned long long mark = 0;
+        JR_CUDA(cudaMemcpyAsync(&mark, c->view.counters + 3, sizeof(mark), cudaMemcpyDeviceToHost, st), who);
+        JR_CUDA(cudaStreamSynchronize(st), who);
+        c->steps = active > 0 ? s0 + k : std::max<uint64_t>(mark, s0) + 1;
     }
     JR_CUDA(launch_fold(c->view, st), who);
     if (remaining) *remaining = active;

@@ -11,10 +11,13 @@
 // Sampling", 2019).  The MLP GEMMs run as mma.sync m16n8k16 with bf16
 // operands and FP32 accumulation; everything else is FP32.
 //
-// One CTA of 128 threads works on tiles of 64 rows (4 warps x 16 rows).  Per
-// layer it stages the bf16 weights in shared memory; each warp runs the three
-// GEMMs of its 16 rows; the 64-column chunks of logits go through shared
-// memory to the per-coordinate softmax / bin / CDF step.
+// This file holds the training side (forward with stored layer inputs,
+// backward, Adam, parameter packing, training rows from the chains); the
+// inference kernels are in jr_flow_infer.cu.  The forward pass here works on
+// tiles of 64 rows (4 warps x 16 rows) per CTA of 128 threads: per layer it
+// stages the bf16 weights in shared memory; each warp runs the three GEMMs of
+// its 16 rows; the 64-column chunks of logits go through shared memory to the
+// per-coordinate softmax / bin / CDF step.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -224,62 +227,6 @@ __device__ __forceinline__ void coupling_layer(const FlowView& f, int l, FlowSme
         dlq += __shfl_down_sync(0xffffffffu, dlq, 16);
         if (lane < 16) sm.lq[r] += dlq;
         __syncwarp();
-    }
-}
-
-// Rows: chains idx[j] (or j when idx is null) for j < *count (or n_rows).
-// Row i lives in SoA buffer [D][n] bufA, or -- when par is given -- in bufA if
-// par[i] is 1 and bufB otherwise (the wavefront's candidate buffer).  Density:
-// u_out[i] = beta q + 1 - beta.  Sample: the row is replaced by T^{-1}(row),
-// u_out as above, and the camera ray of the new state goes to path (if given).
-template <bool kSample>
-__global__ void __launch_bounds__(128) flow_kernel(FlowView f, SceneView s, float* bufA, float* bufB,
-                                                   const uint8_t* par, uint64_t n, const uint32_t* idx,
-                                                   const unsigned int* count_dev, uint32_t n_rows, float* u_out,
-                                                   float4* path, float* lq_out) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    FlowSmem& sm = *reinterpret_cast<FlowSmem*>(smem_raw);
-    const uint32_t count = count_dev ? *count_dev : n_rows;
-    const int D = (int)f.D;
-    auto row_buf = [&](uint32_t i) -> float* { return (par && !par[i]) ? bufB : bufA; };
-    for (uint32_t tile = blockIdx.x; tile * kRows < count; tile += gridDim.x) {
-        __syncthreads();
-        for (int r = threadIdx.x; r < kRows; r += blockDim.x) {
-            const uint32_t j = tile * kRows + r;
-            sm.row_idx[r] = j < count ? (idx ? idx[j] : j) : 0xffffffffu;
-            sm.lq[r] = 0.f;
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < kRows * D; e += blockDim.x) {
-            const int r = e / D, d = e % D;
-            const uint32_t i = sm.row_idx[r];
-            sm.x[r * kXs + d] = i != 0xffffffffu ? row_buf(i)[(uint64_t)d * n + i] : 0.5f;
-        }
-        if (!kSample)
-            for (int l = 0; l < kFL; ++l) coupling_layer<false>(f, l, sm);
-        else
-            for (int l = kFL - 1; l >= 0; --l) coupling_layer<true>(f, l, sm);
-        __syncthreads();
-        if (kSample)
-            for (int e = threadIdx.x; e < kRows * D; e += blockDim.x) {
-                const int r = e / D, d = e % D;
-                const uint32_t i = sm.row_idx[r];
-                if (i != 0xffffffffu) row_buf(i)[(uint64_t)d * n + i] = sm.x[r * kXs + d];
-            }
-        for (int r = threadIdx.x; r < kRows; r += blockDim.x) {
-            const uint32_t i = sm.row_idx[r];
-            if (i == 0xffffffffu) continue;
-            const float lq = sm.lq[r];
-            if (u_out) u_out[i] = f.beta * __expf(lq) + (1.0f - f.beta);
-            if (lq_out) lq_out[i] = lq;
-            if (kSample && path) {
-                float3 o, d;
-                camera_ray(s, sm.x[r * kXs], sm.x[r * kXs + 1], o, d);
-                path[3 * (uint64_t)i] = make_float4(o.x, o.y, o.z, d.x);
-                path[3 * (uint64_t)i + 1] = make_float4(d.y, d.z, 1.f, 1.f);
-                path[3 * (uint64_t)i + 2] = make_float4(1.f, 0.f, 0.f, 0.f);
-            }
-        }
     }
 }
 
@@ -639,12 +586,37 @@ __global__ void snapshot_kernel(ChainView c, float* x_out, float* w_out) {
     w_out[i] = p > 0.f ? p / (p + c.c_tilde * u) : 0.f;
 }
 
-}  // namespace
+// The rows of weight > 0 appended to a ring: one counter update per warp.
+__global__ void snapshot_append_kernel(ChainView c, float* x_ring, float* w_ring, uint64_t cap,
+                                       unsigned long long* total) {
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    float w = 0.f;
+    if (i < c.n) {
+        const float p = c.fpu[3 * c.n + i], u = c.fpu[4 * c.n + i];
+        w = p > 0.f ? p / (p + c.c_tilde * u) : 0.f;
+    }
+    const unsigned keep = __ballot_sync(0xffffffffu, w > 0.f);
+    if (!keep) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(total, (unsigned long long)__popc(keep));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (!(w > 0.f)) return;
+    const uint64_t slot = (base + __popc(keep & ((1u << lane) - 1u))) % cap;
+    for (uint32_t d = 0; d < c.dim; ++d) x_ring[d * cap + slot] = c.x[d * c.n + i];
+    w_ring[slot] = w;
+}
 
-size_t flow_smem_bytes() { return sizeof(FlowSmem); }
+}  // namespace
 
 cudaError_t launch_snapshot(const ChainView& c, float* x_out, float* w_out, cudaStream_t st) {
     snapshot_kernel<<<(unsigned)((c.n + 255) / 256), 256, 0, st>>>(c, x_out, w_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_snapshot_append(const ChainView& c, float* x_ring, float* w_ring, uint64_t cap,
+                                   unsigned long long* total, cudaStream_t st) {
+    snapshot_append_kernel<<<(unsigned)((c.n + 255) / 256), 256, 0, st>>>(c, x_ring, w_ring, cap, total);
     return cudaGetLastError();
 }
 
@@ -672,39 +644,6 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, uint64_t c
 
 cudaError_t launch_flow_pack(const float* master, __nv_bfloat16* wb, float* bias, uint32_t AK, cudaStream_t st) {
     pack_kernel<<<dim3(16, kFL), 256, 0, st>>>(master, wb, bias, AK);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_flow(const FlowView& f, bool sample, const SceneView* s, float* bufA, float* bufB,
-                        const uint8_t* par, uint64_t n, const uint32_t* idx, const unsigned int* count_dev,
-                        uint32_t n_rows, float* u_out, float4* path, float* lq_out, cudaStream_t st) {
-    static int grid = 0;
-    const size_t shm = sizeof(FlowSmem);
-    if (grid == 0) {
-        int dev = 0, sms = 0, per = 0;
-        cudaError_t e;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(flow_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)) !=
-                cudaSuccess ||
-            (e = cudaFuncSetAttribute(flow_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)) !=
-                cudaSuccess)
-            return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, flow_kernel<false>, 128, shm)) != cudaSuccess)
-            return e;
-        grid = sms * (per > 0 ? per : 1);
-    }
-    SceneView sv{};
-    if (s) sv = *s;
-    unsigned g = (unsigned)grid;
-    if (!count_dev) g = (unsigned)std::min<uint64_t>(g, (n_rows + kRows - 1) / kRows);
-    if (g == 0) return cudaSuccess;
-    if (sample)
-        flow_kernel<true><<<g, 128, shm, st>>>(f, sv, bufA, bufB, par, n, idx, count_dev, n_rows, u_out, path,
-                                               lq_out);
-    else
-        flow_kernel<false><<<g, 128, shm, st>>>(f, sv, bufA, bufB, par, n, idx, count_dev, n_rows, u_out, path,
-                                                lq_out);
     return cudaGetLastError();
 }
 

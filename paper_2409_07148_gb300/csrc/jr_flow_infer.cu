@@ -1,0 +1,464 @@
+// Inference of the regeneration flow (density and sampling directions) on the
+// tensor cores, sm_103a.
+//
+// The flow is the library's own regeneration distribution (not in the paper):
+// mu = beta mu_flow + (1 - beta) uniform, u = beta q + (1 - beta), so that the
+// killing rate k = c~ u / p of Section 6.2 keeps an exact density.  L = 6
+// coupling layers, each an MLP (A -> 64 -> 64 -> A K logits, ReLU) feeding
+// piecewise-linear CDFs of K = 16 bins (Mueller et al., "Neural Importance
+// Sampling", 2019): bin masses Q = (1 - E) softmax(o) + E / K, density factor
+// K Q[bin].
+//
+// Design:
+//   * A CTA of 8 warps works on tiles of 128 rows, 16 rows per warp; the rows of
+//     a warp never leave it.  The three GEMMs of a layer run as mma.sync
+//     m16n8k16 (bf16 operands, FP32 accumulation) and stay in registers: the
+//     accumulator fragments of one GEMM, biased, ReLU'd and rounded to bf16, are
+//     the A fragments of the next.
+//   * The per-coordinate softmax and CDF step works on the logits' accumulator
+//     fragments directly: the 4 lanes of a quad hold the 16 bins of a row, and
+//     max, sum, prefix and bin search are quad shuffles.
+//   * Weights stream through shared memory one layer at a time, double
+//     buffered: one elected thread copies a layer's block (bf16 weights in a
+//     bank-conflict-free XOR-swizzled layout, then the FP32 biases) with one
+//     cp.async.bulk into the buffer freed two layers earlier; an mbarrier
+//     counts the bytes in.  Every wait is bounded; a wait that runs out sets
+//     JR_STATUS_FLOW_WAIT and the kernel stops after its copies have landed.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/jr.h"
+#include "jr_device.cuh"
+#include "jr_internal.h"
+
+namespace jr {
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kTile = 16 * kWarps;  // rows per CTA tile
+constexpr int kThreads = 32 * kWarps;
+constexpr uint32_t kNoRow = 0xffffffffu;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+constexpr uint32_t kWaitIters = 1u << 26;
+
+// Shared-memory layout (bytes): two mbarriers, perm [kFL][D], row ids
+// [kTile], the rows' states [kTile][D + 1] FP32, two layer buffers.
+constexpr size_t kOffBar = 0, kOffPerm = 64, kOffRows = 256, kOffX = kOffRows + 4 * kTile;
+__host__ __device__ constexpr size_t round128(size_t b) { return (b + 127) & ~(size_t)127; }
+__host__ __device__ constexpr size_t x_bytes(uint32_t D) { return round128(sizeof(float) * kTile * (D + 1)); }
+__host__ __device__ constexpr size_t buf_bytes(uint32_t AK) { return round128(flow_ws_layer_bytes(AK)); }
+__host__ __device__ constexpr size_t infer_smem(uint32_t D, uint32_t AK) {
+    return round128(kOffX) + x_bytes(D) + 2 * buf_bytes(AK);
+}
+static_assert(kOffPerm + kFL * kMaxDim <= kOffRows, "perm table overlaps the row ids");
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for phase `parity` of bar; false when the time or iteration budget ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (uint32_t it = 0; it < kWaitIters; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        __nanosleep(32);
+        if ((it & 255) == 255 && globaltimer() - t0 > kWaitNs) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+__device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// B fragment of a swizzled [N][64] bf16 matrix: rows n, k = k0 + 2t (+8).
+__device__ __forceinline__ void frag_b64(const __nv_bfloat16* W, int n, int k0, int t, uint32_t& b0, uint32_t& b1) {
+    const __nv_bfloat16* row = W + n * 64;
+    const int c = k0 >> 3, s = n & 7;
+    b0 = lds32(row + (((c) ^ s) << 3) + 2 * t);
+    b1 = lds32(row + (((c + 1) ^ s) << 3) + 2 * t);
+}
+
+// ReLU(acc + b) of 8 n-tiles (64 columns) as bf16 A fragments of a K = 64 GEMM.
+__device__ __forceinline__ void relu_to_frags(const float (&acc)[8][4], const float* bias, int t, uint32_t (&a)[4][4]) {
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const int c0 = 16 * kk + 2 * t, c1 = c0 + 8;
+        const float b00 = bias[c0], b01 = bias[c0 + 1], b10 = bias[c1], b11 = bias[c1 + 1];
+        a[kk][0] = pack_bf16(fmaxf(acc[2 * kk][0] + b00, 0.f), fmaxf(acc[2 * kk][1] + b01, 0.f));
+        a[kk][1] = pack_bf16(fmaxf(acc[2 * kk][2] + b00, 0.f), fmaxf(acc[2 * kk][3] + b01, 0.f));
+        a[kk][2] = pack_bf16(fmaxf(acc[2 * kk + 1][0] + b10, 0.f), fmaxf(acc[2 * kk + 1][1] + b11, 0.f));
+        a[kk][3] = pack_bf16(fmaxf(acc[2 * kk + 1][2] + b10, 0.f), fmaxf(acc[2 * kk + 1][3] + b11, 0.f));
+    }
+}
+
+__device__ __forceinline__ float quad_sum(float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v + __shfl_xor_sync(0xffffffffu, v, 2);
+}
+__device__ __forceinline__ float quad_max(float v) {
+    v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 1));
+    return fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 2));
+}
+// Exclusive prefix sum of v over the quad's lanes t = 0..3 (in lane order).
+__device__ __forceinline__ float quad_exclusive(float v, int t) {
+    float s = v, n = __shfl_up_sync(0xffffffffu, s, 1, 4);
+    if (t >= 1) s += n;
+    n = __shfl_up_sync(0xffffffffu, s, 2, 4);
+    if (t >= 2) s += n;
+    n = __shfl_up_sync(0xffffffffu, s, 1, 4);
+    return t == 0 ? 0.f : n;
+}
+
+// One coordinate's CDF step for one row.  L holds this lane's 4 logits, of
+// bins 2t, 2t+1, 8+2t, 9+2t.  Density: v = t in [0,1) becomes CDF(t);
+// sampling: v = c becomes CDF^{-1}(c).  Returns log(K Q[bin]).
+template <bool kSample>
+__device__ __forceinline__ float cdf_step(const float (&L)[4], int t, float& v) {
+    const float m = quad_max(fmaxf(fmaxf(L[0], L[1]), fmaxf(L[2], L[3])));
+    float Q[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Q[i] = __expf(L[i] - m);
+    const float S = quad_sum((Q[0] + Q[1]) + (Q[2] + Q[3]));
+    const float sc = (1.0f - kFE) / S;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Q[i] = Q[i] * sc + kFE / kFK;
+    const int kb[4] = {2 * t, 2 * t + 1, 8 + 2 * t, 9 + 2 * t};
+    int b;
+    if (!kSample) {
+        b = min((int)(v * (float)kFK), kFK - 1);
+    } else {
+        // inclusive cumulative masses of this lane's bins, in bin order
+        const float s1 = Q[0] + Q[1], s2 = Q[2] + Q[3];
+        const float e1 = quad_exclusive(s1, t), h0 = quad_sum(s1), e2 = quad_exclusive(s2, t);
+        const float c0 = e1 + Q[0], c1 = c0 + Q[1], c2 = h0 + e2 + Q[2], c3 = c2 + Q[3];
+        float cnt = (float)((c0 <= v) + (c1 <= v) + (c2 <= v) + (c3 <= v));
+        b = min((int)quad_sum(cnt), kFK - 1);
+    }
+    float lo = 0.f, qb = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        lo += kb[i] < b ? Q[i] : 0.f;
+        qb += kb[i] == b ? Q[i] : 0.f;
+    }
+    lo = quad_sum(lo);
+    qb = quad_sum(qb);
+    if (!kSample) {
+        v = lo + (v * (float)kFK - (float)b) * qb;
+    } else {
+        const float xs = ((float)b + (v - lo) / qb) * (1.0f / (float)kFK);
+        v = fminf(fmaxf(xs, 0.0f), 0.99999994f);
+    }
+    return __logf((float)kFK * qb);
+}
+
+// One coupling layer for this warp's 16 rows (xw: [16][xs] FP32 states; pm:
+// the layer's permutation; wl: the layer's block in shared memory).
+template <bool kSample>
+__device__ __forceinline__ void coupling(const unsigned char* wl, const uint8_t* pm, int A, int AK, float* xw, int xs,
+                                         float& lq0, float& lq1) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const __nv_bfloat16* W1 = reinterpret_cast<const __nv_bfloat16*>(wl);
+    const __nv_bfloat16* W2 = W1 + kFH * kFAP;
+    const __nv_bfloat16* W3 = W2 + kFH * kFH;
+    const float* b1 = reinterpret_cast<const float*>(W3 + (size_t)AK * kFH);
+    const float* b2 = b1 + kFH;
+    const float* b3 = b2 + kFH;
+    uint32_t a[4][4];
+    {   // layer 1: K = 16 (the A conditioning coordinates, zero-padded)
+        auto xa = [&](int r, int c) { return c < A ? xw[r * xs + pm[c]] : 0.f; };
+        uint32_t a0[4] = {pack_bf16(xa(g, 2 * t), xa(g, 2 * t + 1)), pack_bf16(xa(g + 8, 2 * t), xa(g + 8, 2 * t + 1)),
+                          pack_bf16(xa(g, 2 * t + 8), xa(g, 2 * t + 9)),
+                          pack_bf16(xa(g + 8, 2 * t + 8), xa(g + 8, 2 * t + 9))};
+        float acc[8][4];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+            const int n = 8 * q + g, s = (n >> 2) & 1;
+            const __nv_bfloat16* row = W1 + n * kFAP;
+            mma(acc[q], a0, lds32(row + ((0 ^ s) << 3) + 2 * t), lds32(row + ((1 ^ s) << 3) + 2 * t));
+        }
+        relu_to_frags(acc, b1, t, a);
+    }
+    {   // layer 2: 64 -> 64
+        float acc[8][4];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                uint32_t b0, bb;
+                frag_b64(W2, 8 * q + g, 16 * kk, t, b0, bb);
+                mma(acc[q], a[kk], b0, bb);
+            }
+        relu_to_frags(acc, b2, t, a);
+    }
+    // layer 3 and the couplings, 4 coordinates (8 n-tiles of logits) at a time
+    for (int j0 = 0; j0 < A; j0 += 4) {
+        float acc[8][4];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+        const int nq = min(8, 2 * (A - j0));
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < nq) {
+                    uint32_t b0, bb;
+                    frag_b64(W3, 16 * j0 + 8 * q + g, 16 * kk, t, b0, bb);
+                    mma(acc[q], a[kk], b0, bb);
+                }
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            if (2 * jj >= nq) break;
+            const int col = 16 * (j0 + jj);
+            const float bl0 = b3[col + 2 * t], bl1 = b3[col + 2 * t + 1], bh0 = b3[col + 8 + 2 * t],
+                        bh1 = b3[col + 9 + 2 * t];
+            const float L0[4] = {acc[2 * jj][0] + bl0, acc[2 * jj][1] + bl1, acc[2 * jj + 1][0] + bh0,
+                                 acc[2 * jj + 1][1] + bh1};
+            const float L1[4] = {acc[2 * jj][2] + bl0, acc[2 * jj][3] + bl1, acc[2 * jj + 1][2] + bh0,
+                                 acc[2 * jj + 1][3] + bh1};
+            const int cb = pm[A + j0 + jj];
+            float v0 = xw[g * xs + cb], v1 = xw[(g + 8) * xs + cb];
+            lq0 += cdf_step<kSample>(L0, t, v0);
+            lq1 += cdf_step<kSample>(L1, t, v1);
+            __syncwarp();
+            if (t == 0) xw[g * xs + cb] = v0;
+            if (t == 1) xw[(g + 8) * xs + cb] = v1;
+        }
+    }
+    __syncwarp();
+}
+
+// Rows: chains idx[j] (or j when idx is null) for j < *count_dev (or n_rows).
+// A row lives in SoA buffer [D][n] bufA, or -- when par is given -- in bufA if
+// par[i] is 1 and bufB otherwise.  Density: u_out[i] = beta q + 1 - beta,
+// lq_out[i] = log q.  Sample: the row is replaced by T^{-1}(row), u_out and
+// lq_out as above, and the camera ray of the new state goes to path.
+template <bool kSample>
+__global__ void __launch_bounds__(kThreads) flow_infer_kernel(FlowView f, SceneView s, float* bufA, float* bufB,
+                                                              const uint8_t* par, uint64_t n, const uint32_t* idx,
+                                                              const unsigned int* count_dev, uint32_t n_rows,
+                                                              float* u_out, float4* path, float* lq_out,
+                                                              unsigned int* status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
+    uint8_t* perm_s = smem + kOffPerm;
+    uint32_t* rows = reinterpret_cast<uint32_t*>(smem + kOffRows);
+    float* xt = reinterpret_cast<float*>(smem + round128(kOffX));
+    const int D = (int)f.D, A = (int)f.A, AK = (int)f.AK, xs = D + 1;
+    unsigned char* wbuf0 = smem + round128(kOffX) + x_bytes(f.D);
+    const size_t bb = buf_bytes(f.AK);
+    const uint32_t lbytes = (uint32_t)flow_ws_layer_bytes(f.AK);
+
+    const uint32_t count = count_dev ? *count_dev : n_rows;
+    const uint32_t first = blockIdx.x * kTile;
+    if (first >= count) return;
+    const uint32_t stride = gridDim.x * kTile;
+    const uint32_t my_tiles = (count - first + stride - 1) / stride;
+    const uint32_t total = my_tiles * kFL;  // layer applications of this CTA
+    auto layer_of = [&](uint32_t st) { return kSample ? kFL - 1 - (int)(st % kFL) : (int)(st % kFL); };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0]);
+        mbar_init(&bar[1]);
+        mbar_fence_init();
+    }
+    for (int e = threadIdx.x; e < kFL * D; e += blockDim.x) perm_s[e] = f.perm[e];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (uint32_t st = 0; st < 2 && st < total; ++st) {
+            mbar_expect(&bar[st], lbytes);
+            bulk_load(wbuf0 + st * bb, f.ws + (size_t)layer_of(st) * lbytes, lbytes, &bar[st]);
+        }
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* xw = xt + warp * 16 * xs;
+    auto row_buf = [&](uint32_t i) -> float* { return (par && !par[i]) ? bufB : bufA; };
+    float lq0 = 0.f, lq1 = 0.f;
+    bool failed = false;
+
+    uint32_t st = 0;
+    for (; st < total; ++st) {
+        const uint32_t tile0 = first + (st / kFL) * stride + warp * 16;  // this warp's first row
+        if (st % kFL == 0) {  // load the warp's rows
+            if (lane < 16) {
+                const uint32_t j = tile0 + lane;
+                rows[warp * 16 + lane] = j < count ? (idx ? idx[j] : j) : kNoRow;
+            }
+            __syncwarp();
+            for (int e = lane; e < 16 * D; e += 32) {
+                const int r = e / D, d = e % D;
+                const uint32_t i = rows[warp * 16 + r];
+                xw[r * xs + d] = i != kNoRow ? row_buf(i)[(uint64_t)d * n + i] : 0.5f;
+            }
+            lq0 = lq1 = 0.f;
+            __syncwarp();
+        }
+        const int b = st & 1;
+        failed = !mbar_wait(&bar[b], (st >> 1) & 1);
+        if (!failed) {
+            const int l = layer_of(st);
+            coupling<kSample>(wbuf0 + b * bb, perm_s + l * D, A, AK, xw, xs, lq0, lq1);
+        }
+        if (__syncthreads_or(failed)) break;  // every warp is done with buffer b
+        if (threadIdx.x == 0 && st + 2 < total) {
+            mbar_expect(&bar[b], lbytes);
+            bulk_load(wbuf0 + b * bb, f.ws + (size_t)layer_of(st + 2) * lbytes, lbytes, &bar[b]);
+        }
+        if (st % kFL == kFL - 1) {  // write the warp's rows
+            const int g = lane >> 2, t = lane & 3;
+            if (kSample)
+                for (int e = lane; e < 16 * D; e += 32) {
+                    const int r = e / D, d = e % D;
+                    const uint32_t i = rows[warp * 16 + r];
+                    if (i != kNoRow) row_buf(i)[(uint64_t)d * n + i] = xw[r * xs + d];
+                }
+            if (t < 2) {
+                const int r = g + 8 * t;
+                const uint32_t i = rows[warp * 16 + r];
+                const float lq = t == 0 ? lq0 : lq1;
+                if (i != kNoRow) {
+                    if (u_out) u_out[i] = f.beta * __expf(lq) + (1.0f - f.beta);
+                    if (lq_out) lq_out[i] = lq;
+                    if (kSample && path) {
+                        float3 o, dd;
+                        camera_ray(s, xw[r * xs], xw[r * xs + 1], o, dd);
+                        path[3 * (uint64_t)i] = make_float4(o.x, o.y, o.z, dd.x);
+                        path[3 * (uint64_t)i + 1] = make_float4(dd.y, dd.z, 1.f, 1.f);
+                        path[3 * (uint64_t)i + 2] = make_float4(1.f, 0.f, 0.f, 0.f);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if (st < total && threadIdx.x == 0) {
+        // A wait ran out: flag it, then let the copies already issued land
+        // (bounded) before the CTA's shared memory goes away.
+        if (status) atomicOr(status, JR_STATUS_FLOW_WAIT);
+        for (uint32_t k = st; k < st + 2 && k < total; ++k) (void)mbar_wait(&bar[k & 1], (k >> 1) & 1);
+    }
+}
+
+// Swizzled inference layout of one layer (see flow_ws_layer_bytes).
+__global__ void pack_ws_kernel(const float* master, unsigned char* ws, uint32_t AK) {
+    const int l = blockIdx.y;
+    const size_t S = (size_t)kFH * kFAP + kFH + kFH * kFH + kFH + (size_t)AK * kFH + AK;
+    const float* m = master + l * S;
+    unsigned char* blk = ws + (size_t)l * flow_ws_layer_bytes(AK);
+    __nv_bfloat16* W1 = reinterpret_cast<__nv_bfloat16*>(blk);
+    __nv_bfloat16* W2 = W1 + kFH * kFAP;
+    __nv_bfloat16* W3 = W2 + kFH * kFH;
+    float* b = reinterpret_cast<float*>(W3 + (size_t)AK * kFH);
+    const float* m1 = m;
+    const float* mb1 = m1 + kFH * kFAP;
+    const float* m2 = mb1 + kFH;
+    const float* mb2 = m2 + kFH * kFH;
+    const float* m3 = mb2 + kFH;
+    const float* mb3 = m3 + (size_t)AK * kFH;
+    const uint32_t n1 = kFH * kFAP, n2 = kFH * kFH, n3 = AK * kFH;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n1 + n2 + n3 + 2 * kFH + AK;
+         e += gridDim.x * blockDim.x) {
+        if (e < n1) {
+            const uint32_t r = e / kFAP, k = e % kFAP;
+            W1[r * kFAP + ((((k >> 3) ^ ((r >> 2) & 1)) << 3) | (k & 7))] = __float2bfloat16_rn(m1[e]);
+        } else if (e < n1 + n2) {
+            const uint32_t q = e - n1, r = q / kFH, k = q % kFH;
+            W2[r * kFH + ((((k >> 3) ^ (r & 7)) << 3) | (k & 7))] = __float2bfloat16_rn(m2[q]);
+        } else if (e < n1 + n2 + n3) {
+            const uint32_t q = e - n1 - n2, r = q / kFH, k = q % kFH;
+            W3[r * kFH + ((((k >> 3) ^ (r & 7)) << 3) | (k & 7))] = __float2bfloat16_rn(m3[q]);
+        } else {
+            const uint32_t q = e - n1 - n2 - n3;
+            b[q] = q < (uint32_t)kFH ? mb1[q] : q < (uint32_t)(2 * kFH) ? mb2[q - kFH] : mb3[q - 2 * kFH];
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_flow_pack_ws(const float* master, unsigned char* ws, uint32_t AK, cudaStream_t st) {
+    pack_ws_kernel<<<dim3(16, kFL), 256, 0, st>>>(master, ws, AK);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flow(const FlowView& f, bool sample, const SceneView* s, float* bufA, float* bufB,
+                        const uint8_t* par, uint64_t n, const uint32_t* idx, const unsigned int* count_dev,
+                        uint32_t n_rows, float* u_out, float4* path, float* lq_out, unsigned int* status,
+                        cudaStream_t st) {
+    static int sms = 0;
+    static size_t attr_bytes = 0;
+    const size_t shm = infer_smem(f.D, f.AK);
+    cudaError_t e;
+    if (sms == 0) {
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    }
+    if (shm > attr_bytes) {
+        if ((e = cudaFuncSetAttribute(flow_infer_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)shm)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(flow_infer_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)shm)) != cudaSuccess)
+            return e;
+        attr_bytes = shm;
+    }
+    int per = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, flow_infer_kernel<false>, kThreads, shm)) !=
+        cudaSuccess)
+        return e;
+    unsigned g = (unsigned)(sms * (per > 0 ? per : 1));
+    if (!count_dev) g = (unsigned)std::min<uint64_t>(g, (n_rows + kTile - 1) / kTile);
+    if (g == 0) return cudaSuccess;
+    SceneView sv{};
+    if (s) sv = *s;
+    if (sample)
+        flow_infer_kernel<true><<<g, kThreads, shm, st>>>(f, sv, bufA, bufB, par, n, idx, count_dev, n_rows, u_out,
+                                                          path, lq_out, status);
+    else
+        flow_infer_kernel<false><<<g, kThreads, shm, st>>>(f, sv, bufA, bufB, par, n, idx, count_dev, n_rows, u_out,
+                                                           path, lq_out, status);
+    return cudaGetLastError();
+}
+
+}  // namespace jr

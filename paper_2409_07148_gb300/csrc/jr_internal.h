@@ -64,11 +64,21 @@ struct SceneView {
 constexpr int kFL = 6, kFH = 64, kFK = 16, kFAP = 16, kFS1 = 24, kFS2 = 72, kFMaxAK = 256;
 constexpr float kFE = 1e-3f;  // bin-mass floor: Q = (1 - E) softmax + E / K
 
+// Inference layout of one flow layer (bytes, 16-byte multiples): W1 [64][16],
+// W2 [64][64], W3 [AK][64] bf16, then b1 [64], b2 [64], b3 [AK] FP32.  Row n of
+// a bf16 matrix is stored in 16-byte chunks; chunk c sits at position c ^ (n & 7)
+// (W2, W3) or c ^ ((n >> 2) & 1) (W1), so the 8 rows of an mma B fragment hit
+// 8 different bank groups.
+__host__ __device__ constexpr size_t flow_ws_layer_bytes(uint32_t AK) {
+    return 2 * ((size_t)kFH * kFAP + kFH * kFH + (size_t)AK * kFH) + 4 * (2 * (size_t)kFH + AK);
+}
+
 struct FlowView {
     uint32_t D = 0, A = 0, AK = 0;      // AK = A * K logits per layer
     const uint8_t* perm = nullptr;      // [kFL][D]
     const __nv_bfloat16* wb = nullptr;  // per layer: W1 [64][kFS1], W2 [64][kFS2], W3 [AK][kFS2]
     const float* bias = nullptr;        // per layer: b1 [64], b2 [64], b3 [AK]
+    const unsigned char* ws = nullptr;  // inference layout, flow_ws_layer_bytes(AK) per layer
     float beta = 0.f;                   // mu = beta mu_flow + (1 - beta) uniform
 };
 
@@ -97,7 +107,7 @@ struct ChainView {
     float* fpu;      // [5][n] F.r F.g F.b p u
     float4* fb;      // [H*W] RGB sum + dt, FP32 (folded into acc64 after each advance)
     double4_32a* acc64;  // [H*W]
-    unsigned long long* counters;  // [0] J, [1] local steps, [2] accepted
+    unsigned long long* counters;  // [0] J, [1] local steps, [2] accepted, [3] drain mark
     unsigned int* status;
     uint64_t n;
     uint32_t chain_offset;
@@ -166,8 +176,10 @@ cudaError_t launch_wavefront_static(const SceneView& s, const ChainView& c, uint
 // path (if not null).  Rows are idx[j], j < *count_dev (device) or n_rows.
 cudaError_t launch_flow(const FlowView& f, bool sample, const SceneView* s, float* bufA, float* bufB,
                         const uint8_t* par, uint64_t n, const uint32_t* idx, const unsigned int* count_dev,
-                        uint32_t n_rows, float* u_out, float4* path, float* lq_out, cudaStream_t st);
-size_t flow_smem_bytes();
+                        uint32_t n_rows, float* u_out, float4* path, float* lq_out, unsigned int* status,
+                        cudaStream_t st);
+// FP32 master parameters [kFL][S] -> the inference layout (flow_ws_layer_bytes per layer).
+cudaError_t launch_flow_pack_ws(const float* master, unsigned char* ws, uint32_t AK, cudaStream_t st);
 // FP32 master parameters [kFL][S] -> padded bf16 weights and biases.
 cudaError_t launch_flow_pack(const float* master, __nv_bfloat16* wb, float* bias, uint32_t AK, cudaStream_t st);
 __host__ __device__ inline size_t flow_layer_floats(uint32_t D) {
@@ -176,6 +188,8 @@ __host__ __device__ inline size_t flow_layer_floats(uint32_t D) {
 }
 // Training rows from chain states (x [D][n], w = p / (p + c~ u)).
 cudaError_t launch_snapshot(const ChainView& c, float* x_out, float* w_out, cudaStream_t st);
+cudaError_t launch_snapshot_append(const ChainView& c, float* x_ring, float* w_ring, uint64_t cap,
+                                   unsigned long long* total, cudaStream_t st);
 // One minibatch of the time-weighted maximum-likelihood loss: gradient into
 // grad (added), minibatch weight sum into *wsum (added), loss into *loss (added).
 cudaError_t launch_flow_train_step(const FlowView& f, const float* x, const float* w, uint64_t n, uint64_t off,

@@ -83,8 +83,13 @@ __device__ __forceinline__ void count_and_flush(uint32_t nJ, uint32_t nL, uint32
 // not a regeneration of Alg. 2: no clocks, no splat, J unchanged); `step` is
 // then the restart epoch and the stream tag is kTagRestart.
 // With a flow attached (c.flow.D > 0), a regeneration draws from the flow when
-// Ub < beta (Ub = fourth value of block 0), else uniformly; the candidates go
-// to the flow queues, whose kernels fill in u(y) (and y for flow draws).
+// Ub < beta (Ub = fourth value of block 0), else uniformly.  Flow draws go to
+// the sampling queue, whose kernel fills in y and u(y) before the bounces
+// (ua = -3 marks them).  u(y) of the other candidates is needed only where the
+// candidate becomes a state with p > 0 (k = c~ u / p is +inf at p = 0 whatever
+// u is; a rejected local candidate never becomes a state), so the shade kernel
+// queues exactly those rows for the density pass after the last bounce; a state
+// with p = 0 keeps u = 1 as a placeholder.
 // mode = kModeDrain: a kill ends the chain's tour (counted in J) and the chain
 // (done = 1); done chains do nothing; no regeneration starts a new tour.
 // Chains still in a tour after the step are counted in qcount[kQActive].
@@ -99,7 +104,7 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
     const bool restart = mode == kModeRestart, drain = mode == kModeDrain;
     uint32_t nJ = 0, nL = 0, nA = 0;
     unsigned status = 0;
-    bool to_density = false, to_sample = false, traced = valid, active = false;
+    bool to_sample = false, traced = valid, active = false;
     if (valid) {
         uint8_t par = w.par[i];
         float Fr = c.fpu[0 * n + i], Fg = c.fpu[1 * n + i], Fb = c.fpu[2 * n + i];
@@ -128,7 +133,7 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
                 Fg = Fy.y;
                 Fb = Fy.z;
                 p = py;
-                u = has_flow ? w.uy[i] : 1.0f;
+                u = has_flow && py > 0.0f ? w.uy[i] : 1.0f;
                 c.fpu[0 * n + i] = Fr;
                 c.fpu[1 * n + i] = Fg;
                 c.fpu[2 * n + i] = Fb;
@@ -155,7 +160,6 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
             if (restart) dt = 0.0f;
             const bool use_flow = has_flow && !local && u01(r0.w) < c.flow.beta;
             to_sample = use_flow;
-            to_density = has_flow && !use_flow;
             const float x0 = cur[i], x1 = cur[n + i];
             if (dt > 0.0f && p > 0.0f) {
                 uint32_t px = min((uint32_t)((double)x0 * (double)c.width), c.width - 1);
@@ -163,13 +167,13 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
                 const float wgt = c.c_tilde * dt * ((float)c.width * (float)c.height) / p;
                 atomicAdd(c.fb + py * c.width + px, make_float4(wgt * Fr, wgt * Fg, wgt * Fb, dt));
             }
-            w.ua[i] = local ? Ua : -1.0f;
+            w.ua[i] = local ? Ua : use_flow ? -3.0f : -1.0f;
             if (drain && !local) {  // the tour ends here; no new tour in a drain
                 nJ++;
                 w.done[i] = 1;
                 w.ua[i] = -2.0f;
                 traced = false;
-                to_sample = to_density = false;
+                to_sample = false;
             }
             active = drain && local;
             float y0 = 0.f, y1 = 0.f;
@@ -220,13 +224,13 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
     }
     if (begin) {
         enqueue(traced, (uint32_t)i, w.queue, w.qcount + 0);
-        if (has_flow) {
-            enqueue(to_density, (uint32_t)i, w.fq, w.qcount + kQFlowDensity);
-            enqueue(to_sample, (uint32_t)i, w.fq + n, w.qcount + kQFlowSample);
-        }
-        if (drain) {
+        if (has_flow) enqueue(to_sample, (uint32_t)i, w.fq + n, w.qcount + kQFlowSample);
+        if (drain) {  // counters[3]: 1 + the last drain step after which a tour was still open
             const unsigned na = __popc(__ballot_sync(kFull, active));
-            if ((threadIdx.x & 31) == 0 && na) atomicAdd(w.qcount + kQActive, na);
+            if ((threadIdx.x & 31) == 0 && na) {
+                atomicAdd(w.qcount + kQActive, na);
+                atomicMax(c.counters + 3, (unsigned long long)step + 1);
+            }
         }
     }
     count_and_flush(nJ, nL, nA, status, c);
@@ -239,6 +243,10 @@ __global__ void __launch_bounds__(128) wf_trace_kernel(SceneView s, ChainView c,
     const WaveView& w = c.wf;
     const uint32_t* qin = w.queue + (uint64_t)(v & 1) * c.n;
     const unsigned count = w.qcount[v];
+    // Blocks past the queue's length have nothing to take that the blocks
+    // before them will not take (they keep fetching until the queue is empty),
+    // so a short queue costs no atomics on the cursor from the rest of the grid.
+    if ((uint64_t)blockIdx.x * blockDim.x >= count) return;
     unsigned int* fetch = w.qcount + (kMaxDepth + 2) + v;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -308,7 +316,10 @@ __global__ void __launch_bounds__(128) wf_trace_kernel(SceneView s, ChainView c,
     if (lane == 0 && status) atomicOr(c.status, status);
 }
 
-// Shade every queued ray of bounce v; survivors to the next queue.
+// Shade every queued ray of bounce v; survivors to the next queue.  With a
+// flow, a finished path whose candidate will become a state with p > 0 and
+// still lacks u(y) joins the density queue (the finish of the next step
+// kernel takes the same decision from the same values).
 __global__ void __launch_bounds__(128) wf_shade_kernel(SceneView s, ChainView c, int v) {
     const WaveView& w = c.wf;
     const uint32_t* qin = w.queue + (uint64_t)(v & 1) * c.n;
@@ -320,7 +331,7 @@ __global__ void __launch_bounds__(128) wf_shade_kernel(SceneView s, ChainView c,
     const int lane = threadIdx.x & 31;
     for (unsigned j0 = warp * 32u; j0 < count; j0 += warps * 32u) {
         const unsigned j = j0 + lane;
-        bool live = false;
+        bool live = false, need_u = false;
         uint32_t i = 0;
         if (j < count) {
             i = qin[j];
@@ -337,26 +348,36 @@ __global__ void __launch_bounds__(128) wf_shade_kernel(SceneView s, ChainView c,
                 }
                 live = shade_vertex(s, k, h.x, v, (int)c.depth, u1, u2, o, d, T, F);
             }
-            if (live)
+            if (live) {
                 store_path(w.path, i, o, d, T, F);
-            else
+            } else {
                 w.path[3 * (uint64_t)i + 2] = make_float4(0.f, F.x, F.y, F.z);
+                if (c.flow.D != 0) {
+                    unsigned ignored = 0;
+                    const float py = lum(finite_or_zero(F, ignored));
+                    const float ua = w.ua[i];
+                    need_u = ua >= 0.0f ? ua * c.fpu[3 * n + i] < py : (ua == -1.0f && py > 0.0f);
+                }
+            }
         }
         enqueue(live, i, qout, w.qcount + v + 1);
+        if (c.flow.D != 0) enqueue(need_u, i, w.fq, w.qcount + kQFlowDensity);
     }
 }
 
 inline unsigned grid_for(uint64_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 
-// The flow stage of a step: u(y) of the density rows (local candidates and
-// uniform regenerations); y = T^{-1}(z) and u(y) of the flow draws.  A chain's
-// candidate lives in x when its parity byte is 1, else in y.
-cudaError_t launch_flow_candidates(const SceneView& s, const ChainView& c, cudaStream_t st) {
-    cudaError_t e = launch_flow(c.flow, false, &s, c.x, c.wf.y, c.wf.par, c.n, c.wf.fq, c.wf.qcount + kQFlowDensity,
-                                0, c.wf.uy, nullptr, nullptr, st);
-    if (e != cudaSuccess) return e;
+// The flow stages of a step (a chain's candidate lives in x when its parity
+// byte is 1, else in y).  Before the bounces: y = T^{-1}(z), u(y) and the
+// camera ray of the flow draws.  After them: u(y) of the rows the shade kernel
+// queued.
+cudaError_t launch_flow_draws(const SceneView& s, const ChainView& c, cudaStream_t st) {
     return launch_flow(c.flow, true, &s, c.x, c.wf.y, c.wf.par, c.n, c.wf.fq + c.n, c.wf.qcount + kQFlowSample, 0,
-                       c.wf.uy, c.wf.path, nullptr, st);
+                       c.wf.uy, c.wf.path, nullptr, c.status, st);
+}
+cudaError_t launch_flow_densities(const SceneView& s, const ChainView& c, cudaStream_t st) {
+    return launch_flow(c.flow, false, &s, c.x, c.wf.y, c.wf.par, c.n, c.wf.fq, c.wf.qcount + kQFlowDensity, 0,
+                       c.wf.uy, nullptr, nullptr, c.status, st);
 }
 
 }  // namespace
@@ -382,11 +403,12 @@ cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t st
         cudaError_t e = cudaMemsetAsync(c.wf.qcount, 0, sizeof(unsigned int) * kQCount, st);
         if (e != cudaSuccess) return e;
         wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + k, k > 0, 1, s, mode);
-        if (has_flow && (e = launch_flow_candidates(s, c, st)) != cudaSuccess) return e;
+        if (has_flow && (e = launch_flow_draws(s, c, st)) != cudaSuccess) return e;
         for (int v = 0; v <= (int)c.depth; ++v) {
             wf_trace_kernel<<<trace_blocks, 128, 0, st>>>(s, c, v);
             wf_shade_kernel<<<shade_blocks, 128, 0, st>>>(s, c, v);
         }
+        if (has_flow && (e = launch_flow_densities(s, c, st)) != cudaSuccess) return e;
     }
     wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + n_steps, n_steps > 0, 0, s, mode);
     return cudaGetLastError();

@@ -93,14 +93,17 @@ _SIGS = {
     "jr_flow_destroy": [_P],
     "jr_flow_set_params": [_P, _P, _P],
     "jr_flow_get_params": [_P, _P, _P],
+    "jr_flow_get_status": [_P, _P, _P],
     "jr_flow_log_density": [_P, _P, _U64, _P, _P],
     "jr_flow_sample": [_P, _P, _U64, _P, _P],
     "jr_chains_set_flow": [_P, _P, ctypes.c_float, _U32, _P, _P],
     "jr_complete_tours": [_P, _U32, _P, _P],
     "jr_flow_copy_params": [_P, _P, _P],
     "jr_chains_snapshot": [_P, _P, _P, _P],
+    "jr_chains_snapshot_append": [_P, _P, _P, _U64, _P, _P],
     "jr_flow_gradient": [_P, _P, _P, _U64, _U64, _U32, _P, _P, _P],
     "jr_flow_train": [_P, _P, _P, _U64, _U32, _U32, ctypes.c_float, _U64, _P, _P],
+    "jr_flow_train_rows": [_P, _P, _P, _U64, _U64, _U32, _U32, ctypes.c_float, _U64, _P, _P],
     "jr_last_error": [],
     "jr_version": [],
 }
@@ -333,6 +336,23 @@ class Flow:
                                    int(seed), _hptr(losses), _stream(stream)))
         return losses[:int(iters)]
 
+    def status(self, stream=None):
+        v = ctypes.c_uint32(0)
+        _check(lib().jr_flow_get_status(self.h, ctypes.byref(v), _stream(stream)))
+        return int(v.value)
+
+    def train_replay(self, buf, iters, batch, lr=1e-3, seed=0, stream=None):
+        """iters Adam steps on the valid rows of a ReplayBuffer; returns the
+        per-step losses (empty when the buffer holds fewer than `batch` rows)."""
+        n = buf.rows()
+        batch = min(int(batch), n // 64 * 64)
+        if batch < 64:
+            return np.zeros(0, np.float32)
+        losses = np.zeros(max(int(iters), 1), np.float32)
+        _check(lib().jr_flow_train_rows(self.h, _dptr(buf.x), _dptr(buf.w), buf.capacity, n, int(iters), batch,
+                                        float(lr), int(seed), _hptr(losses), _stream(stream)))
+        return losses[:int(iters)]
+
     def close(self):
         if getattr(self, "h", None):
             lib().jr_flow_destroy(self.h)
@@ -361,6 +381,25 @@ def snapshot(chains, stream=None):
     w = torch.empty(chains.n, dtype=torch.float32, device="cuda")
     _check(lib().jr_chains_snapshot(chains.h, _dptr(x), _dptr(w), _stream(stream)))
     return x, w
+
+
+class ReplayBuffer:
+    """Device ring of training rows (states with p > 0 and their weights)."""
+
+    def __init__(self, D, capacity):
+        import torch
+        self.D, self.capacity = int(D), int(capacity)
+        self.x = torch.empty((self.D, self.capacity), dtype=torch.float32, device="cuda")
+        self.w = torch.empty(self.capacity, dtype=torch.float32, device="cuda")
+        self.total = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def append(self, chains, stream=None):
+        _check(lib().jr_chains_snapshot_append(chains.h, _dptr(self.x), _dptr(self.w), self.capacity,
+                                               _dptr(self.total), _stream(stream)))
+
+    def rows(self):
+        """Number of valid rows (synchronises)."""
+        return min(int(self.total.item()), self.capacity)
 
 
 def complete_tours(chains, max_steps=1 << 20, stream=None):

@@ -97,15 +97,20 @@ def test_chains_with_flow_step_replay(J):
     oc.u = fpu[4].astype(np.float64)
     oc.step = st["steps_per_chain"]
     # u of the GPU state is the flow's density (up to the tolerance above)
+    # wherever p > 0; at p = 0 the killing rate is +inf whatever u is, and the
+    # chains keep u = 1 there without evaluating the flow
     u_o = FL.regen_density(perm, w, oc.x, 0.6)
-    assert np.mean(np.abs(fpu[4] - u_o) <= 2e-3 * u_o) >= 0.99
+    pos = fpu[3] > 0
+    assert pos.sum() >= 20
+    assert np.mean(np.abs(fpu[4][pos] - u_o[pos]) <= 2e-3 * u_o[pos]) >= 0.99
+    assert np.all(fpu[4][~pos] == 1.0)
     oc.advance(1)
     ch.advance(1)
     x2, fpu2 = ch.get_state()
     dx = np.abs(x2.T - oc.x)
     dx = np.minimum(dx, 1 - dx).max(axis=1)
     assert np.mean(dx <= 1e-4) >= 0.97       # decisions and flow draws agree except near ties / bin edges
-    same = dx <= 1e-4
+    same = (dx <= 1e-4) & (fpu2[3] > 0)
     assert np.mean(np.abs(fpu2[4][same] - oc.u[same]) <= 3e-3 * oc.u[same]) >= 0.98
 
 
