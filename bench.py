@@ -37,6 +37,28 @@ UNIT = "chain steps/s"
 FLOP_PER_NODE = 50
 FLOP_PER_TRI = 45
 SMS, FP32_LANES = 152, 128
+# DRAM traffic of one wf_trace_kernel launch (dram__bytes_read.sum +
+# dram__bytes_write.sum), the mean over 18 launches of an ncu capture of the
+# 2^18-chain case (13.416 MB read + 0.099 MB written), scaled by 4 to the
+# 2^20-chain workload (the rays of a launch grow with the chains).  It stands
+# only while the kernel sources still hash to the values it was taken on.
+TRACE_TRAFFIC = {"bytes_per_launch": 4 * (13.416e6 + 0.099e6),
+                 "sources": {"jr_wavefront.cu": "303ed172e1246b01", "jr_device.cuh": "4bcf7b468f00cebe"},
+                 "summary": "profiles/trace_kernel_cornell_spheres_512x512.md"}
+
+
+def trace_traffic(workload_name, chains):
+    """Per-launch DRAM bytes of the trace kernel, or None when the sources
+    changed since the capture or the workload is not the one it scales to."""
+    import hashlib
+    if workload_name != "cornell_spheres" or chains != 1 << 20:
+        return None
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2409_07148_gb300", "csrc")
+    for f, h in TRACE_TRAFFIC["sources"].items():
+        with open(os.path.join(src, f), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest()[:16] != h:
+                return None
+    return TRACE_TRAFFIC["bytes_per_launch"]
 
 
 def workload(name):
@@ -107,8 +129,8 @@ class ClockSampler:
 def launches_per_advance(mode, chains, chain_steps, depth):
     """Kernels of ours one jr_advance launches (see jr_advance in include/jr.h)."""
     wave = mode == "wave" or (mode == "auto" and chains >= (1 << 16))
-    if wave:   # per step: step kernel + one bounce kernel per depth; then a finish launch and the fold
-        return chain_steps * (1 + depth) + 2
+    if wave:   # per step: step kernel + a trace and a shade kernel per vertex; then a finish launch and the fold
+        return chain_steps * (1 + 2 * (depth + 1)) + 2
     return 2   # the persistent step kernel and the fold
 
 
@@ -450,12 +472,23 @@ def main():
             wc.advance(K, stream=stream)
         work = wc.advance_counted(K, stream=stream)
         del wc
+        # device time per kernel class for the same K steps of an identical chain set
+        wt = jr.Chains(scene, sc.width, sc.height, sc.depth, C, seed=0, chain_offset=rank * C, stream=stream)
+        wt.set_execution(args.exec)
+        for _ in range(args.warmup):
+            wt.advance(K, stream=stream)
+        split = wt.advance_timed(K, stream=stream)
+        del wt
         flop = FLOP_PER_NODE * work["nodes"] + FLOP_PER_TRI * work["tris"]
         pk, pk_kind = peaks()
         sm_mhz_peak = float(pk.get("sm_max_mhz", 2070.0))
         alu_peak = SMS * FP32_LANES * 2 * sm_mhz_peak * 1e6 / 1e12
-        per_launch = total / args.steps / 1.0 if ws == 1 else total / args.steps
-        achieved = flop / 1e12 / (sum(times) / args.steps)
+        split_total = sum(v["ms"] for v in split.values())
+        dom = max(split, key=lambda k: split[k]["ms"])
+        if dom == "trace":   # the traversal work runs in the trace kernel
+            achieved = flop / 1e12 / (split["trace"]["ms"] / 1e3)
+        else:                # one launch does everything (megakernel)
+            achieved = flop / 1e12 / (sum(times) / args.steps)
         # end to end through the C ABI with host buffers: scene upload (BVH built on
         # the host from the caller's arrays), chain init, advance, image read back
         e2e_times = []
@@ -490,10 +523,18 @@ def main():
                    "c_tilde": 1.0, "sigma": 0.01, "regen": "uniform", "global_batch": ws * C, "seq_len": K,
                    "parallelism": f"chains sharded over {ws} GPU(s)", "l2": "flushed by a 512 MB write between timed launches",
                    "block": args.block or 128, "exec": args.exec},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": achieved / alu_peak, "traffic": None,
+        "roofline": {"bound": "alu", "kernel": "wf_trace_kernel" if dom == "trace" else "step_kernel",
+                     "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved / alu_peak,
+                     "traffic": trace_traffic(args.workload, C) if dom == "trace" else None,
+                     "traffic_source": TRACE_TRAFFIC["summary"],
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz_peak:.0f} MHz ({pk_kind} sm_max_mhz)",
-                     "work_per_launch": work, "flop_per_launch": flop},
+                     "work_per_step": work, "flop_per_step": flop,
+                     "launches_per_step": split[dom]["launches"],
+                     "avg_launch_us": 1e3 * split[dom]["ms"] / max(1, split[dom]["launches"]),
+                     "flop_per_launch": flop / max(1, split[dom]["launches"]),
+                     "split_ms": {k: round(v["ms"], 3) for k, v in split.items()},
+                     "share": split[dom]["ms"] / split_total if split_total else None},
         "mrays_per_s": work["rays"] / (sum(times) / args.steps) / 1e6,
         "regen_fraction": st["regenerations"] / max(1, st["regenerations"] + st["local_steps"]),
         "accept_rate": st["accepted"] / max(1, st["local_steps"]),

@@ -154,6 +154,15 @@ jr_status jr_advance(jr_chains* chains, uint32_t n_steps, void* stream);
 jr_status jr_advance_traced(jr_chains* chains, uint32_t n_steps, uint8_t* flags_dev, float* dt_dev,
                             int32_t* pix_dev, void* stream);
 
+/* jr_advance with device timing per kernel class: an event is recorded after
+ * every launch and the time since the previous one is charged to that launch's
+ * class; ms_out[k] / launches_out[k] (host, 4 each) for k = 0 step kernels,
+ * 1 trace, 2 shade, 3 flow (the megakernel counts as one step launch).  Same
+ * chains and results as jr_advance; the events add a little time between
+ * launches, so use it to split a step, not to time it.  Synchronises. */
+jr_status jr_advance_timed(jr_chains* chains, uint32_t n_steps, double ms_out[4], uint64_t launches_out[4],
+                           void* stream);
+
 /* As jr_advance, with the instrumented kernel variant that also counts the
  * work it does: work_out = {ray casts, BVH node visits, ray/triangle tests}
  * summed over every chain and step.  The chains advance exactly as with

@@ -284,6 +284,33 @@ jr_status jr_advance_traced(jr_chains* chains, uint32_t n_steps, uint8_t* flags_
     return advance_impl(chains, n_steps, flags_dev, dt_dev, pix_dev, nullptr, stream, "jr_advance_traced");
 }
 
+jr_status jr_advance_timed(jr_chains* c, uint32_t n_steps, double ms_out[4], uint64_t launches_out[4], void* stream) {
+    if (!c || !ms_out || !launches_out) return fail(JR_ERR_INVALID_ARG, "jr_advance_timed: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool wave = c->view.flow.D != 0 || c->exec == JR_EXEC_WAVEFRONT ||
+                      (c->exec == JR_EXEC_AUTO && c->view.n >= kWavefrontMinChains);
+    KernelTimer tm;
+    if (n_steps > 0) {
+        if (wave) {
+            jr_status a = ensure_wavefront(c, st);
+            if (a != JR_OK) return a;
+            JR_CUDA(launch_wavefront(c->scene->view, c->view, c->steps, n_steps, st, kModeStep, &tm),
+                    "jr_advance_timed");
+        } else {
+            JR_CUDA(tm.mark(-1, st), "jr_advance_timed");
+            JR_CUDA(launch_step(c->scene->view, c->view, c->steps, n_steps, nullptr, nullptr, nullptr, nullptr,
+                                c->block, st),
+                    "jr_advance_timed");
+            JR_CUDA(tm.mark(KernelTimer::kStep, st), "jr_advance_timed");
+        }
+        JR_CUDA(launch_fold(c->view, st), "jr_advance_timed");
+        c->steps += n_steps;
+    }
+    JR_CUDA(cudaStreamSynchronize(st), "jr_advance_timed");
+    JR_CUDA(tm.totals(ms_out, launches_out), "jr_advance_timed");
+    return JR_OK;
+}
+
 jr_status jr_advance_static(jr_chains* chains, uint32_t n_steps, void* stream) {
     if (!chains) return fail(JR_ERR_INVALID_ARG, "jr_advance_static: null chains");
     if (chains->view.n > kStaticMaxChains)

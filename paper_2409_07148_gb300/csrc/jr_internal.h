@@ -155,11 +155,24 @@ cudaError_t launch_fold(const ChainView& c, cudaStream_t st);
 cudaError_t launch_batch(BatchEntry* entries, const BatchItem* items, uint32_t n_items, const uint64_t* px_off,
                          uint32_t n_sets, uint64_t total_px, unsigned int* cursor, uint32_t max_dim, int block,
                          uint32_t n_steps, cudaStream_t st);
+// Device time per kernel class of a sequence of launches on one stream: an
+// event is recorded after every launch, and the time since the previous event
+// is charged to that launch's class.
+struct KernelTimer {
+    enum Kind { kStep = 0, kTrace = 1, kShade = 2, kFlow = 3, kKinds = 4 };
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind;  // class of the launch that ends at ev[i] (-1: the start mark)
+    cudaError_t mark(int k, cudaStream_t st);
+    // After the stream is synchronised: ms[k] and launches[k] per class.
+    cudaError_t totals(double ms[kKinds], uint64_t launches[kKinds]) const;
+    ~KernelTimer();
+};
+
 // jr_wavefront.cu
 // n_steps wavefront steps in `mode` (WaveMode); for kModeRestart step_begin is
-// the restart epoch and n_steps is 1.
+// the restart epoch and n_steps is 1.  tm (optional) times every launch.
 cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
-                             cudaStream_t st, int mode = kModeStep);
+                             cudaStream_t st, int mode = kModeStep, KernelTimer* tm = nullptr);
 // The same wavefront launches with their buffers in a fixed file-scope device
 // array (no allocation); c.wf is ignored.  c.n <= kStaticMaxChains.
 constexpr uint64_t kStaticMaxChains = 1u << 16;

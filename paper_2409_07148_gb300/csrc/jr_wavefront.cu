@@ -382,8 +382,38 @@ cudaError_t launch_flow_densities(const SceneView& s, const ChainView& c, cudaSt
 
 }  // namespace
 
+cudaError_t KernelTimer::mark(int k, cudaStream_t st) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    ev.push_back(e);
+    kind.push_back(k);
+    return cudaEventRecord(e, st);
+}
+
+cudaError_t KernelTimer::totals(double ms[kKinds], uint64_t launches[kKinds]) const {
+    for (int k = 0; k < kKinds; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    for (size_t i = 1; i < ev.size(); ++i) {
+        float t = 0.f;
+        cudaError_t r = cudaEventElapsedTime(&t, ev[i - 1], ev[i]);
+        if (r != cudaSuccess) return r;
+        if (kind[i] >= 0 && kind[i] < kKinds) {
+            ms[kind[i]] += t;
+            launches[kind[i]] += 1;
+        }
+    }
+    return cudaSuccess;
+}
+
+KernelTimer::~KernelTimer() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+}
+
 cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
-                             cudaStream_t st, int mode) {
+                             cudaStream_t st, int mode, KernelTimer* tm) {
     static int trace_blocks = 0, shade_blocks = 0;
     if (trace_blocks == 0) {
         int dev = 0, sms = 0, per_sm = 0, per_sm2 = 0;
@@ -399,18 +429,30 @@ cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t st
     }
     const unsigned G = grid_for(c.n, 128);
     const bool has_flow = c.flow.D != 0;
-    for (uint32_t k = 0; k < n_steps; ++k) {
-        cudaError_t e = cudaMemsetAsync(c.wf.qcount, 0, sizeof(unsigned int) * kQCount, st);
-        if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    auto mark = [&](int kind) {
+        if (tm && e == cudaSuccess) e = tm->mark(kind, st);
+    };
+    mark(-1);
+    for (uint32_t k = 0; k < n_steps && e == cudaSuccess; ++k) {
+        if ((e = cudaMemsetAsync(c.wf.qcount, 0, sizeof(unsigned int) * kQCount, st)) != cudaSuccess) return e;
         wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + k, k > 0, 1, s, mode);
+        mark(KernelTimer::kStep);
         if (has_flow && (e = launch_flow_draws(s, c, st)) != cudaSuccess) return e;
+        if (has_flow) mark(KernelTimer::kFlow);
         for (int v = 0; v <= (int)c.depth; ++v) {
             wf_trace_kernel<<<trace_blocks, 128, 0, st>>>(s, c, v);
+            mark(KernelTimer::kTrace);
             wf_shade_kernel<<<shade_blocks, 128, 0, st>>>(s, c, v);
+            mark(KernelTimer::kShade);
         }
         if (has_flow && (e = launch_flow_densities(s, c, st)) != cudaSuccess) return e;
+        if (has_flow) mark(KernelTimer::kFlow);
     }
+    if (e != cudaSuccess) return e;
     wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + n_steps, n_steps > 0, 0, s, mode);
+    mark(KernelTimer::kStep);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -70,6 +70,7 @@ _SIGS = {
     "jr_advance": [_P, _U32, _P],
     "jr_advance_traced": [_P, _U32, _P, _P, _P, _P],
     "jr_advance_counted": [_P, _U32, _P, _P],
+    "jr_advance_timed": [_P, _U32, _P, _P, _P],
     "jr_set_block_size": [_P, _U32],
     "jr_set_execution": [_P, _U32],
     "jr_advance_static": [_P, _U32, _P],
@@ -214,6 +215,14 @@ class Chains:
         """jr_advance_static: the wavefront advance with no device allocation
         (fixed in-library scratch, at most STATIC_MAX_CHAINS chains)."""
         _check(lib().jr_advance_static(self.h, int(n_steps), _stream(stream)))
+
+    def advance_timed(self, n_steps, stream=None):
+        """Advance with device time per kernel class (step, trace, shade, flow)."""
+        ms = (ctypes.c_double * 4)()
+        nl = (ctypes.c_uint64 * 4)()
+        _check(lib().jr_advance_timed(self.h, int(n_steps), ms, nl, _stream(stream)))
+        names = ("step", "trace", "shade", "flow")
+        return {k: {"ms": ms[i], "launches": int(nl[i])} for i, k in enumerate(names)}
 
     def advance_counted(self, n_steps, stream=None):
         """Advance and return {rays, nodes, tris} counted by the instrumented kernel."""
