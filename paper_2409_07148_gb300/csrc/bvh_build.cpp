@@ -1,8 +1,10 @@
-// Host BVH builder: binned surface-area heuristic (Wald, "On fast construction
-// of SAH-based bounding volume hierarchies", RT'07), 16 bins per axis, leaves
-// of at most kLeafMax triangles, depth-first node order so that the first
-// child of a node usually sits next to it in memory.  The paper renders with
-// pbrt/lmc; the acceleration structure is this library's own.
+// Host BVH builder: a binary tree by the binned surface-area heuristic (Wald,
+// "On fast construction of SAH-based bounding volume hierarchies", RT'07), 16
+// bins per axis, leaves of at most kLeafMax triangles; then collapsed into a
+// 4-wide tree: a node takes the two children of a binary node and keeps
+// opening its largest-area inner child until it holds 4 children or only
+// leaves.  Nodes are emitted depth first.  The paper renders with pbrt/lmc;
+// the acceleration structure is this library's own.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -41,6 +43,12 @@ struct Prim {
     float c[3];
 };
 
+// Binary node of the first pass: both children's (widened) boxes and refs.
+struct BinNode {
+    Box box[2];
+    int ref[2];
+};
+
 struct Builder {
     const float* verts;
     const uint32_t* tris;
@@ -48,6 +56,7 @@ struct Builder {
     std::vector<Prim> prims;
     std::vector<uint32_t> idx;
     HostBvh* out;
+    std::vector<BinNode> bin;
     int max_depth_seen = 0;
 
     // Widen a box so that a FP32 slab test never rejects a box whose triangle
@@ -154,18 +163,74 @@ struct Builder {
         } else {
             mid = b + n / 2;  // all centroids coincide
         }
-        int me = (int)out->nodes.size();
-        out->nodes.push_back(BvhNode{});
+        int me = (int)bin.size();
+        bin.push_back(BinNode{});
         int l = build(b, mid, depth + 1);
         int r = build(mid, e, depth + 1);
         Box lb = range_box(b, mid), rb = range_box(mid, e);
         widen(lb);
         widen(rb);
-        BvhNode& nd = out->nodes[me];
-        nd.a = make_float4(lb.lo[0], lb.hi[0], lb.lo[1], lb.hi[1]);
-        nd.b = make_float4(rb.lo[0], rb.hi[0], rb.lo[1], rb.hi[1]);
-        nd.c = make_float4(lb.lo[2], lb.hi[2], rb.lo[2], rb.hi[2]);
-        nd.refs = make_int4(l, r, 0, 0);
+        bin[me].box[0] = lb;
+        bin[me].box[1] = rb;
+        bin[me].ref[0] = l;
+        bin[me].ref[1] = r;
+        return me;
+    }
+
+    // 4-wide node for binary inner node `b`; returns its index.  `need` gets
+    // the most stack entries a traversal below it can hold (a visit pushes at
+    // most children - 1 refs), `depth4` the height of its subtree.
+    int collapse(int b, int& need, int& depth4) {
+        struct Kid {
+            int ref;
+            Box box;
+        };
+        Kid kids[4] = {{bin[b].ref[0], bin[b].box[0]}, {bin[b].ref[1], bin[b].box[1]}};
+        int n = 2;
+        while (n < 4) {
+            int pick = -1;
+            double best = -1.0;
+            for (int j = 0; j < n; ++j)
+                if (kids[j].ref >= 0 && kids[j].box.area() > best) {
+                    best = kids[j].box.area();
+                    pick = j;
+                }
+            if (pick < 0) break;
+            const BinNode& o = bin[kids[pick].ref];
+            kids[pick] = {o.ref[0], o.box[0]};
+            kids[n++] = {o.ref[1], o.box[1]};
+        }
+        const int me = (int)out->nodes.size();
+        out->nodes.push_back(Bvh4Node{});
+        int refs[4] = {kNoChild, kNoChild, kNoChild, kNoChild};
+        int sub_need = 0, sub_depth = 0;
+        for (int j = 0; j < n; ++j) {
+            if (kids[j].ref >= 0) {
+                int nd = 0, dp = 0;
+                refs[j] = collapse(kids[j].ref, nd, dp);
+                sub_need = std::max(sub_need, nd);
+                sub_depth = std::max(sub_depth, dp);
+            } else {
+                refs[j] = kids[j].ref;
+            }
+        }
+        need = (n - 1) + sub_need;
+        depth4 = 1 + sub_depth;
+        Bvh4Node& q = out->nodes[me];
+        float lo[3][4], hi[3][4];
+        for (int j = 0; j < 4; ++j)
+            for (int k = 0; k < 3; ++k) {
+                lo[k][j] = j < n ? kids[j].box.lo[k] : 0.0f;
+                hi[k][j] = j < n ? kids[j].box.hi[k] : 0.0f;
+            }
+        q.lox = make_float4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
+        q.hix = make_float4(hi[0][0], hi[0][1], hi[0][2], hi[0][3]);
+        q.loy = make_float4(lo[1][0], lo[1][1], lo[1][2], lo[1][3]);
+        q.hiy = make_float4(hi[1][0], hi[1][1], hi[1][2], hi[1][3]);
+        q.loz = make_float4(lo[2][0], lo[2][1], lo[2][2], lo[2][3]);
+        q.hiz = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
+        q.refs = make_int4(refs[0], refs[1], refs[2], refs[3]);
+        q.pad = make_int4(n, 0, 0, 0);
         return me;
     }
 };
@@ -205,12 +270,24 @@ bool build_bvh(const float* verts, uint32_t n_verts, const uint32_t* tris, uint3
     }
     B.idx.resize(n_tris);
     std::iota(B.idx.begin(), B.idx.end(), 0u);
-    out->nodes.reserve(2 * (size_t)n_tris / 2 + 1);
+    B.bin.reserve(n_tris);
     out->tris.reserve(n_tris);
-    out->root = B.build(0, n_tris, 0);
-    out->depth = B.max_depth_seen;
-    if (out->depth >= kMaxBvhDepth) {
+    const int root2 = B.build(0, n_tris, 0);
+    if (B.max_depth_seen >= kMaxBvhDepth) {
         *err = "BVH too deep for the traversal stack";
+        return false;
+    }
+    if (root2 < 0) {  // the whole scene is one leaf
+        out->root = root2;
+        out->depth = 0;
+        return true;
+    }
+    out->nodes.reserve(B.bin.size() / 2 + 1);
+    int need = 0, depth4 = 0;
+    out->root = B.collapse(root2, need, depth4);
+    out->depth = depth4;
+    if (need + 1 > kStackSize) {
+        *err = "BVH needs more traversal stack than the kernels hold";
         return false;
     }
     return true;

@@ -47,7 +47,7 @@ cudaError_t dev_alloc(T** p, size_t count) {
 }  // namespace
 
 struct jr_scene {
-    BvhNode* nodes = nullptr;
+    Bvh4Node* nodes = nullptr;
     TriRecord* tris = nullptr;
     Material* mats = nullptr;
     SceneView view{};
@@ -134,7 +134,7 @@ jr_status jr_scene_create(const jr_scene_desc* desc, void* stream, jr_scene** ou
     if ((e = dev_alloc(&s->nodes, bvh.nodes.size())) != cudaSuccess ||
         (e = dev_alloc(&s->tris, bvh.tris.size())) != cudaSuccess ||
         (e = dev_alloc(&s->mats, mats.size())) != cudaSuccess ||
-        (e = cudaMemcpyAsync(s->nodes, bvh.nodes.data(), sizeof(BvhNode) * bvh.nodes.size(), cudaMemcpyHostToDevice,
+        (e = cudaMemcpyAsync(s->nodes, bvh.nodes.data(), sizeof(Bvh4Node) * bvh.nodes.size(), cudaMemcpyHostToDevice,
                              st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(s->tris, bvh.tris.data(), sizeof(TriRecord) * bvh.tris.size(), cudaMemcpyHostToDevice,
                              st)) != cudaSuccess ||
@@ -155,7 +155,7 @@ jr_status jr_scene_create(const jr_scene_desc* desc, void* stream, jr_scene** ou
     s->info.bvh_depth = (uint32_t)bvh.depth;
     s->info.n_materials = desc->n_materials;
     s->info.device_bytes =
-        sizeof(BvhNode) * bvh.nodes.size() + sizeof(TriRecord) * bvh.tris.size() + sizeof(Material) * mats.size();
+        sizeof(Bvh4Node) * bvh.nodes.size() + sizeof(TriRecord) * bvh.tris.size() + sizeof(Material) * mats.size();
     *out = s;
     return JR_OK;
 }

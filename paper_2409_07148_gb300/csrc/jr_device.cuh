@@ -115,9 +115,33 @@ __device__ __forceinline__ void trav_begin(const SceneView& s, Trav& r, float3 o
     r.visits = 0;
 }
 
-// Visit inner node r.ref: slab-test both children against [0, tb], descend to
-// the nearer hit child and push the farther, or pop.  Returns false (and sets
-// a status bit) if the visit budget or the stack ran out: the ray then counts
+// Order two (distance, ref) pairs so that the nearer comes first.
+__device__ __forceinline__ void cswap(float& ta, int& ra, float& tb, int& rb) {
+    const bool sw = tb < ta;
+    const float t = sw ? tb : ta;
+    tb = sw ? ta : tb;
+    ta = t;
+    const int q = sw ? rb : ra;
+    rb = sw ? ra : rb;
+    ra = q;
+}
+
+// Slab test of child box lane (lo, hi per axis) against [0, tb]: entry
+// distance, or +inf for a miss.  The far distance is scaled up by 2 ulp so
+// that a ray grazing a face of a (conservatively widened) box still enters it.
+__device__ __forceinline__ float slab(const Trav& r, float lx, float hx, float ly, float hy, float lz, float hz) {
+    const float l0 = fmaf(lx, r.ix, -r.ox), h0 = fmaf(hx, r.ix, -r.ox);
+    const float l1 = fmaf(ly, r.iy, -r.oy), h1 = fmaf(hy, r.iy, -r.oy);
+    const float l2 = fmaf(lz, r.iz, -r.oz), h2 = fmaf(hz, r.iz, -r.oz);
+    const float tn = fmax3(fminf(l0, h0), fminf(l1, h1), fmaxf(fminf(l2, h2), 0.0f));
+    const float tf = fmin3(fmaxf(l0, h0), fmaxf(l1, h1), fminf(fmaxf(l2, h2), r.tb));
+    return tn <= tf * 1.00000024f ? tn : INFINITY;
+}
+
+// Visit inner node r.ref of the 4-wide BVH: slab-test its children against
+// [0, tb], descend to the nearest hit child and push the other hit children
+// farthest first (front-to-back order), or pop.  Returns false (and sets a
+// status bit) if the visit budget or the stack ran out: the ray then counts
 // as a miss.
 template <bool kCount>
 __device__ __forceinline__ bool trav_node(const SceneView& s, Trav& r, int* stack, unsigned& status, Work& work) {
@@ -126,36 +150,34 @@ __device__ __forceinline__ bool trav_node(const SceneView& s, Trav& r, int* stac
         return false;
     }
     if constexpr (kCount) work.nodes++;
-    const BvhNode* n = s.nodes + r.ref;
-    const float4 a = __ldg(&n->a), b = __ldg(&n->b), c = __ldg(&n->c);
-    const int4 rf = __ldg(&n->refs);
-    const float l0x = fmaf(a.x, r.ix, -r.ox), h0x = fmaf(a.y, r.ix, -r.ox);
-    const float l0y = fmaf(a.z, r.iy, -r.oy), h0y = fmaf(a.w, r.iy, -r.oy);
-    const float l0z = fmaf(c.x, r.iz, -r.oz), h0z = fmaf(c.y, r.iz, -r.oz);
-    const float l1x = fmaf(b.x, r.ix, -r.ox), h1x = fmaf(b.y, r.ix, -r.ox);
-    const float l1y = fmaf(b.z, r.iy, -r.oy), h1y = fmaf(b.w, r.iy, -r.oy);
-    const float l1z = fmaf(c.z, r.iz, -r.oz), h1z = fmaf(c.w, r.iz, -r.oz);
-    const float tn0 = fmax3(fminf(l0x, h0x), fminf(l0y, h0y), fmaxf(fminf(l0z, h0z), 0.0f));
-    const float tf0 = fmin3(fmaxf(l0x, h0x), fmaxf(l0y, h0y), fminf(fmaxf(l0z, h0z), r.tb));
-    const float tn1 = fmax3(fminf(l1x, h1x), fminf(l1y, h1y), fmaxf(fminf(l1z, h1z), 0.0f));
-    const float tf1 = fmin3(fmaxf(l1x, h1x), fmaxf(l1y, h1y), fminf(fmaxf(l1z, h1z), r.tb));
-    const bool h0 = tn0 <= tf0 * 1.00000024f;
-    const bool h1 = tn1 <= tf1 * 1.00000024f;
-    if (h0 && h1) {
-        if (r.sp >= kStackSize) {
-            status |= JR_STATUS_STACK;
-            return false;
-        }
-        const bool first0 = tn0 <= tn1;
-        stack[r.sp++] = first0 ? rf.y : rf.x;
-        r.ref = first0 ? rf.x : rf.y;
-    } else if (h0) {
-        r.ref = rf.x;
-    } else if (h1) {
-        r.ref = rf.y;
-    } else {
-        r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
+    const Bvh4Node* n = s.nodes + r.ref;
+    const float4 lx = __ldg(&n->lox), hx = __ldg(&n->hix), ly = __ldg(&n->loy), hy = __ldg(&n->hiy);
+    const float4 lz = __ldg(&n->loz), hz = __ldg(&n->hiz);
+    int4 rf = __ldg(&n->refs);
+    float t0 = slab(r, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x);
+    float t1 = slab(r, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y);
+    float t2 = slab(r, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z);
+    float t3 = slab(r, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w);
+    if (rf.x == kNoChild) t0 = INFINITY;
+    if (rf.y == kNoChild) t1 = INFINITY;
+    if (rf.z == kNoChild) t2 = INFINITY;
+    if (rf.w == kNoChild) t3 = INFINITY;
+    // 5-comparator sorting network on (distance, ref)
+    cswap(t0, rf.x, t1, rf.y);
+    cswap(t2, rf.z, t3, rf.w);
+    cswap(t0, rf.x, t2, rf.z);
+    cswap(t1, rf.y, t3, rf.w);
+    cswap(t1, rf.y, t2, rf.z);
+    const int pushes = (t1 < INFINITY) + (t2 < INFINITY) + (t3 < INFINITY);
+    if (r.sp + pushes > kStackSize) {
+        status |= JR_STATUS_STACK;
+        return false;
     }
+    if (t3 < INFINITY) stack[r.sp++] = rf.w;
+    if (t2 < INFINITY) stack[r.sp++] = rf.z;
+    if (t1 < INFINITY) stack[r.sp++] = rf.y;
+    if (t0 < INFINITY) r.ref = rf.x;
+    else r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
     return true;
 }
 

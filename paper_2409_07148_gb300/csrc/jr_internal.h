@@ -12,23 +12,25 @@ namespace jr {
 
 constexpr int kMaxDepth = 15;
 constexpr int kMaxDim = 2 + 2 * kMaxDepth;  // 32
-constexpr int kStackSize = 64;              // traversal stack entries
-constexpr int kMaxBvhDepth = kStackSize - 2;
+constexpr int kStackSize = 96;              // traversal stack entries
+constexpr int kMaxBvhDepth = 62;            // depth limit of the binary SAH build (before the 4-wide collapse)
 constexpr int kLeafMax = 8;                 // triangles per leaf (encoded count-1 in 3 bits)
 constexpr uint32_t kNodeVisitBudget = 1u << 16;  // per ray; exceeding it is a watchdog event
 
 constexpr uint32_t kTagStep = 0, kTagInit = 1, kTagPt = 2, kTagRestart = 3;
 constexpr uint64_t kWavefrontMinChains = 1u << 16;  // JR_EXEC_AUTO picks the wavefront from here up
 
-// BVH node, 64 bytes: both children's boxes, Aila & Laine style.
-//   a = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
-//   b = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
-//   c = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
-//   refs.x/.y = child refs: >= 0 inner node index; < 0 leaf = ~((first << 3) | (count - 1))
-struct __align__(16) BvhNode {
-    float4 a, b, c;
+// 4-wide BVH node, 128 bytes (one L2 line): the boxes of up to 4 children,
+// one float4 per plane with child j in component j, then the child refs:
+// >= 0 inner node index; < 0 leaf = ~((first << 3) | (count - 1)); kNoChild
+// marks an empty slot (its box is never used).  The last 16 bytes are unused.
+struct __align__(128) Bvh4Node {
+    float4 lox, hix, loy, hiy, loz, hiz;
     int4 refs;
+    int4 pad;
 };
+static_assert(sizeof(Bvh4Node) == 128, "a 4-wide node is one 128-byte line");
+constexpr int kNoChild = INT32_MIN;
 
 // Triangle in BVH leaf order, 48 bytes: v0 | original id, e1 | material, e2.
 struct __align__(16) TriRecord {
@@ -50,7 +52,7 @@ struct __align__(16) Material {
 };
 
 struct SceneView {
-    const BvhNode* nodes;
+    const Bvh4Node* nodes;
     const TriRecord* tris;
     const Material* mats;
     int root;       // child ref of the root, or INT32_MIN when the scene is empty
@@ -134,7 +136,7 @@ struct BatchItem {
 
 // Host-side BVH build result.
 struct HostBvh {
-    std::vector<BvhNode> nodes;
+    std::vector<Bvh4Node> nodes;
     std::vector<TriRecord> tris;
     int root = 0;
     int depth = 0;
