@@ -130,8 +130,8 @@ class ClockSampler:
 def launches_per_advance(mode, chains, chain_steps, depth):
     """Kernels of ours one jr_advance launches (see jr_advance in include/jr.h)."""
     wave = mode == "wave" or (mode == "auto" and chains >= (1 << 16))
-    if wave:   # per step: step kernel + a trace and a shade kernel per vertex; then a finish launch and the fold
-        return chain_steps * (1 + 2 * (depth + 1)) + 2
+    if wave:   # per step: the step kernel and the path kernel; then a finish launch and the fold
+        return chain_steps * 2 + 2
     return 2   # the persistent step kernel and the fold
 
 
@@ -245,18 +245,26 @@ def run_caustic(args):
     C = args.chains or (1 << 20)
     with torch.cuda.stream(stream):
         g = jr.Scene(sc, stream=stream)
-        # reference: two independent halves of plain path tracing
-        halves = []
+        # reference: two independent halves of plain path tracing (optionally
+        # kept in a file, keyed by the scene size and the sample count)
+        cache = args.ref_file and f"{args.ref_file}.{side}.{args.ref_samples}.npz"
         t0 = time.perf_counter()
-        chunk = 1 << 28
-        n_half = args.ref_samples // 2
-        for h in range(2):
-            acc = torch.zeros((side, side, 4), dtype=torch.float64, device="cuda")
-            for s0 in range(0, n_half, chunk):
-                jr.render_pt(g, side, side, sc.depth, min(chunk, n_half - s0), seed=1000 + h, sample_begin=s0,
-                             accum=acc, stream=stream)
-            halves.append(acc[..., :3] / n_half)
-        stream.synchronize()
+        if cache and os.path.exists(cache):
+            z = np.load(cache)
+            halves = [torch.from_numpy(z["h0"]).cuda(), torch.from_numpy(z["h1"]).cuda()]
+        else:
+            halves = []
+            chunk = 1 << 28
+            n_half = args.ref_samples // 2
+            for h in range(2):
+                acc = torch.zeros((side, side, 4), dtype=torch.float64, device="cuda")
+                for s0 in range(0, n_half, chunk):
+                    jr.render_pt(g, side, side, sc.depth, min(chunk, n_half - s0), seed=1000 + h, sample_begin=s0,
+                                 accum=acc, stream=stream)
+                halves.append(acc[..., :3] / n_half)
+            stream.synchronize()
+            if cache:
+                np.savez(cache, h0=halves[0].cpu().numpy(), h1=halves[1].cpu().numpy())
         t_ref = time.perf_counter() - t0
         ref = 0.5 * (halves[0] + halves[1])
         ref_noise = relmse(halves[0], halves[1]) / 4.0   # relMSE of the mean of two halves vs truth, roughly
@@ -276,6 +284,7 @@ def run_caustic(args):
             parts = {"advance": 0.0, "train": 0.0, "drain_switch": 0.0}
             drain_steps = 0
             diag = []
+            split = None
             prev = ch.stats(stream=stream)
 
             def lap(key, t0):
@@ -310,6 +319,9 @@ def run_caustic(args):
                 clock += t2 - t0
                 cur = ch.stats(stream=stream)
                 drain_steps += cur["steps_per_chain"] - s0
+                if e == args.split_epoch:  # off the clock: device time per kernel class of 16 steps
+                    split = ch.advance_timed(16, stream=stream)
+                    cur = ch.stats(stream=stream)
                 img = torch.zeros((side, side, 3), dtype=torch.float32, device="cuda")
                 ch.resolve(out=img, stream=stream)
                 stream.synchronize()
@@ -337,12 +349,13 @@ def run_caustic(args):
                     "epochs": len(curve),
                     "curve": [[round(t, 3), r] for t, r in curve[:: max(1, len(curve) // 40)]],
                     "seconds": {k: round(v, 3) for k, v in parts.items()}, "drain_steps": drain_steps, "diag": diag,
+                    "split_16_steps": split,
                     "regenerations": st["regenerations"], "local_steps": st["local_steps"],
                     "accepted": st["accepted"], "chain_steps": int(st["steps_per_chain"]) * C,
                     "status_word": st["status_word"]}
 
-        plain = run(False)
-        learned = run(True)
+        plain = run(False) if "plain" in args.arms else None
+        learned = run(True) if "learned" in args.arms else {}
     line = {"metric": METRIC, "workload": f"caustic_slit_{side}x{side}_depth10", "unit": "s to relMSE 1e-2",
             "relmse_eps": 1e-2, "target": target, "time_limit_s": tmax, "chains": C, "epoch_steps": epoch,
             "epoch_growth": args.epoch_growth, "epoch_max": args.epoch_max,
@@ -403,6 +416,9 @@ def main():
     ap.add_argument("--snap-every", type=int, default=16, help="caustic workload: steps between training snapshots")
     ap.add_argument("--replay", type=int, default=1 << 20, help="caustic workload: replay ring rows")
     ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--ref-file", default=None, help="caustic workload: cache the reference image in this file")
+    ap.add_argument("--arms", default="plain,learned", help="caustic workload: arms to run")
+    ap.add_argument("--split-epoch", type=int, default=-1, help="caustic workload: time 16 extra steps per kernel class after this epoch (diagnostic)")
     ap.add_argument("--beta", type=float, default=0.5)
     args = ap.parse_args()
     if args.workload == "batched64" and args.impl == "ours":
@@ -541,7 +557,7 @@ def main():
         "accept_rate": st["accepted"] / max(1, st["local_steps"]),
         "clocks": clocks,
         "e2e": e2e,
-        "gpu_launches": args.steps * launches_per_advance(args.exec, C, K, sc.depth),
+        "gpu_launches": args.steps * (sum(v["launches"] for v in split.values()) + 1),  # + the fold
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

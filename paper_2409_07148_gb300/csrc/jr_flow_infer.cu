@@ -99,7 +99,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
            ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
 }
-__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
 __device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
     asm volatile(
@@ -109,12 +108,29 @@ __device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint3
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// B fragment of a swizzled [N][64] bf16 matrix: rows n, k = k0 + 2t (+8).
-__device__ __forceinline__ void frag_b64(const __nv_bfloat16* W, int n, int k0, int t, uint32_t& b0, uint32_t& b1) {
-    const __nv_bfloat16* row = W + n * 64;
-    const int c = k0 >> 3, s = n & 7;
-    b0 = lds32(row + (((c) ^ s) << 3) + 2 * t);
-    b1 = lds32(row + (((c + 1) ^ s) << 3) + 2 * t);
+// B fragments of two n-tiles (rows n0 .. n0 + 15) at k = k0 .. k0 + 15 of a
+// swizzled [N][64] bf16 matrix, with one ldmatrix.x4: lanes 0-7 address the
+// rows n0 + 0..7 at k-chunk k0/8, lanes 8-15 the same rows at chunk k0/8 + 1,
+// lanes 16-31 rows n0 + 8..15 likewise.  Fragment (b[0], b[1]) is n-tile n0,
+// (b[2], b[3]) n-tile n0 + 8.
+__device__ __forceinline__ void frag_b64x2(const __nv_bfloat16* W, int n0, int k0, uint32_t (&b)[4]) {
+    const int lane = threadIdx.x & 31;
+    const int n = n0 + (lane & 7) + ((lane >> 4) << 3);
+    const int c = (k0 >> 3) + ((lane >> 3) & 1);
+    const __nv_bfloat16* p = W + n * 64 + ((c ^ (n & 7)) << 3);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3])
+                 : "r"(smem_addr(p)));
+}
+// The same for the [64][16] W1 (one k-step; chunk c of row n at c ^ ((n >> 2) & 1)).
+__device__ __forceinline__ void frag_b16x2(const __nv_bfloat16* W, int n0, uint32_t (&b)[4]) {
+    const int lane = threadIdx.x & 31;
+    const int n = n0 + (lane & 7) + ((lane >> 4) << 3);
+    const int c = (lane >> 3) & 1;
+    const __nv_bfloat16* p = W + n * 16 + ((c ^ ((n >> 2) & 1)) << 3);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3])
+                 : "r"(smem_addr(p)));
 }
 
 // ReLU(acc + b) of 8 n-tiles (64 columns) as bf16 A fragments of a K = 64 GEMM.
@@ -154,33 +170,55 @@ __device__ __forceinline__ float quad_exclusive(float v, int t) {
 template <bool kSample>
 __device__ __forceinline__ float cdf_step(const float (&L)[4], int t, float& v) {
     const float m = quad_max(fmaxf(fmaxf(L[0], L[1]), fmaxf(L[2], L[3])));
-    float Q[4];
+    float e[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) Q[i] = __expf(L[i] - m);
-    const float S = quad_sum((Q[0] + Q[1]) + (Q[2] + Q[3]));
-    const float sc = (1.0f - kFE) / S;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) Q[i] = Q[i] * sc + kFE / kFK;
+    for (int i = 0; i < 4; ++i) e[i] = __expf(L[i] - m);
     const int kb[4] = {2 * t, 2 * t + 1, 8 + 2 * t, 9 + 2 * t};
+    // With S = sum e, Q_k = sc e_k + E/K (sc = (1 - E)/S), so the mass below bin b
+    // is sc * (sum_{k<b} e_k) + b E/K and the mass of bin b is sc e_b + E/K.
+    float S, lo_e, qb_e;
     int b;
     if (!kSample) {
         b = min((int)(v * (float)kFK), kFK - 1);
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            s0 += e[i];
+            s1 += kb[i] < b ? e[i] : 0.f;
+            s2 += kb[i] == b ? e[i] : 0.f;
+        }
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
+        S = s0 + __shfl_xor_sync(0xffffffffu, s0, 2);
+        lo_e = s1 + __shfl_xor_sync(0xffffffffu, s1, 2);
+        qb_e = s2 + __shfl_xor_sync(0xffffffffu, s2, 2);
     } else {
+        S = quad_sum((e[0] + e[1]) + (e[2] + e[3]));
+        const float sc = __fdividef(1.0f - kFE, S);
+        float Q[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) Q[i] = e[i] * sc + kFE / kFK;
         // inclusive cumulative masses of this lane's bins, in bin order
         const float s1 = Q[0] + Q[1], s2 = Q[2] + Q[3];
         const float e1 = quad_exclusive(s1, t), h0 = quad_sum(s1), e2 = quad_exclusive(s2, t);
         const float c0 = e1 + Q[0], c1 = c0 + Q[1], c2 = h0 + e2 + Q[2], c3 = c2 + Q[3];
-        float cnt = (float)((c0 <= v) + (c1 <= v) + (c2 <= v) + (c3 <= v));
+        const float cnt = (float)((c0 <= v) + (c1 <= v) + (c2 <= v) + (c3 <= v));
         b = min((int)quad_sum(cnt), kFK - 1);
-    }
-    float lo = 0.f, qb = 0.f;
+        float p1 = 0.f, p2 = 0.f;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        lo += kb[i] < b ? Q[i] : 0.f;
-        qb += kb[i] == b ? Q[i] : 0.f;
+        for (int i = 0; i < 4; ++i) {
+            p1 += kb[i] < b ? e[i] : 0.f;
+            p2 += kb[i] == b ? e[i] : 0.f;
+        }
+        p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
+        p2 += __shfl_xor_sync(0xffffffffu, p2, 1);
+        lo_e = p1 + __shfl_xor_sync(0xffffffffu, p1, 2);
+        qb_e = p2 + __shfl_xor_sync(0xffffffffu, p2, 2);
     }
-    lo = quad_sum(lo);
-    qb = quad_sum(qb);
+    const float sc = __fdividef(1.0f - kFE, S);  // S in [1, 16]
+    const float lo = sc * lo_e + (float)b * (kFE / kFK);
+    const float qb = sc * qb_e + kFE / kFK;
     if (!kSample) {
         v = lo + (v * (float)kFK - (float)b) * qb;
     } else {
@@ -210,11 +248,13 @@ __device__ __forceinline__ void coupling(const unsigned char* wl, const uint8_t*
                           pack_bf16(xa(g + 8, 2 * t + 8), xa(g + 8, 2 * t + 9))};
         float acc[8][4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < 8; q += 2) {
             acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
-            const int n = 8 * q + g, s = (n >> 2) & 1;
-            const __nv_bfloat16* row = W1 + n * kFAP;
-            mma(acc[q], a0, lds32(row + ((0 ^ s) << 3) + 2 * t), lds32(row + ((1 ^ s) << 3) + 2 * t));
+            acc[q + 1][0] = acc[q + 1][1] = acc[q + 1][2] = acc[q + 1][3] = 0.f;
+            uint32_t b[4];
+            frag_b16x2(W1, 8 * q, b);
+            mma(acc[q], a0, b[0], b[1]);
+            mma(acc[q + 1], a0, b[2], b[3]);
         }
         relu_to_frags(acc, b1, t, a);
     }
@@ -225,10 +265,11 @@ __device__ __forceinline__ void coupling(const unsigned char* wl, const uint8_t*
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                uint32_t b0, bb;
-                frag_b64(W2, 8 * q + g, 16 * kk, t, b0, bb);
-                mma(acc[q], a[kk], b0, bb);
+            for (int q = 0; q < 8; q += 2) {
+                uint32_t b[4];
+                frag_b64x2(W2, 8 * q, 16 * kk, b);
+                mma(acc[q], a[kk], b[0], b[1]);
+                mma(acc[q + 1], a[kk], b[2], b[3]);
             }
         relu_to_frags(acc, b2, t, a);
     }
@@ -241,32 +282,47 @@ __device__ __forceinline__ void coupling(const unsigned char* wl, const uint8_t*
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (q < nq) {
-                    uint32_t b0, bb;
-                    frag_b64(W3, 16 * j0 + 8 * q + g, 16 * kk, t, b0, bb);
-                    mma(acc[q], a[kk], b0, bb);
+            for (int q = 0; q < 8; q += 2)
+                if (q < nq) {  // nq is even: a coordinate is two n-tiles
+                    uint32_t b[4];
+                    frag_b64x2(W3, 16 * j0 + 8 * q, 16 * kk, b);
+                    mma(acc[q], a[kk], b[0], b[1]);
+                    mma(acc[q + 1], a[kk], b[2], b[3]);
                 }
+        // the up to 4 coordinates of this group are independent: read them all,
+        // run their CDF steps, then write them back (one warp barrier)
+        float v0[4], v1[4];
+        int cb[4];
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
-            if (2 * jj >= nq) break;
-            const int col = 16 * (j0 + jj);
-            const float bl0 = b3[col + 2 * t], bl1 = b3[col + 2 * t + 1], bh0 = b3[col + 8 + 2 * t],
-                        bh1 = b3[col + 9 + 2 * t];
-            const float L0[4] = {acc[2 * jj][0] + bl0, acc[2 * jj][1] + bl1, acc[2 * jj + 1][0] + bh0,
-                                 acc[2 * jj + 1][1] + bh1};
-            const float L1[4] = {acc[2 * jj][2] + bl0, acc[2 * jj][3] + bl1, acc[2 * jj + 1][2] + bh0,
-                                 acc[2 * jj + 1][3] + bh1};
-            const int cb = pm[A + j0 + jj];
-            float v0 = xw[g * xs + cb], v1 = xw[(g + 8) * xs + cb];
-            lq0 += cdf_step<kSample>(L0, t, v0);
-            lq1 += cdf_step<kSample>(L1, t, v1);
-            __syncwarp();
-            if (t == 0) xw[g * xs + cb] = v0;
-            if (t == 1) xw[(g + 8) * xs + cb] = v1;
+            cb[jj] = 2 * jj < nq ? pm[A + j0 + jj] : 0;
+            v0[jj] = xw[g * xs + cb[jj]];
+            v1[jj] = xw[(g + 8) * xs + cb[jj]];
         }
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            if (2 * jj < nq) {  // warp-uniform
+                const int col = 16 * (j0 + jj);
+                const float bl0 = b3[col + 2 * t], bl1 = b3[col + 2 * t + 1], bh0 = b3[col + 8 + 2 * t],
+                            bh1 = b3[col + 9 + 2 * t];
+                const float L0[4] = {acc[2 * jj][0] + bl0, acc[2 * jj][1] + bl1, acc[2 * jj + 1][0] + bh0,
+                                     acc[2 * jj + 1][1] + bh1};
+                const float L1[4] = {acc[2 * jj][2] + bl0, acc[2 * jj][3] + bl1, acc[2 * jj + 1][2] + bh0,
+                                     acc[2 * jj + 1][3] + bh1};
+                lq0 += cdf_step<kSample>(L0, t, v0[jj]);
+                lq1 += cdf_step<kSample>(L1, t, v1[jj]);
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            if (2 * jj < nq) {
+                if (t == 0) xw[g * xs + cb[jj]] = v0[jj];
+                if (t == 1) xw[(g + 8) * xs + cb[jj]] = v1[jj];
+            }
+        }
+        __syncwarp();
     }
-    __syncwarp();
 }
 
 // Rows: chains idx[j] (or j when idx is null) for j < *count_dev (or n_rows).

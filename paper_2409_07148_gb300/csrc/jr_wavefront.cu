@@ -34,6 +34,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kRefill = 8;  // refill a warp once this many lanes are idle
+constexpr bool kPathKernel = true;  // whole paths per launch (else a trace and a shade launch per vertex)
 
 // Path record of a live path: (o.xyz, d.x) (d.yz, T.xy) (T.z, F.xyz).
 __device__ __forceinline__ void store_path(float4* path, uint64_t i, float3 o, float3 d, float3 T, float3 F) {
@@ -365,6 +366,130 @@ __global__ void __launch_bounds__(128) wf_shade_kernel(SceneView s, ChainView c,
     }
 }
 
+// Whole paths of every queued chain in one persistent launch.  A lane keeps
+// its path (ray, throughput T, emission F, vertex v) in registers and moves
+// between three states: traversing its current ray; waiting to shade (its
+// closest hit is known); idle (no path).  Traversal rounds are warp-
+// synchronous, as in the trace kernel.  A warp shades its waiting lanes
+// together once kShadeBatch of them wait (or none is traversing); a shaded
+// path either continues with its next ray or ends (F goes to the path record,
+// and, with a flow, the row joins the density queue under the same rule as in
+// the shade kernel).  Idle lanes take new paths from the queue.
+constexpr int kShadeBatch = 8;
+enum PathState : uint32_t { kIdle = 0, kTraverse = 1, kWaitShade = 2 };
+
+__global__ void __launch_bounds__(128) wf_path_kernel(SceneView s, ChainView c) {
+    const WaveView& w = c.wf;
+    const uint32_t* qin = w.queue;
+    const unsigned count = w.qcount[0];
+    if ((uint64_t)blockIdx.x * blockDim.x >= count) return;
+    unsigned int* fetch = w.qcount + (kMaxDepth + 2);
+    const uint64_t n = c.n;
+    const int depth = (int)c.depth;
+    const bool has_flow = c.flow.D != 0;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned status = 0;
+    Work wk;
+    Trav r;
+    int stack[kStackSize];
+    uint32_t state = kIdle, i = 0;
+    int v = 0, leaf = kSentinel;
+    bool failed = false, drained = false;
+    float3 T = f3(1.f, 1.f, 1.f), F = f3(0.f, 0.f, 0.f);
+    while (true) {
+        // shade the waiting lanes as a batch
+        const unsigned waiting = __ballot_sync(kFull, state == kWaitShade);
+        const unsigned tracing = __ballot_sync(kFull, state == kTraverse);
+        if (waiting && (__popc(waiting) >= kShadeBatch || tracing == 0)) {
+            bool need_u = false;
+            if (state == kWaitShade) {
+                bool live = false;
+                if (r.best >= 0) {
+                    float u1 = 0.f, u2 = 0.f;
+                    if (v < depth) {
+                        const float* cand = w.par[i] ? c.x : w.y;
+                        u1 = cand[(uint64_t)(2 + 2 * v) * n + i];
+                        u2 = cand[(uint64_t)(3 + 2 * v) * n + i];
+                    }
+                    float3 o = r.o, d = r.d;
+                    live = shade_vertex(s, r.best, r.tb, v, depth, u1, u2, o, d, T, F);
+                    if (live) {
+                        ++v;
+                        trav_begin(s, r, o, d);
+                        state = kTraverse;
+                    }
+                }
+                if (!live) {
+                    w.path[3 * (uint64_t)i + 2] = make_float4(0.f, F.x, F.y, F.z);
+                    if (has_flow) {
+                        unsigned ignored = 0;
+                        const float py = lum(finite_or_zero(F, ignored));
+                        const float ua = w.ua[i];
+                        need_u = ua >= 0.0f ? ua * c.fpu[3 * n + i] < py : (ua == -1.0f && py > 0.0f);
+                    }
+                    state = kIdle;
+                }
+            }
+            if (has_flow) enqueue(need_u, i, w.fq, w.qcount + kQFlowDensity);
+        }
+        // take new paths for idle lanes
+        const unsigned idle = __ballot_sync(kFull, state == kIdle);
+        if (!drained && idle && (__popc(idle) >= kRefill || idle == kFull)) {
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(fetch, (unsigned)__popc(idle));
+            base = __shfl_sync(kFull, base, 0);
+            if (base + (unsigned)__popc(idle) >= count) drained = true;
+            if (state == kIdle) {
+                const unsigned j = base + __popc(idle & lt);
+                if (j < count) {
+                    i = qin[j];
+                    float3 o, d;
+                    load_path(w.path, i, o, d, T, F);
+                    v = 0;
+                    trav_begin(s, r, o, d);
+                    state = s.root != kSentinel ? kTraverse : kWaitShade;  // empty scene: a miss
+                }
+            }
+        }
+        if (!__any_sync(kFull, state != kIdle)) {
+            if (drained) break;
+            continue;
+        }
+        // one speculative while-while traversal round (see the trace kernel)
+        const bool trav = state == kTraverse;
+        if (trav && leaf == kSentinel && r.ref < 0 && r.ref != kSentinel) {
+            leaf = r.ref;
+            r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
+        }
+        while (__any_sync(kFull, trav && leaf == kSentinel && r.ref >= 0)) {
+            if (trav && r.ref >= 0) {
+                if (!trav_node<false>(s, r, stack, status, wk)) {
+                    r.best = -1;
+                    r.ref = kSentinel;
+                    leaf = kSentinel;
+                    failed = true;
+                } else if (leaf == kSentinel && r.ref < 0 && r.ref != kSentinel) {
+                    leaf = r.ref;
+                    r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
+                }
+            }
+        }
+        if (trav) {
+            if (leaf != kSentinel) {
+                trav_test_leaf<false>(s, r, leaf, wk);
+                leaf = kSentinel;
+            }
+            if (failed || r.ref == kSentinel) {
+                state = kWaitShade;
+                failed = false;
+            }
+        }
+    }
+    status = __reduce_or_sync(kFull, status);
+    if (lane == 0 && status) atomicOr(c.status, status);
+}
+
 inline unsigned grid_for(uint64_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 
 // The flow stages of a step (a chain's candidate lives in x when its parity
@@ -414,7 +539,7 @@ KernelTimer::~KernelTimer() {
 
 cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
                              cudaStream_t st, int mode, KernelTimer* tm) {
-    static int trace_blocks = 0, shade_blocks = 0;
+    static int trace_blocks = 0, shade_blocks = 0, path_blocks = 0;
     if (trace_blocks == 0) {
         int dev = 0, sms = 0, per_sm = 0, per_sm2 = 0;
         cudaError_t e;
@@ -426,6 +551,10 @@ cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t st
             return e;
         trace_blocks = sms * (per_sm > 0 ? per_sm : 1);
         shade_blocks = sms * (per_sm2 > 0 ? per_sm2 : 1);
+        int per_sm3 = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3, wf_path_kernel, 128, 0)) != cudaSuccess)
+            return e;
+        path_blocks = sms * (per_sm3 > 0 ? per_sm3 : 1);
     }
     const unsigned G = grid_for(c.n, 128);
     const bool has_flow = c.flow.D != 0;
@@ -440,11 +569,16 @@ cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t st
         mark(KernelTimer::kStep);
         if (has_flow && (e = launch_flow_draws(s, c, st)) != cudaSuccess) return e;
         if (has_flow) mark(KernelTimer::kFlow);
-        for (int v = 0; v <= (int)c.depth; ++v) {
-            wf_trace_kernel<<<trace_blocks, 128, 0, st>>>(s, c, v);
+        if (kPathKernel) {
+            wf_path_kernel<<<path_blocks, 128, 0, st>>>(s, c);
             mark(KernelTimer::kTrace);
-            wf_shade_kernel<<<shade_blocks, 128, 0, st>>>(s, c, v);
-            mark(KernelTimer::kShade);
+        } else {
+            for (int v = 0; v <= (int)c.depth; ++v) {
+                wf_trace_kernel<<<trace_blocks, 128, 0, st>>>(s, c, v);
+                mark(KernelTimer::kTrace);
+                wf_shade_kernel<<<shade_blocks, 128, 0, st>>>(s, c, v);
+                mark(KernelTimer::kShade);
+            }
         }
         if (has_flow && (e = launch_flow_densities(s, c, st)) != cudaSuccess) return e;
         if (has_flow) mark(KernelTimer::kFlow);
