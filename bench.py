@@ -38,28 +38,28 @@ UNIT = "chain steps/s"
 FLOP_PER_NODE = 109
 FLOP_PER_TRI = 45
 SMS, FP32_LANES = 152, 128
-# DRAM traffic of one wf_trace_kernel launch (dram__bytes_read.sum +
-# dram__bytes_write.sum), the mean over 18 launches of an ncu capture of the
-# 2^18-chain case (13.416 MB read + 0.099 MB written), scaled by 4 to the
-# 2^20-chain workload (the rays of a launch grow with the chains).  It stands
-# only while the kernel sources still hash to the values it was taken on.
-TRACE_TRAFFIC = {"bytes_per_launch": 4 * (13.416e6 + 0.099e6),
-                 "sources": {"jr_wavefront.cu": "303ed172e1246b01", "jr_device.cuh": "4bcf7b468f00cebe"},
-                 "summary": "profiles/trace_kernel_cornell_spheres_512x512.md"}
+# DRAM traffic of one wf_path_kernel launch (dram__bytes_read.sum +
+# dram__bytes_write.sum), the mean over 8 launches of an ncu capture of the
+# 2^18-chain case, scaled by 4 to the 2^20-chain workload (the paths of a
+# launch grow with the chains).  It stands only while the kernel sources still
+# hash to the values it was taken on; None until a capture exists.
+PATH_TRAFFIC = {"bytes_per_launch": None,
+                "sources": {"jr_wavefront.cu": "", "jr_device.cuh": ""},
+                "summary": "profiles/path_kernel_cornell_spheres_512x512.md"}
 
 
-def trace_traffic(workload_name, chains):
-    """Per-launch DRAM bytes of the trace kernel, or None when the sources
+def path_traffic(workload_name, chains):
+    """Per-launch DRAM bytes of the path kernel, or None when the sources
     changed since the capture or the workload is not the one it scales to."""
     import hashlib
-    if workload_name != "cornell_spheres" or chains != 1 << 20:
+    if workload_name != "cornell_spheres" or chains != 1 << 20 or PATH_TRAFFIC["bytes_per_launch"] is None:
         return None
     src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2409_07148_gb300", "csrc")
-    for f, h in TRACE_TRAFFIC["sources"].items():
+    for f, h in PATH_TRAFFIC["sources"].items():
         with open(os.path.join(src, f), "rb") as fh:
             if hashlib.sha256(fh.read()).hexdigest()[:16] != h:
                 return None
-    return TRACE_TRAFFIC["bytes_per_launch"]
+    return PATH_TRAFFIC["bytes_per_launch"]
 
 
 def workload(name):
@@ -502,8 +502,8 @@ def main():
         alu_peak = SMS * FP32_LANES * 2 * sm_mhz_peak * 1e6 / 1e12
         split_total = sum(v["ms"] for v in split.values())
         dom = max(split, key=lambda k: split[k]["ms"])
-        if dom == "trace":   # the traversal work runs in the trace kernel
-            achieved = flop / 1e12 / (split["trace"]["ms"] / 1e3)
+        if dom == "path":    # the traversal work runs in the path kernel
+            achieved = flop / 1e12 / (split["path"]["ms"] / 1e3)
         else:                # one launch does everything (megakernel)
             achieved = flop / 1e12 / (sum(times) / args.steps)
         # end to end through the C ABI with host buffers: scene upload (BVH built on
@@ -540,11 +540,11 @@ def main():
                    "c_tilde": 1.0, "sigma": 0.01, "regen": "uniform", "global_batch": ws * C, "seq_len": K,
                    "parallelism": f"chains sharded over {ws} GPU(s)", "l2": "flushed by a 512 MB write between timed launches",
                    "block": args.block or 128, "exec": args.exec},
-        "roofline": {"bound": "alu", "kernel": "wf_trace_kernel" if dom == "trace" else "step_kernel",
+        "roofline": {"bound": "alu", "kernel": "wf_path_kernel" if dom == "path" else "step_kernel",
                      "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved / alu_peak,
-                     "traffic": trace_traffic(args.workload, C) if dom == "trace" else None,
-                     "traffic_source": TRACE_TRAFFIC["summary"],
+                     "traffic": path_traffic(args.workload, C) if dom == "path" else None,
+                     "traffic_source": PATH_TRAFFIC["summary"],
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz_peak:.0f} MHz ({pk_kind} sm_max_mhz)",
                      "work_per_step": work, "flop_per_step": flop,
                      "launches_per_step": split[dom]["launches"],

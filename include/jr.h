@@ -157,7 +157,8 @@ jr_status jr_advance_traced(jr_chains* chains, uint32_t n_steps, uint8_t* flags_
 /* jr_advance with device timing per kernel class: an event is recorded after
  * every launch and the time since the previous one is charged to that launch's
  * class; ms_out[k] / launches_out[k] (host, 4 each) for k = 0 step kernels,
- * 1 trace, 2 shade, 3 flow (the megakernel counts as one step launch).  Same
+ * 1 path kernels (tracing and shading whole paths), 2 reserved (always 0),
+ * 3 flow kernels (the megakernel counts as one step launch).  Same
  * chains and results as jr_advance; the events add a little time between
  * launches, so use it to split a step, not to time it.  Synchronises. */
 jr_status jr_advance_timed(jr_chains* chains, uint32_t n_steps, double ms_out[4], uint64_t launches_out[4],
@@ -197,7 +198,7 @@ jr_status jr_set_execution(jr_chains* chains, uint32_t mode);
  * It runs the wavefront launches of jr_advance (JR_EXEC_WAVEFRONT), with the
  * same results, but their scratch (second state buffer, live-path records and
  * queues) lives in one fixed device array inside the library, sized for at
- * most JR_STATIC_MAX_CHAINS chains of any depth: 12,910,848 bytes, which
+ * most JR_STATIC_MAX_CHAINS chains of any depth: 12,124,416 bytes, which
  * every GPU that loads the library holds until the process exits.  The chain
  * set (state, framebuffer, accumulator, counters) is the caller's, created
  * beforehand with jr_chains_create.  It calls no cudaMalloc, cudaFree or other

@@ -72,7 +72,6 @@ struct jr_chains {
         cudaFree(view.wf.par);
         cudaFree(view.wf.ua);
         cudaFree(view.wf.path);
-        cudaFree(view.wf.hit);
         cudaFree(view.wf.uy);
         cudaFree(view.wf.fq);
         cudaFree(view.wf.done);
@@ -230,8 +229,7 @@ static jr_status ensure_wavefront(jr_chains* c, cudaStream_t st) {
     cudaError_t e;
     if ((e = dev_alloc(&w.y, (size_t)c->view.dim * n)) != cudaSuccess || (e = dev_alloc(&w.par, n)) != cudaSuccess ||
         (e = dev_alloc(&w.ua, n)) != cudaSuccess || (e = dev_alloc(&w.path, 3 * n)) != cudaSuccess ||
-        (e = dev_alloc(&w.hit, n)) != cudaSuccess ||
-        (e = dev_alloc(&w.queue, 2 * n)) != cudaSuccess ||
+        (e = dev_alloc(&w.queue, n)) != cudaSuccess ||
         (e = dev_alloc(&w.qcount, kQCount)) != cudaSuccess || (e = dev_alloc(&w.uy, n)) != cudaSuccess ||
         (e = dev_alloc(&w.fq, 2 * n)) != cudaSuccess || (e = dev_alloc(&w.done, n)) != cudaSuccess ||
         (e = cudaMemsetAsync(w.done, 0, n, st)) != cudaSuccess ||
@@ -241,7 +239,6 @@ static jr_status ensure_wavefront(jr_chains* c, cudaStream_t st) {
         cudaFree(w.par);
         cudaFree(w.ua);
         cudaFree(w.path);
-        cudaFree(w.hit);
         cudaFree(w.queue);
         cudaFree(w.qcount);
         cudaFree(w.uy);

@@ -15,9 +15,10 @@
 //     m16n8k16 (bf16 operands, FP32 accumulation) and stay in registers: the
 //     accumulator fragments of one GEMM, biased, ReLU'd and rounded to bf16, are
 //     the A fragments of the next.
-//   * The per-coordinate softmax and CDF step works on the logits' accumulator
-//     fragments directly: the 4 lanes of a quad hold the 16 bins of a row, and
-//     max, sum, prefix and bin search are quad shuffles.
+//   * The biased logits of two coordinates at a time go through a per-warp
+//     shared tile, so that each lane owns one (row, coordinate) pair with all
+//     16 bins in registers: softmax, cumulative masses and bin search run
+//     sequentially in the lane, with no shuffles.
 //   * Weights stream through shared memory one layer at a time, double
 //     buffered: one elected thread copies a layer's block (bf16 weights in a
 //     bank-conflict-free XOR-swizzled layout, then the FP32 biases) with one
@@ -43,13 +44,16 @@ constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 constexpr uint32_t kWaitIters = 1u << 26;
 
 // Shared-memory layout (bytes): two mbarriers, perm [kFL][D], row ids
-// [kTile], the rows' states [kTile][D + 1] FP32, two layer buffers.
+// [kTile], the rows' states [kTile][D + 1] FP32, per warp a logits tile
+// [16][kLgStride] FP32 (two coordinates' 32 logits per row), two layer buffers.
+constexpr int kLgStride = 36;  // conflict-free 16-byte row reads by quarter warps
 constexpr size_t kOffBar = 0, kOffPerm = 64, kOffRows = 256, kOffX = kOffRows + 4 * kTile;
+constexpr size_t kLgBytes = sizeof(float) * kWarps * 16 * kLgStride;
 __host__ __device__ constexpr size_t round128(size_t b) { return (b + 127) & ~(size_t)127; }
 __host__ __device__ constexpr size_t x_bytes(uint32_t D) { return round128(sizeof(float) * kTile * (D + 1)); }
 __host__ __device__ constexpr size_t buf_bytes(uint32_t AK) { return round128(flow_ws_layer_bytes(AK)); }
 __host__ __device__ constexpr size_t infer_smem(uint32_t D, uint32_t AK) {
-    return round128(kOffX) + x_bytes(D) + 2 * buf_bytes(AK);
+    return round128(kOffX) + x_bytes(D) + round128(kLgBytes) + 2 * buf_bytes(AK);
 }
 static_assert(kOffPerm + kFL * kMaxDim <= kOffRows, "perm table overlaps the row ids");
 
@@ -146,79 +150,43 @@ __device__ __forceinline__ void relu_to_frags(const float (&acc)[8][4], const fl
     }
 }
 
-__device__ __forceinline__ float quad_sum(float v) {
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    return v + __shfl_xor_sync(0xffffffffu, v, 2);
-}
-__device__ __forceinline__ float quad_max(float v) {
-    v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 1));
-    return fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 2));
-}
-// Exclusive prefix sum of v over the quad's lanes t = 0..3 (in lane order).
-__device__ __forceinline__ float quad_exclusive(float v, int t) {
-    float s = v, n = __shfl_up_sync(0xffffffffu, s, 1, 4);
-    if (t >= 1) s += n;
-    n = __shfl_up_sync(0xffffffffu, s, 2, 4);
-    if (t >= 2) s += n;
-    n = __shfl_up_sync(0xffffffffu, s, 1, 4);
-    return t == 0 ? 0.f : n;
-}
-
-// One coordinate's CDF step for one row.  L holds this lane's 4 logits, of
-// bins 2t, 2t+1, 8+2t, 9+2t.  Density: v = t in [0,1) becomes CDF(t);
-// sampling: v = c becomes CDF^{-1}(c).  Returns log(K Q[bin]).
+// One coordinate's CDF step for one row, all 16 bins in this lane.  L: the
+// logits; density: v = t in [0,1) becomes CDF(t); sampling: v = c becomes
+// CDF^{-1}(c).  Returns log(K Q[bin]).  With e_k = exp(L_k - max L) and
+// S = sum e, Q_k = sc e_k + E/K, sc = (1 - E)/S.
 template <bool kSample>
-__device__ __forceinline__ float cdf_step(const float (&L)[4], int t, float& v) {
-    const float m = quad_max(fmaxf(fmaxf(L[0], L[1]), fmaxf(L[2], L[3])));
-    float e[4];
+__device__ __forceinline__ float cdf_row(const float (&L)[kFK], float& v) {
+    float m = fmax3(fmax3(L[0], L[1], L[2]), fmax3(L[3], L[4], L[5]), fmax3(L[6], L[7], L[8]));
+    m = fmax3(m, fmax3(L[9], L[10], L[11]), fmax3(L[12], L[13], fmaxf(L[14], L[15])));
+    float e[kFK];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) e[i] = __expf(L[i] - m);
-    const int kb[4] = {2 * t, 2 * t + 1, 8 + 2 * t, 9 + 2 * t};
-    // With S = sum e, Q_k = sc e_k + E/K (sc = (1 - E)/S), so the mass below bin b
-    // is sc * (sum_{k<b} e_k) + b E/K and the mass of bin b is sc e_b + E/K.
-    float S, lo_e, qb_e;
+    for (int k = 0; k < kFK; ++k) e[k] = __expf(L[k] - m);
+    float s4[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s4[k] = (e[4 * k] + e[4 * k + 1]) + (e[4 * k + 2] + e[4 * k + 3]);
+    const float S = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+    const float sc = __fdividef(1.0f - kFE, S);  // S in [1, 16]
     int b;
     if (!kSample) {
         b = min((int)(v * (float)kFK), kFK - 1);
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            s0 += e[i];
-            s1 += kb[i] < b ? e[i] : 0.f;
-            s2 += kb[i] == b ? e[i] : 0.f;
-        }
-        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
-        S = s0 + __shfl_xor_sync(0xffffffffu, s0, 2);
-        lo_e = s1 + __shfl_xor_sync(0xffffffffu, s1, 2);
-        qb_e = s2 + __shfl_xor_sync(0xffffffffu, s2, 2);
     } else {
-        S = quad_sum((e[0] + e[1]) + (e[2] + e[3]));
-        const float sc = __fdividef(1.0f - kFE, S);
-        float Q[4];
+        float cum = 0.f;
+        int cnt = 0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) Q[i] = e[i] * sc + kFE / kFK;
-        // inclusive cumulative masses of this lane's bins, in bin order
-        const float s1 = Q[0] + Q[1], s2 = Q[2] + Q[3];
-        const float e1 = quad_exclusive(s1, t), h0 = quad_sum(s1), e2 = quad_exclusive(s2, t);
-        const float c0 = e1 + Q[0], c1 = c0 + Q[1], c2 = h0 + e2 + Q[2], c3 = c2 + Q[3];
-        const float cnt = (float)((c0 <= v) + (c1 <= v) + (c2 <= v) + (c3 <= v));
-        b = min((int)quad_sum(cnt), kFK - 1);
-        float p1 = 0.f, p2 = 0.f;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            p1 += kb[i] < b ? e[i] : 0.f;
-            p2 += kb[i] == b ? e[i] : 0.f;
+        for (int k = 0; k < kFK; ++k) {
+            cum += fmaf(e[k], sc, kFE / kFK);
+            cnt += cum <= v;
         }
-        p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
-        p2 += __shfl_xor_sync(0xffffffffu, p2, 1);
-        lo_e = p1 + __shfl_xor_sync(0xffffffffu, p1, 2);
-        qb_e = p2 + __shfl_xor_sync(0xffffffffu, p2, 2);
+        b = min(cnt, kFK - 1);
     }
-    const float sc = __fdividef(1.0f - kFE, S);  // S in [1, 16]
-    const float lo = sc * lo_e + (float)b * (kFE / kFK);
-    const float qb = sc * qb_e + kFE / kFK;
+    float lo_e = 0.f, qb_e = 0.f;
+#pragma unroll
+    for (int k = 0; k < kFK; ++k) {
+        lo_e += k < b ? e[k] : 0.f;
+        qb_e = k == b ? e[k] : qb_e;
+    }
+    const float lo = fmaf(sc, lo_e, (float)b * (kFE / kFK));
+    const float qb = fmaf(sc, qb_e, kFE / kFK);
     if (!kSample) {
         v = lo + (v * (float)kFK - (float)b) * qb;
     } else {
@@ -232,7 +200,7 @@ __device__ __forceinline__ float cdf_step(const float (&L)[4], int t, float& v) 
 // the layer's permutation; wl: the layer's block in shared memory).
 template <bool kSample>
 __device__ __forceinline__ void coupling(const unsigned char* wl, const uint8_t* pm, int A, int AK, float* xw, int xs,
-                                         float& lq0, float& lq1) {
+                                         float* lg, float& lqp) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const __nv_bfloat16* W1 = reinterpret_cast<const __nv_bfloat16*>(wl);
     const __nv_bfloat16* W2 = W1 + kFH * kFAP;
@@ -273,53 +241,50 @@ __device__ __forceinline__ void coupling(const unsigned char* wl, const uint8_t*
             }
         relu_to_frags(acc, b2, t, a);
     }
-    // layer 3 and the couplings, 4 coordinates (8 n-tiles of logits) at a time
-    for (int j0 = 0; j0 < A; j0 += 4) {
-        float acc[8][4];
+    // layer 3 and the couplings, 2 coordinates (4 n-tiles of logits) at a time:
+    // the biased logits go through the warp's shared tile so that lane
+    // (r = lane & 15, jj = lane >> 4) owns coordinate j0 + jj of row r
+    const int r = lane & 15, jj = lane >> 4;
+    for (int j0 = 0; j0 < A; j0 += 2) {
+        const int nq = min(4, 2 * (A - j0));  // 2 or 4 n-tiles (warp-uniform)
+        float acc[4][4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
-        const int nq = min(8, 2 * (A - j0));
+        for (int q = 0; q < 4; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
-            for (int q = 0; q < 8; q += 2)
-                if (q < nq) {  // nq is even: a coordinate is two n-tiles
+            for (int q = 0; q < 4; q += 2)
+                if (q < nq) {
                     uint32_t b[4];
                     frag_b64x2(W3, 16 * j0 + 8 * q, 16 * kk, b);
                     mma(acc[q], a[kk], b[0], b[1]);
                     mma(acc[q + 1], a[kk], b[2], b[3]);
                 }
-        // the up to 4 coordinates of this group are independent: read them all,
-        // run their CDF steps, then write them back (one warp barrier)
-        float v0[4], v1[4];
-        int cb[4];
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-            cb[jj] = 2 * jj < nq ? pm[A + j0 + jj] : 0;
-            v0[jj] = xw[g * xs + cb[jj]];
-            v1[jj] = xw[(g + 8) * xs + cb[jj]];
-        }
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-            if (2 * jj < nq) {  // warp-uniform
-                const int col = 16 * (j0 + jj);
-                const float bl0 = b3[col + 2 * t], bl1 = b3[col + 2 * t + 1], bh0 = b3[col + 8 + 2 * t],
-                            bh1 = b3[col + 9 + 2 * t];
-                const float L0[4] = {acc[2 * jj][0] + bl0, acc[2 * jj][1] + bl1, acc[2 * jj + 1][0] + bh0,
-                                     acc[2 * jj + 1][1] + bh1};
-                const float L1[4] = {acc[2 * jj][2] + bl0, acc[2 * jj][3] + bl1, acc[2 * jj + 1][2] + bh0,
-                                     acc[2 * jj + 1][3] + bh1};
-                lq0 += cdf_step<kSample>(L0, t, v0[jj]);
-                lq1 += cdf_step<kSample>(L1, t, v1[jj]);
+        for (int q = 0; q < 4; ++q)
+            if (q < nq) {
+                const int c = 8 * q + 2 * t;
+                const float2 bb = *reinterpret_cast<const float2*>(b3 + 16 * j0 + c);
+                *reinterpret_cast<float2*>(lg + g * kLgStride + c) = make_float2(acc[q][0] + bb.x, acc[q][1] + bb.y);
+                *reinterpret_cast<float2*>(lg + (g + 8) * kLgStride + c) =
+                    make_float2(acc[q][2] + bb.x, acc[q][3] + bb.y);
             }
-        }
         __syncwarp();
+        if (2 * jj < nq) {
+            float L[kFK];
+            const float4* src = reinterpret_cast<const float4*>(lg + r * kLgStride + 16 * jj);
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-            if (2 * jj < nq) {
-                if (t == 0) xw[g * xs + cb[jj]] = v0[jj];
-                if (t == 1) xw[(g + 8) * xs + cb[jj]] = v1[jj];
+            for (int k = 0; k < 4; ++k) {
+                const float4 q4 = src[k];
+                L[4 * k] = q4.x;
+                L[4 * k + 1] = q4.y;
+                L[4 * k + 2] = q4.z;
+                L[4 * k + 3] = q4.w;
             }
+            const int cb = pm[A + j0 + jj];
+            float vv = xw[r * xs + cb];
+            lqp += cdf_row<kSample>(L, vv);
+            xw[r * xs + cb] = vv;
         }
         __syncwarp();
     }
@@ -342,7 +307,8 @@ __global__ void __launch_bounds__(kThreads) flow_infer_kernel(FlowView f, SceneV
     uint32_t* rows = reinterpret_cast<uint32_t*>(smem + kOffRows);
     float* xt = reinterpret_cast<float*>(smem + round128(kOffX));
     const int D = (int)f.D, A = (int)f.A, AK = (int)f.AK, xs = D + 1;
-    unsigned char* wbuf0 = smem + round128(kOffX) + x_bytes(f.D);
+    float* lgt = reinterpret_cast<float*>(smem + round128(kOffX) + x_bytes(f.D));
+    unsigned char* wbuf0 = smem + round128(kOffX) + x_bytes(f.D) + round128(kLgBytes);
     const size_t bb = buf_bytes(f.AK);
     const uint32_t lbytes = (uint32_t)flow_ws_layer_bytes(f.AK);
 
@@ -369,8 +335,9 @@ __global__ void __launch_bounds__(kThreads) flow_infer_kernel(FlowView f, SceneV
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* xw = xt + warp * 16 * xs;
+    float* lg = lgt + warp * 16 * kLgStride;
     auto row_buf = [&](uint32_t i) -> float* { return (par && !par[i]) ? bufB : bufA; };
-    float lq0 = 0.f, lq1 = 0.f;
+    float lqp = 0.f;  // this lane's part of log q of row lane & 15
     bool failed = false;
 
     uint32_t st = 0;
@@ -387,14 +354,14 @@ __global__ void __launch_bounds__(kThreads) flow_infer_kernel(FlowView f, SceneV
                 const uint32_t i = rows[warp * 16 + r];
                 xw[r * xs + d] = i != kNoRow ? row_buf(i)[(uint64_t)d * n + i] : 0.5f;
             }
-            lq0 = lq1 = 0.f;
+            lqp = 0.f;
             __syncwarp();
         }
         const int b = st & 1;
         failed = !mbar_wait(&bar[b], (st >> 1) & 1);
         if (!failed) {
             const int l = layer_of(st);
-            coupling<kSample>(wbuf0 + b * bb, perm_s + l * D, A, AK, xw, xs, lq0, lq1);
+            coupling<kSample>(wbuf0 + b * bb, perm_s + l * D, A, AK, xw, xs, lg, lqp);
         }
         if (__syncthreads_or(failed)) break;  // every warp is done with buffer b
         if (threadIdx.x == 0 && st + 2 < total) {
@@ -402,17 +369,16 @@ __global__ void __launch_bounds__(kThreads) flow_infer_kernel(FlowView f, SceneV
             bulk_load(wbuf0 + b * bb, f.ws + (size_t)layer_of(st + 2) * lbytes, lbytes, &bar[b]);
         }
         if (st % kFL == kFL - 1) {  // write the warp's rows
-            const int g = lane >> 2, t = lane & 3;
+            const float lq = lqp + __shfl_xor_sync(0xffffffffu, lqp, 16);  // row lane & 15
             if (kSample)
                 for (int e = lane; e < 16 * D; e += 32) {
                     const int r = e / D, d = e % D;
                     const uint32_t i = rows[warp * 16 + r];
                     if (i != kNoRow) row_buf(i)[(uint64_t)d * n + i] = xw[r * xs + d];
                 }
-            if (t < 2) {
-                const int r = g + 8 * t;
+            if (lane < 16) {
+                const int r = lane;
                 const uint32_t i = rows[warp * 16 + r];
-                const float lq = t == 0 ? lq0 : lq1;
                 if (i != kNoRow) {
                     if (u_out) u_out[i] = f.beta * __expf(lq) + (1.0f - f.beta);
                     if (lq_out) lq_out[i] = lq;

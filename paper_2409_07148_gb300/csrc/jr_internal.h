@@ -90,8 +90,7 @@ struct WaveView {
     uint8_t* par = nullptr;       // [n] 1: the current state is in y, 0: in x
     float* ua = nullptr;          // [n] Ua of a local step, -1 for a regeneration step
     float4* path = nullptr;       // [n][3] live path record (o, d, T, F)
-    float2* hit = nullptr;        // [n] closest hit of the path's current ray (t, record index bits)
-    uint32_t* queue = nullptr;    // [2][n] live-path queues (ping-pong)
+    uint32_t* queue = nullptr;    // [n] the step's path queue
     unsigned int* qcount = nullptr;  // [kQCount]: queue lengths, fetch cursors, flow queue lengths
     float* uy = nullptr;          // [n] u of the step's candidate (with a flow)
     uint32_t* fq = nullptr;       // [2][n] candidates for the flow: density rows, then sampling rows
@@ -161,7 +160,7 @@ cudaError_t launch_batch(BatchEntry* entries, const BatchItem* items, uint32_t n
 // event is recorded after every launch, and the time since the previous event
 // is charged to that launch's class.
 struct KernelTimer {
-    enum Kind { kStep = 0, kTrace = 1, kShade = 2, kFlow = 3, kKinds = 4 };
+    enum Kind { kStep = 0, kPath = 1, kReserved = 2, kFlow = 3, kKinds = 4 };
     std::vector<cudaEvent_t> ev;
     std::vector<int> kind;  // class of the launch that ends at ev[i] (-1: the start mark)
     cudaError_t mark(int k, cudaStream_t st);
@@ -180,8 +179,8 @@ cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t st
 constexpr uint64_t kStaticMaxChains = 1u << 16;
 constexpr size_t kStaticScratchBytes =
     sizeof(float) * kMaxDim * kStaticMaxChains + sizeof(float4) * 3 * kStaticMaxChains +
-    sizeof(float2) * kStaticMaxChains + sizeof(float) * kStaticMaxChains + sizeof(uint32_t) * 2 * kStaticMaxChains +
-    sizeof(uint8_t) * kStaticMaxChains + 256;  // = 12 910 848 bytes (every piece but the counters is a multiple of 256)
+    sizeof(float) * kStaticMaxChains + sizeof(uint32_t) * kStaticMaxChains + sizeof(uint8_t) * kStaticMaxChains +
+    256;  // = 12 124 416 bytes (every piece but the counters is a multiple of 256)
 cudaError_t launch_wavefront_static(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
                                     cudaStream_t st);
 

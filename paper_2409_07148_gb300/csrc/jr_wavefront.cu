@@ -2,19 +2,17 @@
 //
 // The megakernel (jr_kernels.cu) keeps one chain per thread for a whole
 // launch; its warps idle while their longest path and their longest ray finish.
-// Here a step of Alg. 2 (Section 7.2) is split at the ray boundaries:
+// Here a step of Alg. 2 (Section 7.2) is split in two launches:
 //
 //   step kernel (all chains, converged): finish the previous step (MH
 //     acceptance or regeneration), draw the new step's clocks t1 ~ Exp(1),
 //     t2 ~ Exp(k), k = c~ u / p (Section 6.2), splat (dt, x) (Sections 6.3/7.4),
 //     build the candidate y (Gaussian small step or a draw from mu) and its
-//     camera ray; every chain joins the ray queue.
-//   trace kernel, per bounce (persistent warps): closest hit of every queued
-//     ray.  Lanes whose ray is done refill from the queue between warp-
-//     synchronous traversal rounds (dynamic ray fetch, Aila & Laine 2009), so
-//     a warp does not idle for its longest ray.
-//   shade kernel, per bounce (converged): emission, BSDF sample, next ray;
-//     survivors join the next queue with one warp-aggregated atomic.
+//     camera ray; every chain joins the path queue.
+//   path kernel (persistent warps): the whole path of every queued candidate,
+//     vertex after vertex, in registers: warp-synchronous BVH traversal, batched
+//     shading, and dynamic fetch of new paths into idle lanes, so that a warp
+//     idles neither for its longest ray nor for its longest path.
 //
 // Per-chain arithmetic is the megakernel's, through the same device functions,
 // so both modes give the same chains for the same Philox streams.  The state
@@ -33,10 +31,9 @@ namespace jr {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kRefill = 8;  // refill a warp once this many lanes are idle
-constexpr bool kPathKernel = true;  // whole paths per launch (else a trace and a shade launch per vertex)
+constexpr int kRefill = 4;  // refill a warp once this many lanes are idle
 
-// Path record of a live path: (o.xyz, d.x) (d.yz, T.xy) (T.z, F.xyz).
+// Path record: (o.xyz, d.x) (d.yz, T.xy) (T.z, F.xyz).
 __device__ __forceinline__ void store_path(float4* path, uint64_t i, float3 o, float3 d, float3 T, float3 F) {
     path[3 * i] = make_float4(o.x, o.y, o.z, d.x);
     path[3 * i + 1] = make_float4(d.y, d.z, T.x, T.y);
@@ -237,145 +234,21 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
     count_and_flush(nJ, nL, nA, status, c);
 }
 
-// Closest hit of every queued ray of bounce v -> w.hit[chain] = (t, record).
-// Persistent warps; each lane keeps its own resumable traversal and idle lanes
-// refill from the queue between warp-synchronous traversal rounds.
-__global__ void __launch_bounds__(128) wf_trace_kernel(SceneView s, ChainView c, int v) {
-    const WaveView& w = c.wf;
-    const uint32_t* qin = w.queue + (uint64_t)(v & 1) * c.n;
-    const unsigned count = w.qcount[v];
-    // Blocks past the queue's length have nothing to take that the blocks
-    // before them will not take (they keep fetching until the queue is empty),
-    // so a short queue costs no atomics on the cursor from the rest of the grid.
-    if ((uint64_t)blockIdx.x * blockDim.x >= count) return;
-    unsigned int* fetch = w.qcount + (kMaxDepth + 2) + v;
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    unsigned status = 0;
-    Work wk;
-    Trav r;
-    int stack[kStackSize];
-    bool has = false, failed = false;
-    int leaf = kSentinel;  // postponed leaf of this lane's ray, or none
-    uint32_t i = 0;
-    bool drained = false;  // warp-uniform: the queue has no entries left
-    while (true) {
-        const unsigned idle = __ballot_sync(kFull, !has);
-        if (!drained && (__popc(idle) >= kRefill || idle == kFull)) {
-            unsigned base = 0;
-            if (lane == 0) base = atomicAdd(fetch, (unsigned)__popc(idle));
-            base = __shfl_sync(kFull, base, 0);
-            if (base + (unsigned)__popc(idle) >= count) drained = true;
-            if (!has) {
-                const unsigned j = base + __popc(idle & lt);
-                if (j < count) {
-                    i = qin[j];
-                    const float4 a = w.path[3 * (uint64_t)i], b = w.path[3 * (uint64_t)i + 1];
-                    trav_begin(s, r, f3(a.x, a.y, a.z), f3(a.w, b.x, b.y));
-                    has = s.root != kSentinel;
-                    if (!has) w.hit[i] = make_float2(INFINITY, __int_as_float(-1));
-                }
-            }
-        }
-        if (!__any_sync(kFull, has)) {
-            if (drained) break;
-            continue;
-        }
-        // One speculative while-while round (Aila & Laine 2009): a lane that
-        // meets a leaf postpones it and keeps descending inner nodes until
-        // every lane holds a leaf; then the postponed leaves are tested together.
-        if (has && leaf == kSentinel && r.ref < 0 && r.ref != kSentinel) {
-            leaf = r.ref;
-            r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
-        }
-        while (__any_sync(kFull, has && leaf == kSentinel && r.ref >= 0)) {
-            if (has && r.ref >= 0) {
-                if (!trav_node<false>(s, r, stack, status, wk)) {
-                    r.best = -1;
-                    r.ref = kSentinel;
-                    leaf = kSentinel;
-                    failed = true;
-                } else if (leaf == kSentinel && r.ref < 0 && r.ref != kSentinel) {
-                    leaf = r.ref;
-                    r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
-                }
-            }
-        }
-        if (has) {
-            if (leaf != kSentinel) {
-                trav_test_leaf<false>(s, r, leaf, wk);
-                leaf = kSentinel;
-            }
-            if (failed || r.ref == kSentinel) {
-                w.hit[i] = make_float2(r.best >= 0 ? r.tb : INFINITY, __int_as_float(r.best));
-                has = false;
-                failed = false;
-            }
-        }
-    }
-    status = __reduce_or_sync(kFull, status);
-    if (lane == 0 && status) atomicOr(c.status, status);
-}
-
-// Shade every queued ray of bounce v; survivors to the next queue.  With a
-// flow, a finished path whose candidate will become a state with p > 0 and
-// still lacks u(y) joins the density queue (the finish of the next step
-// kernel takes the same decision from the same values).
-__global__ void __launch_bounds__(128) wf_shade_kernel(SceneView s, ChainView c, int v) {
-    const WaveView& w = c.wf;
-    const uint32_t* qin = w.queue + (uint64_t)(v & 1) * c.n;
-    uint32_t* qout = w.queue + (uint64_t)((v + 1) & 1) * c.n;
-    const unsigned count = w.qcount[v];
-    const uint64_t n = c.n;
-    const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const unsigned warps = (gridDim.x * blockDim.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    for (unsigned j0 = warp * 32u; j0 < count; j0 += warps * 32u) {
-        const unsigned j = j0 + lane;
-        bool live = false, need_u = false;
-        uint32_t i = 0;
-        if (j < count) {
-            i = qin[j];
-            const float2 h = w.hit[i];
-            float3 o, d, T, F;
-            load_path(w.path, i, o, d, T, F);
-            const int k = __float_as_int(h.y);
-            if (k >= 0) {
-                float u1 = 0.f, u2 = 0.f;
-                if (v < (int)c.depth) {
-                    const float* cand = w.par[i] ? c.x : w.y;
-                    u1 = cand[(uint64_t)(2 + 2 * v) * n + i];
-                    u2 = cand[(uint64_t)(3 + 2 * v) * n + i];
-                }
-                live = shade_vertex(s, k, h.x, v, (int)c.depth, u1, u2, o, d, T, F);
-            }
-            if (live) {
-                store_path(w.path, i, o, d, T, F);
-            } else {
-                w.path[3 * (uint64_t)i + 2] = make_float4(0.f, F.x, F.y, F.z);
-                if (c.flow.D != 0) {
-                    unsigned ignored = 0;
-                    const float py = lum(finite_or_zero(F, ignored));
-                    const float ua = w.ua[i];
-                    need_u = ua >= 0.0f ? ua * c.fpu[3 * n + i] < py : (ua == -1.0f && py > 0.0f);
-                }
-            }
-        }
-        enqueue(live, i, qout, w.qcount + v + 1);
-        if (c.flow.D != 0) enqueue(need_u, i, w.fq, w.qcount + kQFlowDensity);
-    }
-}
-
 // Whole paths of every queued chain in one persistent launch.  A lane keeps
 // its path (ray, throughput T, emission F, vertex v) in registers and moves
 // between three states: traversing its current ray; waiting to shade (its
 // closest hit is known); idle (no path).  Traversal rounds are warp-
-// synchronous, as in the trace kernel.  A warp shades its waiting lanes
+// synchronous while-while rounds with speculative traversal (Aila & Laine
+// 2009): a lane that meets a leaf postpones it and keeps descending inner
+// nodes until every lane holds a leaf.  A warp shades its waiting lanes
 // together once kShadeBatch of them wait (or none is traversing); a shaded
 // path either continues with its next ray or ends (F goes to the path record,
-// and, with a flow, the row joins the density queue under the same rule as in
-// the shade kernel).  Idle lanes take new paths from the queue.
-constexpr int kShadeBatch = 8;
+// and, with a flow, the row joins the density queue: when its candidate will
+// become a state with p > 0 and still lacks u(y); the finish of the next step
+// kernel takes the same decision from the same values).  Idle lanes take new
+// paths from the queue (dynamic fetch, so a warp does not idle for its
+// longest path).
+constexpr int kShadeBatch = 16;
 enum PathState : uint32_t { kIdle = 0, kTraverse = 1, kWaitShade = 2 };
 
 __global__ void __launch_bounds__(128) wf_path_kernel(SceneView s, ChainView c) {
@@ -456,7 +329,7 @@ __global__ void __launch_bounds__(128) wf_path_kernel(SceneView s, ChainView c) 
             if (drained) break;
             continue;
         }
-        // one speculative while-while traversal round (see the trace kernel)
+        // one speculative while-while traversal round
         const bool trav = state == kTraverse;
         if (trav && leaf == kSentinel && r.ref < 0 && r.ref != kSentinel) {
             leaf = r.ref;
@@ -539,22 +412,15 @@ KernelTimer::~KernelTimer() {
 
 cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
                              cudaStream_t st, int mode, KernelTimer* tm) {
-    static int trace_blocks = 0, shade_blocks = 0, path_blocks = 0;
-    if (trace_blocks == 0) {
-        int dev = 0, sms = 0, per_sm = 0, per_sm2 = 0;
+    static int path_blocks = 0;
+    if (path_blocks == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
         cudaError_t e;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wf_trace_kernel, 128, 0)) != cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wf_path_kernel, 128, 0)) != cudaSuccess)
             return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, wf_shade_kernel, 128, 0)) != cudaSuccess)
-            return e;
-        trace_blocks = sms * (per_sm > 0 ? per_sm : 1);
-        shade_blocks = sms * (per_sm2 > 0 ? per_sm2 : 1);
-        int per_sm3 = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3, wf_path_kernel, 128, 0)) != cudaSuccess)
-            return e;
-        path_blocks = sms * (per_sm3 > 0 ? per_sm3 : 1);
+        path_blocks = sms * (per_sm > 0 ? per_sm : 1);
     }
     const unsigned G = grid_for(c.n, 128);
     const bool has_flow = c.flow.D != 0;
@@ -569,17 +435,8 @@ cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t st
         mark(KernelTimer::kStep);
         if (has_flow && (e = launch_flow_draws(s, c, st)) != cudaSuccess) return e;
         if (has_flow) mark(KernelTimer::kFlow);
-        if (kPathKernel) {
-            wf_path_kernel<<<path_blocks, 128, 0, st>>>(s, c);
-            mark(KernelTimer::kTrace);
-        } else {
-            for (int v = 0; v <= (int)c.depth; ++v) {
-                wf_trace_kernel<<<trace_blocks, 128, 0, st>>>(s, c, v);
-                mark(KernelTimer::kTrace);
-                wf_shade_kernel<<<shade_blocks, 128, 0, st>>>(s, c, v);
-                mark(KernelTimer::kShade);
-            }
-        }
+        wf_path_kernel<<<path_blocks, 128, 0, st>>>(s, c);
+        mark(KernelTimer::kPath);
         if (has_flow && (e = launch_flow_densities(s, c, st)) != cudaSuccess) return e;
         if (has_flow) mark(KernelTimer::kFlow);
     }
@@ -595,18 +452,17 @@ cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t st
 // kStaticMaxChains chains live in one file-scope device array instead of
 // memory allocated per chain set.  Every GPU that loads the library holds it
 // until the process exits.  Layout (256-byte aligned pieces): y [kMaxDim][n],
-// path [n][3] float4, hit [n] float2, ua [n], queue [2][n], par [n],
-// qcount [2 (kMaxDepth+2)].
+// path [n][3] float4, ua [n], queue [n], par [n], qcount (256 bytes).
 namespace {
 constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kOffY = 0;
 constexpr size_t kOffPath = kOffY + align256(sizeof(float) * kMaxDim * kStaticMaxChains);
-constexpr size_t kOffHit = kOffPath + align256(sizeof(float4) * 3 * kStaticMaxChains);
-constexpr size_t kOffUa = kOffHit + align256(sizeof(float2) * kStaticMaxChains);
+constexpr size_t kOffUa = kOffPath + align256(sizeof(float4) * 3 * kStaticMaxChains);
 constexpr size_t kOffQueue = kOffUa + align256(sizeof(float) * kStaticMaxChains);
-constexpr size_t kOffPar = kOffQueue + align256(sizeof(uint32_t) * 2 * kStaticMaxChains);
+constexpr size_t kOffPar = kOffQueue + align256(sizeof(uint32_t) * kStaticMaxChains);
 constexpr size_t kOffCount = kOffPar + align256(sizeof(uint8_t) * kStaticMaxChains);
-constexpr size_t kStaticBytes = kOffCount + align256(sizeof(unsigned int) * 2 * (kMaxDepth + 2));
+constexpr size_t kStaticBytes = kOffCount + align256(sizeof(unsigned int) * kQCount);
+static_assert(sizeof(unsigned int) * kQCount <= 256, "the static counters fit their 256 bytes");
 static_assert(kStaticBytes == kStaticScratchBytes, "static scratch layout and its declared size disagree");
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
@@ -644,7 +500,6 @@ cudaError_t launch_wavefront_static(const SceneView& s, const ChainView& c, uint
     ChainView v = c;
     v.wf.y = reinterpret_cast<float*>(b + kOffY);
     v.wf.path = reinterpret_cast<float4*>(b + kOffPath);
-    v.wf.hit = reinterpret_cast<float2*>(b + kOffHit);
     v.wf.ua = reinterpret_cast<float*>(b + kOffUa);
     v.wf.queue = reinterpret_cast<uint32_t*>(b + kOffQueue);
     v.wf.par = b + kOffPar;

@@ -217,11 +217,11 @@ class Chains:
         _check(lib().jr_advance_static(self.h, int(n_steps), _stream(stream)))
 
     def advance_timed(self, n_steps, stream=None):
-        """Advance with device time per kernel class (step, trace, shade, flow)."""
+        """Advance with device time per kernel class (step, path, reserved, flow)."""
         ms = (ctypes.c_double * 4)()
         nl = (ctypes.c_uint64 * 4)()
         _check(lib().jr_advance_timed(self.h, int(n_steps), ms, nl, _stream(stream)))
-        names = ("step", "trace", "shade", "flow")
+        names = ("step", "path", "reserved", "flow")
         return {k: {"ms": ms[i], "launches": int(nl[i])} for i, k in enumerate(names)}
 
     def advance_counted(self, n_steps, stream=None):
