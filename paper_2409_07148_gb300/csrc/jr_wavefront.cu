@@ -82,12 +82,12 @@ __device__ __forceinline__ void count_and_flush(uint32_t nJ, uint32_t nL, uint32
 // then the restart epoch and the stream tag is kTagRestart.
 // With a flow attached (c.flow.D > 0), a regeneration draws from the flow when
 // Ub < beta (Ub = fourth value of block 0), else uniformly.  Flow draws go to
-// the sampling queue, whose kernel fills in y and u(y) before the bounces
+// the sampling queue, whose kernel fills in y and u(y) before the path kernel
 // (ua = -3 marks them).  u(y) of the other candidates is needed only where the
 // candidate becomes a state with p > 0 (k = c~ u / p is +inf at p = 0 whatever
-// u is; a rejected local candidate never becomes a state), so the shade kernel
-// queues exactly those rows for the density pass after the last bounce; a state
-// with p = 0 keeps u = 1 as a placeholder.
+// u is; a rejected local candidate never becomes a state), so the path kernel
+// queues exactly those rows for the density pass after it; a state with p = 0
+// keeps u = 1 as a placeholder.
 // mode = kModeDrain: a kill ends the chain's tour (counted in J) and the chain
 // (done = 1); done chains do nothing; no regeneration starts a new tour.
 // Chains still in a tour after the step are counted in qcount[kQActive].
@@ -366,8 +366,8 @@ __global__ void __launch_bounds__(128) wf_path_kernel(SceneView s, ChainView c) 
 inline unsigned grid_for(uint64_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 
 // The flow stages of a step (a chain's candidate lives in x when its parity
-// byte is 1, else in y).  Before the bounces: y = T^{-1}(z), u(y) and the
-// camera ray of the flow draws.  After them: u(y) of the rows the shade kernel
+// byte is 1, else in y).  Before the path kernel: y = T^{-1}(z), u(y) and the
+// camera ray of the flow draws.  After it: u(y) of the rows the path kernel
 // queued.
 cudaError_t launch_flow_draws(const SceneView& s, const ChainView& c, cudaStream_t st) {
     return launch_flow(c.flow, true, &s, c.x, c.wf.y, c.wf.par, c.n, c.wf.fq + c.n, c.wf.qcount + kQFlowSample, 0,
