@@ -447,10 +447,12 @@ def main():
     dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
     C, K = wl["chains"], wl["chain_steps"]
+    from paper_2409_07148_gb300.shard import chain_range
+    first, _ = chain_range(rank, ws, C * ws)   # weak scaling: C chains per rank, disjoint id ranges
     with torch.cuda.stream(stream):
         scene = jr.Scene(sc, stream=stream)
         info = scene.info()
-        ch = jr.Chains(scene, sc.width, sc.height, sc.depth, C, seed=0, chain_offset=rank * C, stream=stream)
+        ch = jr.Chains(scene, sc.width, sc.height, sc.depth, C, seed=0, chain_offset=first, stream=stream)
         if args.block:
             ch.set_block_size(args.block)
         ch.set_execution(args.exec)
@@ -484,13 +486,13 @@ def main():
         steps_done = ws * C * K * args.steps
         value = steps_done / total
         # algorithmic work of one launch (instrumented variant on a fresh, identical chain set)
-        wc = jr.Chains(scene, sc.width, sc.height, sc.depth, C, seed=0, chain_offset=rank * C, stream=stream)
+        wc = jr.Chains(scene, sc.width, sc.height, sc.depth, C, seed=0, chain_offset=first, stream=stream)
         for _ in range(args.warmup):
             wc.advance(K, stream=stream)
         work = wc.advance_counted(K, stream=stream)
         del wc
         # device time per kernel class for the same K steps of an identical chain set
-        wt = jr.Chains(scene, sc.width, sc.height, sc.depth, C, seed=0, chain_offset=rank * C, stream=stream)
+        wt = jr.Chains(scene, sc.width, sc.height, sc.depth, C, seed=0, chain_offset=first, stream=stream)
         wt.set_execution(args.exec)
         for _ in range(args.warmup):
             wt.advance(K, stream=stream)
@@ -515,7 +517,7 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             s2 = jr.Scene(sc, stream=stream)
-            c2 = jr.Chains(s2, sc.width, sc.height, sc.depth, C, seed=1, chain_offset=rank * C, stream=stream)
+            c2 = jr.Chains(s2, sc.width, sc.height, sc.depth, C, seed=1, chain_offset=first, stream=stream)
             c2.advance(K, stream=stream)
             img = c2.resolve(stream=stream)
             e2e_times.append(time.perf_counter() - t0)
