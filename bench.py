@@ -227,8 +227,9 @@ def relmse(img, ref, eps=1e-2):
 
 
 def run_caustic(args):
-    """Time to relMSE 1e-2 on the slit-caustic scene, learned vs plain
-    regeneration.  Reference: plain path tracing on the GPU (its own noise is
+    """Time to relMSE 1e-2, learned vs plain regeneration, on the slit-caustic
+    scene (1024^2, depth 10, 2^20 chains) or, with --workload terrain, on the
+    fBm terrain lit by 256 small emitters (2048^2, depth 12, 2^22 chains).  Reference: plain path tracing on the GPU (its own noise is
     estimated from two independent halves and reported).  Each arm runs epochs
     of `epoch` chain steps; after every epoch the open tours are completed (so
     the checkpoint image is the completed-tour estimator) and the relMSE is
@@ -238,16 +239,22 @@ def run_caustic(args):
     import torch
     from paper_2409_07148_gb300 import jr, scenes
     from paper_2409_07148_gb300.flowinit import init_flow_params
-    side = args.side
-    sc = scenes.caustic_slit(width=side, height=side, depth=10)
+    if args.workload == "terrain":
+        side = args.side or 2048
+        sc = scenes.terrain(width=side, height=side, depth=12)
+        C = args.chains or (1 << 22)
+    else:
+        side = args.side or 1024
+        sc = scenes.caustic_slit(width=side, height=side, depth=10)
+        C = args.chains or (1 << 20)
+    wname = f"{sc.name}_{side}x{side}_depth{sc.depth}"
     stream = torch.cuda.Stream()
     target, tmax, epoch = 1e-2, args.time_limit, args.epoch
-    C = args.chains or (1 << 20)
     with torch.cuda.stream(stream):
         g = jr.Scene(sc, stream=stream)
         # reference: two independent halves of plain path tracing (optionally
         # kept in a file, keyed by the scene size and the sample count)
-        cache = args.ref_file and f"{args.ref_file}.{side}.{args.ref_samples}.npz"
+        cache = args.ref_file and f"{args.ref_file}.{sc.name}.{side}.{args.ref_samples}.npz"
         t0 = time.perf_counter()
         if cache and os.path.exists(cache):
             z = np.load(cache)
@@ -356,7 +363,7 @@ def run_caustic(args):
 
         plain = run(False) if "plain" in args.arms else None
         learned = run(True) if "learned" in args.arms else {}
-    line = {"metric": METRIC, "workload": f"caustic_slit_{side}x{side}_depth10", "unit": "s to relMSE 1e-2",
+    line = {"metric": METRIC, "workload": wname, "unit": "s to relMSE 1e-2",
             "relmse_eps": 1e-2, "target": target, "time_limit_s": tmax, "chains": C, "epoch_steps": epoch,
             "epoch_growth": args.epoch_growth, "epoch_max": args.epoch_max,
             "reference": {"samples": args.ref_samples, "seconds": round(t_ref, 2), "noise_relmse_est": ref_noise},
@@ -403,28 +410,28 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--chains", type=int, default=0, help="override the chain count (profiling small cases only)")
     ap.add_argument("--chain-steps", type=int, default=0, help="override chain steps per launch (profiling only)")
-    ap.add_argument("--side", type=int, default=1024, help="caustic workload: image side")
+    ap.add_argument("--side", type=int, default=None, help="caustic/terrain workload: image side")
     ap.add_argument("--time-limit", type=float, default=60.0, help="caustic workload: seconds per arm")
     ap.add_argument("--epoch", type=int, default=128, help="caustic workload: chain steps of the first epoch")
     ap.add_argument("--epoch-growth", type=float, default=1.25, help="caustic workload: epoch length factor")
     ap.add_argument("--epoch-max", type=int, default=1024, help="caustic workload: longest epoch (steps)")
     ap.add_argument("--ref-samples", type=int, default=1 << 34, help="caustic workload: reference PT samples")
-    ap.add_argument("--train-iters", type=int, default=50, help="caustic workload: Adam steps per epoch")
-    ap.add_argument("--train-iters0", type=int, default=400, help="caustic workload: Adam steps in the first epochs")
-    ap.add_argument("--warm-epochs", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=16384, help="caustic workload: training minibatch rows")
+    ap.add_argument("--train-iters", type=int, default=25, help="caustic workload: Adam steps per epoch")
+    ap.add_argument("--train-iters0", type=int, default=150, help="caustic workload: Adam steps in the first epochs")
+    ap.add_argument("--warm-epochs", type=int, default=2)
+    ap.add_argument("--batch", type=int, default=8192, help="caustic workload: training minibatch rows")
     ap.add_argument("--snap-every", type=int, default=16, help="caustic workload: steps between training snapshots")
     ap.add_argument("--replay", type=int, default=1 << 20, help="caustic workload: replay ring rows")
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--ref-file", default=None, help="caustic workload: cache the reference image in this file")
     ap.add_argument("--arms", default="plain,learned", help="caustic workload: arms to run")
     ap.add_argument("--split-epoch", type=int, default=-1, help="caustic workload: time 16 extra steps per kernel class after this epoch (diagnostic)")
-    ap.add_argument("--beta", type=float, default=0.5)
+    ap.add_argument("--beta", type=float, default=0.3)
     args = ap.parse_args()
     if args.workload == "batched64" and args.impl == "ours":
         run_batched(args)
         return
-    if args.workload == "caustic" and args.impl == "ours":
+    if args.workload in ("caustic", "terrain") and args.impl == "ours":
         run_caustic(args)
         return
     sc, wl = workload(args.workload)

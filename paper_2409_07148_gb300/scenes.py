@@ -341,6 +341,58 @@ def caustic_slit(width=1024, height=1024, depth=10, n_lon=200, n_lat=201, slit=0
     return b.build("caustic_slit", cam, width, height, depth)
 
 
+def fbm_value_noise(x, z, seed, octaves=6, base=4.0, gain=0.5):
+    """Fractal sum of seeded value noise on [0,1]^2: octave o samples a lattice
+    of uniform values (spacing 1 / (base 2^o)) with smoothstep-weighted
+    bilinear interpolation; weights gain^o, normalised to [0, 1]."""
+    rng = np.random.default_rng(seed)
+    x, z = np.asarray(x, np.float64), np.asarray(z, np.float64)
+    h = np.zeros(np.broadcast(x, z).shape)
+    amp, freq, norm = 1.0, float(base), 0.0
+    for _ in range(octaves):
+        n = int(np.ceil(freq)) + 2
+        lat = rng.random((n, n))
+        gx, gz = x * freq, z * freq
+        i, j = np.floor(gz).astype(np.int64), np.floor(gx).astype(np.int64)
+        fz, fx = gz - i, gx - j
+        sz, sx = fz * fz * (3 - 2 * fz), fx * fx * (3 - 2 * fx)
+        a = lat[i, j] + (lat[i, j + 1] - lat[i, j]) * sx
+        b = lat[i + 1, j] + (lat[i + 1, j + 1] - lat[i + 1, j]) * sx
+        h += amp * (a + (b - a) * sz)
+        norm += amp
+        amp *= gain
+        freq *= 2.0
+    return h / norm
+
+
+def terrain(width=2048, height=2048, depth=12, n_grid=1000, n_lights=256, seed=5, relief=0.25) -> SceneArrays:
+    """A grid terrain of n_grid^2 vertices over [0,1]^2 (2 (n_grid - 1)^2
+    triangles, about 2M by default) displaced by seeded fBm value noise, lit
+    only by n_lights small quad emitters (0.012 wide, facing down, 0.03 above
+    the ground) with L_e log-uniform in [1, 100]; open sky."""
+    b = _Builder()
+    ground = b.add_material(material(LAMBERT, (0.6, 0.6, 0.6)))
+    g = np.linspace(0.0, 1.0, n_grid)
+    X, Z = np.meshgrid(g, g)                       # X along columns (j), Z along rows (i)
+    Y = relief * fbm_value_noise(X, Z, seed)
+    verts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    i, j = np.meshgrid(np.arange(n_grid - 1), np.arange(n_grid - 1), indexing="ij")
+    a = (i * n_grid + j).ravel()
+    bb, c, d = a + 1, a + n_grid, a + n_grid + 1
+    tris = np.concatenate([np.stack([a, c, bb], 1), np.stack([bb, c, d], 1)])   # normals point up
+    b.mesh(verts, tris, ground)
+    rng = np.random.default_rng(seed + 1)
+    lx, lz = rng.uniform(0.05, 0.95, n_lights), rng.uniform(0.05, 0.95, n_lights)
+    ly = relief * fbm_value_noise(lx, lz, seed) + 0.03
+    le = np.exp(rng.uniform(np.log(1.0), np.log(100.0), n_lights))
+    for k in range(n_lights):
+        m = b.add_material(material(LAMBERT, (0.0, 0.0, 0.0), emission=(le[k], le[k], le[k])))
+        b.quad((lx[k], ly[k], lz[k]), (0.012, 0, 0), (0, 0, 0.012), (0, -1, 0), m)
+    cam = pinhole((0.5, 0.75, -0.35), (0.5, 0.05, 0.55), (0, 1, 0), 0.6, width / height)
+    return b.build("terrain", cam, width, height, depth)
+
+
 def by_name(name: str, **kw) -> SceneArrays:
     return {"cornell": cornell, "cornell_spheres": cornell_spheres, "furnace": furnace, "empty": empty,
-            "glass_furnace": glass_furnace, "random_boxes": random_boxes, "caustic_slit": caustic_slit}[name](**kw)
+            "glass_furnace": glass_furnace, "random_boxes": random_boxes, "caustic_slit": caustic_slit,
+            "terrain": terrain}[name](**kw)
