@@ -1024,8 +1024,8 @@ jr_status drain_impl(jr_chains* c, uint32_t max_steps, uint64_t* remaining, cuda
     uint32_t group = 1;
     while (active > 0 && k < max_steps) {
         const uint32_t g = std::min(group, max_steps - k);
-        for (uint32_t j = 0; j < g; ++j)
-            JR_CUDA(launch_wavefront(c->scene->view, c->view, s0 + k + j, 1, st, kModeDrain), who);
+        // one launch sequence per group: a single closing finish launch, not one per step
+        JR_CUDA(launch_wavefront(c->scene->view, c->view, s0 + k, g, st, kModeDrain), who);
         k += g;
         JR_CUDA(cudaMemcpyAsync(&active, c->view.wf.qcount + kQActive, sizeof(active), cudaMemcpyDeviceToHost, st),
                 who);
