@@ -390,8 +390,9 @@ def run_reference(args, sc, wl):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "image": [sc.width, sc.height], "depth": sc.depth,
-                       "n_tris": sc.n_tris, "chains": wl["chains"], "chain_steps_per_step": wl["chain_steps"]},
+            "config": {"workload": f"{args.workload}_{sc.width}x{sc.height}_depth{sc.depth}",
+                       "image": [sc.width, sc.height], "depth": sc.depth, "n_tris": sc.n_tris,
+                       "chains": wl["chains"], "chain_steps_per_step": wl["chain_steps"]},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
