@@ -622,13 +622,14 @@ cudaError_t launch_snapshot_append(const ChainView& c, float* x_ring, float* w_r
 
 cudaError_t launch_flow_train_step(const FlowView& f, const float* x, const float* w, uint64_t n, uint64_t off,
                                    uint32_t batch, float* grad, float* wsum, float* loss, cudaStream_t st) {
-    static bool attr = false;
+    static DeviceOnce once;  // per device: the opt-in to the training kernel's shared memory
     const size_t shm = sizeof(TrainSmem);
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(flow_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e0 = once.get(
+        [&](int, long long*) {
+            return cudaFuncSetAttribute(flow_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        },
+        nullptr);
+    if (e0 != cudaSuccess) return e0;
     wsum_kernel<<<std::min<uint32_t>(64, (batch + 255) / 256), 256, 0, st>>>(w, off, batch, wsum);
     flow_train_kernel<<<(batch + kRows - 1) / kRows, 128, shm, st>>>(f, x, w, n, off, batch, wsum, grad, loss);
     return cudaGetLastError();

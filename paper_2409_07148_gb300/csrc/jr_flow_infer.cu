@@ -448,23 +448,25 @@ cudaError_t launch_flow(const FlowView& f, bool sample, const SceneView* s, floa
                         const uint8_t* par, uint64_t n, const uint32_t* idx, const unsigned int* count_dev,
                         uint32_t n_rows, float* u_out, float4* path, float* lq_out, unsigned int* status,
                         cudaStream_t st) {
-    static int sms = 0;
-    static size_t attr_bytes = 0;
+    static DeviceOnce once;  // per device: the SM count, after opting in to the largest layout
     const size_t shm = infer_smem(f.D, f.AK);
-    cudaError_t e;
-    if (sms == 0) {
-        int dev = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    }
-    if (shm > attr_bytes) {
-        if ((e = cudaFuncSetAttribute(flow_infer_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)shm)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(flow_infer_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)shm)) != cudaSuccess)
-            return e;
-        attr_bytes = shm;
-    }
+    long long sms = 0;
+    cudaError_t e = once.get(
+        [](int dev, long long* v) {
+            const int most = (int)infer_smem(kMaxDim, kFMaxAK);
+            int n = 0;
+            cudaError_t r;
+            if ((r = cudaFuncSetAttribute(flow_infer_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          most)) != cudaSuccess ||
+                (r = cudaFuncSetAttribute(flow_infer_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          most)) != cudaSuccess ||
+                (r = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+                return r;
+            *v = n;
+            return cudaSuccess;
+        },
+        &sms);
+    if (e != cudaSuccess) return e;
     int per = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, flow_infer_kernel<false>, kThreads, shm)) !=
         cudaSuccess)

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -131,6 +132,33 @@ struct BatchEntry {
 // One work item of the batched kernel: chains [begin, end) of set `set`.
 struct BatchItem {
     uint32_t set, begin, end;
+};
+
+// One-time launch set-up per device (an opt-in to large dynamic shared
+// memory, an occupancy-derived grid size), cached by device id: get() runs
+// init(device, &value) for the current device on first use, under a lock, and
+// returns the cached value afterwards; a failed init is retried on the next call.
+struct DeviceOnce {
+    static constexpr int kDevices = 64;
+    std::mutex mu;
+    bool done[kDevices] = {};
+    long long value[kDevices] = {};
+    template <class F>
+    cudaError_t get(F&& init, long long* out) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= kDevices) return cudaErrorInvalidDevice;
+        std::lock_guard<std::mutex> lk(mu);
+        if (!done[dev]) {
+            long long v = 0;
+            if ((e = init(dev, &v)) != cudaSuccess) return e;
+            value[dev] = v;
+            done[dev] = true;
+        }
+        if (out) *out = value[dev];
+        return cudaSuccess;
+    }
 };
 
 // Host-side BVH build result.

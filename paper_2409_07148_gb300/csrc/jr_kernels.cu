@@ -371,19 +371,22 @@ cudaError_t launch_step(const SceneView& s, const ChainView& c, uint64_t step_be
     const unsigned B = (unsigned)block;
     const size_t shm = sizeof(float) * 2 * c.dim * B;  // <= 2 * 32 * 256 * 4 = 64 KB
     const unsigned G = grid_for(c.n, B);
-    static bool attr_set = false;  // opt in to > 48 KB of dynamic shared memory once
-    if (!attr_set) {
-        const int lim = (int)(sizeof(float) * 2 * kMaxDim * 256);
-        cudaError_t e;
-        if ((e = cudaFuncSetAttribute(step_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) !=
-                cudaSuccess ||
-            (e = cudaFuncSetAttribute(step_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) !=
-                cudaSuccess ||
-            (e = cudaFuncSetAttribute(step_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) !=
-                cudaSuccess)
-            return e;
-        attr_set = true;
-    }
+    static DeviceOnce once;  // per device: opt in to > 48 KB of dynamic shared memory
+    cudaError_t e0 = once.get(
+        [](int, long long*) {
+            const int lim = (int)(sizeof(float) * 2 * kMaxDim * 256);
+            cudaError_t e;
+            if ((e = cudaFuncSetAttribute(step_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          lim)) != cudaSuccess ||
+                (e = cudaFuncSetAttribute(step_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          lim)) != cudaSuccess ||
+                (e = cudaFuncSetAttribute(step_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          lim)) != cudaSuccess)
+                return e;
+            return cudaSuccess;
+        },
+        nullptr);
+    if (e0 != cudaSuccess) return e0;
     if (work_out)
         step_kernel<false, true><<<G, B, shm, st>>>(s, c, step_begin, n_steps, nullptr, nullptr, nullptr, work_out);
     else if (tr_flags || tr_dt || tr_pix)
@@ -402,17 +405,22 @@ cudaError_t launch_fold(const ChainView& c, cudaStream_t st) {
 cudaError_t launch_batch(BatchEntry* entries, const BatchItem* items, uint32_t n_items, const uint64_t* px_off,
                          uint32_t n_sets, uint64_t total_px, unsigned int* cursor, uint32_t max_dim, int block,
                          uint32_t n_steps, cudaStream_t st) {
-    static int sms = 0;
-    cudaError_t e;
+    static DeviceOnce once;  // per device: the SM count, after the shared-memory opt-in
     const size_t shm = sizeof(float) * 2 * max_dim * (size_t)block;
-    if (sms == 0) {
-        int dev = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaFuncSetAttribute(batch_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(float) * 2 * kMaxDim * 256))) != cudaSuccess)
-            return e;
-    }
+    long long sms = 0;
+    cudaError_t e = once.get(
+        [](int dev, long long* v) {
+            int n = 0;
+            cudaError_t r;
+            if ((r = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+                (r = cudaFuncSetAttribute(batch_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(sizeof(float) * 2 * kMaxDim * 256))) != cudaSuccess)
+                return r;
+            *v = n;
+            return cudaSuccess;
+        },
+        &sms);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_step_kernel, block, shm)) != cudaSuccess)
         return e;

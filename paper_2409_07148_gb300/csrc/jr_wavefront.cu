@@ -412,15 +412,22 @@ KernelTimer::~KernelTimer() {
 
 cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
                              cudaStream_t st, int mode, KernelTimer* tm) {
-    static int path_blocks = 0;
-    if (path_blocks == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaError_t e;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wf_path_kernel, 128, 0)) != cudaSuccess)
-            return e;
-        path_blocks = sms * (per_sm > 0 ? per_sm : 1);
+    static DeviceOnce once;  // per device: the path kernel's persistent grid
+    long long path_blocks = 0;
+    {
+        cudaError_t e0 = once.get(
+            [](int dev, long long* v) {
+                int sms = 0, per_sm = 0;
+                cudaError_t r;
+                if ((r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+                    (r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wf_path_kernel, 128, 0)) !=
+                        cudaSuccess)
+                    return r;
+                *v = (long long)sms * (per_sm > 0 ? per_sm : 1);
+                return cudaSuccess;
+            },
+            &path_blocks);
+        if (e0 != cudaSuccess) return e0;
     }
     const unsigned G = grid_for(c.n, 128);
     const bool has_flow = c.flow.D != 0;
@@ -435,7 +442,7 @@ cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t st
         mark(KernelTimer::kStep);
         if (has_flow && (e = launch_flow_draws(s, c, st)) != cudaSuccess) return e;
         if (has_flow) mark(KernelTimer::kFlow);
-        wf_path_kernel<<<path_blocks, 128, 0, st>>>(s, c);
+        wf_path_kernel<<<(unsigned)path_blocks, 128, 0, st>>>(s, c);
         mark(KernelTimer::kPath);
         if (has_flow && (e = launch_flow_densities(s, c, st)) != cudaSuccess) return e;
         if (has_flow) mark(KernelTimer::kFlow);
