@@ -427,7 +427,7 @@ def main():
     ap.add_argument("--ref-file", default=None, help="caustic workload: cache the reference image in this file")
     ap.add_argument("--arms", default="plain,learned", help="caustic workload: arms to run")
     ap.add_argument("--split-epoch", type=int, default=-1, help="caustic workload: time 16 extra steps per kernel class after this epoch (diagnostic)")
-    ap.add_argument("--beta", type=float, default=0.3)
+    ap.add_argument("--beta", type=float, default=0.15)
     args = ap.parse_args()
     if args.workload == "batched64" and args.impl == "ours":
         run_batched(args)
