@@ -100,3 +100,22 @@ def test_train_rows_reads_only_the_filled_rows(J):
     assert np.isfinite(pa).all()
     assert np.linalg.norm(pa - pb) <= 0.1 * np.linalg.norm(pb - w0.ravel())
     assert fa.status() == 0 and fb.status() == 0
+
+
+def test_drain_stopped_by_its_step_limit(J):
+    """A drain cut off after max_steps reports the tours still open and
+    advances the step counter by exactly max_steps; an unlimited drain of the
+    same chains finishes every tour and takes more steps."""
+    sc = scenes.cornell(width=16, height=16, depth=3)
+    g = J.Scene(sc)
+    a = J.Chains(g, 16, 16, sc.depth, 1 << 16, seed=21, sigma=0.02)
+    b = J.Chains(g, 16, 16, sc.depth, 1 << 16, seed=21, sigma=0.02)
+    for ch in (a, b):
+        ch.set_execution("wave")
+        ch.advance(5)
+    s0 = a.stats()["steps_per_chain"]
+    assert J.complete_tours(a, max_steps=3) > 0
+    assert a.stats()["steps_per_chain"] == s0 + 3
+    assert J.complete_tours(b) == 0
+    assert b.stats()["steps_per_chain"] - s0 > 3
+    assert b.stats()["regenerations"] > a.stats()["regenerations"]
