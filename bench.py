@@ -127,14 +127,6 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def launches_per_advance(mode, chains, chain_steps, depth):
-    """Kernels of ours one jr_advance launches (see jr_advance in include/jr.h)."""
-    wave = mode == "wave" or (mode == "auto" and chains >= (1 << 16))
-    if wave:   # per step: the step kernel and the path kernel; then a finish launch and the fold
-        return chain_steps * 2 + 2
-    return 2   # the persistent step kernel and the fold
-
-
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
