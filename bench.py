@@ -31,11 +31,12 @@ sys.path.insert(0, ROOT)
 METRIC = "Restore chain steps/s on 1 GB300; time to relMSE 1e-2, learned vs plain regen"
 UNIT = "chain steps/s"
 # FP32 operations issued per unit of traversal work (counted from the kernel
-# source: a visit of a 4-wide node = 4 slab tests of 6 FMA (2 FLOP each) +
-# 12 min/max + 1 scaled compare (2), then 5 compares of the sorting network;
+# source: a visit of a 4-wide node = 4 slab tests of 6 FMA (2 FLOP each) on
+# the octant's near and far planes + 4 min/max + 1 scaled compare (2), then 5
+# compares of the sorting network;
 # a triangle test = Moller-Trumbore: 2 cross, 4 dot, 1 reciprocal, 3 scaled
 # products, 3 subtractions, 5 compares).
-FLOP_PER_NODE = 109
+FLOP_PER_NODE = 77
 FLOP_PER_TRI = 45
 SMS, FP32_LANES = 152, 128
 # DRAM traffic of one wf_path_kernel launch (dram__bytes_read.sum +

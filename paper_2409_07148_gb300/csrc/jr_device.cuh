@@ -93,6 +93,7 @@ struct Trav {
     int best, best_id;  // its leaf-order record and original triangle index
     int ref, sp;        // node/leaf ref being visited, stack depth
     uint32_t visits;
+    int oct;            // ray octant: bit a set when the direction's axis-a component is negative
 };
 
 __device__ __forceinline__ void trav_begin(const SceneView& s, Trav& r, float3 o, float3 d) {
@@ -107,6 +108,7 @@ __device__ __forceinline__ void trav_begin(const SceneView& s, Trav& r, float3 o
     r.ox = o.x * r.ix;
     r.oy = o.y * r.iy;
     r.oz = o.z * r.iz;
+    r.oct = (r.ix < 0.0f ? 1 : 0) | (r.iy < 0.0f ? 2 : 0) | (r.iz < 0.0f ? 4 : 0);
     r.tb = INFINITY;
     r.best = -1;
     r.best_id = INT32_MAX;
@@ -126,15 +128,13 @@ __device__ __forceinline__ void cswap(float& ta, int& ra, float& tb, int& rb) {
     ra = q;
 }
 
-// Slab test of child box lane (lo, hi per axis) against [0, tb]: entry
-// distance, or +inf for a miss.  The far distance is scaled up by 2 ulp so
-// that a ray grazing a face of a (conservatively widened) box still enters it.
-__device__ __forceinline__ float slab(const Trav& r, float lx, float hx, float ly, float hy, float lz, float hz) {
-    const float l0 = fmaf(lx, r.ix, -r.ox), h0 = fmaf(hx, r.ix, -r.ox);
-    const float l1 = fmaf(ly, r.iy, -r.oy), h1 = fmaf(hy, r.iy, -r.oy);
-    const float l2 = fmaf(lz, r.iz, -r.oz), h2 = fmaf(hz, r.iz, -r.oz);
-    const float tn = fmax3(fminf(l0, h0), fminf(l1, h1), fmaxf(fminf(l2, h2), 0.0f));
-    const float tf = fmin3(fmaxf(l0, h0), fmaxf(l1, h1), fminf(fmaxf(l2, h2), r.tb));
+// Slab test of one child box against [0, tb], given its near and far plane
+// per axis (picked by the ray's octant, see trav_node): entry distance, or
+// +inf for a miss.  The far distance is scaled up by 2 ulp so that a ray
+// grazing a face of a (conservatively widened) box still enters it.
+__device__ __forceinline__ float slab(const Trav& r, float nx, float fx, float ny, float fy, float nz, float fz) {
+    const float tn = fmax3(fmaf(nx, r.ix, -r.ox), fmaf(ny, r.iy, -r.oy), fmaxf(fmaf(nz, r.iz, -r.oz), 0.0f));
+    const float tf = fmin3(fmaf(fx, r.ix, -r.ox), fmaf(fy, r.iy, -r.oy), fminf(fmaf(fz, r.iz, -r.oz), r.tb));
     return tn <= tf * 1.00000024f ? tn : INFINITY;
 }
 
@@ -151,13 +151,22 @@ __device__ __forceinline__ bool trav_node(const SceneView& s, Trav& r, int* stac
     }
     if constexpr (kCount) work.nodes++;
     const Bvh4Node* n = s.nodes + r.ref;
-    const float4 lx = __ldg(&n->lox), hx = __ldg(&n->hix), ly = __ldg(&n->loy), hy = __ldg(&n->hiy);
-    const float4 lz = __ldg(&n->loz), hz = __ldg(&n->hiz);
+    // The planes are stored lo, hi per axis.  For a positive direction
+    // component the lo plane is met first, for a negative one the hi plane:
+    // (lo * i - o) <= (hi * i - o) for i > 0 and the reverse for i < 0, and
+    // both sides round monotonically, so for finite ray data the octant picks
+    // exactly the values min and max would pick (with a NaN in the ray the two
+    // forms differ, and such a ray carries no contribution either way).
+    const float4* pl = &n->lox;
+    const int sx = r.oct & 1, sy = (r.oct >> 1) & 1, sz = (r.oct >> 2) & 1;
+    const float4 nx = __ldg(pl + sx), fx = __ldg(pl + (sx ^ 1));
+    const float4 ny = __ldg(pl + 2 + sy), fy = __ldg(pl + 2 + (sy ^ 1));
+    const float4 nz = __ldg(pl + 4 + sz), fz = __ldg(pl + 4 + (sz ^ 1));
     int4 rf = __ldg(&n->refs);
-    float t0 = slab(r, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x);
-    float t1 = slab(r, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y);
-    float t2 = slab(r, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z);
-    float t3 = slab(r, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w);
+    float t0 = slab(r, nx.x, fx.x, ny.x, fy.x, nz.x, fz.x);
+    float t1 = slab(r, nx.y, fx.y, ny.y, fy.y, nz.y, fz.y);
+    float t2 = slab(r, nx.z, fx.z, ny.z, fy.z, nz.z, fz.z);
+    float t3 = slab(r, nx.w, fx.w, ny.w, fy.w, nz.w, fz.w);
     if (rf.x == kNoChild) t0 = INFINITY;
     if (rf.y == kNoChild) t1 = INFINITY;
     if (rf.z == kNoChild) t2 = INFINITY;
