@@ -198,7 +198,7 @@ jr_status jr_set_execution(jr_chains* chains, uint32_t mode);
  * It runs the wavefront launches of jr_advance (JR_EXEC_WAVEFRONT), with the
  * same results, but their scratch (second state buffer, live-path records and
  * queues) lives in one fixed device array inside the library, sized for at
- * most JR_STATIC_MAX_CHAINS chains of any depth: 12,124,416 bytes, which
+ * most JR_STATIC_MAX_CHAINS chains of any depth: 10,027,264 bytes, which
  * every GPU that loads the library holds until the process exits.  The chain
  * set (state, framebuffer, accumulator, counters) is the caller's, created
  * beforehand with jr_chains_create.  It calls no cudaMalloc, cudaFree or other

@@ -71,7 +71,7 @@ struct jr_chains {
         cudaFree(view.wf.y);
         cudaFree(view.wf.par);
         cudaFree(view.wf.ua);
-        cudaFree(view.wf.path);
+        cudaFree(view.wf.fy);
         cudaFree(view.wf.uy);
         cudaFree(view.wf.fq);
         cudaFree(view.wf.done);
@@ -228,7 +228,7 @@ static jr_status ensure_wavefront(jr_chains* c, cudaStream_t st) {
     const uint64_t n = c->view.n;
     cudaError_t e;
     if ((e = dev_alloc(&w.y, (size_t)c->view.dim * n)) != cudaSuccess || (e = dev_alloc(&w.par, n)) != cudaSuccess ||
-        (e = dev_alloc(&w.ua, n)) != cudaSuccess || (e = dev_alloc(&w.path, 3 * n)) != cudaSuccess ||
+        (e = dev_alloc(&w.ua, n)) != cudaSuccess || (e = dev_alloc(&w.fy, n)) != cudaSuccess ||
         (e = dev_alloc(&w.queue, n)) != cudaSuccess ||
         (e = dev_alloc(&w.qcount, kQCount)) != cudaSuccess || (e = dev_alloc(&w.uy, n)) != cudaSuccess ||
         (e = dev_alloc(&w.fq, 2 * n)) != cudaSuccess || (e = dev_alloc(&w.done, n)) != cudaSuccess ||
@@ -238,7 +238,7 @@ static jr_status ensure_wavefront(jr_chains* c, cudaStream_t st) {
         cudaFree(w.y);
         cudaFree(w.par);
         cudaFree(w.ua);
-        cudaFree(w.path);
+        cudaFree(w.fy);
         cudaFree(w.queue);
         cudaFree(w.qcount);
         cudaFree(w.uy);
@@ -880,8 +880,8 @@ jr_status jr_flow_get_params(jr_flow* f, float* params, void* stream) {
 jr_status jr_flow_log_density(jr_flow* f, const float* x_dev, uint64_t n, float* lq_dev, void* stream) {
     if (!f || (n > 0 && (!x_dev || !lq_dev))) return fail(JR_ERR_INVALID_ARG, "jr_flow_log_density: null argument");
     if (n >= (1ull << 32)) return fail(JR_ERR_INVALID_ARG, "jr_flow_log_density: n must be below 2^32");
-    JR_CUDA(launch_flow(f->view(0.f), false, nullptr, const_cast<float*>(x_dev), nullptr, nullptr, n, nullptr,
-                        nullptr, (uint32_t)n, nullptr, nullptr, lq_dev, f->status, (cudaStream_t)stream),
+    JR_CUDA(launch_flow(f->view(0.f), false, const_cast<float*>(x_dev), nullptr, nullptr, n, nullptr, nullptr,
+                        (uint32_t)n, nullptr, lq_dev, f->status, (cudaStream_t)stream),
             "jr_flow_log_density");
     return JR_OK;
 }
@@ -889,8 +889,8 @@ jr_status jr_flow_log_density(jr_flow* f, const float* x_dev, uint64_t n, float*
 jr_status jr_flow_sample(jr_flow* f, float* xz_dev, uint64_t n, float* lq_dev, void* stream) {
     if (!f || (n > 0 && (!xz_dev || !lq_dev))) return fail(JR_ERR_INVALID_ARG, "jr_flow_sample: null argument");
     if (n >= (1ull << 32)) return fail(JR_ERR_INVALID_ARG, "jr_flow_sample: n must be below 2^32");
-    JR_CUDA(launch_flow(f->view(0.f), true, nullptr, xz_dev, nullptr, nullptr, n, nullptr, nullptr, (uint32_t)n,
-                        nullptr, nullptr, lq_dev, f->status, (cudaStream_t)stream),
+    JR_CUDA(launch_flow(f->view(0.f), true, xz_dev, nullptr, nullptr, n, nullptr, nullptr, (uint32_t)n, nullptr,
+                        lq_dev, f->status, (cudaStream_t)stream),
             "jr_flow_sample");
     return JR_OK;
 }

@@ -294,13 +294,12 @@ __device__ __forceinline__ void coupling(const unsigned char* wl, const uint8_t*
 // A row lives in SoA buffer [D][n] bufA, or -- when par is given -- in bufA if
 // par[i] is 1 and bufB otherwise.  Density: u_out[i] = beta q + 1 - beta,
 // lq_out[i] = log q.  Sample: the row is replaced by T^{-1}(row), u_out and
-// lq_out as above, and the camera ray of the new state goes to path.
+// lq_out as above.
 template <bool kSample>
-__global__ void __launch_bounds__(kThreads) flow_infer_kernel(FlowView f, SceneView s, float* bufA, float* bufB,
+__global__ void __launch_bounds__(kThreads) flow_infer_kernel(FlowView f, float* bufA, float* bufB,
                                                               const uint8_t* par, uint64_t n, const uint32_t* idx,
                                                               const unsigned int* count_dev, uint32_t n_rows,
-                                                              float* u_out, float4* path, float* lq_out,
-                                                              unsigned int* status) {
+                                                              float* u_out, float* lq_out, unsigned int* status) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
     uint8_t* perm_s = smem + kOffPerm;
@@ -382,13 +381,6 @@ __global__ void __launch_bounds__(kThreads) flow_infer_kernel(FlowView f, SceneV
                 if (i != kNoRow) {
                     if (u_out) u_out[i] = f.beta * __expf(lq) + (1.0f - f.beta);
                     if (lq_out) lq_out[i] = lq;
-                    if (kSample && path) {
-                        float3 o, dd;
-                        camera_ray(s, xw[r * xs], xw[r * xs + 1], o, dd);
-                        path[3 * (uint64_t)i] = make_float4(o.x, o.y, o.z, dd.x);
-                        path[3 * (uint64_t)i + 1] = make_float4(dd.y, dd.z, 1.f, 1.f);
-                        path[3 * (uint64_t)i + 2] = make_float4(1.f, 0.f, 0.f, 0.f);
-                    }
                 }
             }
             __syncwarp();
@@ -444,10 +436,9 @@ cudaError_t launch_flow_pack_ws(const float* master, unsigned char* ws, uint32_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_flow(const FlowView& f, bool sample, const SceneView* s, float* bufA, float* bufB,
-                        const uint8_t* par, uint64_t n, const uint32_t* idx, const unsigned int* count_dev,
-                        uint32_t n_rows, float* u_out, float4* path, float* lq_out, unsigned int* status,
-                        cudaStream_t st) {
+cudaError_t launch_flow(const FlowView& f, bool sample, float* bufA, float* bufB, const uint8_t* par, uint64_t n,
+                        const uint32_t* idx, const unsigned int* count_dev, uint32_t n_rows, float* u_out,
+                        float* lq_out, unsigned int* status, cudaStream_t st) {
     static DeviceOnce once;  // per device: the SM count, after opting in to the largest layout
     const size_t shm = infer_smem(f.D, f.AK);
     long long sms = 0;
@@ -474,14 +465,12 @@ cudaError_t launch_flow(const FlowView& f, bool sample, const SceneView* s, floa
     unsigned g = (unsigned)(sms * (per > 0 ? per : 1));
     if (!count_dev) g = (unsigned)std::min<uint64_t>(g, (n_rows + kTile - 1) / kTile);
     if (g == 0) return cudaSuccess;
-    SceneView sv{};
-    if (s) sv = *s;
     if (sample)
-        flow_infer_kernel<true><<<g, kThreads, shm, st>>>(f, sv, bufA, bufB, par, n, idx, count_dev, n_rows, u_out,
-                                                          path, lq_out, status);
+        flow_infer_kernel<true><<<g, kThreads, shm, st>>>(f, bufA, bufB, par, n, idx, count_dev, n_rows, u_out,
+                                                          lq_out, status);
     else
-        flow_infer_kernel<false><<<g, kThreads, shm, st>>>(f, sv, bufA, bufB, par, n, idx, count_dev, n_rows, u_out,
-                                                           path, lq_out, status);
+        flow_infer_kernel<false><<<g, kThreads, shm, st>>>(f, bufA, bufB, par, n, idx, count_dev, n_rows, u_out,
+                                                           lq_out, status);
     return cudaGetLastError();
 }
 

@@ -90,8 +90,8 @@ struct WaveView {
     float* y = nullptr;           // [D][n] second state buffer
     uint8_t* par = nullptr;       // [n] 1: the current state is in y, 0: in x
     float* ua = nullptr;          // [n] Ua of a local step, -1 for a regeneration step
-    float4* path = nullptr;       // [n][3] live path record (o, d, T, F)
-    uint32_t* queue = nullptr;    // [n] the step's path queue
+    float4* fy = nullptr;         // [n] F(y) of the step's candidate (xyz; w unused)
+    uint32_t* queue = nullptr;    // [n] the step's path queue (drain steps; otherwise every chain in order)
     unsigned int* qcount = nullptr;  // [kQCount]: queue lengths, fetch cursors, flow queue lengths
     float* uy = nullptr;          // [n] u of the step's candidate (with a flow)
     uint32_t* fq = nullptr;       // [2][n] candidates for the flow: density rows, then sampling rows
@@ -206,20 +206,19 @@ cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t st
 // array (no allocation); c.wf is ignored.  c.n <= kStaticMaxChains.
 constexpr uint64_t kStaticMaxChains = 1u << 16;
 constexpr size_t kStaticScratchBytes =
-    sizeof(float) * kMaxDim * kStaticMaxChains + sizeof(float4) * 3 * kStaticMaxChains +
+    sizeof(float) * kMaxDim * kStaticMaxChains + sizeof(float4) * kStaticMaxChains +
     sizeof(float) * kStaticMaxChains + sizeof(uint32_t) * kStaticMaxChains + sizeof(uint8_t) * kStaticMaxChains +
-    256;  // = 12 124 416 bytes (every piece but the counters is a multiple of 256)
+    256;  // = 10 027 264 bytes (every piece but the counters is a multiple of 256)
 cudaError_t launch_wavefront_static(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
                                     cudaStream_t st);
 
 // jr_flow.cu: flow rows through the tensor cores.  Density: u_out[i] = beta q
 // + 1 - beta (and lq_out[i] = log q) for rows i of buf [D][n]; sample: buf
-// rows replaced by T^{-1}(buf), the camera ray of the new state written to
-// path (if not null).  Rows are idx[j], j < *count_dev (device) or n_rows.
-cudaError_t launch_flow(const FlowView& f, bool sample, const SceneView* s, float* bufA, float* bufB,
-                        const uint8_t* par, uint64_t n, const uint32_t* idx, const unsigned int* count_dev,
-                        uint32_t n_rows, float* u_out, float4* path, float* lq_out, unsigned int* status,
-                        cudaStream_t st);
+// rows replaced by T^{-1}(buf).  Rows are idx[j], j < *count_dev (device) or
+// n_rows.
+cudaError_t launch_flow(const FlowView& f, bool sample, float* bufA, float* bufB, const uint8_t* par, uint64_t n,
+                        const uint32_t* idx, const unsigned int* count_dev, uint32_t n_rows, float* u_out,
+                        float* lq_out, unsigned int* status, cudaStream_t st);
 // FP32 master parameters [kFL][S] -> the inference layout (flow_ws_layer_bytes per layer).
 cudaError_t launch_flow_pack_ws(const float* master, unsigned char* ws, uint32_t AK, cudaStream_t st);
 // FP32 master parameters [kFL][S] -> padded bf16 weights and biases.

@@ -7,8 +7,8 @@
 //   step kernel (all chains, converged): finish the previous step (MH
 //     acceptance or regeneration), draw the new step's clocks t1 ~ Exp(1),
 //     t2 ~ Exp(k), k = c~ u / p (Section 6.2), splat (dt, x) (Sections 6.3/7.4),
-//     build the candidate y (Gaussian small step or a draw from mu) and its
-//     camera ray; every chain joins the path queue.
+//     build the candidate y (Gaussian small step or a draw from mu); every
+//     chain joins the path queue.
 //   path kernel (persistent warps): the whole path of every queued candidate,
 //     vertex after vertex, in registers: warp-synchronous BVH traversal, batched
 //     shading, and dynamic fetch of new paths into idle lanes, so that a warp
@@ -32,22 +32,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kRefill = 4;  // refill a warp once this many lanes are idle
-
-// Path record: (o.xyz, d.x) (d.yz, T.xy) (T.z, F.xyz).
-__device__ __forceinline__ void store_path(float4* path, uint64_t i, float3 o, float3 d, float3 T, float3 F) {
-    path[3 * i] = make_float4(o.x, o.y, o.z, d.x);
-    path[3 * i + 1] = make_float4(d.y, d.z, T.x, T.y);
-    path[3 * i + 2] = make_float4(T.z, F.x, F.y, F.z);
-}
-
-__device__ __forceinline__ void load_path(const float4* path, uint64_t i, float3& o, float3& d, float3& T,
-                                          float3& F) {
-    const float4 a = path[3 * i], b = path[3 * i + 1], c = path[3 * i + 2];
-    o = f3(a.x, a.y, a.z);
-    d = f3(a.w, b.x, b.y);
-    T = f3(b.z, b.w, c.x);
-    F = f3(c.y, c.z, c.w);
-}
 
 // Append chain i to a queue if `live`; one atomic per warp.  All 32 lanes call.
 __device__ __forceinline__ void enqueue(bool live, uint32_t i, uint32_t* q, unsigned int* count) {
@@ -91,8 +75,10 @@ __device__ __forceinline__ void count_and_flush(uint32_t nJ, uint32_t nL, uint32
 // mode = kModeDrain: a kill ends the chain's tour (counted in J) and the chain
 // (done = 1); done chains do nothing; no regeneration starts a new tour.
 // Chains still in a tour after the step are counted in qcount[kQActive].
+// Outside a drain every chain is traced, so the path queue is the identity
+// (chain j is entry j) and is not written; a drain step writes it.
 __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step, int finish, int begin,
-                                                      SceneView s, int mode) {
+                                                      int mode) {
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     const bool valid = i < c.n;
     const int D = (int)c.dim;
@@ -104,14 +90,24 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
     unsigned status = 0;
     bool to_sample = false, traced = valid, active = false;
     if (valid) {
+        // Every load the step needs is issued here, before any store: the film
+        // point of the current state is read from both buffers, so that no
+        // load waits for the parity byte.
         uint8_t par = w.par[i];
         float Fr = c.fpu[0 * n + i], Fg = c.fpu[1 * n + i], Fb = c.fpu[2 * n + i];
         float p = c.fpu[3 * n + i], u = c.fpu[4 * n + i];
+        const float ua = finish ? w.ua[i] : 0.0f;
+        const float4 pf = finish ? w.fy[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float xs0 = 0.f, xs1 = 0.f, ys0 = 0.f, ys1 = 0.f;
+        if (begin) {
+            xs0 = c.x[i];
+            xs1 = c.x[n + i];
+            ys0 = w.y[i];
+            ys1 = w.y[n + i];
+        }
         const bool was_done = drain && w.done[i];
-        if (finish && !(drain && w.ua[i] == -2.0f)) {
-            const float ua = w.ua[i];
-            const float4 pf = w.path[3 * i + 2];
-            const float3 Fy = finite_or_zero(f3(pf.y, pf.z, pf.w), status);
+        if (finish && !(drain && ua == -2.0f)) {
+            const float3 Fy = finite_or_zero(f3(pf.x, pf.y, pf.z), status);
             const float py = lum(Fy);
             bool accept;
             if (restart) {     // a restart: the new tour's start, not a regeneration
@@ -158,7 +154,7 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
             if (restart) dt = 0.0f;
             const bool use_flow = has_flow && !local && u01(r0.w) < c.flow.beta;
             to_sample = use_flow;
-            const float x0 = cur[i], x1 = cur[n + i];
+            const float x0 = par ? ys0 : xs0, x1 = par ? ys1 : xs1;  // = cur[i], cur[n + i]
             if (dt > 0.0f && p > 0.0f) {
                 uint32_t px = min((uint32_t)((double)x0 * (double)c.width), c.width - 1);
                 uint32_t py = min((uint32_t)((double)x1 * (double)c.height), c.height - 1);
@@ -174,7 +170,6 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
                 to_sample = false;
             }
             active = drain && local;
-            float y0 = 0.f, y1 = 0.f;
             for (int b = 0; traced && 4 * b < D; ++b) {
                 const uint4 r = draw(c.seed, tag, (uint32_t)(b + 1), chain, step);
                 const uint64_t o0 = (uint64_t)(4 * b) * n + i;
@@ -204,15 +199,6 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
                     cand[o0 + 2 * n] = v2;
                     cand[o0 + 3 * n] = v3;
                 }
-                if (b == 0) {
-                    y0 = v0;
-                    y1 = v1;
-                }
-            }
-            if (traced && !use_flow) {  // a flow draw gets its camera ray from the flow kernel
-                float3 o, d;
-                camera_ray(s, y0, y1, o, d);
-                store_path(w.path, i, o, d, f3(1.f, 1.f, 1.f), f3(0.f, 0.f, 0.f));
             }
         } else if (par) {
             for (int dd = 0; dd < D; ++dd) c.x[(uint64_t)dd * n + i] = w.y[(uint64_t)dd * n + i];
@@ -221,7 +207,7 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
         w.par[i] = par;
     }
     if (begin) {
-        enqueue(traced, (uint32_t)i, w.queue, w.qcount + 0);
+        if (drain) enqueue(traced, (uint32_t)i, w.queue, w.qcount + 0);
         if (has_flow) enqueue(to_sample, (uint32_t)i, w.fq + n, w.qcount + kQFlowSample);
         if (drain) {  // counters[3]: 1 + the last drain step after which a tour was still open
             const unsigned na = __popc(__ballot_sync(kFull, active));
@@ -242,19 +228,21 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
 // 2009): a lane that meets a leaf postpones it and keeps descending inner
 // nodes until every lane holds a leaf.  A warp shades its waiting lanes
 // together once kShadeBatch of them wait (or none is traversing); a shaded
-// path either continues with its next ray or ends (F goes to the path record,
+// path either continues with its next ray or ends (F goes to fy,
 // and, with a flow, the row joins the density queue: when its candidate will
 // become a state with p > 0 and still lacks u(y); the finish of the next step
 // kernel takes the same decision from the same values).  Idle lanes take new
 // paths from the queue (dynamic fetch, so a warp does not idle for its
-// longest path).
+// longest path); a new path starts at the camera ray through the candidate's
+// film point (y0, y1) with T = 1, F = 0.  ident = 1: the queue is the identity
+// over all n chains (every step but a drain step).
 constexpr int kShadeBatch = 16;
 enum PathState : uint32_t { kIdle = 0, kTraverse = 1, kWaitShade = 2 };
 
-__global__ void __launch_bounds__(128) wf_path_kernel(SceneView s, ChainView c) {
+__global__ void __launch_bounds__(128) wf_path_kernel(SceneView s, ChainView c, int ident) {
     const WaveView& w = c.wf;
     const uint32_t* qin = w.queue;
-    const unsigned count = w.qcount[0];
+    const unsigned count = ident ? (unsigned)c.n : w.qcount[0];
     if ((uint64_t)blockIdx.x * blockDim.x >= count) return;
     unsigned int* fetch = w.qcount + (kMaxDepth + 2);
     const uint64_t n = c.n;
@@ -294,7 +282,7 @@ __global__ void __launch_bounds__(128) wf_path_kernel(SceneView s, ChainView c) 
                     }
                 }
                 if (!live) {
-                    w.path[3 * (uint64_t)i + 2] = make_float4(0.f, F.x, F.y, F.z);
+                    w.fy[i] = make_float4(F.x, F.y, F.z, 0.f);
                     if (has_flow) {
                         unsigned ignored = 0;
                         const float py = lum(finite_or_zero(F, ignored));
@@ -316,9 +304,12 @@ __global__ void __launch_bounds__(128) wf_path_kernel(SceneView s, ChainView c) 
             if (state == kIdle) {
                 const unsigned j = base + __popc(idle & lt);
                 if (j < count) {
-                    i = qin[j];
+                    i = ident ? j : qin[j];
+                    const float* cand = w.par[i] ? c.x : w.y;
                     float3 o, d;
-                    load_path(w.path, i, o, d, T, F);
+                    camera_ray(s, cand[i], cand[n + i], o, d);
+                    T = f3(1.f, 1.f, 1.f);
+                    F = f3(0.f, 0.f, 0.f);
                     v = 0;
                     trav_begin(s, r, o, d);
                     state = s.root != kSentinel ? kTraverse : kWaitShade;  // empty scene: a miss
@@ -366,16 +357,15 @@ __global__ void __launch_bounds__(128) wf_path_kernel(SceneView s, ChainView c) 
 inline unsigned grid_for(uint64_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 
 // The flow stages of a step (a chain's candidate lives in x when its parity
-// byte is 1, else in y).  Before the path kernel: y = T^{-1}(z), u(y) and the
-// camera ray of the flow draws.  After it: u(y) of the rows the path kernel
-// queued.
-cudaError_t launch_flow_draws(const SceneView& s, const ChainView& c, cudaStream_t st) {
-    return launch_flow(c.flow, true, &s, c.x, c.wf.y, c.wf.par, c.n, c.wf.fq + c.n, c.wf.qcount + kQFlowSample, 0,
-                       c.wf.uy, c.wf.path, nullptr, c.status, st);
+// byte is 1, else in y).  Before the path kernel: y = T^{-1}(z) and u(y) of
+// the flow draws.  After it: u(y) of the rows the path kernel queued.
+cudaError_t launch_flow_draws(const ChainView& c, cudaStream_t st) {
+    return launch_flow(c.flow, true, c.x, c.wf.y, c.wf.par, c.n, c.wf.fq + c.n, c.wf.qcount + kQFlowSample, 0,
+                       c.wf.uy, nullptr, c.status, st);
 }
-cudaError_t launch_flow_densities(const SceneView& s, const ChainView& c, cudaStream_t st) {
-    return launch_flow(c.flow, false, &s, c.x, c.wf.y, c.wf.par, c.n, c.wf.fq, c.wf.qcount + kQFlowDensity, 0,
-                       c.wf.uy, nullptr, nullptr, c.status, st);
+cudaError_t launch_flow_densities(const ChainView& c, cudaStream_t st) {
+    return launch_flow(c.flow, false, c.x, c.wf.y, c.wf.par, c.n, c.wf.fq, c.wf.qcount + kQFlowDensity, 0,
+                       c.wf.uy, nullptr, c.status, st);
 }
 
 }  // namespace
@@ -438,17 +428,17 @@ cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t st
     mark(-1);
     for (uint32_t k = 0; k < n_steps && e == cudaSuccess; ++k) {
         if ((e = cudaMemsetAsync(c.wf.qcount, 0, sizeof(unsigned int) * kQCount, st)) != cudaSuccess) return e;
-        wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + k, k > 0, 1, s, mode);
+        wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + k, k > 0, 1, mode);
         mark(KernelTimer::kStep);
-        if (has_flow && (e = launch_flow_draws(s, c, st)) != cudaSuccess) return e;
+        if (has_flow && (e = launch_flow_draws(c, st)) != cudaSuccess) return e;
         if (has_flow) mark(KernelTimer::kFlow);
-        wf_path_kernel<<<(unsigned)path_blocks, 128, 0, st>>>(s, c);
+        wf_path_kernel<<<(unsigned)path_blocks, 128, 0, st>>>(s, c, mode != kModeDrain);
         mark(KernelTimer::kPath);
-        if (has_flow && (e = launch_flow_densities(s, c, st)) != cudaSuccess) return e;
+        if (has_flow && (e = launch_flow_densities(c, st)) != cudaSuccess) return e;
         if (has_flow) mark(KernelTimer::kFlow);
     }
     if (e != cudaSuccess) return e;
-    wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + n_steps, n_steps > 0, 0, s, mode);
+    wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + n_steps, n_steps > 0, 0, mode);
     mark(KernelTimer::kStep);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
@@ -459,12 +449,12 @@ cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t st
 // kStaticMaxChains chains live in one file-scope device array instead of
 // memory allocated per chain set.  Every GPU that loads the library holds it
 // until the process exits.  Layout (256-byte aligned pieces): y [kMaxDim][n],
-// path [n][3] float4, ua [n], queue [n], par [n], qcount (256 bytes).
+// fy [n] float4, ua [n], queue [n], par [n], qcount (256 bytes).
 namespace {
 constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kOffY = 0;
-constexpr size_t kOffPath = kOffY + align256(sizeof(float) * kMaxDim * kStaticMaxChains);
-constexpr size_t kOffUa = kOffPath + align256(sizeof(float4) * 3 * kStaticMaxChains);
+constexpr size_t kOffFy = kOffY + align256(sizeof(float) * kMaxDim * kStaticMaxChains);
+constexpr size_t kOffUa = kOffFy + align256(sizeof(float4) * kStaticMaxChains);
 constexpr size_t kOffQueue = kOffUa + align256(sizeof(float) * kStaticMaxChains);
 constexpr size_t kOffPar = kOffQueue + align256(sizeof(uint32_t) * kStaticMaxChains);
 constexpr size_t kOffCount = kOffPar + align256(sizeof(uint8_t) * kStaticMaxChains);
@@ -506,14 +496,14 @@ cudaError_t launch_wavefront_static(const SceneView& s, const ChainView& c, uint
     unsigned char* b = static_cast<unsigned char*>(base);
     ChainView v = c;
     v.wf.y = reinterpret_cast<float*>(b + kOffY);
-    v.wf.path = reinterpret_cast<float4*>(b + kOffPath);
+    v.wf.fy = reinterpret_cast<float4*>(b + kOffFy);
     v.wf.ua = reinterpret_cast<float*>(b + kOffUa);
     v.wf.queue = reinterpret_cast<uint32_t*>(b + kOffQueue);
     v.wf.par = b + kOffPar;
     v.wf.qcount = reinterpret_cast<unsigned int*>(b + kOffCount);
     // The array keeps the previous call's bytes: the parity must start at 0
     // (every state in x); the queue counters are cleared per step inside
-    // launch_wavefront; y, ua, the path and hit records are written before use.
+    // launch_wavefront; y, ua and fy are written before use.
     if ((e = cudaMemsetAsync(v.wf.par, 0, c.n, st)) != cudaSuccess) return e;
     return launch_wavefront(s, v, step_begin, n_steps, st);
 }
