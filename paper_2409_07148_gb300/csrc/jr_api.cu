@@ -881,7 +881,7 @@ jr_status jr_flow_log_density(jr_flow* f, const float* x_dev, uint64_t n, float*
     if (!f || (n > 0 && (!x_dev || !lq_dev))) return fail(JR_ERR_INVALID_ARG, "jr_flow_log_density: null argument");
     if (n >= (1ull << 32)) return fail(JR_ERR_INVALID_ARG, "jr_flow_log_density: n must be below 2^32");
     JR_CUDA(launch_flow(f->view(0.f), false, const_cast<float*>(x_dev), nullptr, nullptr, n, nullptr, nullptr,
-                        (uint32_t)n, nullptr, lq_dev, f->status, (cudaStream_t)stream),
+                        (uint32_t)n, nullptr, lq_dev, nullptr, f->status, (cudaStream_t)stream),
             "jr_flow_log_density");
     return JR_OK;
 }
@@ -890,7 +890,7 @@ jr_status jr_flow_sample(jr_flow* f, float* xz_dev, uint64_t n, float* lq_dev, v
     if (!f || (n > 0 && (!xz_dev || !lq_dev))) return fail(JR_ERR_INVALID_ARG, "jr_flow_sample: null argument");
     if (n >= (1ull << 32)) return fail(JR_ERR_INVALID_ARG, "jr_flow_sample: n must be below 2^32");
     JR_CUDA(launch_flow(f->view(0.f), true, xz_dev, nullptr, nullptr, n, nullptr, nullptr, (uint32_t)n, nullptr,
-                        lq_dev, f->status, (cudaStream_t)stream),
+                        lq_dev, nullptr, f->status, (cudaStream_t)stream),
             "jr_flow_sample");
     return JR_OK;
 }

@@ -294,12 +294,14 @@ __device__ __forceinline__ void coupling(const unsigned char* wl, const uint8_t*
 // A row lives in SoA buffer [D][n] bufA, or -- when par is given -- in bufA if
 // par[i] is 1 and bufB otherwise.  Density: u_out[i] = beta q + 1 - beta,
 // lq_out[i] = log q.  Sample: the row is replaced by T^{-1}(row), u_out and
-// lq_out as above.
+// lq_out as above, and start[i] (if given) = the new row's first four
+// coordinates.
 template <bool kSample>
 __global__ void __launch_bounds__(kThreads) flow_infer_kernel(FlowView f, float* bufA, float* bufB,
                                                               const uint8_t* par, uint64_t n, const uint32_t* idx,
                                                               const unsigned int* count_dev, uint32_t n_rows,
-                                                              float* u_out, float* lq_out, unsigned int* status) {
+                                                              float* u_out, float* lq_out, float4* start,
+                                                              unsigned int* status) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
     uint8_t* perm_s = smem + kOffPerm;
@@ -381,6 +383,10 @@ __global__ void __launch_bounds__(kThreads) flow_infer_kernel(FlowView f, float*
                 if (i != kNoRow) {
                     if (u_out) u_out[i] = f.beta * __expf(lq) + (1.0f - f.beta);
                     if (lq_out) lq_out[i] = lq;
+                    if (kSample && start) {
+                        const float* x = xw + r * xs;
+                        start[i] = make_float4(x[0], D > 1 ? x[1] : 0.f, D > 2 ? x[2] : 0.f, D > 3 ? x[3] : 0.f);
+                    }
                 }
             }
             __syncwarp();
@@ -438,7 +444,7 @@ cudaError_t launch_flow_pack_ws(const float* master, unsigned char* ws, uint32_t
 
 cudaError_t launch_flow(const FlowView& f, bool sample, float* bufA, float* bufB, const uint8_t* par, uint64_t n,
                         const uint32_t* idx, const unsigned int* count_dev, uint32_t n_rows, float* u_out,
-                        float* lq_out, unsigned int* status, cudaStream_t st) {
+                        float* lq_out, float4* start, unsigned int* status, cudaStream_t st) {
     static DeviceOnce once;  // per device: the SM count, after opting in to the largest layout
     const size_t shm = infer_smem(f.D, f.AK);
     long long sms = 0;
@@ -467,10 +473,10 @@ cudaError_t launch_flow(const FlowView& f, bool sample, float* bufA, float* bufB
     if (g == 0) return cudaSuccess;
     if (sample)
         flow_infer_kernel<true><<<g, kThreads, shm, st>>>(f, bufA, bufB, par, n, idx, count_dev, n_rows, u_out,
-                                                          lq_out, status);
+                                                          lq_out, start, status);
     else
         flow_infer_kernel<false><<<g, kThreads, shm, st>>>(f, bufA, bufB, par, n, idx, count_dev, n_rows, u_out,
-                                                           lq_out, status);
+                                                           lq_out, nullptr, status);
     return cudaGetLastError();
 }
 

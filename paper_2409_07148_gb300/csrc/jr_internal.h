@@ -90,7 +90,8 @@ struct WaveView {
     float* y = nullptr;           // [D][n] second state buffer
     uint8_t* par = nullptr;       // [n] 1: the current state is in y, 0: in x
     float* ua = nullptr;          // [n] Ua of a local step, -1 for a regeneration step
-    float4* fy = nullptr;         // [n] F(y) of the step's candidate (xyz; w unused)
+    float4* fy = nullptr;         // [n] the candidate's (y0, y1, y2, y3) from the step launch until its path
+                                  // starts, then F(y) (xyz; w unused)
     uint32_t* queue = nullptr;    // [n] the step's path queue (drain steps; otherwise every chain in order)
     unsigned int* qcount = nullptr;  // [kQCount]: queue lengths, fetch cursors, flow queue lengths
     float* uy = nullptr;          // [n] u of the step's candidate (with a flow)
@@ -214,11 +215,12 @@ cudaError_t launch_wavefront_static(const SceneView& s, const ChainView& c, uint
 
 // jr_flow.cu: flow rows through the tensor cores.  Density: u_out[i] = beta q
 // + 1 - beta (and lq_out[i] = log q) for rows i of buf [D][n]; sample: buf
-// rows replaced by T^{-1}(buf).  Rows are idx[j], j < *count_dev (device) or
+// rows replaced by T^{-1}(buf), and start[i] (if not null) = the row's first
+// four coordinates (0 past D).  Rows are idx[j], j < *count_dev (device) or
 // n_rows.
 cudaError_t launch_flow(const FlowView& f, bool sample, float* bufA, float* bufB, const uint8_t* par, uint64_t n,
                         const uint32_t* idx, const unsigned int* count_dev, uint32_t n_rows, float* u_out,
-                        float* lq_out, unsigned int* status, cudaStream_t st);
+                        float* lq_out, float4* start, unsigned int* status, cudaStream_t st);
 // FP32 master parameters [kFL][S] -> the inference layout (flow_ws_layer_bytes per layer).
 cudaError_t launch_flow_pack_ws(const float* master, unsigned char* ws, uint32_t AK, cudaStream_t st);
 // FP32 master parameters [kFL][S] -> padded bf16 weights and biases.

@@ -77,7 +77,7 @@ __device__ __forceinline__ void count_and_flush(uint32_t nJ, uint32_t nL, uint32
 // Chains still in a tour after the step are counted in qcount[kQActive].
 // Outside a drain every chain is traced, so the path queue is the identity
 // (chain j is entry j) and is not written; a drain step writes it.
-__global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step, int finish, int begin,
+__global__ void __launch_bounds__(128, 12) wf_step_kernel(ChainView c, uint64_t step, int finish, int begin,
                                                       int mode) {
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     const bool valid = i < c.n;
@@ -199,6 +199,11 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
                     cand[o0 + 2 * n] = v2;
                     cand[o0 + 3 * n] = v3;
                 }
+                if (b == 0) {  // the path's start record
+                    float2* f = reinterpret_cast<float2*>(w.fy + i);
+                    f[0] = make_float2(v0, v1);
+                    f[1] = make_float2(v2, v3);
+                }
             }
         } else if (par) {
             for (int dd = 0; dd < D; ++dd) c.x[(uint64_t)dd * n + i] = w.y[(uint64_t)dd * n + i];
@@ -236,6 +241,10 @@ __global__ void __launch_bounds__(128) wf_step_kernel(ChainView c, uint64_t step
 // longest path); a new path starts at the camera ray through the candidate's
 // film point (y0, y1) with T = 1, F = 0.  ident = 1: the queue is the identity
 // over all n chains (every step but a drain step).
+// A path's loads never wait on one another: the start record fy[i] =
+// (y0, y1, y2, y3) and the parity byte arrive together, and the two
+// coordinates of vertex v + 1 are loaded when vertex v is shaded, so they
+// arrive while the next ray traverses.
 constexpr int kShadeBatch = 16;
 enum PathState : uint32_t { kIdle = 0, kTraverse = 1, kWaitShade = 2 };
 
@@ -258,6 +267,8 @@ __global__ void __launch_bounds__(128) wf_path_kernel(SceneView s, ChainView c, 
     int v = 0, leaf = kSentinel;
     bool failed = false, drained = false;
     float3 T = f3(1.f, 1.f, 1.f), F = f3(0.f, 0.f, 0.f);
+    float u1 = 0.f, u2 = 0.f;  // the coordinates of vertex v
+    bool cx = false;           // the candidate lives in x (else in y)
     while (true) {
         // shade the waiting lanes as a batch
         const unsigned waiting = __ballot_sync(kFull, state == kWaitShade);
@@ -267,18 +278,18 @@ __global__ void __launch_bounds__(128) wf_path_kernel(SceneView s, ChainView c, 
             if (state == kWaitShade) {
                 bool live = false;
                 if (r.best >= 0) {
-                    float u1 = 0.f, u2 = 0.f;
-                    if (v < depth) {
-                        const float* cand = w.par[i] ? c.x : w.y;
-                        u1 = cand[(uint64_t)(2 + 2 * v) * n + i];
-                        u2 = cand[(uint64_t)(3 + 2 * v) * n + i];
-                    }
                     float3 o = r.o, d = r.d;
-                    live = shade_vertex(s, r.best, r.tb, v, depth, u1, u2, o, d, T, F);
+                    live = shade_vertex(s, r.best, r.tb, v, depth, v < depth ? u1 : 0.f, v < depth ? u2 : 0.f, o,
+                                        d, T, F);
                     if (live) {
                         ++v;
                         trav_begin(s, r, o, d);
                         state = kTraverse;
+                        if (v < depth) {
+                            const float* cand = cx ? c.x : w.y;
+                            u1 = cand[(uint64_t)(2 + 2 * v) * n + i];
+                            u2 = cand[(uint64_t)(3 + 2 * v) * n + i];
+                        }
                     }
                 }
                 if (!live) {
@@ -305,9 +316,12 @@ __global__ void __launch_bounds__(128) wf_path_kernel(SceneView s, ChainView c, 
                 const unsigned j = base + __popc(idle & lt);
                 if (j < count) {
                     i = ident ? j : qin[j];
-                    const float* cand = w.par[i] ? c.x : w.y;
+                    const float4 y = w.fy[i];
+                    cx = w.par[i] != 0;
+                    u1 = y.z;
+                    u2 = y.w;
                     float3 o, d;
-                    camera_ray(s, cand[i], cand[n + i], o, d);
+                    camera_ray(s, y.x, y.y, o, d);
                     T = f3(1.f, 1.f, 1.f);
                     F = f3(0.f, 0.f, 0.f);
                     v = 0;
@@ -361,11 +375,11 @@ inline unsigned grid_for(uint64_t n, unsigned b) { return (unsigned)((n + b - 1)
 // the flow draws.  After it: u(y) of the rows the path kernel queued.
 cudaError_t launch_flow_draws(const ChainView& c, cudaStream_t st) {
     return launch_flow(c.flow, true, c.x, c.wf.y, c.wf.par, c.n, c.wf.fq + c.n, c.wf.qcount + kQFlowSample, 0,
-                       c.wf.uy, nullptr, c.status, st);
+                       c.wf.uy, nullptr, c.wf.fy, c.status, st);
 }
 cudaError_t launch_flow_densities(const ChainView& c, cudaStream_t st) {
     return launch_flow(c.flow, false, c.x, c.wf.y, c.wf.par, c.n, c.wf.fq, c.wf.qcount + kQFlowDensity, 0,
-                       c.wf.uy, nullptr, c.status, st);
+                       c.wf.uy, nullptr, nullptr, c.status, st);
 }
 
 }  // namespace
