@@ -198,6 +198,11 @@ def run_batched(args):
         clocks = sampler.stop()
         chains = sum(c.n for c in sets)
         ok = all(c.stats(stream=stream)["status_word"] == 0 for c in sets)
+    wave = tune["best_block"] == 0
+    # per advance: the batched wavefront's step and path launches per chain
+    # step, its closing step launch and the fold; else one persistent launch
+    # and the fold
+    launches = 2 * K + 2 if wave else 2
     if rank != 0:
         return
     total = sum(times)
@@ -207,10 +212,12 @@ def run_batched(args):
             "config": {"workload": "batched64", "scenes": len(scs), "n_tris_total": sum(s.n_tris for s in scs),
                        "pixels_total": sum(s.width * s.height for s in scs), "chains": chains,
                        "chain_steps_per_step": K, "depths": sorted({s.depth for s in scs}),
-                       "launch": "one persistent launch + one fold per advance, replayed from a CUDA graph",
+                       "launch": ("batched wavefront: a step and a path launch per chain step, a closing step "
+                                  "launch and the fold per advance, replayed from a CUDA graph") if wave else
+                                 "one persistent launch + one fold per advance, replayed from a CUDA graph",
                        "autotune": tune, "l2": "flushed by a 512 MB write between timed launches",
                        "status_ok": ok},
-            "clocks": clocks, "gpu_launches": 2 * args.steps}
+            "clocks": clocks, "gpu_launches": launches * args.steps}
     print(json.dumps(line), flush=True)
 
 

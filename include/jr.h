@@ -272,7 +272,8 @@ jr_status jr_philox(uint64_t seed, uint32_t tag, uint32_t block, uint64_t chain_
  * Batches: many chain sets -- scenes of uneven size, images, depths -- advanced
  * by ONE persistent launch.  Blocks of the launch take work items (a block of
  * chains of one set) from a global cursor; items are ordered by estimated cost
- * (depth + 1) x log2(triangles), longest first.  Every set advances exactly as
+ * (depth + 1) x log2(triangles), longest first.  Or, with JR_BATCH_WAVEFRONT,
+ * by shared wavefront launches over all the sets.  Every set advances exactly as
  * jr_advance would advance it on its own (same Philox streams, same
  * per-chain arithmetic; Alg. 2 of Section 7.2 per chain).  The sets stay owned
  * by the caller and must outlive the batch; a set may still be advanced,
@@ -282,21 +283,32 @@ typedef struct jr_batch jr_batch;
 
 typedef struct {
     uint32_t n;                   /* candidates tried */
-    uint32_t block[8];            /* chains per work item (= threads per block) */
+    uint32_t block[8];            /* chains per work item (= threads per block), or JR_BATCH_WAVEFRONT */
     double ns_per_chain_step[8];  /* measured device time per chain step */
     uint32_t best_block;          /* the candidate now in use */
 } jr_tune_report;
+
+/* jr_batch_set_block value that selects the batched wavefront: every set's
+ * chains take part in the same step and path launches (whole paths per lane
+ * with dynamic fetch, as JR_EXEC_WAVEFRONT for one set) over one device copy
+ * of all the sets' scenes, merged when the batch first uses it (each distinct
+ * scene once; at most 1024 sets, 2^28 triangles, 2^31 chains).  Every set
+ * also gets its wavefront buffers.  n_steps steps take 2 n_steps + 2 launches
+ * (plus one 4-byte memset per step). */
+#define JR_BATCH_WAVEFRONT 0u
 
 /* Build a batch over n_sets distinct chain sets (device descriptors, work
  * items, one set-up launch).  Synchronises `stream`. */
 jr_status jr_batch_create(jr_chains* const* sets, uint32_t n_sets, void* stream, jr_batch** out);
 void jr_batch_destroy(jr_batch* batch);
 
-/* Chains per work item (= threads per block): a multiple of 32 in [32, 256]. */
+/* Chains per work item (= threads per block): a multiple of 32 in [32, 256];
+ * or JR_BATCH_WAVEFRONT. */
 jr_status jr_batch_set_block(jr_batch* batch, uint32_t block);
 
 /* Advance every set of the batch by n_steps: one persistent launch plus one
- * fold launch for all sets.  Asynchronous. */
+ * fold launch for all sets (the batched wavefront: its launches, then the
+ * fold).  Asynchronous, except the batched wavefront's one-time set-up. */
 jr_status jr_batch_advance(jr_batch* batch, uint32_t n_steps, void* stream);
 
 /* As jr_batch_advance, replayed from a CUDA graph that holds the two launches
@@ -306,9 +318,10 @@ jr_status jr_batch_advance(jr_batch* batch, uint32_t n_steps, void* stream);
 jr_status jr_batch_advance_graph(jr_batch* batch, uint32_t n_steps, void* stream);
 
 /* Autotuner: time probe_steps chain steps of the whole batch for each work-item
- * size in {32, 64, 128, 256} (CUDA events on `stream`) and keep the fastest.
- * The probes are real steps: every set advances by 4 x probe_steps.
- * Synchronises `stream`. */
+ * size in {32, 64, 128, 256} and for JR_BATCH_WAVEFRONT (CUDA events on
+ * `stream`; the wavefront only for at most 1024 sets) and keep the fastest.
+ * The probes are real steps: every set advances by n x probe_steps, n the
+ * number of candidates.  Synchronises `stream`. */
 jr_status jr_batch_autotune(jr_batch* batch, uint32_t probe_steps, void* stream, jr_tune_report* out);
 
 /* ---------------------------------------------------------------------------

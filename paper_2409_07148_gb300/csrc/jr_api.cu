@@ -506,11 +506,22 @@ struct jr_batch {
     uint32_t n_items = 0;
     uint32_t max_dim = 0;
     uint64_t total_px = 0, total_chains = 0;
-    int block = 128;
+    int block = 128;  // chains per megakernel work item; 0: the batched wavefront
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint32_t graph_steps = 0;
-    int graph_block = 0;
+    int graph_block = -1;
+    // the batched wavefront, set up on first use: the merged scene, roots,
+    // chain prefix sums, step-launch work items, the path launches' cursor
+    Bvh4Node* m_nodes = nullptr;
+    TriRecord* m_tris = nullptr;
+    Material* m_mats = nullptr;
+    int* roots = nullptr;
+    uint64_t* chain_off = nullptr;
+    BatchItem* wf_items = nullptr;
+    unsigned int* fetch = nullptr;
+    BatchWave bw{};
+    bool wf_ready = false;
     ~jr_batch() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
@@ -518,6 +529,13 @@ struct jr_batch {
         cudaFree(px_off);
         cudaFree(cursor);
         cudaFree(items);
+        cudaFree(m_nodes);
+        cudaFree(m_tris);
+        cudaFree(m_mats);
+        cudaFree(roots);
+        cudaFree(chain_off);
+        cudaFree(wf_items);
+        cudaFree(fetch);
     }
 };
 
@@ -581,10 +599,127 @@ void after_launch(jr_batch* b, uint32_t n_steps) {
     }
 }
 
+// Set up the batched wavefront once: every set's wavefront buffers (and the
+// device descriptors that point at them), the merged scene (each distinct
+// scene copied once and rebased), the sets' roots in it, the chain prefix
+// sums and the step launches' work items.
+jr_status prepare_wave(jr_batch* b, cudaStream_t st) {
+    if (b->wf_ready) return JR_OK;
+    const uint32_t S = (uint32_t)b->sets.size();
+    if (S > kBatchMaxSets)
+        return fail(JR_ERR_INVALID_ARG, "jr_batch: the batched wavefront takes at most " +
+                                            std::to_string(kBatchMaxSets) + " sets");
+    for (jr_chains* c : b->sets) {
+        jr_status a = ensure_wavefront(c, st);
+        if (a != JR_OK) return a;
+    }
+    std::vector<BatchEntry> h(S);
+    std::vector<const jr_scene*> uniq;
+    std::vector<uint64_t> noff, toff, moff;  // per distinct scene
+    uint64_t nn = 0, nt = 0, nm = 0;
+    std::vector<int> root(S);
+    std::vector<uint64_t> coff(S + 1, 0);
+    std::vector<BatchItem> items;
+    for (uint32_t k = 0; k < S; ++k) {
+        const jr_chains* c = b->sets[k];
+        h[k].s = c->scene->view;
+        h[k].c = c->view;
+        h[k].step = b->dev_steps[k];
+        size_t u = 0;
+        while (u < uniq.size() && uniq[u] != c->scene) ++u;
+        if (u == uniq.size()) {
+            uniq.push_back(c->scene);
+            noff.push_back(nn);
+            toff.push_back(nt);
+            moff.push_back(nm);
+            nn += (uint64_t)c->scene->view.n_nodes;
+            nt += c->scene->info.n_tris;
+            nm += c->scene->info.n_materials;
+        }
+        root[k] = rebase_ref(c->scene->view.root, (int)noff[u], (int)toff[u]);
+        coff[k + 1] = coff[k] + c->view.n;
+        for (uint64_t beg = 0; beg < c->view.n; beg += 128)
+            items.push_back(BatchItem{k, (uint32_t)beg, (uint32_t)std::min<uint64_t>(beg + 128, c->view.n)});
+    }
+    if (nt >= (1ull << 28) || nn >= (1ull << 31) || coff[S] >= (1ull << 31))
+        return fail(JR_ERR_INVALID_ARG, "jr_batch: the merged scene or the chain count is too large for the "
+                                        "batched wavefront (2^28 triangles, 2^31 nodes or chains)");
+    const char* who = "jr_batch (batched wavefront set-up)";
+    JR_CUDA(dev_alloc(&b->m_nodes, std::max<uint64_t>(nn, 1)), who);
+    JR_CUDA(dev_alloc(&b->m_tris, std::max<uint64_t>(nt, 1)), who);
+    JR_CUDA(dev_alloc(&b->m_mats, std::max<uint64_t>(nm, 1)), who);
+    JR_CUDA(dev_alloc(&b->roots, S), who);
+    JR_CUDA(dev_alloc(&b->chain_off, S + 1), who);
+    JR_CUDA(dev_alloc(&b->wf_items, std::max<size_t>(items.size(), 1)), who);
+    JR_CUDA(dev_alloc(&b->fetch, 1), who);
+    for (size_t u = 0; u < uniq.size(); ++u) {
+        const jr_scene* sc = uniq[u];
+        const uint32_t n_nodes = (uint32_t)sc->view.n_nodes, n_tris = sc->info.n_tris,
+                       n_mats = sc->info.n_materials;
+        if (n_nodes)
+            JR_CUDA(cudaMemcpyAsync(b->m_nodes + noff[u], sc->nodes, sizeof(Bvh4Node) * n_nodes,
+                                    cudaMemcpyDeviceToDevice, st),
+                    who);
+        if (n_tris)
+            JR_CUDA(cudaMemcpyAsync(b->m_tris + toff[u], sc->tris, sizeof(TriRecord) * n_tris,
+                                    cudaMemcpyDeviceToDevice, st),
+                    who);
+        if (n_mats)
+            JR_CUDA(cudaMemcpyAsync(b->m_mats + moff[u], sc->mats, sizeof(Material) * n_mats,
+                                    cudaMemcpyDeviceToDevice, st),
+                    who);
+        JR_CUDA(launch_rebase_scene(b->m_nodes + noff[u], n_nodes, b->m_tris + toff[u], n_tris, (int)noff[u],
+                                    (int)toff[u], (int)moff[u], st),
+                who);
+    }
+    JR_CUDA(cudaMemcpyAsync(b->entries, h.data(), sizeof(BatchEntry) * S, cudaMemcpyHostToDevice, st), who);
+    JR_CUDA(cudaMemcpyAsync(b->roots, root.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st), who);
+    JR_CUDA(cudaMemcpyAsync(b->chain_off, coff.data(), sizeof(uint64_t) * (S + 1), cudaMemcpyHostToDevice, st), who);
+    if (!items.empty())
+        JR_CUDA(cudaMemcpyAsync(b->wf_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
+                                st),
+                who);
+    JR_CUDA(cudaStreamSynchronize(st), who);
+    BatchWave& bw = b->bw;
+    bw.merged = SceneView{};
+    bw.merged.nodes = b->m_nodes;
+    bw.merged.tris = b->m_tris;
+    bw.merged.mats = b->m_mats;
+    bw.merged.root = kNoChild;
+    bw.merged.n_nodes = (int)nn;
+    bw.roots = b->roots;
+    bw.chain_off = b->chain_off;
+    bw.items = b->wf_items;
+    bw.n_sets = S;
+    bw.n_items = (uint32_t)items.size();
+    bw.fetch = b->fetch;
+    long long blocks = 0;
+    JR_CUDA(batch_wavefront_grid(&blocks), who);
+    b->wf_ready = true;
+    return JR_OK;
+}
+
+// Enqueue one batch advance (no allocation, so it can be captured): the
+// megakernel launch, or the batched wavefront's launches; then the fold,
+// which also moves every set's device step index on by n_steps.
+cudaError_t enqueue_batch(jr_batch* b, uint32_t n_steps, cudaStream_t st) {
+    const uint32_t S = (uint32_t)b->sets.size();
+    if (b->block == 0) {
+        cudaError_t e = launch_batch_wavefront(b->bw, b->entries, n_steps, st);
+        if (e != cudaSuccess) return e;
+        return launch_batch(b->entries, b->items, 0, b->px_off, S, b->total_px, b->cursor, b->max_dim, 128,
+                            n_steps, st);
+    }
+    return launch_batch(b->entries, b->items, b->n_items, b->px_off, S, b->total_px, b->cursor, b->max_dim, b->block,
+                        n_steps, st);
+}
+
 jr_status batch_launch(jr_batch* b, uint32_t n_steps, cudaStream_t st, const char* who) {
-    JR_CUDA(launch_batch(b->entries, b->items, b->n_items, b->px_off, (uint32_t)b->sets.size(), b->total_px,
-                         b->cursor, b->max_dim, b->block, n_steps, st),
-            who);
+    if (b->block == 0) {
+        jr_status a = prepare_wave(b, st);
+        if (a != JR_OK) return a;
+    }
+    JR_CUDA(enqueue_batch(b, n_steps, st), who);
     return JR_OK;
 }
 
@@ -649,8 +784,13 @@ void jr_batch_destroy(jr_batch* batch) { delete batch; }
 
 jr_status jr_batch_set_block(jr_batch* b, uint32_t block) {
     if (!b) return fail(JR_ERR_INVALID_ARG, "jr_batch_set_block: null batch");
+    if (block == JR_BATCH_WAVEFRONT) {
+        b->block = 0;
+        return JR_OK;
+    }
     if (block < 32 || block > 256 || block % 32 != 0)
-        return fail(JR_ERR_INVALID_ARG, "jr_batch_set_block: block must be a multiple of 32 in [32, 256]");
+        return fail(JR_ERR_INVALID_ARG,
+                    "jr_batch_set_block: block must be a multiple of 32 in [32, 256], or JR_BATCH_WAVEFRONT");
     return build_items(b, (int)block, nullptr);
 }
 
@@ -669,6 +809,7 @@ jr_status jr_batch_advance_graph(jr_batch* b, uint32_t n_steps, void* stream) {
     if (n_steps == 0) return JR_OK;
     cudaStream_t st = (cudaStream_t)stream;
     jr_status r = sync_steps(b, st);
+    if (r == JR_OK && b->block == 0) r = prepare_wave(b, st);
     if (r != JR_OK) return r;
     if (!b->exec || b->graph_steps != n_steps || b->graph_block != b->block) {
         if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -679,8 +820,7 @@ jr_status jr_batch_advance_graph(jr_batch* b, uint32_t n_steps, void* stream) {
         JR_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "jr_batch_advance_graph");
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t el = launch_batch(b->entries, b->items, b->n_items, b->px_off, (uint32_t)b->sets.size(),
-                                          b->total_px, b->cursor, b->max_dim, b->block, n_steps, cap);
+            cudaError_t el = enqueue_batch(b, n_steps, cap);
             e = cudaStreamEndCapture(cap, &b->graph);
             if (e == cudaSuccess) e = el;
         }
@@ -703,15 +843,21 @@ jr_status jr_batch_advance_graph(jr_batch* b, uint32_t n_steps, void* stream) {
 jr_status jr_batch_autotune(jr_batch* b, uint32_t probe_steps, void* stream, jr_tune_report* out) {
     if (!b || !out || probe_steps == 0) return fail(JR_ERR_INVALID_ARG, "jr_batch_autotune: bad argument");
     cudaStream_t st = (cudaStream_t)stream;
-    const uint32_t cands[] = {32, 64, 128, 256};
+    const uint32_t cands[] = {32, 64, 128, 256, JR_BATCH_WAVEFRONT};
+    const uint32_t n_cands = b->sets.size() <= kBatchMaxSets ? 5 : 4;
     jr_tune_report rep{};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     JR_CUDA(cudaEventCreate(&e0), "jr_batch_autotune");
     JR_CUDA(cudaEventCreate(&e1), "jr_batch_autotune");
     double best = INFINITY;
     jr_status r = JR_OK;
-    for (uint32_t q = 0; q < 4 && r == JR_OK; ++q) {
-        r = build_items(b, (int)cands[q], st);
+    for (uint32_t q = 0; q < n_cands && r == JR_OK; ++q) {
+        if (cands[q] == JR_BATCH_WAVEFRONT) {
+            b->block = 0;
+            r = prepare_wave(b, st);  // one-time set-up, outside the timed probe
+        } else {
+            r = build_items(b, (int)cands[q], st);
+        }
         if (r == JR_OK) r = sync_steps(b, st);
         if (r != JR_OK) break;
         cudaError_t e;
@@ -740,8 +886,12 @@ jr_status jr_batch_autotune(jr_batch* b, uint32_t probe_steps, void* stream, jr_
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (r != JR_OK) return r;
-    r = build_items(b, (int)rep.best_block, st);
-    if (r != JR_OK) return r;
+    if (rep.best_block == JR_BATCH_WAVEFRONT) {
+        b->block = 0;
+    } else {
+        r = build_items(b, (int)rep.best_block, st);
+        if (r != JR_OK) return r;
+    }
     *out = rep;
     return JR_OK;
 }

@@ -96,7 +96,7 @@ struct Trav {
     int oct;            // ray octant: bit a set when the direction's axis-a component is negative
 };
 
-__device__ __forceinline__ void trav_begin(const SceneView& s, Trav& r, float3 o, float3 d) {
+__device__ __forceinline__ void trav_begin_at(Trav& r, float3 o, float3 d, int root) {
     r.o = o;
     r.d = d;
     const float dx = fabsf(d.x) < 1e-20f ? copysignf(1e-20f, d.x) : d.x;
@@ -112,9 +112,12 @@ __device__ __forceinline__ void trav_begin(const SceneView& s, Trav& r, float3 o
     r.tb = INFINITY;
     r.best = -1;
     r.best_id = INT32_MAX;
-    r.ref = s.root;
+    r.ref = root;
     r.sp = 0;
     r.visits = 0;
+}
+__device__ __forceinline__ void trav_begin(const SceneView& s, Trav& r, float3 o, float3 d) {
+    trav_begin_at(r, o, d, s.root);
 }
 
 // Order two (distance, ref) pairs so that the nearer comes first.

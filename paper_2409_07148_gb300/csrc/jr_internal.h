@@ -135,6 +135,36 @@ struct BatchItem {
     uint32_t set, begin, end;
 };
 
+// Batched wavefront (jr_wavefront.cu): the sets of a batch advance in shared
+// step and path launches over one merged device scene.  rebase_ref moves a
+// node child ref of a scene whose nodes and triangles were placed at node_off,
+// tri_off in the merged arrays.
+constexpr uint32_t kBatchMaxSets = 1024;
+__host__ __device__ inline int rebase_ref(int r, int node_off, int tri_off) {
+    if (r == kNoChild) return r;
+    if (r >= 0) return r + node_off;
+    const int enc = ~r;  // (first << 3) | (count - 1)
+    return ~((((enc >> 3) + tri_off) << 3) | (enc & 7));
+}
+struct BatchWave {
+    SceneView merged;           // every set's scene; root and camera unused
+    const int* roots;           // [n_sets] each set's root ref in the merged scene
+    const uint64_t* chain_off;  // [n_sets + 1] prefix sums of the sets' chain counts
+    const BatchItem* items;     // [n_items] work items of 128 chains for the step launches
+    uint32_t n_sets = 0, n_items = 0;
+    unsigned int* fetch;        // the path launches' item cursor
+};
+// Rebase one scene's nodes and triangles, already copied into the
+// merged arrays (refs via rebase_ref, material indices + mat_off).
+cudaError_t launch_rebase_scene(Bvh4Node* nodes, uint32_t n_nodes, TriRecord* tris, uint32_t n_tris, int node_off,
+                                int tri_off, int mat_off, cudaStream_t st);
+// The batched path kernel's persistent grid (set up once per device; call it
+// outside stream capture before the first launch_batch_wavefront).
+cudaError_t batch_wavefront_grid(long long* blocks);
+// n_steps batched wavefront steps of every set (step indices entries[q].step + k),
+// ending with the closing step launch; the caller folds afterwards.
+cudaError_t launch_batch_wavefront(const BatchWave& bw, BatchEntry* entries, uint32_t n_steps, cudaStream_t st);
+
 // One-time launch set-up per device (an opt-in to large dynamic shared
 // memory, an occupancy-derived grid size), cached by device id: get() runs
 // init(device, &value) for the current device on first use, under a lock, and

@@ -77,140 +77,152 @@ __device__ __forceinline__ void count_and_flush(uint32_t nJ, uint32_t nL, uint32
 // Chains still in a tour after the step are counted in qcount[kQActive].
 // Outside a drain every chain is traced, so the path queue is the identity
 // (chain j is entry j) and is not written; a drain step writes it.
-__global__ void __launch_bounds__(128, 12) wf_step_kernel(ChainView c, uint64_t step, int finish, int begin,
-                                                      int mode) {
-    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    const bool valid = i < c.n;
+//
+// step_chain is one chain's part (the body of the step kernel and of the
+// batched step kernel).  traced: the candidate is traced this step;
+// to_sample: it is a flow draw; active: in a drain, the tour goes on.
+__device__ __forceinline__ void step_chain(const ChainView& c, uint64_t i, uint64_t step, bool finish, bool begin,
+                                           int mode, uint32_t& nJ, uint32_t& nL, uint32_t& nA, unsigned& status,
+                                           bool& traced, bool& to_sample, bool& active) {
     const int D = (int)c.dim;
     const uint64_t n = c.n;
     const WaveView& w = c.wf;
     const bool has_flow = c.flow.D != 0;
     const bool restart = mode == kModeRestart, drain = mode == kModeDrain;
+    // Every load the step needs is issued here, before any store: the film
+    // point of the current state is read from both buffers, so that no
+    // load waits for the parity byte.
+    uint8_t par = w.par[i];
+    float Fr = c.fpu[0 * n + i], Fg = c.fpu[1 * n + i], Fb = c.fpu[2 * n + i];
+    float p = c.fpu[3 * n + i], u = c.fpu[4 * n + i];
+    const float ua = finish ? w.ua[i] : 0.0f;
+    const float4 pf = finish ? w.fy[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float xs0 = 0.f, xs1 = 0.f, ys0 = 0.f, ys1 = 0.f;
+    if (begin) {
+        xs0 = c.x[i];
+        xs1 = c.x[n + i];
+        ys0 = w.y[i];
+        ys1 = w.y[n + i];
+    }
+    const bool was_done = drain && w.done[i];
+    if (finish && !(drain && ua == -2.0f)) {
+        const float3 Fy = finite_or_zero(f3(pf.x, pf.y, pf.z), status);
+        const float py = lum(Fy);
+        bool accept;
+        if (restart) {     // a restart: the new tour's start, not a regeneration
+            accept = true;
+            w.done[i] = 0;
+        } else if (ua >= 0.0f) {  // local branch: MH acceptance, U < min(1, p(y)/p(x))
+            accept = ua * p < py;
+            nL++;
+            nA += accept;
+        } else {           // regeneration: the candidate is the new tour's start
+            accept = true;
+            nJ++;
+        }
+        if (accept) {
+            par ^= 1;
+            Fr = Fy.x;
+            Fg = Fy.y;
+            Fb = Fy.z;
+            p = py;
+            u = has_flow && py > 0.0f ? w.uy[i] : 1.0f;
+            c.fpu[0 * n + i] = Fr;
+            c.fpu[1 * n + i] = Fg;
+            c.fpu[2 * n + i] = Fb;
+            c.fpu[3 * n + i] = p;
+            c.fpu[4 * n + i] = u;
+        }
+    }
+    float* cur = par ? w.y : c.x;
+    float* cand = par ? c.x : w.y;
+    if (begin && was_done) {  // finished its tour during this drain
+        w.ua[i] = -2.0f;
+        traced = false;
+    } else if (begin) {
+        const uint32_t chain = c.chain_offset + (uint32_t)i;
+        const uint32_t tag = restart ? kTagRestart : kTagStep;
+        const uint4 r0 = draw(c.seed, tag, 0, chain, step);
+        const float E1 = -logf(1.0f - u01(r0.x));
+        const float E2 = -logf(1.0f - u01(r0.y));
+        const float Ua = u01(r0.z);
+        const float t2 = p > 0.0f ? E2 * p / (c.c_tilde * u) : 0.0f;
+        const bool local = !restart && E1 < t2;  // a tie goes to the killing branch
+        float dt = local ? E1 : t2;
+        if (c.flags & JR_FLAG_RAO_BLACKWELL) dt = p > 0.0f ? p / (p + c.c_tilde * u) : 0.0f;
+        if (restart) dt = 0.0f;
+        const bool use_flow = has_flow && !local && u01(r0.w) < c.flow.beta;
+        to_sample = use_flow;
+        const float x0 = par ? ys0 : xs0, x1 = par ? ys1 : xs1;  // = cur[i], cur[n + i]
+        if (dt > 0.0f && p > 0.0f) {
+            uint32_t px = min((uint32_t)((double)x0 * (double)c.width), c.width - 1);
+            uint32_t py = min((uint32_t)((double)x1 * (double)c.height), c.height - 1);
+            const float wgt = c.c_tilde * dt * ((float)c.width * (float)c.height) / p;
+            atomicAdd(c.fb + py * c.width + px, make_float4(wgt * Fr, wgt * Fg, wgt * Fb, dt));
+        }
+        w.ua[i] = local ? Ua : use_flow ? -3.0f : -1.0f;
+        if (drain && !local) {  // the tour ends here; no new tour in a drain
+            nJ++;
+            w.done[i] = 1;
+            w.ua[i] = -2.0f;
+            traced = false;
+            to_sample = false;
+        }
+        active = drain && local;
+        for (int b = 0; traced && 4 * b < D; ++b) {
+            const uint4 r = draw(c.seed, tag, (uint32_t)(b + 1), chain, step);
+            const uint64_t o0 = (uint64_t)(4 * b) * n + i;
+            float v0, v1, v2 = 0.f, v3 = 0.f;
+            const bool two = 4 * b + 2 < D;
+            if (local) {
+                float sn, cs;
+                float R = sqrtf(-2.0f * logf(1.0f - u01(r.x)));
+                sincospif(2.0f * u01(r.y), &sn, &cs);
+                v0 = wrap01((b == 0 ? x0 : cur[o0]) + c.sigma * R * cs);
+                v1 = wrap01((b == 0 ? x1 : cur[o0 + n]) + c.sigma * R * sn);
+                if (two) {
+                    R = sqrtf(-2.0f * logf(1.0f - u01(r.z)));
+                    sincospif(2.0f * u01(r.w), &sn, &cs);
+                    v2 = wrap01(cur[o0 + 2 * n] + c.sigma * R * cs);
+                    v3 = wrap01(cur[o0 + 3 * n] + c.sigma * R * sn);
+                }
+            } else {
+                v0 = u01(r.x);
+                v1 = u01(r.y);
+                v2 = u01(r.z);
+                v3 = u01(r.w);
+            }
+            cand[o0] = v0;
+            cand[o0 + n] = v1;
+            if (two) {
+                cand[o0 + 2 * n] = v2;
+                cand[o0 + 3 * n] = v3;
+            }
+            if (b == 0) {  // the path's start record
+                float2* f = reinterpret_cast<float2*>(w.fy + i);
+                f[0] = make_float2(v0, v1);
+                f[1] = make_float2(v2, v3);
+            }
+        }
+    } else if (par) {
+        for (int dd = 0; dd < D; ++dd) c.x[(uint64_t)dd * n + i] = w.y[(uint64_t)dd * n + i];
+        par = 0;
+    }
+    w.par[i] = par;
+}
+
+__global__ void __launch_bounds__(128, 12) wf_step_kernel(ChainView c, uint64_t step, int finish, int begin,
+                                                          int mode) {
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const bool valid = i < c.n;
+    const uint64_t n = c.n;
+    const WaveView& w = c.wf;
+    const bool has_flow = c.flow.D != 0;
+    const bool drain = mode == kModeDrain;
     uint32_t nJ = 0, nL = 0, nA = 0;
     unsigned status = 0;
     bool to_sample = false, traced = valid, active = false;
-    if (valid) {
-        // Every load the step needs is issued here, before any store: the film
-        // point of the current state is read from both buffers, so that no
-        // load waits for the parity byte.
-        uint8_t par = w.par[i];
-        float Fr = c.fpu[0 * n + i], Fg = c.fpu[1 * n + i], Fb = c.fpu[2 * n + i];
-        float p = c.fpu[3 * n + i], u = c.fpu[4 * n + i];
-        const float ua = finish ? w.ua[i] : 0.0f;
-        const float4 pf = finish ? w.fy[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float xs0 = 0.f, xs1 = 0.f, ys0 = 0.f, ys1 = 0.f;
-        if (begin) {
-            xs0 = c.x[i];
-            xs1 = c.x[n + i];
-            ys0 = w.y[i];
-            ys1 = w.y[n + i];
-        }
-        const bool was_done = drain && w.done[i];
-        if (finish && !(drain && ua == -2.0f)) {
-            const float3 Fy = finite_or_zero(f3(pf.x, pf.y, pf.z), status);
-            const float py = lum(Fy);
-            bool accept;
-            if (restart) {     // a restart: the new tour's start, not a regeneration
-                accept = true;
-                w.done[i] = 0;
-            } else if (ua >= 0.0f) {  // local branch: MH acceptance, U < min(1, p(y)/p(x))
-                accept = ua * p < py;
-                nL++;
-                nA += accept;
-            } else {           // regeneration: the candidate is the new tour's start
-                accept = true;
-                nJ++;
-            }
-            if (accept) {
-                par ^= 1;
-                Fr = Fy.x;
-                Fg = Fy.y;
-                Fb = Fy.z;
-                p = py;
-                u = has_flow && py > 0.0f ? w.uy[i] : 1.0f;
-                c.fpu[0 * n + i] = Fr;
-                c.fpu[1 * n + i] = Fg;
-                c.fpu[2 * n + i] = Fb;
-                c.fpu[3 * n + i] = p;
-                c.fpu[4 * n + i] = u;
-            }
-        }
-        float* cur = par ? w.y : c.x;
-        float* cand = par ? c.x : w.y;
-        if (begin && was_done) {  // finished its tour during this drain
-            w.ua[i] = -2.0f;
-            traced = false;
-        } else if (begin) {
-            const uint32_t chain = c.chain_offset + (uint32_t)i;
-            const uint32_t tag = restart ? kTagRestart : kTagStep;
-            const uint4 r0 = draw(c.seed, tag, 0, chain, step);
-            const float E1 = -logf(1.0f - u01(r0.x));
-            const float E2 = -logf(1.0f - u01(r0.y));
-            const float Ua = u01(r0.z);
-            const float t2 = p > 0.0f ? E2 * p / (c.c_tilde * u) : 0.0f;
-            const bool local = !restart && E1 < t2;  // a tie goes to the killing branch
-            float dt = local ? E1 : t2;
-            if (c.flags & JR_FLAG_RAO_BLACKWELL) dt = p > 0.0f ? p / (p + c.c_tilde * u) : 0.0f;
-            if (restart) dt = 0.0f;
-            const bool use_flow = has_flow && !local && u01(r0.w) < c.flow.beta;
-            to_sample = use_flow;
-            const float x0 = par ? ys0 : xs0, x1 = par ? ys1 : xs1;  // = cur[i], cur[n + i]
-            if (dt > 0.0f && p > 0.0f) {
-                uint32_t px = min((uint32_t)((double)x0 * (double)c.width), c.width - 1);
-                uint32_t py = min((uint32_t)((double)x1 * (double)c.height), c.height - 1);
-                const float wgt = c.c_tilde * dt * ((float)c.width * (float)c.height) / p;
-                atomicAdd(c.fb + py * c.width + px, make_float4(wgt * Fr, wgt * Fg, wgt * Fb, dt));
-            }
-            w.ua[i] = local ? Ua : use_flow ? -3.0f : -1.0f;
-            if (drain && !local) {  // the tour ends here; no new tour in a drain
-                nJ++;
-                w.done[i] = 1;
-                w.ua[i] = -2.0f;
-                traced = false;
-                to_sample = false;
-            }
-            active = drain && local;
-            for (int b = 0; traced && 4 * b < D; ++b) {
-                const uint4 r = draw(c.seed, tag, (uint32_t)(b + 1), chain, step);
-                const uint64_t o0 = (uint64_t)(4 * b) * n + i;
-                float v0, v1, v2 = 0.f, v3 = 0.f;
-                const bool two = 4 * b + 2 < D;
-                if (local) {
-                    float sn, cs;
-                    float R = sqrtf(-2.0f * logf(1.0f - u01(r.x)));
-                    sincospif(2.0f * u01(r.y), &sn, &cs);
-                    v0 = wrap01((b == 0 ? x0 : cur[o0]) + c.sigma * R * cs);
-                    v1 = wrap01((b == 0 ? x1 : cur[o0 + n]) + c.sigma * R * sn);
-                    if (two) {
-                        R = sqrtf(-2.0f * logf(1.0f - u01(r.z)));
-                        sincospif(2.0f * u01(r.w), &sn, &cs);
-                        v2 = wrap01(cur[o0 + 2 * n] + c.sigma * R * cs);
-                        v3 = wrap01(cur[o0 + 3 * n] + c.sigma * R * sn);
-                    }
-                } else {
-                    v0 = u01(r.x);
-                    v1 = u01(r.y);
-                    v2 = u01(r.z);
-                    v3 = u01(r.w);
-                }
-                cand[o0] = v0;
-                cand[o0 + n] = v1;
-                if (two) {
-                    cand[o0 + 2 * n] = v2;
-                    cand[o0 + 3 * n] = v3;
-                }
-                if (b == 0) {  // the path's start record
-                    float2* f = reinterpret_cast<float2*>(w.fy + i);
-                    f[0] = make_float2(v0, v1);
-                    f[1] = make_float2(v2, v3);
-                }
-            }
-        } else if (par) {
-            for (int dd = 0; dd < D; ++dd) c.x[(uint64_t)dd * n + i] = w.y[(uint64_t)dd * n + i];
-            par = 0;
-        }
-        w.par[i] = par;
-    }
+    if (valid) step_chain(c, i, step, finish, begin, mode, nJ, nL, nA, status, traced, to_sample, active);
     if (begin) {
         if (drain) enqueue(traced, (uint32_t)i, w.queue, w.qcount + 0);
         if (has_flow) enqueue(to_sample, (uint32_t)i, w.fq + n, w.qcount + kQFlowSample);
@@ -368,6 +380,171 @@ __global__ void __launch_bounds__(128) wf_path_kernel(SceneView s, ChainView c, 
     if (lane == 0 && status) atomicOr(c.status, status);
 }
 
+// ---------------------------------------------------------------------------
+// Batched wavefront: the chain sets of a batch (one scene each) advance in the
+// same step and path launches.  Their scenes are merged into one device scene
+// (nodes, triangles and materials concatenated, with child, leaf and material
+// indices rebased), so the traversal's pointers are uniform over a warp and a
+// lane keeps only its set, the set's chain buffers and its root.
+
+// Rebase one scene's nodes and triangles after they were copied into the
+// merged arrays at offsets node_off, tri_off, mat_off.
+__global__ void rebase_scene_kernel(Bvh4Node* nodes, uint32_t n_nodes, TriRecord* tris, uint32_t n_tris,
+                                    int node_off, int tri_off, int mat_off) {
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n_nodes) {
+        int4 r = nodes[j].refs;
+        int* rr = &r.x;
+        for (int q = 0; q < 4; ++q) rr[q] = rebase_ref(rr[q], node_off, tri_off);
+        nodes[j].refs = r;
+    }
+    if (j < n_tris) tris[j].e1_mat.w = __int_as_float(__float_as_int(tris[j].e1_mat.w) + mat_off);
+}
+
+// The step kernel over every set: one block per work item (128 chains of one
+// set); the set's step index is entries[set].step + k.
+__global__ void __launch_bounds__(128) wf_batch_step_kernel(const BatchEntry* entries, const BatchItem* items,
+                                                                uint32_t k, int finish, int begin) {
+    const BatchItem it = items[blockIdx.x];
+    const BatchEntry& e = entries[it.set];
+    const uint64_t i = it.begin + threadIdx.x;
+    uint32_t nJ = 0, nL = 0, nA = 0;
+    unsigned status = 0;
+    bool traced = true, to_sample = false, active = false;
+    if (i < it.end)
+        step_chain(e.c, i, e.step + k, finish, begin, kModeStep, nJ, nL, nA, status, traced, to_sample, active);
+    count_and_flush(nJ, nL, nA, status, e.c);
+}
+
+// The path kernel over every set's candidates: item j of the launch is chain
+// j - off[q] of set q, off[q] <= j < off[q + 1] (off = the sets' chain
+// prefix sums, copied to shared memory).  The lane logic is the single-set
+// path kernel's; per lane it keeps the set, its depth, the candidate buffer
+// and its stride, and starts each ray at the set's root in the merged scene.
+__global__ void __launch_bounds__(128, 7) wf_batch_path_kernel(SceneView m, const BatchEntry* entries, const int* roots,
+                                                            const uint64_t* chain_off, uint32_t n_sets,
+                                                            unsigned int* fetch) {
+    extern __shared__ uint64_t off_s[];
+    for (uint32_t q = threadIdx.x; q <= n_sets; q += blockDim.x) off_s[q] = chain_off[q];
+    __syncthreads();
+    const unsigned count = (unsigned)off_s[n_sets];
+    if ((uint64_t)blockIdx.x * blockDim.x >= count) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned status = 0;
+    Work wk;
+    Trav r;
+    int stack[kStackSize];
+    uint32_t state = kIdle, i = 0, set = 0, nst = 0;
+    int v = 0, leaf = kSentinel, depth = 0;
+    bool failed = false, drained = false;
+    float3 T = f3(1.f, 1.f, 1.f), F = f3(0.f, 0.f, 0.f);
+    float u1 = 0.f, u2 = 0.f;       // the coordinates of vertex v
+    const float* cand = nullptr;     // the candidate's buffer ([D][nst])
+    while (true) {
+        // shade the waiting lanes as a batch
+        const unsigned waiting = __ballot_sync(kFull, state == kWaitShade);
+        const unsigned tracing = __ballot_sync(kFull, state == kTraverse);
+        if (waiting && (__popc(waiting) >= kShadeBatch || tracing == 0)) {
+            if (state == kWaitShade) {
+                bool live = false;
+                if (r.best >= 0) {
+                    float3 o = r.o, d = r.d;
+                    live = shade_vertex(m, r.best, r.tb, v, depth, v < depth ? u1 : 0.f, v < depth ? u2 : 0.f, o,
+                                        d, T, F);
+                    if (live) {
+                        ++v;
+                        trav_begin_at(r, o, d, roots[set]);
+                        state = kTraverse;
+                        if (v < depth) {
+                            u1 = cand[(uint64_t)(2 + 2 * v) * nst + i];
+                            u2 = cand[(uint64_t)(3 + 2 * v) * nst + i];
+                        }
+                    }
+                }
+                if (!live) {
+                    const ChainView& c = entries[set].c;
+                    c.wf.fy[i] = make_float4(F.x, F.y, F.z, 0.f);
+                    if (status) {
+                        atomicOr(c.status, status);
+                        status = 0;
+                    }
+                    state = kIdle;
+                }
+            }
+        }
+        // take new paths for idle lanes
+        const unsigned idle = __ballot_sync(kFull, state == kIdle);
+        if (!drained && idle && (__popc(idle) >= kRefill || idle == kFull)) {
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(fetch, (unsigned)__popc(idle));
+            base = __shfl_sync(kFull, base, 0);
+            if (base + (unsigned)__popc(idle) >= count) drained = true;
+            if (state == kIdle) {
+                const unsigned j = base + __popc(idle & lt);
+                if (j < count) {
+                    uint32_t lo = 0, hi = n_sets;  // the set whose chain range holds j
+                    while (hi - lo > 1) {
+                        const uint32_t mid = (lo + hi) / 2;
+                        if (off_s[mid] <= j) lo = mid;
+                        else hi = mid;
+                    }
+                    set = lo;
+                    i = j - (uint32_t)off_s[lo];
+                    const BatchEntry& e = entries[set];
+                    const float4 y = e.c.wf.fy[i];
+                    cand = e.c.wf.par[i] ? e.c.x : e.c.wf.y;
+                    nst = (uint32_t)e.c.n;
+                    depth = (int)e.c.depth;
+                    u1 = y.z;
+                    u2 = y.w;
+                    float3 o, d;
+                    camera_ray(e.s, y.x, y.y, o, d);
+                    T = f3(1.f, 1.f, 1.f);
+                    F = f3(0.f, 0.f, 0.f);
+                    v = 0;
+                    const int root = roots[set];
+                    trav_begin_at(r, o, d, root);
+                    state = root != kSentinel ? kTraverse : kWaitShade;  // empty scene: a miss
+                }
+            }
+        }
+        if (!__any_sync(kFull, state != kIdle)) {
+            if (drained) break;
+            continue;
+        }
+        // one speculative while-while traversal round
+        const bool trav = state == kTraverse;
+        if (trav && leaf == kSentinel && r.ref < 0 && r.ref != kSentinel) {
+            leaf = r.ref;
+            r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
+        }
+        while (__any_sync(kFull, trav && leaf == kSentinel && r.ref >= 0)) {
+            if (trav && r.ref >= 0) {
+                if (!trav_node<false>(m, r, stack, status, wk)) {
+                    r.best = -1;
+                    r.ref = kSentinel;
+                    leaf = kSentinel;
+                    failed = true;
+                } else if (leaf == kSentinel && r.ref < 0 && r.ref != kSentinel) {
+                    leaf = r.ref;
+                    r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
+                }
+            }
+        }
+        if (trav) {
+            if (leaf != kSentinel) {
+                trav_test_leaf<false>(m, r, leaf, wk);
+                leaf = kSentinel;
+            }
+            if (failed || r.ref == kSentinel) {
+                state = kWaitShade;
+                failed = false;
+            }
+        }
+    }
+}
+
 inline unsigned grid_for(uint64_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 
 // The flow stages of a step (a chain's candidate lives in x when its parity
@@ -455,6 +632,48 @@ cudaError_t launch_wavefront(const SceneView& s, const ChainView& c, uint64_t st
     wf_step_kernel<<<G, 128, 0, st>>>(c, step_begin + n_steps, n_steps > 0, 0, mode);
     mark(KernelTimer::kStep);
     if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rebase_scene(Bvh4Node* nodes, uint32_t n_nodes, TriRecord* tris, uint32_t n_tris, int node_off,
+                                int tri_off, int mat_off, cudaStream_t st) {
+    const uint32_t n = n_nodes > n_tris ? n_nodes : n_tris;
+    if (n == 0) return cudaSuccess;
+    rebase_scene_kernel<<<grid_for(n, 256), 256, 0, st>>>(nodes, n_nodes, tris, n_tris, node_off, tri_off, mat_off);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_wavefront_grid(long long* blocks) {
+    static DeviceOnce once;  // per device: the batched path kernel's persistent grid
+    return once.get(
+        [](int dev, long long* v) {
+            int sms = 0, per_sm = 0;
+            cudaError_t r;
+            if ((r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+                (r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wf_batch_path_kernel, 128,
+                                                                   sizeof(uint64_t) * (kBatchMaxSets + 1))) !=
+                    cudaSuccess)
+                return r;
+            *v = (long long)sms * (per_sm > 0 ? per_sm : 1);
+            return cudaSuccess;
+        },
+        blocks);
+}
+
+cudaError_t launch_batch_wavefront(const BatchWave& bw, BatchEntry* entries, uint32_t n_steps, cudaStream_t st) {
+    long long blocks = 0;
+    cudaError_t e = batch_wavefront_grid(&blocks);
+    if (e != cudaSuccess) return e;
+    if (bw.n_items == 0) return cudaSuccess;
+    if (bw.n_sets == 0 || bw.n_sets > kBatchMaxSets) return cudaErrorInvalidValue;
+    const size_t shm = sizeof(uint64_t) * (bw.n_sets + 1);
+    for (uint32_t k = 0; k < n_steps; ++k) {
+        if ((e = cudaMemsetAsync(bw.fetch, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
+        wf_batch_step_kernel<<<bw.n_items, 128, 0, st>>>(entries, bw.items, k, k > 0, 1);
+        wf_batch_path_kernel<<<(unsigned)blocks, 128, shm, st>>>(bw.merged, entries, bw.roots, bw.chain_off,
+                                                                 bw.n_sets, bw.fetch);
+    }
+    wf_batch_step_kernel<<<bw.n_items, 128, 0, st>>>(entries, bw.items, n_steps, n_steps > 0, 0);
     return cudaGetLastError();
 }
 

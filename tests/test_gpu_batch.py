@@ -67,16 +67,48 @@ def test_autotune_and_interleaved_individual_advance(J):
     bat = _make(J)
     for _, _, c in ref:
         c.set_execution("mega")
-        c.advance(4 * 2 + 3 + 2)
+        c.advance(5 * 2 + 3 + 2)
     b = J.Batch([c for _, _, c in bat])
-    rep = b.autotune(2)                     # 4 candidates x 2 real steps
-    assert rep["best_block"] in (32, 64, 128, 256) and len(rep["ns_per_chain_step"]) == 4
+    rep = b.autotune(2)                     # 5 candidates (4 block sizes, the wavefront) x 2 real steps
+    assert rep["best_block"] in (0, 32, 64, 128, 256) and len(rep["ns_per_chain_step"]) == 5
     assert all(v > 0 for v in rep["ns_per_chain_step"].values())
     bat[2][2].advance(3)                    # one set moves on its own ...
     for k, (_, _, c) in enumerate(bat):     # ... the others catch up individually
         if k != 2:
             c.advance(3)
     b.advance_graph(2)                      # the batch picks up every set's step index
+    for (_, _, r), (_, _, c) in zip(ref, bat):
+        _compare(r, c)
+
+
+def _make_shared(J):
+    """SETS plus two more chain sets on the scenes of the first two (a
+    distinct scene is merged once and shared)."""
+    out = _make(J)
+    for k, seed in ((0, 11), (1, 12)):
+        sc, g, _ = out[k]
+        out.append((sc, g, J.Chains(g, sc.width, sc.height, sc.depth, 300, seed=seed, sigma=0.03)))
+    return out
+
+
+def test_batch_wavefront_equals_individual_wavefronts(J):
+    """The batched wavefront (every set in the same step and path launches,
+    over the merged scene) runs each set's chains as that set's own wavefront
+    advance does: the same states, and F, p, counters and images up to the
+    rounding of separately compiled kernels (a contraction into an FMA may
+    differ) and the order of the framebuffer's atomic sums."""
+    ref = _make_shared(J)
+    bat = _make_shared(J)
+    for _, _, c in ref:
+        c.set_execution("wave")
+        c.advance(5)
+        c.advance(6)
+        c.advance(6)
+    b = J.Batch([c for _, _, c in bat])
+    b.set_block(0)
+    b.advance(5)
+    b.advance_graph(6)
+    b.advance_graph(6)   # a replay continues the chains
     for (_, _, r), (_, _, c) in zip(ref, bat):
         _compare(r, c)
 
