@@ -43,9 +43,9 @@ SMS, FP32_LANES = 152, 128
 # dram__bytes_write.sum), the mean over 8 launches of an ncu capture of the
 # 2^18-chain case, scaled by 4 to the 2^20-chain workload (the paths of a
 # launch grow with the chains).  It stands only while the kernel sources still
-# hash to the values it was taken on (39.148 MB read + 0.299 MB written).
-PATH_TRAFFIC = {"bytes_per_launch": 4 * (39.148e6 + 0.299e6),
-                "sources": {"jr_wavefront.cu": "bad9a676191a953c", "jr_device.cuh": "2fb7c13b7652d2f8"},
+# hash to the values it was taken on (27.213 MB read + 0.208 MB written).
+PATH_TRAFFIC = {"bytes_per_launch": 4 * (27.213e6 + 0.208e6),
+                "sources": {"jr_wavefront.cu": "308961e060928716", "jr_device.cuh": "7b8dc478cc886c38"},
                 "summary": "profiles/path_kernel_cornell_spheres_512x512.md"}
 
 
