@@ -236,6 +236,8 @@ def run_caustic(args):
     taken off the clock.  The learned arm trains the flow on a snapshot of the
     chain states (weights p / (p + c~ u)) between epochs and regenerates from
     mu = beta mu_flow + (1 - beta) uniform in the next epoch."""
+    if args.ref_samples is None:
+        args.ref_samples = (1 << 37) if args.workload == "terrain" else (1 << 36)
     import torch
     from paper_2409_07148_gb300 import jr, scenes
     from paper_2409_07148_gb300.flowinit import init_flow_params
@@ -416,7 +418,8 @@ def main():
     ap.add_argument("--epoch", type=int, default=128, help="caustic workload: chain steps of the first epoch")
     ap.add_argument("--epoch-growth", type=float, default=1.25, help="caustic workload: epoch length factor")
     ap.add_argument("--epoch-max", type=int, default=1024, help="caustic workload: longest epoch (steps)")
-    ap.add_argument("--ref-samples", type=int, default=1 << 34, help="caustic workload: reference PT samples")
+    ap.add_argument("--ref-samples", type=int, default=None,
+                    help="caustic / terrain workload: reference PT samples (default 2^36 / 2^37)")
     ap.add_argument("--train-iters", type=int, default=25, help="caustic workload: Adam steps per epoch")
     ap.add_argument("--train-iters0", type=int, default=150, help="caustic workload: Adam steps in the first epochs")
     ap.add_argument("--warm-epochs", type=int, default=2)
