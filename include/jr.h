@@ -177,10 +177,12 @@ jr_status jr_set_block_size(jr_chains* chains, uint32_t block);
 /* Execution mode of jr_advance for this chain set (jr_advance_traced and
  * jr_advance_counted always use the megakernel):
  *   JR_EXEC_MEGAKERNEL  one thread per chain for the whole launch;
- *   JR_EXEC_WAVEFRONT   one launch per step plus one per bounce, over a queue
- *                       of live paths (better SIMD use for many chains; its
- *                       buffers, about (4 D + 66) bytes per chain, are
- *                       allocated by the first wavefront advance);
+ *   JR_EXEC_WAVEFRONT   a step launch over all chains and a persistent path
+ *                       launch per step; a lane traces whole paths and takes
+ *                       a new one from the step's queue when its path ends
+ *                       (better SIMD use for many chains with uneven path
+ *                       lengths; its buffers, about (4 D + 38) bytes per
+ *                       chain, are allocated by the first wavefront advance);
  *   JR_EXEC_AUTO        wavefront from 2^16 chains up, else the megakernel.
  * Both modes run the same per-chain arithmetic on the same Philox streams. */
 #define JR_EXEC_AUTO 0u
@@ -196,7 +198,7 @@ jr_status jr_set_execution(jr_chains* chains, uint32_t mode);
  * locks and (cudaFree) synchronise the whole device.
  *
  * It runs the wavefront launches of jr_advance (JR_EXEC_WAVEFRONT), with the
- * same results, but their scratch (second state buffer, live-path records and
+ * same results, but their scratch (second state buffer, F records and
  * queues) lives in one fixed device array inside the library, sized for at
  * most JR_STATIC_MAX_CHAINS chains of any depth: 10,027,264 bytes, which
  * every GPU that loads the library holds until the process exits.  The chain
