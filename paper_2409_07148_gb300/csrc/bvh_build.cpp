@@ -218,10 +218,13 @@ struct Builder {
         depth4 = 1 + sub_depth;
         Bvh4Node& q = out->nodes[me];
         float lo[3][4], hi[3][4];
+        // an empty slot gets the empty box (lo = +inf, hi = -inf): its entry
+        // distance is +inf and its exit distance -inf whatever the ray, so the
+        // slab test misses it without looking at the ref
         for (int j = 0; j < 4; ++j)
             for (int k = 0; k < 3; ++k) {
-                lo[k][j] = j < n ? kids[j].box.lo[k] : 0.0f;
-                hi[k][j] = j < n ? kids[j].box.hi[k] : 0.0f;
+                lo[k][j] = j < n ? kids[j].box.lo[k] : INFINITY;
+                hi[k][j] = j < n ? kids[j].box.hi[k] : -INFINITY;
             }
         q.lox = make_float4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
         q.hix = make_float4(hi[0][0], hi[0][1], hi[0][2], hi[0][3]);

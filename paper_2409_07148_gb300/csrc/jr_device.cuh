@@ -169,11 +169,7 @@ __device__ __forceinline__ bool trav_node(const SceneView& s, Trav& r, int* stac
     float t0 = slab(r, nx.x, fx.x, ny.x, fy.x, nz.x, fz.x);
     float t1 = slab(r, nx.y, fx.y, ny.y, fy.y, nz.y, fz.y);
     float t2 = slab(r, nx.z, fx.z, ny.z, fy.z, nz.z, fz.z);
-    float t3 = slab(r, nx.w, fx.w, ny.w, fy.w, nz.w, fz.w);
-    if (rf.x == kNoChild) t0 = INFINITY;
-    if (rf.y == kNoChild) t1 = INFINITY;
-    if (rf.z == kNoChild) t2 = INFINITY;
-    if (rf.w == kNoChild) t3 = INFINITY;
+    float t3 = slab(r, nx.w, fx.w, ny.w, fy.w, nz.w, fz.w);  // an empty slot's box misses (+inf)
     // 5-comparator sorting network on (distance, ref)
     cswap(t0, rf.x, t1, rf.y);
     cswap(t2, rf.z, t3, rf.w);

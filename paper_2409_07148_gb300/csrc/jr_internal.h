@@ -24,7 +24,9 @@ constexpr uint64_t kWavefrontMinChains = 1u << 16;  // JR_EXEC_AUTO picks the wa
 // 4-wide BVH node, 128 bytes (one L2 line): the boxes of up to 4 children,
 // one float4 per plane with child j in component j, then the child refs:
 // >= 0 inner node index; < 0 leaf = ~((first << 3) | (count - 1)); kNoChild
-// marks an empty slot (its box is never used).  The last 16 bytes are unused.
+// marks an empty slot, whose box is the empty box (lo = +inf, hi = -inf), so
+// that the slab test misses it.  pad.x holds the child count; the rest of the
+// last 16 bytes is unused.
 struct __align__(128) Bvh4Node {
     float4 lox, hix, loy, hiy, loz, hiz;
     int4 refs;
