@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <future>
 #include <numeric>
 
 #include "jr_internal.h"
@@ -38,9 +39,12 @@ struct Box {
     }
 };
 
+// A triangle's box and centroid, and its index; the build partitions these
+// records in place, so every pass reads them in order.
 struct Prim {
     Box box;
     float c[3];
+    uint32_t id;
 };
 
 // Binary node of the first pass: both children's (widened) boxes and refs.
@@ -49,15 +53,39 @@ struct BinNode {
     int ref[2];
 };
 
+// The output of a (sub)tree build: binary nodes and leaf triangle records in
+// depth-first order, refs relative to these arrays.
+struct Part {
+    std::vector<BinNode> bin;
+    std::vector<TriRecord> tris;
+    int max_depth = 0;
+};
+
+// Append part q after part p, moving q's refs by p's sizes; returns ref moved.
+// Appending a node's left and then its right part reproduces the order a
+// sequential depth-first build would give.
+int append_part(Part& p, Part& q, int ref) {
+    const int node_off = (int)p.bin.size(), tri_off = (int)p.tris.size();
+    for (BinNode& nd : q.bin)
+        for (int j = 0; j < 2; ++j) nd.ref[j] = rebase_ref(nd.ref[j], node_off, tri_off);
+    p.bin.insert(p.bin.end(), q.bin.begin(), q.bin.end());
+    p.tris.insert(p.tris.end(), q.tris.begin(), q.tris.end());
+    p.max_depth = std::max(p.max_depth, q.max_depth);
+    return rebase_ref(ref, node_off, tri_off);
+}
+
+// Subtrees of at least this many triangles, this close to the root, are
+// built on their own thread (the left one; the right one on the caller's).
+constexpr uint32_t kParallelMin = 8192;
+constexpr int kParallelDepth = 4;
+
 struct Builder {
     const float* verts;
     const uint32_t* tris;
     const uint32_t* tri_mat;
     std::vector<Prim> prims;
-    std::vector<uint32_t> idx;
-    HostBvh* out;
-    std::vector<BinNode> bin;
-    int max_depth_seen = 0;
+    std::vector<BinNode> bin;  // the binary tree, for collapse()
+    HostBvh* out;              // collapse() writes the 4-wide nodes here
 
     // Widen a box so that a FP32 slab test never rejects a box whose triangle
     // the ray/triangle test accepts (coordinates are rounded outward by a
@@ -71,14 +99,14 @@ struct Builder {
 
     Box range_box(uint32_t b, uint32_t e) const {
         Box r;
-        for (uint32_t i = b; i < e; ++i) r.grow(prims[idx[i]].box);
+        for (uint32_t i = b; i < e; ++i) r.grow(prims[i].box);
         return r;
     }
 
-    int make_leaf(uint32_t b, uint32_t e) {
-        uint32_t first = (uint32_t)out->tris.size();
+    int make_leaf(uint32_t b, uint32_t e, Part& out) {
+        uint32_t first = (uint32_t)out.tris.size();
         for (uint32_t i = b; i < e; ++i) {
-            uint32_t t = idx[i];
+            uint32_t t = prims[i].id;
             const float* v0 = verts + 3 * tris[3 * t];
             const float* v1 = verts + 3 * tris[3 * t + 1];
             const float* v2 = verts + 3 * tris[3 * t + 2];
@@ -90,52 +118,70 @@ struct Builder {
             r.v0_id = make_float4(v0[0], v0[1], v0[2], fid);
             r.e1_mat = make_float4(v1[0] - v0[0], v1[1] - v0[1], v1[2] - v0[2], fmat);
             r.e2 = make_float4(v2[0] - v0[0], v2[1] - v0[1], v2[2] - v0[2], 0.0f);
-            out->tris.push_back(r);
+            out.tris.push_back(r);
         }
         return ~(int)((first << 3) | (e - b - 1));
     }
 
-    // Returns the child ref of range [b, e).
-    int build(uint32_t b, uint32_t e, int depth) {
-        uint32_t n = e - b;
-        max_depth_seen = std::max(max_depth_seen, depth);
-        Box bounds = range_box(b, e);
-        Box cb;
-        for (uint32_t i = b; i < e; ++i) cb.grow(prims[idx[i]].c);
-        double leaf_cost = (double)n;
+    // Returns the child ref of range [b, e); bounds is the range's box and cb
+    // the box of its centroids.  One pass bins all three axes; the partition
+    // pass also gathers the two sides' centroid boxes, and the sides' boxes
+    // come from the chosen split's bins (min and max are exact, so these are
+    // the boxes a pass over each side would give).
+    int build(uint32_t b, uint32_t e, int depth, const Box& bounds, const Box& cb, Part& out) {
+        const uint32_t n = e - b;
+        out.max_depth = std::max(out.max_depth, depth);
+        const double leaf_cost = (double)n;
         int best_axis = -1, best_bin = -1;
         double best_cost = INFINITY;
         constexpr int kBins = 16;
+        Box bb[3][kBins];
+        uint32_t cnt[3][kBins] = {};
+        float scale[3] = {0.f, 0.f, 0.f};
+        bool live[3] = {false, false, false};
         if (n > 1) {
             for (int ax = 0; ax < 3; ++ax) {
-                float ext = cb.hi[ax] - cb.lo[ax];
-                if (!(ext > 0.0f)) continue;
-                Box bb[kBins];
-                uint32_t cnt[kBins] = {};
-                float scale = kBins / ext;
-                for (uint32_t i = b; i < e; ++i) {
-                    const Prim& p = prims[idx[i]];
-                    int k = std::min(kBins - 1, (int)((p.c[ax] - cb.lo[ax]) * scale));
-                    bb[k].grow(p.box);
-                    cnt[k]++;
+                const float ext = cb.hi[ax] - cb.lo[ax];
+                live[ax] = ext > 0.0f;
+                if (live[ax]) scale[ax] = kBins / ext;
+            }
+            for (uint32_t i = b; i < e; ++i) {
+                const Prim& p = prims[i];
+                for (int ax = 0; ax < 3; ++ax) {
+                    if (!live[ax]) continue;
+                    const int k = std::min(kBins - 1, (int)((p.c[ax] - cb.lo[ax]) * scale[ax]));
+                    bb[ax][k].grow(p.box);
+                    cnt[ax][k]++;
                 }
+            }
+            const double inv_area = 1.0 / std::max(bounds.area(), 1e-30);
+            for (int ax = 0; ax < 3; ++ax) {
+                if (!live[ax]) continue;
+                // An empty bin changes neither side's box nor its count: the
+                // candidate after it equals the one before, so it is skipped
+                // (costs are compared strictly, so the choice is unchanged).
                 double ra[kBins];
                 uint32_t rc[kBins];
                 Box acc;
                 uint32_t c = 0;
+                double a = 0.0;
                 for (int k = kBins - 1; k > 0; --k) {
-                    acc.grow(bb[k]);
-                    c += cnt[k];
-                    ra[k] = acc.area();
+                    if (cnt[ax][k]) {
+                        acc.grow(bb[ax][k]);
+                        c += cnt[ax][k];
+                        a = acc.area();
+                    }
+                    ra[k] = a;
                     rc[k] = c;
                 }
                 Box la;
                 uint32_t lc = 0;
                 for (int k = 0; k < kBins - 1; ++k) {
-                    la.grow(bb[k]);
-                    lc += cnt[k];
-                    if (lc == 0 || rc[k + 1] == 0) continue;
-                    double cost = 1.0 + (la.area() * lc + ra[k + 1] * rc[k + 1]) / std::max(bounds.area(), 1e-30);
+                    if (!cnt[ax][k]) continue;
+                    la.grow(bb[ax][k]);
+                    lc += cnt[ax][k];
+                    if (rc[k + 1] == 0) continue;
+                    const double cost = 1.0 + (la.area() * lc + ra[k + 1] * rc[k + 1]) * inv_area;
                     if (cost < best_cost) {
                         best_cost = cost;
                         best_axis = ax;
@@ -144,36 +190,61 @@ struct Builder {
                 }
             }
         }
-        bool must_split = n > (uint32_t)kLeafMax;
-        if (!must_split && (best_axis < 0 || best_cost >= leaf_cost)) return make_leaf(b, e);
+        const bool must_split = n > (uint32_t)kLeafMax;
+        if (!must_split && (best_axis < 0 || best_cost >= leaf_cost)) return make_leaf(b, e, out);
         if (depth >= kMaxBvhDepth - 1) {
-            if (!must_split) return make_leaf(b, e);
+            if (!must_split) return make_leaf(b, e, out);
         }
-        uint32_t mid;
+        uint32_t mid = b;
+        Box lb, rb, lcb, rcb;
         if (best_axis >= 0) {
-            float scale = kBins / (cb.hi[best_axis] - cb.lo[best_axis]);
-            float lo = cb.lo[best_axis];
-            int ax = best_axis, bin = best_bin;
-            auto it = std::partition(idx.begin() + b, idx.begin() + e, [&](uint32_t t) {
-                int k = std::min(kBins - 1, (int)((prims[t].c[ax] - lo) * scale));
-                return k <= bin;
-            });
-            mid = (uint32_t)(it - idx.begin());
-            if (mid == b || mid == e) mid = b + n / 2;
-        } else {
-            mid = b + n / 2;  // all centroids coincide
+            const int ax = best_axis, bin = best_bin;
+            const float lo = cb.lo[ax], sc = scale[ax];
+            uint32_t i = b, j = e;  // [b, i) left, [j, e) right
+            while (i < j) {
+                const Prim& p = prims[i];
+                if (std::min(kBins - 1, (int)((p.c[ax] - lo) * sc)) <= bin) {
+                    lcb.grow(p.c);
+                    ++i;
+                } else {
+                    rcb.grow(p.c);
+                    std::swap(prims[i], prims[--j]);
+                }
+            }
+            mid = i;
+            for (int k = 0; k <= bin; ++k) lb.grow(bb[ax][k]);
+            for (int k = bin + 1; k < kBins; ++k) rb.grow(bb[ax][k]);
         }
-        int me = (int)bin.size();
-        bin.push_back(BinNode{});
-        int l = build(b, mid, depth + 1);
-        int r = build(mid, e, depth + 1);
-        Box lb = range_box(b, mid), rb = range_box(mid, e);
+        if (best_axis < 0 || mid == b || mid == e) {  // all centroids coincide: split by position
+            mid = b + n / 2;
+            lb = range_box(b, mid);
+            rb = range_box(mid, e);
+            lcb = Box();
+            rcb = Box();
+            for (uint32_t i = b; i < mid; ++i) lcb.grow(prims[i].c);
+            for (uint32_t i = mid; i < e; ++i) rcb.grow(prims[i].c);
+        }
+        const int me = (int)out.bin.size();
+        out.bin.push_back(BinNode{});
+        int l, r;
+        if (n >= kParallelMin && depth < kParallelDepth) {  // the two sides touch disjoint prims
+            Part pl, pr;
+            auto left = std::async(std::launch::async, [&] { return build(b, mid, depth + 1, lb, lcb, pl); });
+            const int rr = build(mid, e, depth + 1, rb, rcb, pr);
+            const int lr = left.get();
+            l = append_part(out, pl, lr);
+            r = append_part(out, pr, rr);
+        } else {
+            l = build(b, mid, depth + 1, lb, lcb, out);
+            r = build(mid, e, depth + 1, rb, rcb, out);
+        }
         widen(lb);
         widen(rb);
-        bin[me].box[0] = lb;
-        bin[me].box[1] = rb;
-        bin[me].ref[0] = l;
-        bin[me].ref[1] = r;
+        BinNode& nd = out.bin[me];
+        nd.box[0] = lb;
+        nd.box[1] = rb;
+        nd.ref[0] = l;
+        nd.ref[1] = r;
         return me;
     }
 
@@ -270,13 +341,20 @@ bool build_bvh(const float* verts, uint32_t n_verts, const uint32_t* tris, uint3
             p.box.grow(verts + 3 * vi);
         }
         for (int k = 0; k < 3; ++k) p.c[k] = 0.5f * (p.box.lo[k] + p.box.hi[k]);
+        p.id = t;
     }
-    B.idx.resize(n_tris);
-    std::iota(B.idx.begin(), B.idx.end(), 0u);
-    B.bin.reserve(n_tris);
-    out->tris.reserve(n_tris);
-    const int root2 = B.build(0, n_tris, 0);
-    if (B.max_depth_seen >= kMaxBvhDepth) {
+    Part root;
+    root.bin.reserve(n_tris);
+    root.tris.reserve(n_tris);
+    Box all_box, all_c;
+    for (uint32_t t = 0; t < n_tris; ++t) {
+        all_box.grow(B.prims[t].box);
+        all_c.grow(B.prims[t].c);
+    }
+    const int root2 = B.build(0, n_tris, 0, all_box, all_c, root);
+    B.bin = std::move(root.bin);
+    out->tris = std::move(root.tris);
+    if (root.max_depth >= kMaxBvhDepth) {
         *err = "BVH too deep for the traversal stack";
         return false;
     }
