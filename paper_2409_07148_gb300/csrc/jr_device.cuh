@@ -228,6 +228,15 @@ __device__ __forceinline__ bool trav_leaf(const SceneView& s, Trav& r, const int
     return r.ref != kSentinel;
 }
 
+// The inner-node loop of a warp-synchronous traversal round ends once at most
+// kSearchExit lanes are still on their way to a leaf (after at least one node
+// visit), instead of when none is: the few lanes with the longest way no
+// longer hold the warp's other lanes, which test their leaves and go on; the
+// rest carry on in the next round.  Measured on the 512^2 Cornell + spheres
+// workload (wavefront): 1.04 (exit at 0), 1.17 (4), 1.19 (6 and 8), 1.14 (16)
+// x 10^9 chain steps/s.
+constexpr int kSearchExit = 6;
+
 // Closest hit for the lanes in `mask`, which must all call together (lanes
 // without a ray pass want = false).  Warp-synchronous while-while traversal
 // (Aila & Laine, HPG 2009): each inner-node round and each leaf round ends in
@@ -248,8 +257,9 @@ __device__ __forceinline__ int closest_hit(const SceneView& s, unsigned mask, bo
                 active = false;
                 r.best = -1;
             }
+            if (__popc(__ballot_sync(mask, active && r.ref >= 0)) <= kSearchExit) break;
         }
-        if (active) active = r.ref != kSentinel && trav_leaf<kCount>(s, r, stack, work);
+        if (active && r.ref < 0) active = r.ref != kSentinel && trav_leaf<kCount>(s, r, stack, work);
     }
     t_out = r.best >= 0 ? r.tb : INFINITY;
     return r.best;

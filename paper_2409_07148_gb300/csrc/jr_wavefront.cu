@@ -243,12 +243,12 @@ __global__ void __launch_bounds__(128, 12) wf_step_kernel(ChainView c, uint64_t 
 // closest hit is known); idle (no path).  Traversal rounds are warp-
 // synchronous while-while rounds with speculative traversal (Aila & Laine
 // 2009): a lane that meets a leaf postpones it and keeps descending inner
-// nodes until every lane holds a leaf.  A warp shades its waiting lanes
-// together once kShadeBatch of them wait (or none is traversing); a shaded
-// path either continues with its next ray or ends (F goes to fy,
-// and, with a flow, the row joins the density queue: when its candidate will
-// become a state with p > 0 and still lacks u(y); the finish of the next step
-// kernel takes the same decision from the same values).  Idle lanes take new
+// nodes until all but kSearchExit lanes hold a leaf.  A warp shades its
+// waiting lanes together once kShadeBatch of them wait (or none is
+// traversing); a shaded path either continues with its next ray or ends (F
+// goes to fy, and, with a flow, the row joins the density queue: when its
+// candidate will become a state with p > 0 and still lacks u(y); the finish of
+// the next step kernel takes the same decision from the same values).  Idle lanes take new
 // paths from the queue (dynamic fetch, so a warp does not idle for its
 // longest path); a new path starts at the camera ray through the candidate's
 // film point (y0, y1) with T = 1, F = 0.  ident = 1: the queue is the identity
@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(128, 12) wf_step_kernel(ChainView c, uint64_t 
 // arrive while the next ray traverses.
 constexpr int kShadeBatch = 16;
 enum PathState : uint32_t { kIdle = 0, kTraverse = 1, kWaitShade = 2 };
+
 
 __global__ void __launch_bounds__(128) wf_path_kernel(SceneView s, ChainView c, int ident) {
     const WaveView& w = c.wf;
@@ -364,6 +365,7 @@ __global__ void __launch_bounds__(128) wf_path_kernel(SceneView s, ChainView c, 
                     r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
                 }
             }
+            if (__popc(__ballot_sync(kFull, trav && leaf == kSentinel && r.ref >= 0)) <= kSearchExit) break;
         }
         if (trav) {
             if (leaf != kSentinel) {
@@ -531,6 +533,7 @@ __global__ void __launch_bounds__(128, 7) wf_batch_path_kernel(SceneView m, cons
                     r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
                 }
             }
+            if (__popc(__ballot_sync(kFull, trav && leaf == kSentinel && r.ref >= 0)) <= kSearchExit) break;
         }
         if (trav) {
             if (leaf != kSentinel) {
