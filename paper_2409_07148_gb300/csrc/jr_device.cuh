@@ -234,8 +234,14 @@ __device__ __forceinline__ bool trav_leaf(const SceneView& s, Trav& r, const int
 // longer hold the warp's other lanes, which test their leaves and go on; the
 // rest carry on in the next round.  Measured on the 512^2 Cornell + spheres
 // workload (wavefront): 1.04 (exit at 0), 1.17 (4), 1.19 (6 and 8), 1.14 (16)
-// x 10^9 chain steps/s.
+// x 10^9 chain steps/s.  The exit waits while the searching lanes outnumber
+// the others (a sparse warp, late in a drain, has nobody to release and would
+// only pay an extra round per node visit).
 constexpr int kSearchExit = 6;
+__device__ __forceinline__ bool search_done(unsigned searching, unsigned tracing) {
+    const int ns = __popc(searching);
+    return ns <= kSearchExit && 2 * ns <= __popc(tracing);
+}
 
 // Closest hit for the lanes in `mask`, which must all call together (lanes
 // without a ray pass want = false).  Warp-synchronous while-while traversal
@@ -252,12 +258,13 @@ __device__ __forceinline__ int closest_hit(const SceneView& s, unsigned mask, bo
     if constexpr (kCount) work.rays += want ? 1u : 0u;
     int stack[kStackSize];
     while (__any_sync(mask, active)) {
+        const unsigned tracing = __ballot_sync(mask, active);
         while (__any_sync(mask, active && r.ref >= 0)) {
             if (active && r.ref >= 0 && !trav_node<kCount>(s, r, stack, status, work)) {
                 active = false;
                 r.best = -1;
             }
-            if (__popc(__ballot_sync(mask, active && r.ref >= 0)) <= kSearchExit) break;
+            if (search_done(__ballot_sync(mask, active && r.ref >= 0), tracing)) break;
         }
         if (active && r.ref < 0) active = r.ref != kSentinel && trav_leaf<kCount>(s, r, stack, work);
     }

@@ -353,6 +353,7 @@ __global__ void __launch_bounds__(128) wf_path_kernel(SceneView s, ChainView c, 
             leaf = r.ref;
             r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
         }
+        const unsigned tracing_now = __ballot_sync(kFull, trav);
         while (__any_sync(kFull, trav && leaf == kSentinel && r.ref >= 0)) {
             if (trav && r.ref >= 0) {
                 if (!trav_node<false>(s, r, stack, status, wk)) {
@@ -365,7 +366,7 @@ __global__ void __launch_bounds__(128) wf_path_kernel(SceneView s, ChainView c, 
                     r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
                 }
             }
-            if (__popc(__ballot_sync(kFull, trav && leaf == kSentinel && r.ref >= 0)) <= kSearchExit) break;
+            if (search_done(__ballot_sync(kFull, trav && leaf == kSentinel && r.ref >= 0), tracing_now)) break;
         }
         if (trav) {
             if (leaf != kSentinel) {
@@ -521,6 +522,7 @@ __global__ void __launch_bounds__(128, 7) wf_batch_path_kernel(SceneView m, cons
             leaf = r.ref;
             r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
         }
+        const unsigned tracing_now = __ballot_sync(kFull, trav);
         while (__any_sync(kFull, trav && leaf == kSentinel && r.ref >= 0)) {
             if (trav && r.ref >= 0) {
                 if (!trav_node<false>(m, r, stack, status, wk)) {
@@ -533,7 +535,7 @@ __global__ void __launch_bounds__(128, 7) wf_batch_path_kernel(SceneView m, cons
                     r.ref = r.sp > 0 ? stack[--r.sp] : kSentinel;
                 }
             }
-            if (__popc(__ballot_sync(kFull, trav && leaf == kSentinel && r.ref >= 0)) <= kSearchExit) break;
+            if (search_done(__ballot_sync(kFull, trav && leaf == kSentinel && r.ref >= 0), tracing_now)) break;
         }
         if (trav) {
             if (leaf != kSentinel) {
