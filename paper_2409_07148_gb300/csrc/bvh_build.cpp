@@ -9,7 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <future>
-#include <numeric>
+#include <system_error>
 
 #include "jr_internal.h"
 
@@ -227,9 +227,15 @@ struct Builder {
         const int me = (int)out.bin.size();
         out.bin.push_back(BinNode{});
         int l, r;
+        Part pl, pr;
+        std::future<int> left;
         if (n >= kParallelMin && depth < kParallelDepth) {  // the two sides touch disjoint prims
-            Part pl, pr;
-            auto left = std::async(std::launch::async, [&] { return build(b, mid, depth + 1, lb, lcb, pl); });
+            try {
+                left = std::async(std::launch::async, [&] { return build(b, mid, depth + 1, lb, lcb, pl); });
+            } catch (const std::system_error&) {  // no thread to be had: both sides here
+            }
+        }
+        if (left.valid()) {
             const int rr = build(mid, e, depth + 1, rb, rcb, pr);
             const int lr = left.get();
             l = append_part(out, pl, lr);

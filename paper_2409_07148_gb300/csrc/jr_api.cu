@@ -125,6 +125,8 @@ jr_status jr_scene_create(const jr_scene_desc* desc, void* stream, jr_scene** ou
             return fail(JR_ERR_INVALID_ARG, "jr_scene_create: " + err);
     } catch (const std::bad_alloc&) {
         return fail(JR_ERR_OOM, "jr_scene_create: host allocation failed in the BVH build");
+    } catch (const std::exception& ex) {
+        return fail(JR_ERR_INVALID_ARG, std::string("jr_scene_create: BVH build failed: ") + ex.what());
     }
     jr_scene* s = new (std::nothrow) jr_scene();
     if (!s) return fail(JR_ERR_OOM, "jr_scene_create: host allocation failed");
