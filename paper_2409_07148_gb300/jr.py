@@ -20,6 +20,7 @@ JR_OK, JR_ERR_INVALID_ARG, JR_ERR_CUDA, JR_ERR_OOM, JR_ERR_WATCHDOG, JR_ERR_NUME
 JR_FLAG_RAO_BLACKWELL = 1
 JR_EXEC_AUTO, JR_EXEC_MEGAKERNEL, JR_EXEC_WAVEFRONT = 0, 1, 2
 JR_STATUS_NONFINITE, JR_STATUS_TRAVERSAL, JR_STATUS_STACK = 1, 2, 4
+JR_BATCH_WAVEFRONT = 0
 MATERIAL_FLOATS = 12
 MAX_DEPTH = 15
 STATIC_MAX_CHAINS = 65536
@@ -431,6 +432,9 @@ class Batch:
         self.h = h
 
     def set_block(self, block):
+        """Chains per megakernel work item (a multiple of 32 in [32, 256]), or
+        JR_BATCH_WAVEFRONT (0): every set in shared wavefront launches over a
+        merged copy of the sets' scenes."""
         _check(lib().jr_batch_set_block(self.h, int(block)))
 
     def advance(self, n_steps, stream=None):
@@ -440,6 +444,9 @@ class Batch:
         _check(lib().jr_batch_advance_graph(self.h, int(n_steps), _stream(stream)))
 
     def autotune(self, probe_steps, stream=None):
+        """Time probe_steps real steps for each megakernel item size and for the
+        batched wavefront, keep the fastest; returns {"best_block", "ns_per_chain_step"}
+        (block 0 is the batched wavefront)."""
         r = TuneReport()
         _check(lib().jr_batch_autotune(self.h, int(probe_steps), _stream(stream), ctypes.byref(r)))
         return {"best_block": int(r.best_block),
