@@ -59,6 +59,40 @@ __device__ __forceinline__ void count_and_flush(uint32_t nJ, uint32_t nL, uint32
     }
 }
 
+// count_and_flush for a whole block of the step kernel (4 warps): one atomic
+// per block and counter instead of one per warp (the counters are three
+// addresses that every block of a launch updates).  All threads call.
+__device__ __forceinline__ void count_and_flush_block(uint32_t nJ, uint32_t nL, uint32_t nA, unsigned status,
+                                                      const ChainView& c) {
+    __shared__ unsigned red_s[4][4];
+    nJ = __reduce_add_sync(kFull, nJ);
+    nL = __reduce_add_sync(kFull, nL);
+    nA = __reduce_add_sync(kFull, nA);
+    status = __reduce_or_sync(kFull, status);
+    const int wq = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red_s[wq][0] = nJ;
+        red_s[wq][1] = nL;
+        red_s[wq][2] = nA;
+        red_s[wq][3] = status;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long sJ = 0, sL = 0, sA = 0;
+        unsigned st = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            sJ += red_s[q][0];
+            sL += red_s[q][1];
+            sA += red_s[q][2];
+            st |= red_s[q][3];
+        }
+        if (sJ) atomicAdd(c.counters + 0, sJ);
+        if (sL) atomicAdd(c.counters + 1, sL);
+        if (sA) atomicAdd(c.counters + 2, sA);
+        if (st) atomicOr(c.status, st);
+    }
+}
+
 // finish = 1: complete step `step - 1` of every chain.  begin = 1: start step
 // `step`.  With begin = 0 the launch also moves every state back into x.
 // restart = 1: the step is a restart of every chain from mu (a new tour that is
@@ -234,7 +268,7 @@ __global__ void __launch_bounds__(128, 12) wf_step_kernel(ChainView c, uint64_t 
             }
         }
     }
-    count_and_flush(nJ, nL, nA, status, c);
+    count_and_flush_block(nJ, nL, nA, status, c);  // launched with 128 threads
 }
 
 // Whole paths of every queued chain in one persistent launch.  A lane keeps
@@ -416,7 +450,7 @@ __global__ void __launch_bounds__(128) wf_batch_step_kernel(const BatchEntry* en
     bool traced = true, to_sample = false, active = false;
     if (i < it.end)
         step_chain(e.c, i, e.step + k, finish, begin, kModeStep, nJ, nL, nA, status, traced, to_sample, active);
-    count_and_flush(nJ, nL, nA, status, e.c);
+    count_and_flush_block(nJ, nL, nA, status, e.c);  // a block's chains are one set's
 }
 
 // The path kernel over every set's candidates: item j of the launch is chain
