@@ -5,7 +5,14 @@
 // materials u32[n_tris]) from argv[1], builds the tree twice and prints one
 // line of key=value results.  argv[2] = "shrink" or "drop" first damages the
 // tree (the root's first child box loses its x extent; a leaf of two or more
-// triangles loses one), so that the test can see the checks fail.  Results:
+// triangles loses one), so that the test can see the checks fail.
+// argv[2] = "merge" with a second scene in argv[3]: both trees are put into one
+// pair of arrays as a batch merges its scenes (the second one's nodes and
+// records after the first one's, its refs moved by rebase_ref and its
+// material indices by the first scene's count), and each scene's part is
+// checked from its moved root: merge_a, merge_b = cover, refs, contain and
+// records all hold.  "merge_off_by_one" moves the second scene's leaves by one
+// record too few, which the check must see.  Results:
 //   ok          the builder accepted the scene
 //   same        the two builds are byte-identical (the top subtrees are built
 //               on separate threads; their merge must not depend on timing)
@@ -127,12 +134,83 @@ struct Checker {
 
 }  // namespace
 
+// The checks of one scene's part of a tree whose root is `root`: cover,
+// refs, contain, and records (material index moved by mat_off).
+bool part_ok(const Scene& s, const jr::HostBvh& t, int root, int mat_off) {
+    const uint32_t nt = (uint32_t)s.m.size();
+    Checker c{s, t, std::vector<int>(nt, 0)};
+    c.walk(root);
+    bool ok = c.refs && c.contain && c.empty;
+    for (uint32_t k = 0; k < nt && ok; ++k) ok = c.seen[k] == 1;
+    // records of this part: the leaves reached from root
+    std::vector<int> stack{root};
+    while (ok && !stack.empty()) {
+        const int ref = stack.back();
+        stack.pop_back();
+        if (ref == jr::kNoChild) continue;
+        if (ref >= 0) {
+            const jr::Bvh4Node& n = t.nodes[ref];
+            stack.insert(stack.end(), {n.refs.x, n.refs.y, n.refs.z, n.refs.w});
+            continue;
+        }
+        const int enc = ~ref, first = enc >> 3, cnt = (enc & 7) + 1;
+        for (int k = first; k < first + cnt && ok; ++k) {
+            int id, mat;
+            std::memcpy(&id, &t.tris[k].v0_id.w, 4);
+            std::memcpy(&mat, &t.tris[k].e1_mat.w, 4);
+            const float* p0 = &s.v[3 * (size_t)s.t[3 * (size_t)id]];
+            ok = t.tris[k].v0_id.x == p0[0] && t.tris[k].v0_id.y == p0[1] && t.tris[k].v0_id.z == p0[2] &&
+                 mat == (int)s.m[id] + mat_off;
+        }
+    }
+    return ok;
+}
+
+int merge_main(const Scene& sa, const char* other, bool off_by_one) {
+    Scene sb;
+    if (!read_scene(other, sb)) {
+        std::printf("error=read\n");
+        return 2;
+    }
+    jr::HostBvh a, b;
+    std::string err;
+    if (!jr::build_bvh(sa.v.data(), (uint32_t)(sa.v.size() / 3), sa.t.data(), (uint32_t)sa.m.size(), sa.m.data(), &a,
+                       &err) ||
+        !jr::build_bvh(sb.v.data(), (uint32_t)(sb.v.size() / 3), sb.t.data(), (uint32_t)sb.m.size(), sb.m.data(), &b,
+                       &err)) {
+        std::printf("ok=0 error=%s\n", err.c_str());
+        return 0;
+    }
+    // scene a's materials are numbered 0 .. max + 1 in this check
+    int mat_count = 0;
+    for (uint32_t m : sa.m) mat_count = std::max(mat_count, (int)m + 1);
+    jr::HostBvh m = a;
+    const int node_off = (int)a.nodes.size(), tri_off = (int)a.tris.size() - (off_by_one ? 1 : 0);
+    for (jr::Bvh4Node n : b.nodes) {
+        int* r = &n.refs.x;
+        for (int j = 0; j < 4; ++j) r[j] = jr::rebase_ref(r[j], node_off, tri_off);
+        m.nodes.push_back(n);
+    }
+    for (jr::TriRecord r : b.tris) {
+        int mat;
+        std::memcpy(&mat, &r.e1_mat.w, 4);
+        mat += mat_count;
+        std::memcpy(&r.e1_mat.w, &mat, 4);
+        m.tris.push_back(r);
+    }
+    const int root_b = jr::rebase_ref(b.root, node_off, tri_off);
+    std::printf("ok=1 merge_a=%d merge_b=%d\n", part_ok(sa, m, a.root, 0), part_ok(sb, m, root_b, mat_count));
+    return 0;
+}
+
 int main(int argc, char** argv) {
     Scene s;
     if (argc < 2 || !read_scene(argv[1], s)) {
         std::printf("error=read\n");
         return 2;
     }
+    if (argc > 3 && std::string(argv[2]) == "merge") return merge_main(s, argv[3], false);
+    if (argc > 3 && std::string(argv[2]) == "merge_off_by_one") return merge_main(s, argv[3], true);
     const uint32_t nv = (uint32_t)(s.v.size() / 3), nt = (uint32_t)s.m.size();
     jr::HostBvh a, b;
     std::string err;

@@ -3,7 +3,9 @@ is compiled with the host compiler against the builder and checks the tree of
 seeded scenes -- every triangle in exactly one leaf, its record exact, every
 child box containing its subtree, refs in range, empty slots empty, the stack
 bound, and two builds byte-identical (the top subtrees are built on separate
-threads).  Damaged trees must fail the checks, so they are not vacuous."""
+threads).  Damaged trees must fail the checks, so they are not vacuous.  Two
+trees merged as a batch merges its scenes (refs moved by rebase_ref, the same
+function the GPU's merge kernel applies) keep both scenes' trees intact."""
 import os
 import shutil
 import subprocess
@@ -41,8 +43,9 @@ def _write(path, verts, tris, mats):
         f.write(np.ascontiguousarray(mats, np.uint32).tobytes())
 
 
-def _run(checker, path, mode=None):
-    r = subprocess.run([checker, path] + ([mode] if mode else []), capture_output=True, text=True, timeout=120)
+def _run(checker, path, mode=None, other=None):
+    r = subprocess.run([checker, path] + ([mode] if mode else []) + ([other] if other else []), capture_output=True,
+                       text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     return dict(kv.split("=", 1) for kv in r.stdout.split())
 
@@ -81,3 +84,16 @@ def test_bvh_checks_catch_damage(checker, tmp_path):
     _write(path, sc.verts, sc.tris, sc.tri_mat)
     assert _run(checker, path, "shrink")["contain"] == "0"
     assert _run(checker, path, "drop")["cover"] == "0"
+
+
+def test_bvh_merge_as_in_a_batch(checker, tmp_path):
+    a = scenes.cornell_spheres(width=32, height=32, depth=4, n_lon=24, n_lat=13)
+    b = scenes.random_boxes(8, 6000, 32, 32, 4)
+    pa, pb = str(tmp_path / "a.bin"), str(tmp_path / "b.bin")
+    _write(pa, a.verts, a.tris, a.tri_mat)
+    _write(pb, b.verts, b.tris, b.tri_mat)
+    for x, y in ((pa, pb), (pb, pa)):
+        res = _run(checker, x, "merge", y)
+        assert res["merge_a"] == "1" and res["merge_b"] == "1", res
+    res = _run(checker, pa, "merge_off_by_one", pb)
+    assert res["merge_a"] == "1" and res["merge_b"] == "0", res
