@@ -275,9 +275,11 @@ jr_status jr_philox(uint64_t seed, uint32_t tag, uint32_t block, uint64_t chain_
  * by ONE persistent launch.  Blocks of the launch take work items (a block of
  * chains of one set) from a global cursor; items are ordered by estimated cost
  * (depth + 1) x log2(triangles), longest first.  Or, with JR_BATCH_WAVEFRONT,
- * by shared wavefront launches over all the sets.  Every set advances exactly as
+ * by shared wavefront launches over all the sets.  Every set advances as
  * jr_advance would advance it on its own (same Philox streams, same
- * per-chain arithmetic; Alg. 2 of Section 7.2 per chain).  The sets stay owned
+ * per-chain arithmetic; Alg. 2 of Section 7.2 per chain): the same states,
+ * with F and p equal up to the rounding of separately compiled kernels (one
+ * may contract a multiply-add into an FMA where the other does not).  The sets stay owned
  * by the caller and must outlive the batch; a set may still be advanced,
  * resolved or inspected on its own between batch advances.
  */
@@ -296,7 +298,9 @@ typedef struct {
  * of all the sets' scenes, merged when the batch first uses it (each distinct
  * scene once; at most 1024 sets, 2^28 triangles, 2^31 chains).  Every set
  * also gets its wavefront buffers.  n_steps steps take 2 n_steps + 2 launches
- * (plus one 4-byte memset per step). */
+ * (plus one 4-byte memset per step).  The set-up fails with
+ * JR_ERR_INVALID_ARG beyond those limits (the batch itself stays usable with
+ * a megakernel block size). */
 #define JR_BATCH_WAVEFRONT 0u
 
 /* Build a batch over n_sets distinct chain sets (device descriptors, work
@@ -313,10 +317,11 @@ jr_status jr_batch_set_block(jr_batch* batch, uint32_t block);
  * fold).  Asynchronous, except the batched wavefront's one-time set-up. */
 jr_status jr_batch_advance(jr_batch* batch, uint32_t n_steps, void* stream);
 
-/* As jr_batch_advance, replayed from a CUDA graph that holds the two launches
- * (captured on the first call, and again whenever n_steps or the block size
- * changes).  The step indices live on the device, so every replay continues
- * the chains.  Asynchronous after the first capture. */
+/* As jr_batch_advance, replayed from a CUDA graph that holds its launches
+ * (two; the batched wavefront's 2 n_steps + 2 and their memsets), captured on
+ * the first call and again whenever n_steps or the block size changes.  The
+ * step indices live on the device, so every replay continues the chains.
+ * Asynchronous after the first capture. */
 jr_status jr_batch_advance_graph(jr_batch* batch, uint32_t n_steps, void* stream);
 
 /* Autotuner: time probe_steps chain steps of the whole batch for each work-item
