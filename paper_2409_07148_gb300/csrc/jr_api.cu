@@ -647,6 +647,21 @@ jr_status prepare_wave(jr_batch* b, cudaStream_t st) {
         return fail(JR_ERR_INVALID_ARG, "jr_batch: the merged scene or the chain count is too large for the "
                                         "batched wavefront (2^28 triangles, 2^31 nodes or chains)");
     const char* who = "jr_batch (batched wavefront set-up)";
+    // a set-up that failed part way may have left buffers: free them first
+    cudaFree(b->m_nodes);
+    cudaFree(b->m_tris);
+    cudaFree(b->m_mats);
+    cudaFree(b->roots);
+    cudaFree(b->chain_off);
+    cudaFree(b->wf_items);
+    cudaFree(b->fetch);
+    b->m_nodes = nullptr;
+    b->m_tris = nullptr;
+    b->m_mats = nullptr;
+    b->roots = nullptr;
+    b->chain_off = nullptr;
+    b->wf_items = nullptr;
+    b->fetch = nullptr;
     JR_CUDA(dev_alloc(&b->m_nodes, std::max<uint64_t>(nn, 1)), who);
     JR_CUDA(dev_alloc(&b->m_tris, std::max<uint64_t>(nt, 1)), who);
     JR_CUDA(dev_alloc(&b->m_mats, std::max<uint64_t>(nm, 1)), who);
