@@ -133,8 +133,11 @@ void jr_scene_destroy(jr_scene* scene);
 /* Create a set of chains (library-owned SoA state, RGBA float framebuffer,
  * FP64 accumulator, counters) and draw each initial state x0 ~ mu (Alg. 2
  * "initial state"; tag 1).  Asynchronous on `stream`.  The scene must outlive
- * the chains.  Errors: JR_ERR_INVALID_ARG (sizes, depth > JR_MAX_DEPTH,
- * c_tilde <= 0, sigma <= 0, chain ids beyond 2^32), JR_ERR_OOM. */
+ * the chains.  The first chain set created on a device also sets up the fixed
+ * scratch array of jr_advance_static there (10,027,264 bytes, once per
+ * device, held until the process exits).  Errors: JR_ERR_INVALID_ARG (sizes,
+ * depth > JR_MAX_DEPTH, c_tilde <= 0, sigma <= 0, chain ids beyond 2^32),
+ * JR_ERR_OOM. */
 jr_status jr_chains_create(const jr_scene* scene, const jr_params* params, void* stream, jr_chains** out);
 void jr_chains_destroy(jr_chains* chains);
 
@@ -200,20 +203,28 @@ jr_status jr_set_execution(jr_chains* chains, uint32_t mode);
  * It runs the wavefront launches of jr_advance (JR_EXEC_WAVEFRONT), with the
  * same results, but their scratch (second state buffer, F records and
  * queues) lives in one fixed device array inside the library, sized for at
- * most JR_STATIC_MAX_CHAINS chains of any depth: 10,027,264 bytes, which
- * every GPU that loads the library holds until the process exits.  The chain
- * set (state, framebuffer, accumulator, counters) is the caller's, created
- * beforehand with jr_chains_create.  It calls no cudaMalloc, cudaFree or other
- * allocating routine.
+ * most JR_STATIC_MAX_CHAINS chains of any depth (D <= 32, which
+ * jr_chains_create already enforces): 10,027,264 bytes.  The CUDA runtime
+ * loads the array's module on a device lazily, and loading it allocates the
+ * array; jr_chains_create does that (and looks up the array's device address
+ * for the device then current), so the array is allocated on every device on
+ * which a chain set was created, at that point, and held until the process
+ * exits.  The chain set (state, framebuffer, accumulator, counters) is the
+ * caller's, created beforehand with jr_chains_create on the same device.
+ * jr_advance_static itself calls no cudaMalloc, cudaFree or other allocating
+ * routine.
  *
- * The first call on a device looks up the array's device address for that
- * device (once per device, with the device current), so make the first call
- * on each device before any stream capture.  Every call shares the one array
- * and it keeps the last call's contents: the call clears what must start at
- * zero, but calls whose work overlaps on the GPU (other streams, other
- * threads, other chain sets) race on it -- order them on one stream.
+ * Every call shares the one array and it keeps the last call's contents: the
+ * call clears what must start at zero, but calls whose work overlaps on the
+ * GPU (other streams, other threads, other chain sets) race on it -- order
+ * them on one stream.  The cached device address does not survive a reset of
+ * the device (cudaDeviceReset or a lost primary context): the library's
+ * handles and this address are then invalid, and the process must not use the
+ * library again.
  * Errors: JR_ERR_INVALID_ARG for a null handle or more than
- * JR_STATIC_MAX_CHAINS chains (nothing is launched); JR_ERR_CUDA. */
+ * JR_STATIC_MAX_CHAINS chains; JR_ERR_STATE for chains with a flow attached
+ * (they advance with jr_advance); in both cases nothing is launched.
+ * JR_ERR_CUDA for a failed launch. */
 #define JR_STATIC_MAX_CHAINS 65536u
 jr_status jr_advance_static(jr_chains* chains, uint32_t n_steps, void* stream);
 

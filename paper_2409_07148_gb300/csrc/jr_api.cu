@@ -213,7 +213,8 @@ jr_status jr_chains_create(const jr_scene* scene, const jr_params* params, void*
         (e = cudaMemsetAsync(v.acc64, 0, sizeof(double4_32a) * npx, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(v.counters, 0, sizeof(unsigned long long) * 4, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(v.status, 0, sizeof(unsigned int), st)) != cudaSuccess ||
-        (e = launch_init(scene->view, v, st)) != cudaSuccess) {
+        (e = launch_init(scene->view, v, st)) != cudaSuccess ||
+        (e = prepare_static_scratch()) != cudaSuccess) {  // jr_advance_static's array, see jr_wavefront.cu
         delete c;
         return cuda_fail(e, "jr_chains_create");
     }

@@ -244,6 +244,9 @@ constexpr size_t kStaticScratchBytes =
     256;  // = 10 027 264 bytes (every piece but the counters is a multiple of 256)
 cudaError_t launch_wavefront_static(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
                                     cudaStream_t st);
+// Load the module that holds the static scratch on the current device and cache
+// the array's device address (the first call on a device allocates the array).
+cudaError_t prepare_static_scratch();
 
 // jr_flow.cu: flow rows through the tensor cores.  Density: u_out[i] = beta q
 // + 1 - beta (and lq_out[i] = log q) for rows i of buf [D][n]; sample: buf

@@ -721,8 +721,12 @@ cudaError_t launch_batch_wavefront(const BatchWave& bw, BatchEntry* entries, uin
 // ---------------------------------------------------------------------------
 // Fixed-size scratch for jr_advance_static: the wavefront buffers of up to
 // kStaticMaxChains chains live in one file-scope device array instead of
-// memory allocated per chain set.  Every GPU that loads the library holds it
-// until the process exits.  Layout (256-byte aligned pieces): y [kMaxDim][n],
+// memory allocated per chain set.  The array belongs to this file's module,
+// which the CUDA runtime loads on a device on first use (lazy loading), and
+// loading it allocates the array.  jr_chains_create therefore looks the
+// address up (prepare_static_scratch), so the module is loaded, and the array
+// allocated, where allocation is allowed; a device keeps it until the process
+// exits.  Layout (256-byte aligned pieces): y [kMaxDim][n],
 // fy [n] float4, ua [n], queue [n], par [n], qcount (256 bytes).
 namespace {
 constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -760,6 +764,11 @@ cudaError_t static_scratch_base(void** out) {
     return cudaSuccess;
 }
 }  // namespace
+
+cudaError_t prepare_static_scratch() {
+    void* base = nullptr;
+    return static_scratch_base(&base);
+}
 
 cudaError_t launch_wavefront_static(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
                                     cudaStream_t st) {

@@ -21,15 +21,16 @@ REL = 1e-5
 
 
 def _compare(a, b):
+    """jr_advance_static runs the wavefront kernels of jr_advance on the same
+    Philox counters, so states, cached F/p/u and counters are bit-identical.
+    Only the framebuffer is summed by float atomics in an order that varies from
+    run to run, so the accumulator and the image agree to rounding."""
     (xa, fa), (xb, fb) = a.get_state(), b.get_state()
-    same = np.all(xa == xb, axis=0)
-    assert np.mean(same) >= 0.999, np.mean(same)
-    nz = fa[:, same] != 0
-    rel = np.abs(fa[:, same] - fb[:, same])[nz] / np.abs(fa[:, same])[nz]
-    assert rel.max(initial=0) <= REL
+    assert np.array_equal(xa, xb)
+    assert np.array_equal(fa, fb)
     sa, sb = a.stats(), b.stats()
     for k in ("steps_per_chain", "regenerations", "local_steps", "accepted", "status_word"):
-        assert abs(sa[k] - sb[k]) <= max(0, int(1e-3 * a.n)), (k, sa[k], sb[k])
+        assert sa[k] == sb[k], (k, sa[k], sb[k])
     acc_a, acc_b = a.accumulator(), b.accumulator()
     assert np.allclose(acc_a, acc_b, rtol=REL, atol=1e-6 * np.abs(acc_a).max())
     ia, ib = a.resolve(), b.resolve()
@@ -52,9 +53,15 @@ def test_advance_static_matches_advance_two_calls(name, kw, n):
     stream = torch.cuda.current_stream()
     for _ in range(2):
         ref.advance(9)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
         rc = lib.jr_advance_static(fixed.h, 9, ctypes.c_void_p(stream.cuda_stream))
         assert rc == jr.JR_OK, lib.jr_last_error()
         torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        # the call allocated nothing on the device (on the first call too: the
+        # scratch array was set up when the chain sets were created)
+        assert free1 == free0, (free0, free1)
         _compare(ref, fixed)
 
 
