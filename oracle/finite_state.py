@@ -54,3 +54,25 @@ def jump_chain_matrix(p: np.ndarray, mu: np.ndarray, c_tilde: float) -> np.ndarr
     k = np.array([_o.killing_rate(p[i], mu[i], c_tilde) for i in range(M)])
     a = 1.0 / (1.0 + k)
     return a[:, None] * K + (1.0 - a)[:, None] * np.outer(np.ones(M), mu)
+
+
+def mh_mixture_kernel(p: np.ndarray, mu: np.ndarray, ell: float, accept=None) -> np.ndarray:
+    """MH transition matrix of the baseline "Metropolis" (Alg. 1 with the
+    mixture proposal of Section 5, Q_l(x, .) = l mu + (1 - l) zeta(x, .)) on a
+    ring of M states, zeta = one step to either neighbour with probability 1/2.
+
+    With mu uniform Q_l is symmetric, so the acceptance is the oracle's
+    min(1, p(y)/p(x)); `accept(px, py)` replaces it (negative controls)."""
+    M = len(p)
+    acc = accept if accept is not None else _o.mh_accept_prob
+    Q = ell * np.outer(np.ones(M), mu)
+    for i in range(M):
+        Q[i, (i - 1) % M] += 0.5 * (1.0 - ell)
+        Q[i, (i + 1) % M] += 0.5 * (1.0 - ell)
+    K = np.zeros((M, M))
+    for i in range(M):
+        for j in range(M):
+            if j != i and Q[i, j] > 0.0:
+                K[i, j] = Q[i, j] * acc(p[i], p[j])
+        K[i, i] = 1.0 - K[i].sum()
+    return K

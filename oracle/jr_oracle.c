@@ -19,6 +19,9 @@
  *   - estimator: normalisation-free tour estimator (Section 6.3),
  *     (c~/j) * sum_i dt_i * g(x_{i-1}) / p(x_{i-1}), left-rectangle rule of
  *     Section 7.4 ("approx").
+ *   - the MH baseline of Section 8 ("Metropolis"): Alg. 1 with the mixture
+ *     proposal of Section 5, l mu + (1 - l) zeta, and its ergodic-average
+ *     estimator after a burn-in (Section 9 parameters).
  *   - the integrand: primary-sample-space (Section 2, Kelemen et al.) path
  *     contribution of a unidirectional path tracer with emission collected at
  *     every vertex; p = luminance of the RGB contribution.
@@ -844,6 +847,166 @@ ORC_EXPORT int orc_chains_advance(int target_kind, const orc_scene* scene, const
         L += jobs[t].locals;
     }
     out3[0] = J; out3[1] = A; out3[2] = L;
+    free(jobs);
+    free(th);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The MH baseline "Metropolis" of the paper's practical pairing (Section 8):  */
+/* one MH chain per chain id with the mixture proposal of Section 5 (eq.       */
+/* "mixture-proposal-kernel"): Q_l(x, .) = l mu + (1 - l) zeta(x, .), with the */
+/* large-step distribution mu = uniform on [0,1)^D and the small-step kernel   */
+/* zeta = N(x, sigma^2) wrapped onto the torus (both symmetric in x and y, so  */
+/* the Hastings ratio of Q_l is 1 and the acceptance of Section 4 is           */
+/* min(1, p(y)/p(x))); Alg. 1 takes one step.  Section 9: l = 0.3 and the      */
+/* estimate uses only the iterations after the first burn_in.                  */
+/*                                                                             */
+/* Estimator (the ergodic average of the MH chain, pi = p / b): pixel j =      */
+/* b_hat * (1/N) sum_{i >= burn_in} W H 1[pix(x_i) = j] F(x_i) / p(x_i), with  */
+/* x_i the state before iteration i, N the number of such iterations, and the  */
+/* normalisation b = integral of p estimated by the mean of p over the         */
+/* large-step proposals (uniform draws, so an unbiased estimate of b).         */
+/*                                                                             */
+/* Random numbers (a reading): the Restore step's counters (tag 0).  Block 0   */
+/* gives (U_s, -, U_a, -): a large step if U_s < l; U_a decides acceptance.    */
+/* Blocks 1.. give the D coordinates: uniforms for a large step, Gaussian      */
+/* pairs for a small step, exactly as in the Restore step.                     */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    const orc_params* P;
+    double ell;
+    uint64_t burn_in;
+    uint64_t chain_begin, c_lo, c_hi;
+    uint64_t step_begin, n_steps;
+    double* state;
+    double* accum;            /* W*H*4: RGB sums of W H F / p and the count of splats */
+    uint64_t n_large, n_small, accepts, splats;
+    double p_sum_large;       /* sum of p(y) over the large-step proposals */
+    uint8_t* tr_flags;        /* optional [chain][step]: bit0 large step, bit1 accepted, bit2 splatted */
+    int32_t* tr_pix;
+    double* tr_margin;        /* optional: U_a p(x) - p(y) */
+} orc_mh_job;
+
+static void run_chain_mh(orc_mh_job* jb, uint64_t c)
+{
+    const orc_params* P = jb->P;
+    int D = P->D, S = D + 5;
+    double* st = jb->state + c * S;
+    uint32_t chain = (uint32_t)(jb->chain_begin + c);
+    double v[ORC_MAX_DIM + 8], y[ORC_MAX_DIM], cand[ORC_MAX_DIM + 5];
+    double WH = (double)P->width * (double)P->height;
+    for (uint64_t i = 0; i < jb->n_steps; ++i) {
+        uint64_t step = jb->step_begin + i;
+        double U[4];
+        draw_block(P->seed, ORC_TAG_STEP, 0, chain, step, U);
+        double p = st[D + 3];
+        /* the estimator's term for the state x_i held at this iteration */
+        int pix = -1, splatted = 0;
+        if (step >= jb->burn_in) {
+            jb->splats += 1;
+            splatted = 1;
+            if (p > 0.0) {
+                int px, py;
+                pixel_of(P, st, &px, &py);
+                pix = py * P->width + px;
+                double wgt = WH / p;
+                double* a = jb->accum + 4 * (size_t)pix;
+                a[0] += wgt * st[D];
+                a[1] += wgt * st[D + 1];
+                a[2] += wgt * st[D + 2];
+                a[3] += 1.0;
+            }
+        }
+        /* proposal y ~ Q_l(x, .): large step from mu with probability l */
+        int large = U[0] < jb->ell;
+        draw_coords(P->seed, ORC_TAG_STEP, chain, step, D, v);
+        if (large) {
+            for (int d = 0; d < D; ++d) y[d] = v[d];
+        } else {
+            for (int k = 0; k < (D + 1) / 2; ++k) {
+                double R = sqrt(-2.0 * log(1.0 - v[2 * k]));
+                double ang = 2.0 * M_PI * v[2 * k + 1];
+                y[2 * k] = wrap01(st[2 * k] + P->sigma * R * cos(ang));
+                if (2 * k + 1 < D) y[2 * k + 1] = wrap01(st[2 * k + 1] + P->sigma * R * sin(ang));
+            }
+        }
+        eval_into_state(P, y, cand);
+        double py = cand[D + 3];
+        if (large) {
+            jb->n_large += 1;
+            jb->p_sum_large += py;
+        } else {
+            jb->n_small += 1;
+        }
+        /* Alg. 1: accept with probability alpha = min(1, p(y)/p(x)) (1 if p(x) = 0) */
+        int accepted = U[2] < orc_mh_accept_prob(p, py);
+        if (accepted) memcpy(st, cand, sizeof(double) * (size_t)S);
+        jb->accepts += (uint64_t)accepted;
+        if (jb->tr_flags) {
+            size_t o = (size_t)c * jb->n_steps + i;
+            jb->tr_flags[o] = (uint8_t)((large ? 1 : 0) | (accepted ? 2 : 0) | (splatted ? 4 : 0));
+            jb->tr_pix[o] = pix;
+            if (jb->tr_margin) jb->tr_margin[o] = U[2] * p - py;
+        }
+    }
+}
+
+static void* run_worker_mh(void* arg)
+{
+    orc_mh_job* jb = (orc_mh_job*)arg;
+    for (uint64_t c = jb->c_lo; c < jb->c_hi; ++c) run_chain_mh(jb, c);
+    return NULL;
+}
+
+/* Public: advance n MH chains by n_steps (global step indices step_begin..).  *
+ * accum (W*H*4) is ADDED to; out4 = (large-step proposals, small-step         *
+ * proposals, accepted, splatted iterations); *p_sum_large is ADDED to.        *
+ * States are initialised with orc_chains_init (x0 ~ mu).                      */
+ORC_EXPORT int orc_mh_advance(int target_kind, const orc_scene* scene, const orc_analytic* an, int D, int depth,
+                              int width, int height, double sigma, double ell, uint64_t burn_in, uint64_t seed,
+                              uint64_t chain_begin, uint64_t n, uint64_t step_begin, uint64_t n_steps, double* state,
+                              double* accum, uint64_t* out4, double* p_sum_large, uint8_t* tr_flags, int32_t* tr_pix,
+                              double* tr_margin, int n_threads)
+{
+    if (D > ORC_MAX_DIM || D < 1 || !(ell >= 0.0 && ell <= 1.0)) return -1;
+    orc_params P = make_params(target_kind, scene, an, D, depth, width, height, 1.0, sigma, seed, 0);
+    int T = resolve_threads(n_threads, n);
+    orc_mh_job* jobs = (orc_mh_job*)calloc((size_t)T, sizeof(orc_mh_job));
+    pthread_t* th = (pthread_t*)calloc((size_t)T, sizeof(pthread_t));
+    size_t npx = (size_t)width * (size_t)height * 4;
+    for (int t = 0; t < T; ++t) {
+        orc_mh_job* jb = &jobs[t];
+        jb->P = &P;
+        jb->ell = ell;
+        jb->burn_in = burn_in;
+        jb->chain_begin = chain_begin;
+        jb->c_lo = n * (uint64_t)t / (uint64_t)T;
+        jb->c_hi = n * (uint64_t)(t + 1) / (uint64_t)T;
+        jb->step_begin = step_begin;
+        jb->n_steps = n_steps;
+        jb->state = state;
+        jb->accum = (double*)calloc(npx, sizeof(double));
+        jb->tr_flags = tr_flags;
+        jb->tr_pix = tr_pix;
+        jb->tr_margin = tr_margin;
+        if (T > 1) pthread_create(&th[t], NULL, run_worker_mh, jb);
+    }
+    if (T == 1) run_worker_mh(&jobs[0]);
+    uint64_t L = 0, Sm = 0, A = 0, N = 0;
+    double ps = 0.0;
+    for (int t = 0; t < T; ++t) {
+        if (T > 1) pthread_join(th[t], NULL);
+        for (size_t k = 0; k < npx; ++k) accum[k] += jobs[t].accum[k];
+        free(jobs[t].accum);
+        L += jobs[t].n_large;
+        Sm += jobs[t].n_small;
+        A += jobs[t].accepts;
+        N += jobs[t].splats;
+        ps += jobs[t].p_sum_large;
+    }
+    out4[0] = L; out4[1] = Sm; out4[2] = A; out4[3] = N;
+    *p_sum_large += ps;
     free(jobs);
     free(th);
     return 0;

@@ -80,6 +80,9 @@ def lib():
             L.orc_chains_advance.argtypes = [I, P, P, I, I, I, I, D, D, U64, I, U64, U64, U64, U64,
                                              P, P, P, P, P, P, P, I]
             L.orc_chains_advance.restype = I
+            L.orc_mh_advance.argtypes = [I, P, P, I, I, I, I, D, D, U64, U64, U64, U64, U64, U64, P, P, P, P,
+                                         P, P, P, I]
+            L.orc_mh_advance.restype = I
             L.orc_eval_states.argtypes = [I, P, P, I, I, D, U64, P, P, P, P, P, P]
             L.orc_render_pt.argtypes = [I, P, P, I, I, I, I, U64, U64, U64, P, I]
             L.orc_threads_default.restype = I
@@ -261,6 +264,63 @@ class Chains:
     def image(self):
         """Normalisation-free estimate (Section 6.3): accum / J."""
         return self.accum[:, :, :3] / max(self.J, 1)
+
+
+class MHChains:
+    """MH chains with the mixture proposal l mu + (1 - l) zeta (the baseline
+    "Metropolis" of Section 8) run by the oracle; x0 ~ mu as for Restore."""
+
+    def __init__(self, target, D, width, height, sigma=0.01, ell=0.3, burn_in=10_000, seed=0, depth=None,
+                 chain_begin=0, n_chains=1):
+        self.target = target
+        self.kind, self.sh, self.ah = _target(target)
+        self.D = int(D)
+        self.depth = int(depth) if depth is not None else (self.D - 2) // 2
+        self.W, self.H = int(width), int(height)
+        self.sigma, self.ell, self.burn_in, self.seed = float(sigma), float(ell), int(burn_in), int(seed)
+        self.chain_begin, self.n = int(chain_begin), int(n_chains)
+        self.S = lib().orc_state_stride(self.D)
+        self.state = np.zeros((self.n, self.S))
+        lib().orc_chains_init(self.kind, self.sh, self.ah, self.D, self.depth, self.W, self.H, 1.0, self.sigma,
+                              self.seed, self.chain_begin, self.n, _ptr(self.state))
+        self.accum = np.zeros((self.H, self.W, 4))
+        self.step = 0
+        self.n_large = self.n_small = self.accepts = self.splats = 0
+        self.p_sum_large = 0.0
+
+    x = Chains.x
+    F = Chains.F
+    p = Chains.p
+
+    def advance(self, n_steps, trace=False, margins=False, n_threads=0):
+        out = np.zeros(4, dtype=np.uint64)
+        ps = np.zeros(1)
+        tr = None
+        if trace:
+            tr = dict(flags=np.zeros((self.n, n_steps), np.uint8), pix=np.zeros((self.n, n_steps), np.int32),
+                      margin=np.zeros((self.n, n_steps)) if margins else None)
+        rc = lib().orc_mh_advance(
+            self.kind, self.sh, self.ah, self.D, self.depth, self.W, self.H, self.sigma, self.ell, self.burn_in,
+            self.seed, self.chain_begin, self.n, self.step, n_steps, _ptr(self.state), _ptr(self.accum), _ptr(out),
+            _ptr(ps), _ptr(tr["flags"]) if tr else None, _ptr(tr["pix"]) if tr else None,
+            _ptr(tr["margin"]) if tr and margins else None, int(n_threads))
+        if rc != 0:
+            raise ValueError("oracle: invalid dimension or large-step probability")
+        self.step += n_steps
+        self.n_large += int(out[0])
+        self.n_small += int(out[1])
+        self.accepts += int(out[2])
+        self.splats += int(out[3])
+        self.p_sum_large += float(ps[0])
+        return tr
+
+    def b_hat(self):
+        """Estimate of b = integral of p from the large-step proposals."""
+        return self.p_sum_large / max(self.n_large, 1)
+
+    def image(self):
+        """MH ergodic-average estimate: b_hat * accum / N."""
+        return self.b_hat() * self.accum[:, :, :3] / max(self.splats, 1)
 
 
 def eval_states(target, x, c_tilde=1.0, depth=None, hit_ids=False):
