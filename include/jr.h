@@ -64,6 +64,20 @@ typedef enum {
 #define JR_MAT_DIELECTRIC 2   /* smooth dielectric, Fresnel-chosen reflect/refract, weight 1 */
 #define JR_MAX_DEPTH 15       /* D = 2 + 2 * max_depth <= 32 */
 #define JR_FLAG_RAO_BLACKWELL 1u /* splat the conditional mean 1/(1+k) instead of the sampled dt */
+/* The chain set runs the paper's MH baseline "Metropolis" (Section 8, practical
+ * pairing) instead of Jump Restore: Alg. 1 (Section 4) with the mixture
+ * proposal of Section 5 (eq. "mixture-proposal-kernel"), Q_l(x, .) = l mu +
+ * (1 - l) zeta(x, .), mu uniform on [0,1)^D, zeta the Gaussian small step;
+ * both parts are symmetric, so alpha = min(1, p(y)/p(x)) (1 if p(x) = 0).  The
+ * estimate is the chain's ergodic average after `burn_in` iterations (Section
+ * 9 uses l = 0.3 and 10,000): pixel j = b_hat (1/N) sum_i W H 1[pix(x_i) = j]
+ * F(x_i) / p(x_i), x_i the state held at iteration i >= burn_in, N the number
+ * of such iterations over all chains, and b_hat = the mean of p over the
+ * large-step proposals (uniform draws: an unbiased estimate of the integral of
+ * p).  Random numbers: the Restore step's counters; block 0 gives (U_s, -, U_a,
+ * -), a large step if U_s < l; blocks 1.. give the D uniforms (large) or
+ * Gaussian pairs (small).  Not with JR_FLAG_RAO_BLACKWELL, flows or drains. */
+#define JR_FLAG_MH 2u
 
 /* status-word bits (jr_stats.status_word) */
 #define JR_STATUS_NONFINITE 1u  /* F(x) was NaN/Inf for some state: it was treated as 0 */
@@ -105,15 +119,18 @@ typedef struct {
     uint64_t seed;          /* Philox key */
     float c_tilde;          /* c~ > 0 of the killing rate (the paper uses 1, Section 9) */
     float sigma;            /* std of the Gaussian small-step kernel zeta, > 0 */
+    float large_step;       /* JR_FLAG_MH: large-step probability l in [0, 1] (Section 9: 0.3) */
+    uint32_t burn_in;       /* JR_FLAG_MH: iterations (step index) before the estimator starts */
 } jr_params;
 
 typedef struct {
     uint64_t steps_per_chain; /* Alg. 2 iterations each chain has taken */
-    uint64_t regenerations;   /* J: killings followed by a draw from mu (completed tours) */
-    uint64_t local_steps;     /* iterations that took the local branch */
-    uint64_t accepted;        /* accepted local MH proposals */
+    uint64_t regenerations;   /* J: killings followed by a draw from mu (completed tours); MH: large-step proposals */
+    uint64_t local_steps;     /* iterations that took the local branch; MH: small-step proposals */
+    uint64_t accepted;        /* accepted local MH proposals; MH: accepted proposals of both kinds */
     uint32_t status_word;     /* JR_STATUS_* bits, sticky */
     uint32_t dim;             /* D */
+    double p_sum_large;       /* MH: sum of p over the large-step proposals (b_hat = p_sum_large / regenerations) */
 } jr_stats;
 
 typedef struct {
@@ -153,6 +170,8 @@ jr_status jr_advance(jr_chains* chains, uint32_t n_steps, void* stream);
  *   flags: bit0 = the regeneration branch was taken, bit1 = a local proposal
  *          was accepted;  dt: the splatted holding time (0 if nothing was
  *          splatted);  pix: y*W + x of the splat, or -1.
+ *   JR_FLAG_MH: bit0 = a large-step proposal, bit1 = the proposal was
+ *          accepted; dt = 1 where the held state was splatted.
  * Any of the three pointers may be NULL. */
 jr_status jr_advance_traced(jr_chains* chains, uint32_t n_steps, uint8_t* flags_dev, float* dt_dev,
                             int32_t* pix_dev, void* stream);
@@ -229,13 +248,16 @@ jr_status jr_set_execution(jr_chains* chains, uint32_t mode);
 jr_status jr_advance_static(jr_chains* chains, uint32_t n_steps, void* stream);
 
 /* Resolve the estimate (Section 6.3): rgb_out[H][W][3] = accumulator / J
- * (zeros while J = 0).  out_is_device = 1: rgb_out is device memory and the
- * call is asynchronous; 0: host memory, the call synchronises `stream`. */
+ * (zeros while J = 0); with JR_FLAG_MH, b_hat accumulator / N (see JR_FLAG_MH;
+ * zeros before the first large step or the end of the burn-in).
+ * out_is_device = 1: rgb_out is device memory and the call is asynchronous;
+ * 0: host memory, the call synchronises `stream`. */
 jr_status jr_resolve(jr_chains* chains, float* rgb_out, int out_is_device, void* stream);
 
 /* Raw FP64 accumulator, out[H][W][4] = (sum of c~ dt W H F / p per channel,
- * sum of dt in the pixel), for batch statistics and shard reductions.  Same
- * device/host convention as jr_resolve. */
+ * sum of dt in the pixel), for batch statistics and shard reductions (MH: the
+ * sum of W H F / p and the number of splatted iterations).  Same device/host
+ * convention as jr_resolve. */
 jr_status jr_get_accumulator(jr_chains* chains, double* out, int out_is_device, void* stream);
 
 /* Counters and status word; synchronises `stream`.  Returns JR_ERR_NUMERIC or

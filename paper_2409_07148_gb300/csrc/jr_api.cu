@@ -86,6 +86,12 @@ struct jr_chains {
     }
 };
 
+// Post-burn-in iterations of an MH chain set over all chains (the N of its estimator).
+static uint64_t mh_samples(const jr_chains* c) {
+    if (!(c->view.flags & JR_FLAG_MH)) return 0;
+    return c->steps > c->view.burn_in ? (c->steps - c->view.burn_in) * c->view.n : 0;
+}
+
 extern "C" {
 
 const char* jr_last_error(void) { return g_err.c_str(); }
@@ -178,6 +184,12 @@ static jr_status check_params(const jr_params* p, const char* who) {
         return fail(JR_ERR_INVALID_ARG, std::string(who) + ": c_tilde must be finite and > 0");
     if (!(p->sigma > 0.f) || !std::isfinite(p->sigma))
         return fail(JR_ERR_INVALID_ARG, std::string(who) + ": sigma must be finite and > 0");
+    if (p->flags & ~(JR_FLAG_RAO_BLACKWELL | JR_FLAG_MH))
+        return fail(JR_ERR_INVALID_ARG, std::string(who) + ": unknown flag");
+    if ((p->flags & JR_FLAG_MH) && (p->flags & JR_FLAG_RAO_BLACKWELL))
+        return fail(JR_ERR_INVALID_ARG, std::string(who) + ": the MH baseline has no holding times to Rao-Blackwellise");
+    if ((p->flags & JR_FLAG_MH) && !(p->large_step >= 0.f && p->large_step <= 1.f))
+        return fail(JR_ERR_INVALID_ARG, std::string(who) + ": large_step must be in [0, 1]");
     return JR_OK;
 }
 
@@ -203,15 +215,17 @@ jr_status jr_chains_create(const jr_scene* scene, const jr_params* params, void*
     v.seed = params->seed;
     v.c_tilde = params->c_tilde;
     v.sigma = params->sigma;
+    v.large_step = (params->flags & JR_FLAG_MH) ? params->large_step : 0.f;
+    v.burn_in = (params->flags & JR_FLAG_MH) ? params->burn_in : 0;
     const size_t npx = (size_t)params->width * params->height;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     if ((e = dev_alloc(&v.x, (size_t)v.dim * v.n)) != cudaSuccess || (e = dev_alloc(&v.fpu, 5 * v.n)) != cudaSuccess ||
         (e = dev_alloc(&v.fb, npx)) != cudaSuccess || (e = dev_alloc(&v.acc64, npx)) != cudaSuccess ||
-        (e = dev_alloc(&v.counters, 4)) != cudaSuccess || (e = dev_alloc(&v.status, 1)) != cudaSuccess ||
+        (e = dev_alloc(&v.counters, kCounters)) != cudaSuccess || (e = dev_alloc(&v.status, 1)) != cudaSuccess ||
         (e = cudaMemsetAsync(v.fb, 0, sizeof(float4) * npx, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(v.acc64, 0, sizeof(double4_32a) * npx, st)) != cudaSuccess ||
-        (e = cudaMemsetAsync(v.counters, 0, sizeof(unsigned long long) * 4, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(v.counters, 0, sizeof(unsigned long long) * kCounters, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(v.status, 0, sizeof(unsigned int), st)) != cudaSuccess ||
         (e = launch_init(scene->view, v, st)) != cudaSuccess ||
         (e = prepare_static_scratch()) != cudaSuccess) {  // jr_advance_static's array, see jr_wavefront.cu
@@ -372,13 +386,13 @@ jr_status jr_resolve(jr_chains* c, float* rgb_out, int out_is_device, void* stre
     cudaStream_t st = (cudaStream_t)stream;
     const size_t npx = (size_t)c->view.width * c->view.height;
     if (out_is_device) {
-        JR_CUDA(launch_resolve(c->view, rgb_out, st), "jr_resolve");
+        JR_CUDA(launch_resolve(c->view, rgb_out, mh_samples(c), st), "jr_resolve");
         return JR_OK;
     }
     float* tmp = nullptr;
     JR_CUDA(dev_alloc(&tmp, 3 * npx), "jr_resolve");
     cudaError_t e;
-    if ((e = launch_resolve(c->view, tmp, st)) != cudaSuccess ||
+    if ((e = launch_resolve(c->view, tmp, mh_samples(c), st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(rgb_out, tmp, sizeof(float) * 3 * npx, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess) {
         cudaFree(tmp);
@@ -402,7 +416,7 @@ jr_status jr_get_accumulator(jr_chains* c, double* out, int out_is_device, void*
 jr_status jr_get_stats(jr_chains* c, jr_stats* out, void* stream) {
     if (!c || !out) return fail(JR_ERR_INVALID_ARG, "jr_get_stats: null argument");
     cudaStream_t st = (cudaStream_t)stream;
-    unsigned long long cnt[4];
+    unsigned long long cnt[kCounters];
     unsigned int status = 0;
     JR_CUDA(cudaMemcpyAsync(cnt, c->view.counters, sizeof(cnt), cudaMemcpyDeviceToHost, st), "jr_get_stats");
     JR_CUDA(cudaMemcpyAsync(&status, c->view.status, sizeof(status), cudaMemcpyDeviceToHost, st), "jr_get_stats");
@@ -413,6 +427,7 @@ jr_status jr_get_stats(jr_chains* c, jr_stats* out, void* stream) {
     out->accepted = cnt[2];
     out->status_word = status;
     out->dim = c->view.dim;
+    std::memcpy(&out->p_sum_large, &cnt[kCounterPSum], sizeof(double));
     if (status & (JR_STATUS_TRAVERSAL | JR_STATUS_STACK))
         return fail(JR_ERR_WATCHDOG, "jr_get_stats: a ray exhausted the traversal budget or stack");
     if (status & JR_STATUS_NONFINITE) return fail(JR_ERR_NUMERIC, "jr_get_stats: non-finite path contribution");
@@ -451,7 +466,8 @@ jr_status jr_set_state(jr_chains* c, const float* x_in, const float* fpu_in, voi
 jr_status jr_set_counters(jr_chains* c, const jr_stats* in, const double* acc_host, void* stream) {
     if (!c || !in) return fail(JR_ERR_INVALID_ARG, "jr_set_counters: null argument");
     cudaStream_t st = (cudaStream_t)stream;
-    unsigned long long cnt[4] = {in->regenerations, in->local_steps, in->accepted, 0};
+    unsigned long long cnt[kCounters] = {in->regenerations, in->local_steps, in->accepted, 0, 0, 0, 0, 0};
+    std::memcpy(&cnt[kCounterPSum], &in->p_sum_large, sizeof(double));
     unsigned int status = in->status_word;
     JR_CUDA(cudaMemcpyAsync(c->view.counters, cnt, sizeof(cnt), cudaMemcpyHostToDevice, st), "jr_set_counters");
     JR_CUDA(cudaMemcpyAsync(c->view.status, &status, sizeof(status), cudaMemcpyHostToDevice, st), "jr_set_counters");
@@ -1226,6 +1242,7 @@ extern "C" {
 
 jr_status jr_complete_tours(jr_chains* c, uint32_t max_steps, uint64_t* remaining, void* stream) {
     if (!c) return fail(JR_ERR_INVALID_ARG, "jr_complete_tours: null chains");
+    if (c->view.flags & JR_FLAG_MH) return fail(JR_ERR_STATE, "jr_complete_tours: an MH chain set has no tours");
     cudaStream_t st = (cudaStream_t)stream;
     jr_status r = drain_impl(c, max_steps, remaining, st, "jr_complete_tours");
     if (r == JR_OK) r = restart_impl(c, st, "jr_complete_tours");
@@ -1235,6 +1252,8 @@ jr_status jr_complete_tours(jr_chains* c, uint32_t max_steps, uint64_t* remainin
 jr_status jr_chains_set_flow(jr_chains* c, const jr_flow* f, float beta, uint32_t max_drain_steps,
                              uint64_t* remaining, void* stream) {
     if (!c) return fail(JR_ERR_INVALID_ARG, "jr_chains_set_flow: null chains");
+    if (c->view.flags & JR_FLAG_MH)
+        return fail(JR_ERR_STATE, "jr_chains_set_flow: the MH baseline regenerates from the uniform mu only");
     if (f && f->D != c->view.dim) return fail(JR_ERR_INVALID_ARG, "jr_chains_set_flow: flow and chain dimensions differ");
     if (f && !(beta >= 0.f && beta < 1.f))
         return fail(JR_ERR_INVALID_ARG, "jr_chains_set_flow: beta must be in [0, 1)");

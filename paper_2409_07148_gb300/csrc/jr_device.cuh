@@ -424,5 +424,12 @@ __device__ __forceinline__ void flush_status(unsigned status, unsigned int* word
     if (status) atomicOr(word, status);
 }
 
+// Sum of a double over the 32 lanes of a warp (all lanes call; every lane gets the sum).
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 }  // namespace
 }  // namespace jr

@@ -19,6 +19,8 @@ constexpr int kLeafMax = 8;                 // triangles per leaf (encoded count
 constexpr uint32_t kNodeVisitBudget = 1u << 16;  // per ray; exceeding it is a watchdog event
 
 constexpr uint32_t kTagStep = 0, kTagInit = 1, kTagPt = 2, kTagRestart = 3;
+constexpr int kCounters = 8;   // ChainView::counters entries
+constexpr int kCounterPSum = 5;  // MH: sum of p over the large-step proposals (double)
 constexpr uint64_t kWavefrontMinChains = 1u << 16;  // JR_EXEC_AUTO picks the wavefront from here up
 
 // 4-wide BVH node, 128 bytes (one L2 line): the boxes of up to 4 children,
@@ -112,14 +114,19 @@ struct ChainView {
     float* fpu;      // [5][n] F.r F.g F.b p u
     float4* fb;      // [H*W] RGB sum + dt, FP32 (folded into acc64 after each advance)
     double4_32a* acc64;  // [H*W]
-    unsigned long long* counters;  // [0] J, [1] local steps, [2] accepted, [3] drain mark
+    // [0] J (MH: large-step proposals), [1] local steps (MH: small-step
+    // proposals), [2] accepted, [3] drain mark, [4] unused, [5] MH: the sum of
+    // p over the large-step proposals (a double's bits), [6..7] unused
+    unsigned long long* counters;
     unsigned int* status;
     uint64_t n;
     uint32_t chain_offset;
     uint32_t width, height, depth, dim;
-    uint32_t flags;
+    uint32_t flags;                // JR_FLAG_*; JR_FLAG_MH: the MH baseline instead of Jump Restore
     uint64_t seed;
     float c_tilde, sigma;
+    float large_step;              // MH: large-step probability l of the mixture proposal
+    uint64_t burn_in;              // MH: iterations before the estimator starts
     WaveView wf;
     FlowView flow;   // flow.D == 0: uniform regeneration (u = 1)
 };
@@ -274,7 +281,9 @@ cudaError_t launch_flow_train_step(const FlowView& f, const float* x, const floa
                                    uint32_t batch, float* grad, float* wsum, float* loss, cudaStream_t st);
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, uint64_t count, float lr, uint64_t t,
                         cudaStream_t st);
-cudaError_t launch_resolve(const ChainView& c, float* rgb, cudaStream_t st);
+// image = accumulator / J (Jump Restore), or b_hat accumulator / mh_samples
+// with b_hat = (sum of p over large steps) / (large steps) (MH, JR_FLAG_MH).
+cudaError_t launch_resolve(const ChainView& c, float* rgb, uint64_t mh_samples, cudaStream_t st);
 cudaError_t launch_reeval(const SceneView& s, const ChainView& c, cudaStream_t st);
 cudaError_t launch_eval_states(const SceneView& s, uint32_t depth, float c_tilde, const float* x, uint64_t n,
                                float* F, float* p, float* u, float* k, int32_t* ids, cudaStream_t st);

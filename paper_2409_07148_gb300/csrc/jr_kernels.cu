@@ -83,6 +83,8 @@ __device__ __forceinline__ void chain_steps(const SceneView& s, const ChainView&
     uint32_t nJ = 0, nL = 0, nA = 0;
     unsigned status = 0;
     Work work;
+    const bool mh = (c.flags & JR_FLAG_MH) != 0;
+    double psum = 0.0;  // MH: sum of p over this chain's large-step proposals
     if (active) {
         for (int d = 0; d < D; ++d) buf0[d * B] = c.x[d * c.n + i];
         float Fr = c.fpu[0 * c.n + i], Fg = c.fpu[1 * c.n + i], Fb = c.fpu[2 * c.n + i];
@@ -96,23 +98,34 @@ __device__ __forceinline__ void chain_steps(const SceneView& s, const ChainView&
         for (uint32_t st = 0; st < n_steps; ++st) {
             const uint64_t step = step_begin + st;
             const uint4 r0 = draw(c.seed, kTagStep, 0, chain, step);
-            // Alg. 2: holding time t1 ~ Exp(1); killing time t2 ~ Exp(k), k = c~ u / p.
-            const float E1 = -logf(1.0f - u01(r0.x));
-            const float E2 = -logf(1.0f - u01(r0.y));
             const float Ua = u01(r0.z);
-            const float t2 = p > 0.0f ? E2 * p / (c_tilde * u) : 0.0f;
-            const bool local = E1 < t2;  // a tie goes to the killing branch
-            float dt = local ? E1 : t2;
-            if (rb) dt = p > 0.0f ? p / (p + c_tilde * u) : 0.0f;
+            bool local;
+            float dt;
+            if (mh) {
+                // the MH baseline: a large step (from mu) with probability l, else
+                // a small step; the state before the iteration enters the
+                // estimator once the burn-in is over (dt = 1 counts it)
+                local = !(u01(r0.x) < c.large_step);
+                dt = step >= c.burn_in ? 1.0f : 0.0f;
+            } else {
+                // Alg. 2: holding time t1 ~ Exp(1); killing time t2 ~ Exp(k), k = c~ u / p.
+                const float E1 = -logf(1.0f - u01(r0.x));
+                const float E2 = -logf(1.0f - u01(r0.y));
+                const float t2 = p > 0.0f ? E2 * p / (c_tilde * u) : 0.0f;
+                local = E1 < t2;  // a tie goes to the killing branch
+                dt = local ? E1 : t2;
+                if (rb) dt = p > 0.0f ? p / (p + c_tilde * u) : 0.0f;
+            }
             int32_t pix = -1;
             if (dt > 0.0f && p > 0.0f) {
-                // left-rectangle estimator: x_{i-1} weighted by dt_i (Section 7.4)
+                // left-rectangle estimator: x_{i-1} weighted by dt_i (Section 7.4);
+                // MH: the ergodic average's term W H F / p of the held state
                 uint32_t px = (uint32_t)((double)cur[0] * (double)c.width);
                 uint32_t py = (uint32_t)((double)cur[B] * (double)c.height);
                 px = min(px, c.width - 1);
                 py = min(py, c.height - 1);
                 pix = (int32_t)(py * c.width + px);
-                const float wgt = c_tilde * dt * WH / p;
+                const float wgt = mh ? WH / p : c_tilde * dt * WH / p;
                 atomicAdd(c.fb + pix, make_float4(wgt * Fr, wgt * Fg, wgt * Fb, dt));
             }
             // candidate y: Gaussian small step (local) or a fresh draw from mu
@@ -143,7 +156,16 @@ __device__ __forceinline__ void chain_steps(const SceneView& s, const ChainView&
             const float3 Fy = eval_path_w<kCount>(s, mask, true, (int)c.depth, cand, B, nullptr, 0, status, work);
             const float py_ = lum(Fy);
             bool accept;
-            if (local) {
+            if (mh) {  // Alg. 1: U < min(1, p(y)/p(x)), 1 if p(x) = 0
+                accept = !(p > 0.0f) || Ua * p < py_;
+                if (local) {
+                    nL++;
+                } else {
+                    nJ++;
+                    psum += (double)py_;
+                }
+                nA += accept;
+            } else if (local) {
                 accept = Ua * p < py_;  // U < min(1, p(y)/p(x)), p(x) > 0 on this branch
                 nL++;
                 nA += accept;
@@ -163,7 +185,7 @@ __device__ __forceinline__ void chain_steps(const SceneView& s, const ChainView&
             }
             if (kTrace) {
                 const uint64_t o = i * n_steps + st;
-                if (tr_flags) tr_flags[o] = (uint8_t)((local ? 0 : 1) | (local && accept ? 2 : 0));
+                if (tr_flags) tr_flags[o] = (uint8_t)((local ? 0 : 1) | ((mh || local) && accept ? 2 : 0));
                 if (tr_dt) tr_dt[o] = pix >= 0 ? dt : 0.0f;
                 if (tr_pix) tr_pix[o] = pix;
             }
@@ -180,6 +202,7 @@ __device__ __forceinline__ void chain_steps(const SceneView& s, const ChainView&
     nL = __reduce_add_sync(0xffffffffu, nL);
     nA = __reduce_add_sync(0xffffffffu, nA);
     status = __reduce_or_sync(0xffffffffu, status);
+    if (mh) psum = warp_sum(psum);
     if constexpr (kCount) {
         const uint32_t r = __reduce_add_sync(0xffffffffu, work.rays);
         const uint32_t nd = __reduce_add_sync(0xffffffffu, work.nodes);
@@ -194,6 +217,7 @@ __device__ __forceinline__ void chain_steps(const SceneView& s, const ChainView&
         if (nJ) atomicAdd(c.counters + 0, (unsigned long long)nJ);
         if (nL) atomicAdd(c.counters + 1, (unsigned long long)nL);
         if (nA) atomicAdd(c.counters + 2, (unsigned long long)nA);
+        if (psum != 0.0) atomicAdd(reinterpret_cast<double*>(c.counters + kCounterPSum), psum);
         flush_status(status, c.status);
     }
 }
@@ -280,13 +304,20 @@ __global__ void fold_kernel(float4* fb, double4_32a* acc, uint32_t n) {
     }
 }
 
-// image = accumulator / J (Section 6.3, normalisation-free estimator).
-__global__ void resolve_kernel(const double4_32a* acc, const unsigned long long* counters, float* rgb, uint32_t n) {
+// image = accumulator / J (Section 6.3, normalisation-free estimator); MH
+// (mh_samples > 0): image = b_hat accumulator / N, the ergodic average over the
+// N post-burn-in iterations scaled by b_hat = mean p of the large-step proposals.
+__global__ void resolve_kernel(const double4_32a* acc, const unsigned long long* counters, float* rgb, uint32_t n,
+                               int mh, uint64_t mh_samples) {
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const unsigned long long J = counters[0];
     const double4_32a a = acc[j];
-    const double inv = J > 0 ? 1.0 / (double)J : 0.0;
+    double inv = J > 0 ? 1.0 / (double)J : 0.0;
+    if (mh) {
+        const double psum = __longlong_as_double((long long)counters[kCounterPSum]);
+        inv = J > 0 && mh_samples > 0 ? psum / (double)J / (double)mh_samples : 0.0;
+    }
     rgb[3 * j] = (float)(a.x * inv);
     rgb[3 * j + 1] = (float)(a.y * inv);
     rgb[3 * j + 2] = (float)(a.z * inv);
@@ -432,9 +463,10 @@ cudaError_t launch_batch(BatchEntry* entries, const BatchItem* items, uint32_t n
     return cudaGetLastError();
 }
 
-cudaError_t launch_resolve(const ChainView& c, float* rgb, cudaStream_t st) {
+cudaError_t launch_resolve(const ChainView& c, float* rgb, uint64_t mh_samples, cudaStream_t st) {
     const uint32_t n = c.width * c.height;
-    resolve_kernel<<<grid_for(n, 256), 256, 0, st>>>(c.acc64, c.counters, rgb, n);
+    resolve_kernel<<<grid_for(n, 256), 256, 0, st>>>(c.acc64, c.counters, rgb, n, (c.flags & JR_FLAG_MH) != 0,
+                                                     mh_samples);
     return cudaGetLastError();
 }
 

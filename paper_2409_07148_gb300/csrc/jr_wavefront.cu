@@ -62,34 +62,42 @@ __device__ __forceinline__ void count_and_flush(uint32_t nJ, uint32_t nL, uint32
 // count_and_flush for a whole block of the step kernel (4 warps): one atomic
 // per block and counter instead of one per warp (the counters are three
 // addresses that every block of a launch updates).  All threads call.
+// With JR_FLAG_MH, ps (the sum of p over large-step proposals) is summed too.
 __device__ __forceinline__ void count_and_flush_block(uint32_t nJ, uint32_t nL, uint32_t nA, unsigned status,
-                                                      const ChainView& c) {
+                                                      double ps, const ChainView& c) {
     __shared__ unsigned red_s[4][4];
+    __shared__ double ps_s[4];
+    const bool mh = (c.flags & JR_FLAG_MH) != 0;
     nJ = __reduce_add_sync(kFull, nJ);
     nL = __reduce_add_sync(kFull, nL);
     nA = __reduce_add_sync(kFull, nA);
     status = __reduce_or_sync(kFull, status);
+    if (mh) ps = warp_sum(ps);
     const int wq = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
         red_s[wq][0] = nJ;
         red_s[wq][1] = nL;
         red_s[wq][2] = nA;
         red_s[wq][3] = status;
+        ps_s[wq] = ps;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long sJ = 0, sL = 0, sA = 0;
         unsigned st = 0;
+        double sp = 0.0;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
             sJ += red_s[q][0];
             sL += red_s[q][1];
             sA += red_s[q][2];
             st |= red_s[q][3];
+            sp += ps_s[q];
         }
         if (sJ) atomicAdd(c.counters + 0, sJ);
         if (sL) atomicAdd(c.counters + 1, sL);
         if (sA) atomicAdd(c.counters + 2, sA);
         if (st) atomicOr(c.status, st);
+        if (mh && sp != 0.0) atomicAdd(reinterpret_cast<double*>(c.counters + kCounterPSum), sp);
     }
 }
 
@@ -115,13 +123,21 @@ __device__ __forceinline__ void count_and_flush_block(uint32_t nJ, uint32_t nL, 
 // step_chain is one chain's part (the body of the step kernel and of the
 // batched step kernel).  traced: the candidate is traced this step;
 // to_sample: it is a flow draw; active: in a drain, the tour goes on.
+// With JR_FLAG_MH the chain runs the MH baseline (Alg. 1 with the mixture
+// proposal of Section 5): the candidate is a large step (a draw from mu, as a
+// regeneration's) with probability l, else a small step (as a local move's);
+// every candidate goes through the MH acceptance; the held state is splatted
+// (weight W H F / p, count 1) once the step index reaches the burn-in.  The
+// stored Ua carries the large-step flag in its sign bit (-Ua, -0 included), so
+// the acceptance sees the exact Ua.  ps collects p of the large-step proposals.
 __device__ __forceinline__ void step_chain(const ChainView& c, uint64_t i, uint64_t step, bool finish, bool begin,
                                            int mode, uint32_t& nJ, uint32_t& nL, uint32_t& nA, unsigned& status,
-                                           bool& traced, bool& to_sample, bool& active) {
+                                           double& ps, bool& traced, bool& to_sample, bool& active) {
     const int D = (int)c.dim;
     const uint64_t n = c.n;
     const WaveView& w = c.wf;
     const bool has_flow = c.flow.D != 0;
+    const bool mh = (c.flags & JR_FLAG_MH) != 0;
     const bool restart = mode == kModeRestart, drain = mode == kModeDrain;
     // Every load the step needs is issued here, before any store: the film
     // point of the current state is read from both buffers, so that no
@@ -146,6 +162,16 @@ __device__ __forceinline__ void step_chain(const ChainView& c, uint64_t i, uint6
         if (restart) {     // a restart: the new tour's start, not a regeneration
             accept = true;
             w.done[i] = 0;
+        } else if (mh) {   // MH baseline: U < min(1, p(y)/p(x)), 1 if p(x) = 0
+            const bool large = signbit(ua);
+            accept = !(p > 0.0f) || fabsf(ua) * p < py;
+            if (large) {
+                nJ++;
+                ps += (double)py;
+            } else {
+                nL++;
+            }
+            nA += accept;
         } else if (ua >= 0.0f) {  // local branch: MH acceptance, U < min(1, p(y)/p(x))
             accept = ua * p < py;
             nL++;
@@ -177,24 +203,32 @@ __device__ __forceinline__ void step_chain(const ChainView& c, uint64_t i, uint6
         const uint32_t chain = c.chain_offset + (uint32_t)i;
         const uint32_t tag = restart ? kTagRestart : kTagStep;
         const uint4 r0 = draw(c.seed, tag, 0, chain, step);
-        const float E1 = -logf(1.0f - u01(r0.x));
-        const float E2 = -logf(1.0f - u01(r0.y));
         const float Ua = u01(r0.z);
-        const float t2 = p > 0.0f ? E2 * p / (c.c_tilde * u) : 0.0f;
-        const bool local = !restart && E1 < t2;  // a tie goes to the killing branch
-        float dt = local ? E1 : t2;
-        if (c.flags & JR_FLAG_RAO_BLACKWELL) dt = p > 0.0f ? p / (p + c.c_tilde * u) : 0.0f;
-        if (restart) dt = 0.0f;
+        bool local;
+        float dt;
+        if (mh) {
+            local = !(u01(r0.x) < c.large_step);
+            dt = step >= c.burn_in ? 1.0f : 0.0f;
+        } else {
+            const float E1 = -logf(1.0f - u01(r0.x));
+            const float E2 = -logf(1.0f - u01(r0.y));
+            const float t2 = p > 0.0f ? E2 * p / (c.c_tilde * u) : 0.0f;
+            local = !restart && E1 < t2;  // a tie goes to the killing branch
+            dt = local ? E1 : t2;
+            if (c.flags & JR_FLAG_RAO_BLACKWELL) dt = p > 0.0f ? p / (p + c.c_tilde * u) : 0.0f;
+            if (restart) dt = 0.0f;
+        }
         const bool use_flow = has_flow && !local && u01(r0.w) < c.flow.beta;
         to_sample = use_flow;
         const float x0 = par ? ys0 : xs0, x1 = par ? ys1 : xs1;  // = cur[i], cur[n + i]
         if (dt > 0.0f && p > 0.0f) {
             uint32_t px = min((uint32_t)((double)x0 * (double)c.width), c.width - 1);
             uint32_t py = min((uint32_t)((double)x1 * (double)c.height), c.height - 1);
-            const float wgt = c.c_tilde * dt * ((float)c.width * (float)c.height) / p;
+            const float WH = (float)c.width * (float)c.height;
+            const float wgt = mh ? WH / p : c.c_tilde * dt * WH / p;
             atomicAdd(c.fb + py * c.width + px, make_float4(wgt * Fr, wgt * Fg, wgt * Fb, dt));
         }
-        w.ua[i] = local ? Ua : use_flow ? -3.0f : -1.0f;
+        w.ua[i] = mh ? (local ? Ua : -Ua) : local ? Ua : use_flow ? -3.0f : -1.0f;
         if (drain && !local) {  // the tour ends here; no new tour in a drain
             nJ++;
             w.done[i] = 1;
@@ -255,8 +289,9 @@ __global__ void __launch_bounds__(128, 12) wf_step_kernel(ChainView c, uint64_t 
     const bool drain = mode == kModeDrain;
     uint32_t nJ = 0, nL = 0, nA = 0;
     unsigned status = 0;
+    double ps = 0.0;
     bool to_sample = false, traced = valid, active = false;
-    if (valid) step_chain(c, i, step, finish, begin, mode, nJ, nL, nA, status, traced, to_sample, active);
+    if (valid) step_chain(c, i, step, finish, begin, mode, nJ, nL, nA, status, ps, traced, to_sample, active);
     if (begin) {
         if (drain) enqueue(traced, (uint32_t)i, w.queue, w.qcount + 0);
         if (has_flow) enqueue(to_sample, (uint32_t)i, w.fq + n, w.qcount + kQFlowSample);
@@ -268,7 +303,7 @@ __global__ void __launch_bounds__(128, 12) wf_step_kernel(ChainView c, uint64_t 
             }
         }
     }
-    count_and_flush_block(nJ, nL, nA, status, c);  // launched with 128 threads
+    count_and_flush_block(nJ, nL, nA, status, ps, c);  // launched with 128 threads
 }
 
 // Whole paths of every queued chain in one persistent launch.  A lane keeps
@@ -449,10 +484,11 @@ __global__ void __launch_bounds__(128) wf_batch_step_kernel(const BatchEntry* en
     const uint64_t i = it.begin + threadIdx.x;
     uint32_t nJ = 0, nL = 0, nA = 0;
     unsigned status = 0;
+    double ps = 0.0;
     bool traced = true, to_sample = false, active = false;
     if (i < it.end)
-        step_chain(e.c, i, e.step + k, finish, begin, kModeStep, nJ, nL, nA, status, traced, to_sample, active);
-    count_and_flush_block(nJ, nL, nA, status, e.c);  // a block's chains are one set's
+        step_chain(e.c, i, e.step + k, finish, begin, kModeStep, nJ, nL, nA, status, ps, traced, to_sample, active);
+    count_and_flush_block(nJ, nL, nA, status, ps, e.c);  // a block's chains are one set's
 }
 
 // The path kernel over every set's candidates: item j of the launch is chain

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libjr_gb300.so")
 
 JR_OK, JR_ERR_INVALID_ARG, JR_ERR_CUDA, JR_ERR_OOM, JR_ERR_WATCHDOG, JR_ERR_NUMERIC, JR_ERR_STATE = range(7)
 JR_FLAG_RAO_BLACKWELL = 1
+JR_FLAG_MH = 2
 JR_EXEC_AUTO, JR_EXEC_MEGAKERNEL, JR_EXEC_WAVEFRONT = 0, 1, 2
 JR_STATUS_NONFINITE, JR_STATUS_TRAVERSAL, JR_STATUS_STACK = 1, 2, 4
 JR_BATCH_WAVEFRONT = 0
@@ -41,16 +42,18 @@ class SceneDesc(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("width", ctypes.c_uint32), ("height", ctypes.c_uint32), ("max_depth", ctypes.c_uint32),
                 ("flags", ctypes.c_uint32), ("n_chains", ctypes.c_uint64), ("chain_offset", ctypes.c_uint64),
-                ("seed", ctypes.c_uint64), ("c_tilde", ctypes.c_float), ("sigma", ctypes.c_float)]
+                ("seed", ctypes.c_uint64), ("c_tilde", ctypes.c_float), ("sigma", ctypes.c_float),
+                ("large_step", ctypes.c_float), ("burn_in", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("steps_per_chain", ctypes.c_uint64), ("regenerations", ctypes.c_uint64),
                 ("local_steps", ctypes.c_uint64), ("accepted", ctypes.c_uint64), ("status_word", ctypes.c_uint32),
-                ("dim", ctypes.c_uint32)]
+                ("dim", ctypes.c_uint32), ("p_sum_large", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+        return {k: (float(getattr(self, k)) if k == "p_sum_large" else int(getattr(self, k)))
+                for k, _ in self._fields_}
 
 
 class SceneInfo(ctypes.Structure):
@@ -157,9 +160,10 @@ def _hptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
-def make_params(width, height, depth, n_chains=1, seed=0, c_tilde=1.0, sigma=0.01, chain_offset=0, flags=0):
+def make_params(width, height, depth, n_chains=1, seed=0, c_tilde=1.0, sigma=0.01, chain_offset=0, flags=0,
+                large_step=0.0, burn_in=0):
     return Params(int(width), int(height), int(depth), int(flags), int(n_chains), int(chain_offset), int(seed),
-                  float(c_tilde), float(sigma))
+                  float(c_tilde), float(sigma), float(large_step), int(burn_in))
 
 
 class Scene:
@@ -197,9 +201,12 @@ class Chains:
     """A set of Jump Restore chains on the GPU (state, framebuffer, counters)."""
 
     def __init__(self, scene: Scene, width, height, depth, n_chains, seed=0, c_tilde=1.0, sigma=0.01,
-                 chain_offset=0, flags=0, stream=None):
+                 chain_offset=0, flags=0, large_step=0.3, burn_in=10_000, stream=None):
+        """flags may include JR_FLAG_MH: the MH baseline with large-step
+        probability `large_step` and `burn_in` (both ignored otherwise)."""
         self.scene = scene
-        self.params = make_params(width, height, depth, n_chains, seed, c_tilde, sigma, chain_offset, flags)
+        self.params = make_params(width, height, depth, n_chains, seed, c_tilde, sigma, chain_offset, flags,
+                                  large_step, burn_in)
         self.W, self.H, self.depth, self.n = int(width), int(height), int(depth), int(n_chains)
         self.D = 2 + 2 * self.depth
         h = ctypes.c_void_p()
@@ -275,7 +282,7 @@ class Chains:
         _check(lib().jr_set_state(self.h, _hptr(x), _hptr(f), _stream(stream)))
 
     def set_counters(self, stats: dict, accumulator=None, stream=None):
-        s = Stats(*[int(stats[k]) for k, _ in Stats._fields_])
+        s = Stats(*[(float(stats.get(k, 0.0)) if k == "p_sum_large" else int(stats[k])) for k, _ in Stats._fields_])
         a = None if accumulator is None else np.ascontiguousarray(accumulator, np.float64)
         _check(lib().jr_set_counters(self.h, ctypes.byref(s), _hptr(a), _stream(stream)))
 

@@ -94,7 +94,10 @@ def test_train_rows_reads_only_the_filled_rows(J):
     la = fa.train_replay(r, iters=20, batch=1024, lr=2e-3, seed=9)
     lb = fb.train(torch.from_numpy(x).cuda(), torch.from_numpy(wt).cuda(), iters=20, batch=1024, lr=2e-3, seed=9)
     assert np.isfinite(la).all()
-    assert np.allclose(la[:4], lb[:4], rtol=1e-5, atol=1e-6)   # before the rounding drift builds up
+    # the loss before any update and after the first one agree to rounding; from
+    # the second Adam step on, the atomics' summation order (which varies from run
+    # to run) reaches the losses through Adam's normalisation of near-zero gradients
+    assert np.allclose(la[:2], lb[:2], rtol=1e-5, atol=1e-6)
     assert np.abs(la - lb).max() <= 3e-3
     pa, pb = fa.get_params().astype(np.float64), fb.get_params().astype(np.float64)
     assert np.isfinite(pa).all()
