@@ -38,7 +38,7 @@ UNIT = "chain steps/s"
 # products, 3 subtractions, 5 compares).
 FLOP_PER_NODE = 77
 FLOP_PER_TRI = 45
-SMS, FP32_LANES = 152, 128
+FP32_LANES = 128   # FP32 lanes per SM on sm_103a (the nominal-peak cross-check only)
 # DRAM traffic of one wf_path_kernel launch (dram__bytes_read.sum +
 # dram__bytes_write.sum), the mean over 8 launches of an ncu capture of the
 # 2^18-chain case, scaled by 4 to the 2^20-chain workload (the paths of a
@@ -135,17 +135,17 @@ def dist_env():
     return ws, rank, local
 
 
-def cpu_oracle_rate(sc, wl, budget_s=12.0, seed=0):
-    """The FP64 oracle as it stands (its own BVH, all host cores) on a bounded
-    sample: a prefix of the chains, a few chain steps each."""
+def cpu_oracle_rate(sc, wl, budget_s=12.0, seed=0, n_threads=0, max_chains=1 << 12):
+    """The FP64 oracle as it stands (its own BVH; all host cores, or n_threads)
+    on a bounded sample: a prefix of the chains, a few chain steps each."""
     from oracle import oracle as O
     osc = O.Scene(sc, bvh=sc.n_tris > 64)
-    cores = O.threads_default()
-    n_chains = min(wl["chains"], 1 << 12)
+    cores = n_threads or O.threads_default()
+    n_chains = min(wl["chains"], max_chains)
     steps = 2
     ch = O.Chains(osc, sc.D, sc.width, sc.height, seed=seed, n_chains=n_chains)
     t0 = time.perf_counter()
-    ch.advance(steps)
+    ch.advance(steps, n_threads=n_threads)
     dt = time.perf_counter() - t0
     # grow the sample to about budget_s of CPU work (bounded)
     total_steps, total_t = n_chains * steps, dt
@@ -153,10 +153,23 @@ def cpu_oracle_rate(sc, wl, budget_s=12.0, seed=0):
     if grow > 1 and dt < budget_s:
         k = min(grow * steps, 256)
         t0 = time.perf_counter()
-        ch.advance(k)
+        ch.advance(k, n_threads=n_threads)
         total_t += time.perf_counter() - t0
         total_steps += n_chains * k
     return total_steps / total_t, cores, f"{n_chains} chains x {total_steps // n_chains} chain steps of the same workload"
+
+
+def cpu_oracle_config1():
+    """The oracle on the whole 64x64 Cornell workload (24 triangles, depth 3,
+    256 chains x 10^4 steps, seed 0), all host cores: chain steps/s."""
+    from oracle import oracle as O
+    from paper_2409_07148_gb300 import scenes
+    sc = scenes.cornell()
+    ch = O.Chains(O.Scene(sc), sc.D, sc.width, sc.height, seed=0, n_chains=256)
+    t0 = time.perf_counter()
+    ch.advance(10_000)
+    dt = time.perf_counter() - t0
+    return 256 * 10_000 / dt, O.threads_default(), dt
 
 
 def run_batched(args):
@@ -227,6 +240,10 @@ def relmse(img, ref, eps=1e-2):
 
 
 def run_caustic(args):
+    print(json.dumps(time_to_target(args)), flush=True)
+
+
+def time_to_target(args):
     """Time to relMSE 1e-2, learned vs plain regeneration, on the slit-caustic
     scene (1024^2, depth 10, 2^20 chains) or, with --workload terrain, on the
     fBm terrain lit by 256 small emitters (2048^2, depth 12, 2^22 chains).  Reference: plain path tracing on the GPU (its own noise is
@@ -237,7 +254,7 @@ def run_caustic(args):
     chain states (weights p / (p + c~ u)) between epochs and regenerates from
     mu = beta mu_flow + (1 - beta) uniform in the next epoch."""
     if args.ref_samples is None:
-        args.ref_samples = (1 << 37) if args.workload == "terrain" else (1 << 36)
+        args.ref_samples = {"terrain": 1 << 37, "spheres_t2t": 1 << 35}.get(args.workload, 1 << 36)
     import torch
     from paper_2409_07148_gb300 import jr, scenes
     from paper_2409_07148_gb300.flowinit import init_flow_params
@@ -245,6 +262,10 @@ def run_caustic(args):
         side = args.side or 2048
         sc = scenes.terrain(width=side, height=side, depth=12)
         C = args.chains or (1 << 22)
+    elif args.workload == "spheres_t2t":
+        side = args.side or 512
+        sc = scenes.cornell_spheres(width=side, height=side, depth=8)
+        C = args.chains or (1 << 20)
     else:
         side = args.side or 1024
         sc = scenes.caustic_slit(width=side, height=side, depth=10)
@@ -278,9 +299,56 @@ def run_caustic(args):
         ref = 0.5 * (halves[0] + halves[1])
         ref_noise = relmse(halves[0], halves[1]) / 4.0   # relMSE of the mean of two halves vs truth, roughly
 
+        def run_mh():
+            """The MH baseline (Section 8): l = --mh-large-step, burn-in --mh-burn-in
+            (Section 9: 0.3 and 10^4), --mh-chains chains; the burn-in runs on
+            the clock; checkpoints after it, off the clock (no tours to drain)."""
+            Cm = args.mh_chains or C
+            ch = jr.Chains(g, side, side, sc.depth, Cm, seed=7, flags=jr.JR_FLAG_MH, large_step=args.mh_large_step,
+                           burn_in=args.mh_burn_in, stream=stream)
+            ch.set_execution("wave")
+            sampler = ClockSampler(torch.cuda.current_device())
+            sampler.start()
+            clock, curve, e, done = 0.0, [], 0, 0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            while done < args.mh_burn_in:            # the burn-in: no estimate yet
+                k = min(args.epoch_max, args.mh_burn_in - done)
+                ch.advance(k, stream=stream)
+                done += k
+            torch.cuda.synchronize()
+            clock = time.perf_counter() - t0
+            t_burn = clock
+            while clock < tmax:
+                n_ep = min(int(round(epoch * args.epoch_growth ** e)), args.epoch_max)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ch.advance(n_ep, stream=stream)
+                torch.cuda.synchronize()
+                clock += time.perf_counter() - t0
+                img = torch.zeros((side, side, 3), dtype=torch.float32, device="cuda")
+                ch.resolve(out=img, stream=stream)
+                stream.synchronize()
+                curve.append((clock, relmse(img.double(), ref)))
+                e += 1
+                if curve[-1][1] <= target:
+                    break
+            clocks = sampler.stop()
+            st = ch.stats(stream=stream, check=False)
+            hit = next((t for t, r in curve if r <= target), None)
+            return {"time_to_target_s": hit, "final_relmse": curve[-1][1] if curve else None, "chains": Cm,
+                    "large_step": args.mh_large_step, "burn_in": args.mh_burn_in, "burn_in_s": round(t_burn, 3),
+                    "curve": [[round(t, 3), r] for t, r in curve[:: max(1, len(curve) // 40)]],
+                    "large_steps": st["regenerations"], "small_steps": st["local_steps"],
+                    "accepted": st["accepted"], "b_hat": st["p_sum_large"] / max(1, st["regenerations"]),
+                    "chain_steps": int(st["steps_per_chain"]) * Cm, "status_word": st["status_word"],
+                    "clocks": clocks}
+
         def run(learned):
             ch = jr.Chains(g, side, side, sc.depth, C, seed=5 if learned else 6, stream=stream)
             ch.set_execution("wave")
+            sampler = ClockSampler(torch.cuda.current_device())
+            sampler.start()
             curve = []
             clock = 0.0
             trainer = render = None
@@ -345,6 +413,7 @@ def run_caustic(args):
                 e += 1
                 if curve[-1][1] <= target:
                     break
+            clocks = sampler.stop()
             st = ch.stats(stream=stream, check=False)
             hit = next((t for t, r in curve if r <= target), None)
             # log-log interpolation between the checkpoints around the crossing
@@ -361,20 +430,42 @@ def run_caustic(args):
                     "split_16_steps": split,
                     "regenerations": st["regenerations"], "local_steps": st["local_steps"],
                     "accepted": st["accepted"], "chain_steps": int(st["steps_per_chain"]) * C,
-                    "status_word": st["status_word"]}
+                    "status_word": st["status_word"], "clocks": clocks}
 
         plain = run(False) if "plain" in args.arms else None
         learned = run(True) if "learned" in args.arms else {}
+        mh = run_mh() if "mh" in args.arms else None
     line = {"metric": METRIC, "workload": wname, "unit": "s to relMSE 1e-2",
             "relmse_eps": 1e-2, "target": target, "time_limit_s": tmax, "chains": C, "epoch_steps": epoch,
             "epoch_growth": args.epoch_growth, "epoch_max": args.epoch_max,
             "reference": {"samples": args.ref_samples, "seconds": round(t_ref, 2), "noise_relmse_est": ref_noise},
-            "plain": plain, "learned": {**learned, "beta": args.beta, "train_iters_per_epoch": args.train_iters,
+            "plain": plain, "mh": mh, "learned": {**learned, "beta": args.beta, "train_iters_per_epoch": args.train_iters,
                                         "train_iters_first": args.train_iters0, "warm_epochs": args.warm_epochs,
                                         "batch": args.batch, "snap_every": args.snap_every, "replay": args.replay,
                                         "lr": args.lr, "flow": "6 coupling layers, MLP 2x64, 16 bins, bf16/FP32"},
             "n_tris": sc.n_tris, "data": "synthetic"}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def default_time_to_relmse(args):
+    """Metric 2 for the default line: time to relMSE 1e-2 on the slit caustic
+    (1024^2, depth 10, 2^20 chains), plain against learned regeneration, with
+    the harness defaults (a 2^36-sample reference, 20 s at most per arm) and a
+    clock record per arm; the curves are left out of the line."""
+    import copy
+    a = copy.copy(args)
+    a.workload, a.arms, a.chains, a.side, a.ref_samples = "caustic", "plain,learned", 0, None, None
+    a.time_limit, a.split_epoch, a.ref_file = 20.0, -1, None
+    r = time_to_target(a)
+    keep = ("time_to_target_s", "time_to_target_interp_s", "final_relmse", "epochs", "seconds", "clocks",
+            "chain_steps", "status_word")
+    out = {"workload": r["workload"], "unit": r["unit"], "target": r["target"], "relmse_eps": r["relmse_eps"],
+           "chains": r["chains"], "reference": r["reference"],
+           "plain": {k: r["plain"].get(k) for k in keep},
+           "learned": {**{k: r["learned"].get(k) for k in keep}, "beta": r["learned"]["beta"]}}
+    tp, tl = out["plain"]["time_to_target_s"], out["learned"]["time_to_target_s"]
+    out["learned_over_plain"] = tl / tp if tp and tl else None
+    return out
 
 
 def run_reference(args, sc, wl):
@@ -410,6 +501,7 @@ def main():
     ap.add_argument("--block", type=int, default=0, help="step-kernel block size (0 = library default)")
     ap.add_argument("--exec", default="auto", choices=["auto", "mega", "wave"], help="execution mode")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-t2t", action="store_true", help="skip the time-to-relMSE object of the default line")
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--chains", type=int, default=0, help="override the chain count (profiling small cases only)")
     ap.add_argument("--chain-steps", type=int, default=0, help="override chain steps per launch (profiling only)")
@@ -431,11 +523,14 @@ def main():
     ap.add_argument("--arms", default="plain,learned", help="caustic workload: arms to run")
     ap.add_argument("--split-epoch", type=int, default=-1, help="caustic workload: time 16 extra steps per kernel class after this epoch (diagnostic)")
     ap.add_argument("--beta", type=float, default=0.15)
+    ap.add_argument("--mh-large-step", type=float, default=0.3, help="MH arm: large-step probability l")
+    ap.add_argument("--mh-burn-in", type=int, default=10_000, help="MH arm: iterations before the estimate starts")
+    ap.add_argument("--mh-chains", type=int, default=0, help="MH arm: chains (0 = the Restore arms' count)")
     args = ap.parse_args()
     if args.workload == "batched64" and args.impl == "ours":
         run_batched(args)
         return
-    if args.workload in ("caustic", "terrain") and args.impl == "ours":
+    if args.workload in ("caustic", "terrain", "spheres_t2t") and args.impl == "ours":
         run_caustic(args)
         return
     sc, wl = workload(args.workload)
@@ -512,7 +607,10 @@ def main():
         flop = FLOP_PER_NODE * work["nodes"] + FLOP_PER_TRI * work["tris"]
         pk, pk_kind = peaks()
         sm_mhz_peak = float(pk.get("sm_max_mhz", 2070.0))
-        alu_peak = SMS * FP32_LANES * 2 * sm_mhz_peak * 1e6 / 1e12
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        nominal_peak = sms * FP32_LANES * 2 * sm_mhz_peak * 1e6 / 1e12
+        fma_tflops, fma_ms = jr.fp32_peak(stream=stream)   # measured: our FMA microbenchmark kernel
+        alu_peak = fma_tflops
         split_total = sum(v["ms"] for v in split.values())
         dom = max(split, key=lambda k: split[k]["ms"])
         if dom == "path":    # the traversal work runs in the path kernel
@@ -539,10 +637,18 @@ def main():
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
+    t2t = None
+    if not args.no_t2t and ws == 1:
+        t2t = default_time_to_relmse(args)
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         r, cores, sample = cpu_oracle_rate(sc, wl)
-        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        r1, _, sample1 = cpu_oracle_rate(sc, wl, budget_s=4.0, n_threads=1, max_chains=256)
+        rc1, cores1, tc1 = cpu_oracle_config1()
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "single_thread": {"value": r1, "unit": UNIT, "cores": 1, "sample": sample1},
+               "config1_full": {"value": rc1, "unit": UNIT, "cores": cores1, "seconds": round(tc1, 3),
+                                "sample": "the whole 64x64 Cornell workload: 256 chains x 10^4 steps, depth 3"}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -558,7 +664,10 @@ def main():
                      "frac": achieved / alu_peak,
                      "traffic": path_traffic(args.workload, C) if dom == "path" else None,
                      "traffic_source": PATH_TRAFFIC["summary"],
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz_peak:.0f} MHz ({pk_kind} sm_max_mhz)",
+                     "peak_source": (f"measured: jr_fp32_peak, independent FMA chains on all {sms} SMs "
+                                     f"({fma_ms:.2f} ms launch); nominal {sms} SMs x {FP32_LANES} lanes x 2 x "
+                                     f"{sm_mhz_peak:.0f} MHz = {nominal_peak:.1f} TFLOP/s"),
+                     "peak_nominal": nominal_peak, "sms": sms,
                      "work_per_step": work, "flop_per_step": flop,
                      "launches_per_step": split[dom]["launches"],
                      "avg_launch_us": 1e3 * split[dom]["ms"] / max(1, split[dom]["launches"]),
@@ -572,6 +681,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": args.steps * (sum(v["launches"] for v in split.values()) + 1),  # + the fold
         "cpu_baseline": cpu,
+        "time_to_relmse": t2t,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:

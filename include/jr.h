@@ -298,6 +298,14 @@ jr_status jr_eval_states(const jr_scene* scene, const jr_params* params, const f
 jr_status jr_render_pt(const jr_scene* scene, const jr_params* params, uint64_t sample_begin, uint64_t n_samples,
                        double* accum_dev, void* stream);
 
+/* Measured FP32 throughput of the current device, the denominator of the
+ * path kernels' ALU roofline (the method has no part in it): a kernel of 8
+ * independent FMA chains per thread on every SM at full occupancy, 2^21 FMA
+ * per thread; *tflops_out = 2 x FMAs / the best of four launch times (CUDA
+ * events on `stream`, each launch after an untimed one), ms_out (may be NULL)
+ * that time.  Synchronises `stream`. */
+jr_status jr_fp32_peak(double* tflops_out, double* ms_out, void* stream);
+
 /* Raw Philox4x32-10 blocks for chains chain_begin .. +n at one (tag, block,
  * step): out_dev[i][4] uint32 (device).  For bit-exact RNG parity tests. */
 jr_status jr_philox(uint64_t seed, uint32_t tag, uint32_t block, uint64_t chain_begin, uint64_t step, uint64_t n,

@@ -502,6 +502,12 @@ jr_status jr_render_pt(const jr_scene* scene, const jr_params* params, uint64_t 
     return JR_OK;
 }
 
+jr_status jr_fp32_peak(double* tflops_out, double* ms_out, void* stream) {
+    if (!tflops_out) return fail(JR_ERR_INVALID_ARG, "jr_fp32_peak: null output");
+    JR_CUDA(measure_fma_peak(tflops_out, ms_out, (cudaStream_t)stream), "jr_fp32_peak");
+    return JR_OK;
+}
+
 jr_status jr_philox(uint64_t seed, uint32_t tag, uint32_t block, uint64_t chain_begin, uint64_t step, uint64_t n,
                     uint32_t* out_dev, void* stream) {
     if (n > 0 && !out_dev) return fail(JR_ERR_INVALID_ARG, "jr_philox: null output");

@@ -289,6 +289,9 @@ cudaError_t launch_eval_states(const SceneView& s, uint32_t depth, float c_tilde
                                float* F, float* p, float* u, float* k, int32_t* ids, cudaStream_t st);
 cudaError_t launch_render_pt(const SceneView& s, uint32_t width, uint32_t height, uint32_t depth, uint64_t seed,
                              uint64_t sample_begin, uint64_t n, double* accum, cudaStream_t st);
+// FP32 FMA throughput of the device (TFLOP/s, best of four timed launches of
+// a kernel of independent FMA chains over every SM); ms_out = its launch time.
+cudaError_t measure_fma_peak(double* tflops, double* ms_out, cudaStream_t st);
 cudaError_t launch_philox(uint64_t seed, uint32_t tag, uint32_t block, uint64_t chain_begin, uint64_t step,
                           uint64_t n, uint32_t* out, cudaStream_t st);
 

@@ -380,9 +380,67 @@ __global__ void philox_kernel(uint64_t seed, uint32_t tag, uint32_t block, uint6
     reinterpret_cast<uint4*>(out)[i] = r;
 }
 
+// FP32 peak: every thread runs kChainsFma independent FMA chains for `iters`
+// rounds (2 FLOP per FMA), so the FMA pipes never wait on a dependency; the
+// values stay finite (a contraction towards 1) and are written out only if a
+// condition that never holds is met, so nothing is optimised away.
+constexpr int kChainsFma = 8;
+__global__ void __launch_bounds__(256) fma_peak_kernel(uint32_t iters, float* sink) {
+    float a[kChainsFma];
+    const float m = 0.999f, c = 1e-3f * (float)(threadIdx.x & 7);
+#pragma unroll
+    for (int k = 0; k < kChainsFma; ++k) a[k] = 1.0f + 1e-3f * (float)k;
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+#pragma unroll
+            for (int k = 0; k < kChainsFma; ++k) a[k] = fmaf(a[k], m, c);
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kChainsFma; ++k) s += a[k];
+    if (s == -1.0f && sink) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 inline unsigned grid_for(uint64_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
+
+cudaError_t measure_fma_peak(double* tflops, double* ms_out, cudaStream_t st) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fma_peak_kernel, 256, 0)) != cudaSuccess)
+        return e;
+    const unsigned grid = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
+    const uint32_t iters = 1u << 14;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return e;
+    }
+    float best = 0.f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // the first launch warms up
+        fma_peak_kernel<<<grid, 256, 0, st>>>(iters, nullptr);
+        if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+        fma_peak_kernel<<<grid, 256, 0, st>>>(iters, nullptr);
+        if ((e = cudaEventRecord(e1, st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float t = 0.f;
+        if ((e = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) break;
+        if (rep == 0 || t < best) best = t;
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    const double flop = 2.0 * (double)grid * 256.0 * (double)iters * 16.0 * kChainsFma;
+    *tflops = flop / (best * 1e-3) / 1e12;
+    if (ms_out) *ms_out = best;
+    return cudaSuccess;
+}
 
 cudaError_t launch_init(const SceneView& s, const ChainView& c, cudaStream_t st) {
     const unsigned B = 128;

@@ -87,6 +87,7 @@ _SIGS = {
     "jr_eval_states": [_P, ctypes.POINTER(Params), _P, _U64, _P, _P, _P, _P, _P, _P],
     "jr_render_pt": [_P, ctypes.POINTER(Params), _U64, _U64, _P, _P],
     "jr_philox": [_U64, _U32, _U32, _U64, _U64, _U64, _P, _P],
+    "jr_fp32_peak": [_P, _P, _P],
     "jr_batch_create": [_P, _U32, _P, ctypes.POINTER(_P)],
     "jr_batch_destroy": [_P],
     "jr_batch_set_block": [_P, _U32],
@@ -504,6 +505,14 @@ def philox(seed, tag, block, chain_begin, step, n, stream=None):
     _check(lib().jr_philox(int(seed), int(tag), int(block), int(chain_begin), int(step), int(n), _dptr(out),
                            _stream(stream)))
     return out
+
+
+def fp32_peak(stream=None):
+    """Measured FP32 FMA throughput of the device: (TFLOP/s, ms of one launch)."""
+    t = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(lib().jr_fp32_peak(ctypes.byref(t), ctypes.byref(ms), _stream(stream)))
+    return t.value, ms.value
 
 
 def version():
