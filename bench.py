@@ -345,7 +345,7 @@ def time_to_target(args):
                     "clocks": clocks}
 
         def run(learned):
-            ch = jr.Chains(g, side, side, sc.depth, C, seed=5 if learned else 6, stream=stream)
+            ch = jr.Chains(g, side, side, sc.depth, C, seed=5 if learned else 6, c_tilde=args.c_tilde, stream=stream)
             ch.set_execution("wave")
             sampler = ClockSampler(torch.cuda.current_device())
             sampler.start()
@@ -436,7 +436,8 @@ def time_to_target(args):
         learned = run(True) if "learned" in args.arms else {}
         mh = run_mh() if "mh" in args.arms else None
     line = {"metric": METRIC, "workload": wname, "unit": "s to relMSE 1e-2",
-            "relmse_eps": 1e-2, "target": target, "time_limit_s": tmax, "chains": C, "epoch_steps": epoch,
+            "relmse_eps": 1e-2, "target": target, "time_limit_s": tmax, "chains": C, "c_tilde": args.c_tilde,
+            "epoch_steps": epoch,
             "epoch_growth": args.epoch_growth, "epoch_max": args.epoch_max,
             "reference": {"samples": args.ref_samples, "seconds": round(t_ref, 2), "noise_relmse_est": ref_noise},
             "plain": plain, "mh": mh, "learned": {**learned, "beta": args.beta, "train_iters_per_epoch": args.train_iters,
@@ -455,7 +456,7 @@ def default_time_to_relmse(args):
     import copy
     a = copy.copy(args)
     a.workload, a.arms, a.chains, a.side, a.ref_samples = "caustic", "plain,learned", 0, None, None
-    a.time_limit, a.split_epoch, a.ref_file = 20.0, -1, None
+    a.time_limit, a.split_epoch, a.ref_file, a.c_tilde = 20.0, -1, None, 1.0
     r = time_to_target(a)
     keep = ("time_to_target_s", "time_to_target_interp_s", "final_relmse", "epochs", "seconds", "clocks",
             "chain_steps", "status_word")
@@ -523,6 +524,7 @@ def main():
     ap.add_argument("--arms", default="plain,learned", help="caustic workload: arms to run")
     ap.add_argument("--split-epoch", type=int, default=-1, help="caustic workload: time 16 extra steps per kernel class after this epoch (diagnostic)")
     ap.add_argument("--beta", type=float, default=0.15)
+    ap.add_argument("--c-tilde", type=float, default=1.0, help="time-to-target harness: c~ of the Restore arms")
     ap.add_argument("--mh-large-step", type=float, default=0.3, help="MH arm: large-step probability l")
     ap.add_argument("--mh-burn-in", type=int, default=10_000, help="MH arm: iterations before the estimate starts")
     ap.add_argument("--mh-chains", type=int, default=0, help="MH arm: chains (0 = the Restore arms' count)")

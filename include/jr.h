@@ -477,6 +477,34 @@ jr_status jr_complete_tours(jr_chains* chains, uint32_t max_steps, uint64_t* rem
 jr_status jr_chains_set_flow(jr_chains* chains, const jr_flow* flow, float beta, uint32_t max_drain_steps,
                              uint64_t* remaining, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Failure detection and its testing hooks (the paper has no counterpart).  The
+ * device reports the method's faults in the status word (JR_STATUS_*), which
+ * jr_get_stats turns into JR_ERR_WATCHDOG / JR_ERR_NUMERIC; these calls let a
+ * test provoke each failure from the host, without faulting the device.
+ */
+
+/* Traversal limits of this chain set's launches: a ray that visits more than
+ * node_visit_budget BVH nodes, or whose stack would hold more than
+ * stack_entries entries (<= 96), stops and counts as a miss, and the set's
+ * status word gets JR_STATUS_TRAVERSAL or JR_STATUS_STACK.  0 keeps the
+ * default (2^16 visits; 96 entries, which the BVH builder guarantees is never
+ * exceeded).  Errors: JR_ERR_INVALID_ARG for stack_entries > 96. */
+jr_status jr_chains_set_limits(jr_chains* chains, uint32_t node_visit_budget, uint32_t stack_entries);
+
+/* The library's (n+1)-th device allocation from now fails as if the device were
+ * out of memory (n >= 0; n < 0 switches the hook off).  The call that meets it
+ * returns JR_ERR_OOM, frees what it had allocated and leaves its outputs
+ * untouched.  Process-wide; for tests. */
+jr_status jr_debug_fail_alloc(int64_t n);
+
+/* enable != 0: this flow's own launches (jr_flow_log_density, jr_flow_sample)
+ * arm their first weight barrier for 16 bytes more than the copy delivers, so
+ * the kernel's bounded wait (2 s) runs out: it sets JR_STATUS_FLOW_WAIT,
+ * waits (bounded) for its copies in flight and returns without writing its
+ * outputs.  For tests of that path; 0 switches it off. */
+jr_status jr_debug_flow_wait(jr_flow* flow, int enable);
+
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char* jr_last_error(void);
 /* Library version string. */

@@ -155,3 +155,91 @@ def nll_and_grad_torch(perm, w, x, wt):
     loss = -(wt_ * lq).sum() / wt_.sum()
     loss.backward()
     return float(loss.detach()), params.grad.numpy()
+
+
+# --------------------------------------------------------------------------
+# Rounding margins.  The GPU accumulates the GEMMs in FP32 and runs the
+# couplings in FP32, the oracle exactly; the two agree to FP32 rounding except
+# where that rounding decides a discrete step: the bf16 rounding of an
+# activation (h1, h2, or a conditioner coordinate transformed by an earlier
+# layer) or the bin of a coordinate (density: floor(t K); sampling: the CDF
+# edge below c).  These functions give, per row, the smallest distance of any
+# such value to its decision edge, in units of the FP32 error the GPU can make
+# there: ACC_ERR times the sum of the magnitudes that formed an activation, or
+# COORD_ERR for a coordinate.  A row with margin < 1 may legitimately take the
+# other side on the GPU; every other row must agree to FP32 accuracy.
+ACC_ERR = 2.0 ** -19      # FP32 accumulation of <= 64 exact bf16 products plus a bias, relative to sum |terms|
+COORD_ERR = 2.0 ** -19    # a coordinate in [0, 1) after up to 6 FP32 coupling transforms (absolute)
+
+
+def _bf16_edge_distance(v):
+    """Distance of v to the nearest bf16 rounding edge (the midpoint between
+    the two bf16 neighbours of float32(v))."""
+    v = np.asarray(v, np.float64)
+    u = np.ascontiguousarray(v.astype(np.float32)).view(np.uint32).astype(np.uint64)
+    lo = (((u >> 16) << 16) & 0xFFFFFFFF).astype(np.uint32).view(np.float32).astype(np.float64)
+    hi = ((((u >> 16) + 1) << 16) & 0xFFFFFFFF).astype(np.uint32).view(np.float32).astype(np.float64)
+    return np.abs(v - 0.5 * (lo + hi))
+
+
+def _layer_margin(w_layer, xa, D, first, acc_err, coord_err):
+    """Per-row margin (in units of the GPU's error) of one layer's bf16
+    roundings: the conditioner coordinates (exact inputs in the first layer)
+    and the positive pre-activations of h1 and h2."""
+    W1, b1, W2, b2, W3, b3 = unpack(w_layer, D)
+    n = len(xa)
+    m = np.full(n, np.inf)
+    if not first:
+        m = np.minimum(m, (_bf16_edge_distance(xa) / coord_err).min(axis=1))
+    xb = bf16(xa)
+    pre1 = xb @ bf16(W1).T + b1
+    s1 = np.abs(xb) @ np.abs(bf16(W1)).T + np.abs(b1)
+    m1 = np.where(pre1 > 0, _bf16_edge_distance(pre1) / (acc_err * np.maximum(s1, 1e-300)), np.inf)
+    h1 = bf16(np.maximum(pre1, 0.0))
+    pre2 = h1 @ bf16(W2).T + b2
+    s2 = np.abs(h1) @ np.abs(bf16(W2)).T + np.abs(b2)
+    m2 = np.where(pre2 > 0, _bf16_edge_distance(pre2) / (acc_err * np.maximum(s2, 1e-300)), np.inf)
+    return np.minimum(m, np.minimum(m1.min(axis=1), m2.min(axis=1)))
+
+
+def log_density_margin(perm, w, x, acc_err=ACC_ERR, coord_err=COORD_ERR):
+    """Per-row rounding margin of log_density (see above)."""
+    x = np.array(x, np.float64, copy=True)
+    n, D = x.shape
+    A = D // 2
+    m = np.full(n, np.inf)
+    for l in range(len(perm)):
+        ca, cb = perm[l][:A], perm[l][A:]
+        m = np.minimum(m, _layer_margin(w[l], x[:, ca], D, l == 0, acc_err, coord_err))
+        t = x[:, cb]
+        tk = t * K
+        edge = np.abs(tk - np.round(tk)) / K
+        m = np.minimum(m, (edge / coord_err).min(axis=1))
+        Q = bins(w[l], x[:, ca], D)
+        b = np.minimum(np.floor(tk), K - 1).astype(np.int64)
+        cum = np.concatenate([np.zeros((n, A, 1)), np.cumsum(Q, axis=2)], axis=2)
+        qb = np.take_along_axis(Q, b[..., None], axis=2)[..., 0]
+        x[:, cb] = np.take_along_axis(cum, b[..., None], axis=2)[..., 0] + (tk - b) * qb
+    return m
+
+
+def sample_margin(perm, w, z, acc_err=ACC_ERR, coord_err=COORD_ERR):
+    """Per-row rounding margin of sample (see above)."""
+    x = np.array(z, np.float64, copy=True)
+    n, D = x.shape
+    A = D // 2
+    m = np.full(n, np.inf)
+    L = len(perm)
+    for l in reversed(range(L)):
+        ca, cb = perm[l][:A], perm[l][A:]
+        m = np.minimum(m, _layer_margin(w[l], x[:, ca], D, l == L - 1, acc_err, coord_err))
+        Q = bins(w[l], x[:, ca], D)
+        c = x[:, cb]
+        cum = np.cumsum(Q, axis=2)
+        m = np.minimum(m, (np.abs(cum[..., :-1] - c[..., None]) / coord_err).min(axis=(1, 2)))
+        b = np.minimum((cum <= c[..., None]).sum(axis=2), K - 1)
+        lo = np.concatenate([np.zeros((n, A, 1)), cum], axis=2)
+        clo = np.take_along_axis(lo, b[..., None], axis=2)[..., 0]
+        qb = np.take_along_axis(Q, b[..., None], axis=2)[..., 0]
+        x[:, cb] = np.clip((b + (c - clo) / qb) / K, 0.0, 1.0 - 2.0 ** -24)
+    return m

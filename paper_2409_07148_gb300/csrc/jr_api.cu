@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -39,8 +40,16 @@ jr_status cuda_fail(cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
+// Testing hook (jr_debug_fail_alloc): when >= 0, the number of device
+// allocations still to succeed before one fails with cudaErrorMemoryAllocation.
+std::atomic<long long> g_fail_alloc_in{-1};
+
 template <class T>
 cudaError_t dev_alloc(T** p, size_t count) {
+    long long k = g_fail_alloc_in.load();
+    while (k >= 0 && !g_fail_alloc_in.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 0) return cudaErrorMemoryAllocation;
     return cudaMalloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
 }
 
@@ -67,6 +76,15 @@ struct jr_chains {
     int block = 128;
     uint32_t exec = JR_EXEC_AUTO;
     uint64_t epochs = 0;  // restarts from a new regeneration distribution (Philox tag 3 key)
+    uint32_t visit_budget = 0;  // traversal watchdog limits of this set's launches (0: the scene's)
+    int stack_limit = 0;
+    // The scene as this set's launches see it (with the set's traversal limits).
+    SceneView scene_view() const {
+        SceneView v = scene->view;
+        if (visit_budget) v.visit_budget = visit_budget;
+        if (stack_limit) v.stack_limit = stack_limit;
+        return v;
+    }
     ~jr_chains() {
         cudaFree(view.wf.y);
         cudaFree(view.wf.par);
@@ -156,6 +174,8 @@ jr_status jr_scene_create(const jr_scene_desc* desc, void* stream, jr_scene** ou
     s->view.mats = s->mats;
     s->view.root = bvh.root;
     s->view.n_nodes = (int)bvh.nodes.size();
+    s->view.visit_budget = kNodeVisitBudget;
+    s->view.stack_limit = kStackSize;
     std::memcpy(s->view.cam, desc->camera, sizeof(float) * 12);
     s->info.n_tris = desc->n_tris;
     s->info.n_nodes = (uint32_t)bvh.nodes.size();
@@ -280,9 +300,9 @@ static jr_status advance_impl(jr_chains* c, uint32_t n_steps, uint8_t* f, float*
     if (wave) {
         jr_status a = ensure_wavefront(c, st);
         if (a != JR_OK) return a;
-        JR_CUDA(launch_wavefront(c->scene->view, c->view, c->steps, n_steps, st), who);
+        JR_CUDA(launch_wavefront(c->scene_view(), c->view, c->steps, n_steps, st), who);
     } else {
-        JR_CUDA(launch_step(c->scene->view, c->view, c->steps, n_steps, f, dt, pix, work, c->block, st), who);
+        JR_CUDA(launch_step(c->scene_view(), c->view, c->steps, n_steps, f, dt, pix, work, c->block, st), who);
     }
     JR_CUDA(launch_fold(c->view, st), who);
     c->steps += n_steps;
@@ -308,11 +328,11 @@ jr_status jr_advance_timed(jr_chains* c, uint32_t n_steps, double ms_out[4], uin
         if (wave) {
             jr_status a = ensure_wavefront(c, st);
             if (a != JR_OK) return a;
-            JR_CUDA(launch_wavefront(c->scene->view, c->view, c->steps, n_steps, st, kModeStep, &tm),
+            JR_CUDA(launch_wavefront(c->scene_view(), c->view, c->steps, n_steps, st, kModeStep, &tm),
                     "jr_advance_timed");
         } else {
             JR_CUDA(tm.mark(-1, st), "jr_advance_timed");
-            JR_CUDA(launch_step(c->scene->view, c->view, c->steps, n_steps, nullptr, nullptr, nullptr, nullptr,
+            JR_CUDA(launch_step(c->scene_view(), c->view, c->steps, n_steps, nullptr, nullptr, nullptr, nullptr,
                                 c->block, st),
                     "jr_advance_timed");
             JR_CUDA(tm.mark(KernelTimer::kStep, st), "jr_advance_timed");
@@ -335,7 +355,7 @@ jr_status jr_advance_static(jr_chains* chains, uint32_t n_steps, void* stream) {
         return fail(JR_ERR_STATE, "jr_advance_static: chains with a flow attached advance with jr_advance");
     if (n_steps == 0) return JR_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    JR_CUDA(launch_wavefront_static(chains->scene->view, chains->view, chains->steps, n_steps, st),
+    JR_CUDA(launch_wavefront_static(chains->scene_view(), chains->view, chains->steps, n_steps, st),
             "jr_advance_static");
     JR_CUDA(launch_fold(chains->view, st), "jr_advance_static");
     chains->steps += n_steps;
@@ -354,6 +374,21 @@ jr_status jr_set_block_size(jr_chains* chains, uint32_t block) {
     if (block < 32 || block > 256 || block % 32 != 0)
         return fail(JR_ERR_INVALID_ARG, "jr_set_block_size: block must be a multiple of 32 in [32, 256]");
     chains->block = (int)block;
+    return JR_OK;
+}
+
+jr_status jr_chains_set_limits(jr_chains* chains, uint32_t node_visit_budget, uint32_t stack_entries) {
+    if (!chains) return fail(JR_ERR_INVALID_ARG, "jr_chains_set_limits: null chains");
+    if (stack_entries > (uint32_t)kStackSize)
+        return fail(JR_ERR_INVALID_ARG, "jr_chains_set_limits: at most " + std::to_string(kStackSize) +
+                                            " stack entries");
+    chains->visit_budget = node_visit_budget;
+    chains->stack_limit = (int)stack_entries;
+    return JR_OK;
+}
+
+jr_status jr_debug_fail_alloc(int64_t n) {
+    g_fail_alloc_in.store(n < 0 ? -1 : (long long)n);
     return JR_OK;
 }
 
@@ -458,7 +493,7 @@ jr_status jr_set_state(jr_chains* c, const float* x_in, const float* fpu_in, voi
         JR_CUDA(cudaMemcpyAsync(c->view.fpu, fpu_in, sizeof(float) * 5 * c->view.n, cudaMemcpyHostToDevice, st),
                 "jr_set_state");
     else
-        JR_CUDA(launch_reeval(c->scene->view, c->view, st), "jr_set_state");
+        JR_CUDA(launch_reeval(c->scene_view(), c->view, st), "jr_set_state");
     JR_CUDA(cudaStreamSynchronize(st), "jr_set_state");
     return JR_OK;
 }
@@ -647,7 +682,7 @@ jr_status prepare_wave(jr_batch* b, cudaStream_t st) {
     std::vector<BatchItem> items;
     for (uint32_t k = 0; k < S; ++k) {
         const jr_chains* c = b->sets[k];
-        h[k].s = c->scene->view;
+        h[k].s = c->scene_view();
         h[k].c = c->view;
         h[k].step = b->dev_steps[k];
         size_t u = 0;
@@ -727,6 +762,8 @@ jr_status prepare_wave(jr_batch* b, cudaStream_t st) {
     bw.merged.mats = b->m_mats;
     bw.merged.root = kNoChild;
     bw.merged.n_nodes = (int)nn;
+    bw.merged.visit_budget = kNodeVisitBudget;
+    bw.merged.stack_limit = kStackSize;
     bw.roots = b->roots;
     bw.chain_off = b->chain_off;
     bw.items = b->wf_items;
@@ -789,7 +826,7 @@ jr_status jr_batch_create(jr_chains* const* sets, uint32_t n_sets, void* stream,
             delete b;
             return fail(JR_ERR_STATE, "jr_batch_create: a chain set with a flow attached cannot join a batch");
         }
-        h[k].s = c->scene->view;
+        h[k].s = c->scene_view();
         h[k].c = c->view;
         h[k].step = c->steps;
         off[k + 1] = off[k] + (uint64_t)c->view.width * c->view.height;
@@ -953,8 +990,10 @@ struct jr_flow {
     float* adam_v = nullptr;
     float* grad = nullptr;         // [kFL][S] gradient accumulator
     uint64_t adam_t = 0;
+    uint32_t extra_tx = 0;  // testing hook, see jr_debug_flow_wait
     FlowView view(float beta) const {
         FlowView f;
+        f.extra_tx = extra_tx;
         f.D = D;
         f.A = A;
         f.AK = AK;
@@ -1054,6 +1093,12 @@ jr_status jr_flow_get_status(jr_flow* f, uint32_t* status_out, void* stream) {
     JR_CUDA(cudaMemcpyAsync(&v, f->status, sizeof(v), cudaMemcpyDeviceToHost, st), "jr_flow_get_status");
     JR_CUDA(cudaStreamSynchronize(st), "jr_flow_get_status");
     *status_out = v;
+    return JR_OK;
+}
+
+jr_status jr_debug_flow_wait(jr_flow* f, int enable) {
+    if (!f) return fail(JR_ERR_INVALID_ARG, "jr_debug_flow_wait: null flow");
+    f->extra_tx = enable ? 16u : 0u;
     return JR_OK;
 }
 
@@ -1215,7 +1260,7 @@ jr_status drain_impl(jr_chains* c, uint32_t max_steps, uint64_t* remaining, cuda
     while (active > 0 && k < max_steps) {
         const uint32_t g = std::min(group, max_steps - k);
         // one launch sequence per group: a single closing finish launch, not one per step
-        JR_CUDA(launch_wavefront(c->scene->view, c->view, s0 + k, g, st, kModeDrain), who);
+        JR_CUDA(launch_wavefront(c->scene_view(), c->view, s0 + k, g, st, kModeDrain), who);
         k += g;
         JR_CUDA(cudaMemcpyAsync(&active, c->view.wf.qcount + kQActive, sizeof(active), cudaMemcpyDeviceToHost, st),
                 who);
@@ -1238,7 +1283,7 @@ jr_status restart_impl(jr_chains* c, cudaStream_t st, const char* who) {
     jr_status a = ensure_wavefront(c, st);
     if (a != JR_OK) return a;
     c->epochs += 1;
-    JR_CUDA(launch_wavefront(c->scene->view, c->view, c->epochs, 1, st, kModeRestart), who);
+    JR_CUDA(launch_wavefront(c->scene_view(), c->view, c->epochs, 1, st, kModeRestart), who);
     return JR_OK;
 }
 

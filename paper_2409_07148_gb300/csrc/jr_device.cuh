@@ -148,7 +148,7 @@ __device__ __forceinline__ float slab(const Trav& r, float nx, float fx, float n
 // as a miss.
 template <bool kCount>
 __device__ __forceinline__ bool trav_node(const SceneView& s, Trav& r, int* stack, unsigned& status, Work& work) {
-    if (++r.visits > kNodeVisitBudget) {
+    if (++r.visits > s.visit_budget) {
         status |= JR_STATUS_TRAVERSAL;
         return false;
     }
@@ -177,7 +177,7 @@ __device__ __forceinline__ bool trav_node(const SceneView& s, Trav& r, int* stac
     cswap(t1, rf.y, t3, rf.w);
     cswap(t1, rf.y, t2, rf.z);
     const int pushes = (t1 < INFINITY) + (t2 < INFINITY) + (t3 < INFINITY);
-    if (r.sp + pushes > kStackSize) {
+    if (r.sp + pushes > s.stack_limit) {
         status |= JR_STATUS_STACK;
         return false;
     }

@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(kThreads) flow_infer_kernel(FlowView f, float*
     __syncthreads();
     if (threadIdx.x == 0)
         for (uint32_t st = 0; st < 2 && st < total; ++st) {
-            mbar_expect(&bar[st], lbytes);
+            mbar_expect(&bar[st], lbytes + (st == 0 ? f.extra_tx : 0u));
             bulk_load(wbuf0 + st * bb, f.ws + (size_t)layer_of(st) * lbytes, lbytes, &bar[st]);
         }
 

@@ -63,6 +63,8 @@ struct SceneView {
     int root;       // child ref of the root, or INT32_MIN when the scene is empty
     int n_nodes;
     float cam[12];
+    uint32_t visit_budget;  // node visits per ray before the watchdog stops it (kNodeVisitBudget)
+    int stack_limit;        // traversal stack entries a ray may use (<= kStackSize)
 };
 
 // The regeneration flow (jr_flow.cu): L coupling layers, MLP of 2 x 64 hidden
@@ -87,6 +89,7 @@ struct FlowView {
     const float* bias = nullptr;        // per layer: b1 [64], b2 [64], b3 [AK]
     const unsigned char* ws = nullptr;  // inference layout, flow_ws_layer_bytes(AK) per layer
     float beta = 0.f;                   // mu = beta mu_flow + (1 - beta) uniform
+    uint32_t extra_tx = 0;              // testing hook: bytes the first weight barrier expects beyond its copy
 };
 
 // Buffers of the wavefront execution mode (allocated on first use).

@@ -88,6 +88,9 @@ _SIGS = {
     "jr_render_pt": [_P, ctypes.POINTER(Params), _U64, _U64, _P, _P],
     "jr_philox": [_U64, _U32, _U32, _U64, _U64, _U64, _P, _P],
     "jr_fp32_peak": [_P, _P, _P],
+    "jr_chains_set_limits": [_P, _U32, _U32],
+    "jr_debug_fail_alloc": [ctypes.c_int64],
+    "jr_debug_flow_wait": [_P, ctypes.c_int],
     "jr_batch_create": [_P, _U32, _P, ctypes.POINTER(_P)],
     "jr_batch_destroy": [_P],
     "jr_batch_set_block": [_P, _U32],
@@ -238,6 +241,10 @@ class Chains:
         w = (ctypes.c_uint64 * 3)()
         _check(lib().jr_advance_counted(self.h, int(n_steps), w, _stream(stream)))
         return {"rays": int(w[0]), "nodes": int(w[1]), "tris": int(w[2])}
+
+    def set_limits(self, node_visit_budget=0, stack_entries=0):
+        """Traversal watchdog limits of this set's launches (0 = default)."""
+        _check(lib().jr_chains_set_limits(self.h, int(node_visit_budget), int(stack_entries)))
 
     def set_block_size(self, block):
         _check(lib().jr_set_block_size(self.h, int(block)))

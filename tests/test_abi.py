@@ -99,3 +99,13 @@ def test_no_device_is_a_status_not_a_crash(L):
     rc = lib.jr_scene_create(ctypes.byref(d), None, ctypes.byref(h))
     assert rc in (L.JR_ERR_CUDA, L.JR_ERR_OOM)
     assert lib.jr_last_error()
+
+
+def test_failure_hooks_reject_bad_arguments(L):
+    """The traversal-limit and testing-hook entry points check their arguments
+    before touching the device."""
+    lib = L.lib()
+    assert lib.jr_chains_set_limits(None, 5, 5) == L.JR_ERR_INVALID_ARG
+    assert lib.jr_debug_flow_wait(None, 1) == L.JR_ERR_INVALID_ARG
+    assert lib.jr_debug_fail_alloc(-1) == L.JR_OK
+    assert lib.jr_fp32_peak(None, None, None) == L.JR_ERR_INVALID_ARG

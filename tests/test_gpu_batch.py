@@ -124,3 +124,65 @@ def test_batch_images_are_estimates(J):
         st = c.stats()
         assert np.all(np.isfinite(img)) and np.all(img >= 0)
         assert st["regenerations"] + st["local_steps"] == c.n * 20
+
+
+# --------------------------------------------------------------------------
+# Batched chains replayed by the FP64 oracle (Alg. 2 per chain): every set of a
+# batch, after a batched advance, hands a contiguous sample of its chains to
+# the oracle, which takes the next step on the same Philox counters; the
+# batch's next states must match except at the rounding ties and FP32 topology
+# differences the single-set replay tests allow (0.5 % of the sample).
+def _oracle_replay_sets(J, sets, before, after, step, m=256):
+    from oracle import oracle as O
+    from tests.gpu_util import oracle_state_from_gpu, rel_err, torus_diff
+    worst = 1.0
+    for (sc, _, c), (x, fpu), (x2, fpu2) in zip(sets, before, after):
+        mm = min(m, c.n)
+        first = (c.n - mm) // 2
+        oc = O.Chains(O.Scene(sc, bvh=sc.n_tris > 64), sc.D, sc.width, sc.height, sigma=float(c.params.sigma),
+                      seed=int(c.params.seed), chain_begin=first, n_chains=mm)
+        oc.state[:] = oracle_state_from_gpu(x[:, first:first + mm], fpu[:, first:first + mm])
+        oc.step = step
+        oc.advance(1)
+        dx = torus_diff(x2[:, first:first + mm].T, oc.state[:, :sc.D]).max(axis=1)
+        ref = oc.state[:, sc.D:sc.D + 4]
+        gf = fpu2[:4, first:first + mm].T
+        eF = rel_err(gf, ref)
+        ok = (dx <= 2e-6) & np.all((eF <= 1e-5) | ((ref == 0) & (gf == 0)), axis=1)
+        worst = min(worst, float(np.mean(ok)))
+        assert np.mean(ok) >= 0.995 or (mm < 200 and np.sum(~ok) <= 1), (sc.name, np.mean(ok))
+    return worst
+
+
+@pytest.mark.parametrize("block", [64, 0])
+def test_batched_chains_replayed_by_oracle(J, block):
+    """Megakernel batch (64-chain work items) and batched wavefront (block 0)."""
+    bat = _make_shared(J)
+    b = J.Batch([c for _, _, c in bat])
+    b.set_block(block)
+    b.advance(4)
+    b.advance_graph(3)
+    before = [c.get_state() for _, _, c in bat]
+    b.advance(1)
+    after = [c.get_state() for _, _, c in bat]
+    _oracle_replay_sets(J, bat, before, after, step=7)
+
+
+def test_batched64_workload_replayed_by_oracle(J):
+    """The 64-scene workload (1k-200k triangles, 128^2-1024^2, depths 4-10, one
+    chain per pixel) in the launch form the autotuner picks for it (the batched
+    wavefront, replayed from a CUDA graph): after 3 graph-replayed steps every
+    set's next step is replayed by the oracle on 256 sampled chains."""
+    scs = scenes.batched_workload(seed=0)
+    sets = []
+    for sc in scs:
+        g = J.Scene(sc)
+        sets.append((sc, g, J.Chains(g, sc.width, sc.height, sc.depth, sc.width * sc.height, seed=0)))
+    b = J.Batch([c for _, _, c in sets])
+    b.set_block(0)
+    b.advance_graph(3)
+    before = [c.get_state() for _, _, c in sets]
+    b.advance_graph(1)
+    after = [c.get_state() for _, _, c in sets]
+    assert all(c.stats()["status_word"] == 0 for _, _, c in sets)
+    _oracle_replay_sets(J, sets, before, after, step=3)

@@ -302,3 +302,34 @@ def test_full_size_wavefront_step_sampled(J, torch_cuda):
     same = (dx <= 2e-6) & ok_f
     assert np.mean(same) >= 0.995, np.mean(same)
     assert ch.stats()["status_word"] == 0
+
+
+def test_full_size_wavefront_replay_eight_steps(J, torch_cuda):
+    """The bench workload in the bench's launch configuration (40k triangles,
+    512^2, depth 8, 2^20 chains, wavefront), replayed step by step for 8
+    steps: before every GPU step a contiguous sample of 2048 chains goes to the
+    oracle with the GPU's state, and the oracle's next states must match the
+    GPU's (the budget of the replay tests: rounding ties, FP32 topology)."""
+    sc = scenes.cornell_spheres()
+    n, first, m = 1 << 20, 777_777, 2048
+    ch = J.Chains(J.Scene(sc), sc.width, sc.height, sc.depth, n, seed=2)
+    ch.advance(2)
+    osc = O.Scene(sc, bvh=True)
+    x, fpu = ch.get_state()
+    fracs = []
+    for s in range(2, 10):
+        ch.advance(1)
+        x2, fpu2 = ch.get_state()
+        oc = O.Chains(osc, sc.D, sc.width, sc.height, seed=2, chain_begin=first, n_chains=m)
+        oc.state[:] = oracle_state_from_gpu(x[:, first:first + m], fpu[:, first:first + m])
+        oc.step = s
+        oc.advance(1)
+        dx = torus_diff(x2[:, first:first + m].T, oc.state[:, :sc.D]).max(axis=1)
+        ref = oc.state[:, sc.D:sc.D + 4]
+        gf = fpu2[:4, first:first + m].T
+        eF = rel_err(gf, ref)
+        ok = (dx <= 2e-6) & np.all((eF <= REL) | ((ref == 0) & (gf == 0)), axis=1)
+        fracs.append(np.mean(ok))
+        x, fpu = x2, fpu2
+    assert min(fracs) >= 0.995, fracs
+    assert ch.stats()["status_word"] == 0
