@@ -323,6 +323,12 @@ jr_status jr_philox(uint64_t seed, uint32_t tag, uint32_t block, uint64_t chain_
  * may contract a multiply-add into an FMA where the other does not).  The sets stay owned
  * by the caller and must outlive the batch; a set may still be advanced,
  * resolved or inspected on its own between batch advances.
+ * Sets with a learned regeneration flow attached (jr_chains_set_flow, before or
+ * after jr_batch_create) advance in the batched wavefront only: their flow
+ * draws and density rows are queued per set by the shared launches and their
+ * flow launches run between them.  A batch holding such a set selects
+ * JR_BATCH_WAVEFRONT; another block size is then refused with JR_ERR_STATE.
+ * Changing a set's flow re-captures the batch's graph on its next replay.
  */
 typedef struct jr_batch jr_batch;
 

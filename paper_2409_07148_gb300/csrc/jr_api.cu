@@ -76,6 +76,7 @@ struct jr_chains {
     int block = 128;
     uint32_t exec = JR_EXEC_AUTO;
     uint64_t epochs = 0;  // restarts from a new regeneration distribution (Philox tag 3 key)
+    uint64_t flow_gen = 0;      // bumped whenever the attached flow (or its weight) changes
     uint32_t visit_budget = 0;  // traversal watchdog limits of this set's launches (0: the scene's)
     int stack_limit = 0;
     // The scene as this set's launches see it (with the set's traversal limits).
@@ -558,6 +559,7 @@ jr_status jr_philox(uint64_t seed, uint32_t tag, uint32_t block, uint64_t chain_
 struct jr_batch {
     std::vector<jr_chains*> sets;
     std::vector<uint64_t> dev_steps;  // the step index each set has on the device side
+    std::vector<uint64_t> dev_flow_gen;  // the flow generation of each set's device descriptor
     BatchEntry* entries = nullptr;
     uint64_t* px_off = nullptr;
     unsigned int* cursor = nullptr;
@@ -635,10 +637,41 @@ jr_status build_items(jr_batch* b, int block, cudaStream_t st) {
     return JR_OK;
 }
 
+bool batch_has_flow(const jr_batch* b) {
+    for (const jr_chains* c : b->sets)
+        if (c->view.flow.D != 0) return true;
+    return false;
+}
+
+// The host views of the sets with a flow attached (their flow launches).
+std::vector<ChainView> flow_views(const jr_batch* b) {
+    std::vector<ChainView> v;
+    for (const jr_chains* c : b->sets)
+        if (c->view.flow.D != 0) v.push_back(c->view);
+    return v;
+}
+
 // Bring the device-side step index of every set up to date with its host
-// counter (a set may have been advanced on its own since the last batch).
+// counter (a set may have been advanced on its own since the last batch), and
+// a set's device descriptor with its flow when jr_chains_set_flow changed it
+// (a captured graph holds the old flow's launches, so it is dropped).
 jr_status sync_steps(jr_batch* b, cudaStream_t st) {
     for (size_t k = 0; k < b->sets.size(); ++k) {
+        const jr_chains* c = b->sets[k];
+        if (c->flow_gen != b->dev_flow_gen[k]) {
+            BatchEntry h{};
+            h.s = c->scene_view();
+            h.c = c->view;
+            h.step = c->steps;
+            JR_CUDA(cudaMemcpyAsync(b->entries + k, &h, sizeof(h), cudaMemcpyHostToDevice, st), "jr_batch (flow)");
+            JR_CUDA(cudaStreamSynchronize(st), "jr_batch (flow)");
+            b->dev_flow_gen[k] = c->flow_gen;
+            b->dev_steps[k] = c->steps;
+            if (b->exec) cudaGraphExecDestroy(b->exec);
+            if (b->graph) cudaGraphDestroy(b->graph);
+            b->exec = nullptr;
+            b->graph = nullptr;
+        }
         const uint64_t s = b->sets[k]->steps;
         if (s != b->dev_steps[k]) {
             unsigned long long v = s;
@@ -782,7 +815,7 @@ jr_status prepare_wave(jr_batch* b, cudaStream_t st) {
 cudaError_t enqueue_batch(jr_batch* b, uint32_t n_steps, cudaStream_t st) {
     const uint32_t S = (uint32_t)b->sets.size();
     if (b->block == 0) {
-        cudaError_t e = launch_batch_wavefront(b->bw, b->entries, n_steps, st);
+        cudaError_t e = launch_batch_wavefront(b->bw, b->entries, n_steps, flow_views(b), st);
         if (e != cudaSuccess) return e;
         return launch_batch(b->entries, b->items, 0, b->px_off, S, b->total_px, b->cursor, b->max_dim, 128,
                             n_steps, st);
@@ -792,6 +825,8 @@ cudaError_t enqueue_batch(jr_batch* b, uint32_t n_steps, cudaStream_t st) {
 }
 
 jr_status batch_launch(jr_batch* b, uint32_t n_steps, cudaStream_t st, const char* who) {
+    if (b->block != 0 && batch_has_flow(b))
+        return fail(JR_ERR_STATE, std::string(who) + ": a set has a flow attached; select JR_BATCH_WAVEFRONT");
     if (b->block == 0) {
         jr_status a = prepare_wave(b, st);
         if (a != JR_OK) return a;
@@ -822,10 +857,6 @@ jr_status jr_batch_create(jr_chains* const* sets, uint32_t n_sets, void* stream,
                 delete b;
                 return fail(JR_ERR_INVALID_ARG, "jr_batch_create: a chain set appears twice");
             }
-        if (c->view.flow.D != 0) {
-            delete b;
-            return fail(JR_ERR_STATE, "jr_batch_create: a chain set with a flow attached cannot join a batch");
-        }
         h[k].s = c->scene_view();
         h[k].c = c->view;
         h[k].step = c->steps;
@@ -834,6 +865,7 @@ jr_status jr_batch_create(jr_chains* const* sets, uint32_t n_sets, void* stream,
         b->total_chains += c->view.n;
         b->sets.push_back(c);
         b->dev_steps.push_back(c->steps);
+        b->dev_flow_gen.push_back(c->flow_gen);
     }
     b->total_px = off[n_sets];
     cudaError_t e;
@@ -848,6 +880,7 @@ jr_status jr_batch_create(jr_chains* const* sets, uint32_t n_sets, void* stream,
         return cuda_fail(e, "jr_batch_create");
     }
     jr_status r = build_items(b, 128, st);
+    if (r == JR_OK && batch_has_flow(b)) b->block = 0;  // sets with a flow advance in the batched wavefront only
     if (r == JR_OK) r = batch_launch(b, 0, st, "jr_batch_create");  // set-up launch: no steps
     if (r != JR_OK) {
         delete b;
@@ -868,6 +901,8 @@ jr_status jr_batch_set_block(jr_batch* b, uint32_t block) {
     if (block < 32 || block > 256 || block % 32 != 0)
         return fail(JR_ERR_INVALID_ARG,
                     "jr_batch_set_block: block must be a multiple of 32 in [32, 256], or JR_BATCH_WAVEFRONT");
+    if (batch_has_flow(b))
+        return fail(JR_ERR_STATE, "jr_batch_set_block: sets with a flow attached advance in the batched wavefront");
     return build_items(b, (int)block, nullptr);
 }
 
@@ -886,6 +921,8 @@ jr_status jr_batch_advance_graph(jr_batch* b, uint32_t n_steps, void* stream) {
     if (n_steps == 0) return JR_OK;
     cudaStream_t st = (cudaStream_t)stream;
     jr_status r = sync_steps(b, st);
+    if (r == JR_OK && b->block != 0 && batch_has_flow(b))
+        r = fail(JR_ERR_STATE, "jr_batch_advance_graph: a set has a flow attached; select JR_BATCH_WAVEFRONT");
     if (r == JR_OK && b->block == 0) r = prepare_wave(b, st);
     if (r != JR_OK) return r;
     if (!b->exec || b->graph_steps != n_steps || b->graph_block != b->block) {
@@ -920,8 +957,10 @@ jr_status jr_batch_advance_graph(jr_batch* b, uint32_t n_steps, void* stream) {
 jr_status jr_batch_autotune(jr_batch* b, uint32_t probe_steps, void* stream, jr_tune_report* out) {
     if (!b || !out || probe_steps == 0) return fail(JR_ERR_INVALID_ARG, "jr_batch_autotune: bad argument");
     cudaStream_t st = (cudaStream_t)stream;
-    const uint32_t cands[] = {32, 64, 128, 256, JR_BATCH_WAVEFRONT};
-    const uint32_t n_cands = b->sets.size() <= kBatchMaxSets ? 5 : 4;
+    const bool flows = batch_has_flow(b);  // only the batched wavefront runs flows
+    const uint32_t all[] = {32, 64, 128, 256, JR_BATCH_WAVEFRONT}, wave_only[] = {JR_BATCH_WAVEFRONT};
+    const uint32_t* cands = flows ? wave_only : all;
+    const uint32_t n_cands = flows ? 1 : b->sets.size() <= kBatchMaxSets ? 5 : 4;
     jr_tune_report rep{};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     JR_CUDA(cudaEventCreate(&e0), "jr_batch_autotune");
@@ -1314,6 +1353,7 @@ jr_status jr_chains_set_flow(jr_chains* c, const jr_flow* f, float beta, uint32_
     if (r != JR_OK) return r;
     if (remaining) *remaining = rem;
     c->view.flow = f ? f->view(beta) : FlowView{};
+    c->flow_gen += 1;
     return restart_impl(c, st, "jr_chains_set_flow");
 }
 

@@ -174,8 +174,11 @@ cudaError_t launch_rebase_scene(Bvh4Node* nodes, uint32_t n_nodes, TriRecord* tr
 // outside stream capture before the first launch_batch_wavefront).
 cudaError_t batch_wavefront_grid(long long* blocks);
 // n_steps batched wavefront steps of every set (step indices entries[q].step + k),
-// ending with the closing step launch; the caller folds afterwards.
-cudaError_t launch_batch_wavefront(const BatchWave& bw, BatchEntry* entries, uint32_t n_steps, cudaStream_t st);
+// ending with the closing step launch; the caller folds afterwards.  flow_sets:
+// the host views of the sets with a flow attached (their flow launches run
+// between the shared step and path launches).
+cudaError_t launch_batch_wavefront(const BatchWave& bw, BatchEntry* entries, uint32_t n_steps,
+                                   const std::vector<ChainView>& flow_sets, cudaStream_t st);
 
 // One-time launch set-up per device (an opt-in to large dynamic shared
 // memory, an occupancy-derived grid size), cached by device id: get() runs

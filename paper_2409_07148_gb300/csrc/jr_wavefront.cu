@@ -22,6 +22,7 @@
 #include <stdint.h>
 
 #include <mutex>
+#include <vector>
 
 #include "../../include/jr.h"
 #include "jr_device.cuh"
@@ -488,6 +489,10 @@ __global__ void __launch_bounds__(128) wf_batch_step_kernel(const BatchEntry* en
     bool traced = true, to_sample = false, active = false;
     if (i < it.end)
         step_chain(e.c, i, e.step + k, finish, begin, kModeStep, nJ, nL, nA, status, ps, traced, to_sample, active);
+    // a set with a flow: its flow draws go to the set's sampling queue (a
+    // block's chains are one set's, so the warp's enqueue has one queue)
+    if (begin && e.c.flow.D != 0)
+        enqueue(to_sample && i < it.end, (uint32_t)i, e.c.wf.fq + e.c.n, e.c.wf.qcount + kQFlowSample);
     count_and_flush_block(nJ, nL, nA, status, ps, e.c);  // a block's chains are one set's
 }
 
@@ -521,6 +526,7 @@ __global__ void __launch_bounds__(128, 7) wf_batch_path_kernel(SceneView m, cons
         const unsigned waiting = __ballot_sync(kFull, state == kWaitShade);
         const unsigned tracing = __ballot_sync(kFull, state == kTraverse);
         if (waiting && (__popc(waiting) >= kShadeBatch || __popc(waiting) >= __popc(tracing))) {
+            bool need_u = false;
             if (state == kWaitShade) {
                 bool live = false;
                 if (r.best >= 0) {
@@ -544,8 +550,26 @@ __global__ void __launch_bounds__(128, 7) wf_batch_path_kernel(SceneView m, cons
                         atomicOr(c.status, status);
                         status = 0;
                     }
+                    if (c.flow.D != 0) {  // as in the single-set path kernel
+                        unsigned ignored = 0;
+                        const float py = lum(finite_or_zero(F, ignored));
+                        const float ua = c.wf.ua[i];
+                        need_u = ua >= 0.0f ? ua * c.fpu[3 * c.n + i] < py : (ua == -1.0f && py > 0.0f);
+                    }
                     state = kIdle;
                 }
+            }
+            // rows whose u(y) the density pass must fill, appended to their set's
+            // queue: lanes of one warp may hold different sets, so the lanes of
+            // each set share one atomic (all 32 lanes take part)
+            const unsigned peers = __match_any_sync(kFull, need_u ? set : 0xffffffffu);
+            if (need_u) {
+                const int leader = __ffs(peers) - 1;
+                unsigned base = 0;
+                if (lane == leader)
+                    base = atomicAdd(entries[set].c.wf.qcount + kQFlowDensity, (unsigned)__popc(peers));
+                base = __shfl_sync(peers, base, leader);
+                entries[set].c.wf.fq[base + __popc(peers & lt)] = i;
             }
         }
         // take new paths for idle lanes
@@ -737,7 +761,8 @@ cudaError_t batch_wavefront_grid(long long* blocks) {
         blocks);
 }
 
-cudaError_t launch_batch_wavefront(const BatchWave& bw, BatchEntry* entries, uint32_t n_steps, cudaStream_t st) {
+cudaError_t launch_batch_wavefront(const BatchWave& bw, BatchEntry* entries, uint32_t n_steps,
+                                   const std::vector<ChainView>& flow_sets, cudaStream_t st) {
     long long blocks = 0;
     cudaError_t e = batch_wavefront_grid(&blocks);
     if (e != cudaSuccess) return e;
@@ -746,9 +771,16 @@ cudaError_t launch_batch_wavefront(const BatchWave& bw, BatchEntry* entries, uin
     const size_t shm = sizeof(uint64_t) * (bw.n_sets + 1);
     for (uint32_t k = 0; k < n_steps; ++k) {
         if ((e = cudaMemsetAsync(bw.fetch, 0, sizeof(unsigned int), st)) != cudaSuccess) return e;
+        for (const ChainView& c : flow_sets)  // the sets' flow queues start empty
+            if ((e = cudaMemsetAsync(c.wf.qcount + kQFlowDensity, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess)
+                return e;
         wf_batch_step_kernel<<<bw.n_items, 128, 0, st>>>(entries, bw.items, k, k > 0, 1);
+        for (const ChainView& c : flow_sets)  // y = T^{-1}(z) and u(y) of the flow draws
+            if ((e = launch_flow_draws(c, st)) != cudaSuccess) return e;
         wf_batch_path_kernel<<<(unsigned)blocks, 128, shm, st>>>(bw.merged, entries, bw.roots, bw.chain_off,
                                                                  bw.n_sets, bw.fetch);
+        for (const ChainView& c : flow_sets)  // u(y) of the candidates that become states with p > 0
+            if ((e = launch_flow_densities(c, st)) != cudaSuccess) return e;
     }
     wf_batch_step_kernel<<<bw.n_items, 128, 0, st>>>(entries, bw.items, n_steps, n_steps > 0, 0);
     return cudaGetLastError();

@@ -186,3 +186,119 @@ def test_batched64_workload_replayed_by_oracle(J):
     after = [c.get_state() for _, _, c in sets]
     assert all(c.stats()["status_word"] == 0 for _, _, c in sets)
     _oracle_replay_sets(J, sets, before, after, step=3)
+
+
+# --------------------------------------------------------------------------
+# Sets with a learned regeneration flow in the batched wavefront (the learned +
+# batched configuration): the batch advances each set as the set's own
+# wavefront advance with the same flow does.
+def _flow_params(D, seed, sd=0.1):
+    from paper_2409_07148_gb300.flowinit import init_flow_params
+    perm, w = init_flow_params(D, seed)
+    A = D // 2
+    tail = A * 16 * 64 + A * 16
+    w[:, -tail:] = np.random.default_rng(seed + 100).normal(0.0, sd, (w.shape[0], tail)).astype(np.float32)
+    return perm, w
+
+
+FLOW_SETS = [("cornell", dict(width=16, height=16), 3000, 1, 0.6),
+             ("random_boxes", dict(seed=4, n_tris=2500, width=48, height=48, depth=6), 2047, 4, None),
+             ("cornell_spheres", dict(width=32, height=24, depth=5, n_lon=30, n_lat=16), 2500, 2, 0.3),
+             ("furnace", dict(depth=2), 700, 5, None)]
+
+
+def _make_flow_sets(J):
+    out = []
+    for name, kw, n, seed, beta in FLOW_SETS:
+        sc = scenes.by_name(name, **kw)
+        g = J.Scene(sc)
+        c = J.Chains(g, sc.width, sc.height, sc.depth, n, seed=seed, sigma=0.03)
+        c.set_execution("wave")
+        f = None
+        if beta is not None:
+            perm, w = _flow_params(sc.D, seed)
+            f = J.Flow(sc.D, perm, w)
+            J.set_flow(c, f, beta)
+        out.append((sc, g, c, f))
+    return out
+
+
+def test_batched_wavefront_with_flows_equals_individual_advances(J):
+    ref = _make_flow_sets(J)
+    bat = _make_flow_sets(J)
+    for _, _, c, _ in ref:
+        c.advance(4)
+        c.advance(5)
+        c.advance(5)
+    b = J.Batch([c for _, _, c, _ in bat])
+    lib = J.lib()
+    assert lib.jr_batch_set_block(b.h, 64) == J.JR_ERR_STATE       # flows run in the batched wavefront only
+    b.advance(4)
+    b.advance_graph(5)
+    b.advance_graph(5)
+    for (_, _, r, _), (_, _, c, _) in zip(ref, bat):
+        _compare(r, c)
+        assert c.stats()["status_word"] == 0
+
+
+def test_flow_attached_after_the_batch_was_built(J):
+    """A set gets its flow after jr_batch_create: the batch picks the new
+    regeneration density up (its descriptor and graph are renewed)."""
+    sets = [("cornell", dict(width=16, height=16), 3000, 1, 0.6),
+            ("random_boxes", dict(seed=4, n_tris=2500, width=48, height=48, depth=6), 2047, 4, None)]
+    mk = []
+    for name, kw, n, seed, beta in sets:
+        sc = scenes.by_name(name, **kw)
+        g = J.Scene(sc)
+        mk.append((sc, g, J.Chains(g, sc.width, sc.height, sc.depth, n, seed=seed, sigma=0.03),
+                   J.Chains(g, sc.width, sc.height, sc.depth, n, seed=seed, sigma=0.03)))
+    for sc, _, r, c in mk:
+        r.set_execution("wave")
+        c.set_execution("wave")
+    b = J.Batch([c for _, _, _, c in mk])
+    b.set_block(0)
+    b.advance_graph(3)
+    for _, _, r, _ in mk:
+        r.advance(3)
+    sc0 = mk[0][0]
+    perm, w = _flow_params(sc0.D, 1)
+    fr, fc = J.Flow(sc0.D, perm, w), J.Flow(sc0.D, perm, w)
+    J.set_flow(mk[0][2], fr, 0.6)
+    J.set_flow(mk[0][3], fc, 0.6)
+    b.advance_graph(3)             # the old graph had no flow launches
+    for _, _, r, _ in mk:
+        if r.stats()["steps_per_chain"] < mk[0][3].stats()["steps_per_chain"]:
+            r.advance(mk[0][3].stats()["steps_per_chain"] - r.stats()["steps_per_chain"])
+    for _, _, r, c in mk:
+        _compare(r, c)
+
+
+def test_batched_flow_set_replayed_by_oracle(J):
+    """One batched step of the flow set, replayed by the oracle's Alg. 2 with
+    the FP64 flow (u = beta q + 1 - beta) from the GPU's state."""
+    from oracle import learned as LR
+    from oracle import oracle as O
+    bat = _make_flow_sets(J)
+    b = J.Batch([c for _, _, c, _ in bat])
+    b.advance_graph(4)
+    sc, _, ch, f = bat[0]
+    x, fpu = ch.get_state()
+    st = ch.stats()
+    b.advance_graph(1)
+    x2, fpu2 = ch.get_state()
+    perm, w = _flow_params(sc.D, 1)
+    osc = O.Scene(sc)
+    F_of = lambda xx: O.eval_states(osc, xx)[0]
+    oc = LR.LearnedChains(F_of, sc.D, sc.width, sc.height, perm, w, beta=0.6, sigma=float(ch.params.sigma), seed=1,
+                          n_chains=ch.n)
+    oc.x = x.T.astype(np.float64)
+    oc.F = fpu[:3].T.astype(np.float64)
+    oc.p = fpu[3].astype(np.float64)
+    oc.u = fpu[4].astype(np.float64)
+    oc.step = st["steps_per_chain"]
+    oc.advance(1)
+    dx = np.abs(x2.T - oc.x)
+    dx = np.minimum(dx, 1 - dx).max(axis=1)
+    assert np.mean(dx <= 1e-4) >= 0.97, np.mean(dx <= 1e-4)
+    same = (dx <= 1e-4) & (fpu2[3] > 0)
+    assert np.mean(np.abs(fpu2[4][same] - oc.u[same]) <= 3e-3 * oc.u[same]) >= 0.98
