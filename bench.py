@@ -344,9 +344,30 @@ def time_to_target(args):
                     "chain_steps": int(st["steps_per_chain"]) * Cm, "status_word": st["status_word"],
                     "clocks": clocks}
 
+        companions = []
+        if args.batched:   # companion chain sets that share the arm's batched launches
+            for q, csc in enumerate(scenes.batched_workload(seed=7, n_scenes=args.batch_companions)):
+                cg = jr.Scene(csc, stream=stream)
+                companions.append((cg, csc))
+
         def run(learned):
             ch = jr.Chains(g, side, side, sc.depth, C, seed=5 if learned else 6, c_tilde=args.c_tilde, stream=stream)
             ch.set_execution("wave")
+            batch, comp_sets = None, []
+            if args.batched:
+                # the learned + batched form: the arm's chains advance through the
+                # batched wavefront (one persistent launch set for every set of the
+                # batch, replayed from a CUDA graph), beside the companion sets
+                comp_sets = [jr.Chains(cg, csc.width, csc.height, csc.depth, csc.width * csc.height, seed=9,
+                                       stream=stream) for cg, csc in companions]
+                batch = jr.Batch([ch] + comp_sets, stream=stream)
+                batch.set_block(0)
+
+            def adv(n):
+                if batch is not None:
+                    batch.advance_graph(n, stream=stream)
+                else:
+                    ch.advance(n, stream=stream)
             sampler = ClockSampler(torch.cuda.current_device())
             sampler.start()
             curve = []
@@ -375,7 +396,7 @@ def time_to_target(args):
                 t0 = time.perf_counter()
                 n_ep = min(int(round(epoch * args.epoch_growth ** e)), args.epoch_max)
                 for k in range(0, n_ep, args.snap_every):
-                    ch.advance(min(args.snap_every, n_ep - k), stream=stream)
+                    adv(min(args.snap_every, n_ep - k))
                     if learned:
                         buf.append(ch, stream=stream)
                 t1 = lap("advance", t0)
@@ -437,6 +458,9 @@ def time_to_target(args):
         mh = run_mh() if "mh" in args.arms else None
     line = {"metric": METRIC, "workload": wname, "unit": "s to relMSE 1e-2",
             "relmse_eps": 1e-2, "target": target, "time_limit_s": tmax, "chains": C, "c_tilde": args.c_tilde,
+            "batched": ({"companions": len(companions),
+                         "companion_chains": sum(csc.width * csc.height for _, csc in companions)}
+                        if args.batched else None),
             "epoch_steps": epoch,
             "epoch_growth": args.epoch_growth, "epoch_max": args.epoch_max,
             "reference": {"samples": args.ref_samples, "seconds": round(t_ref, 2), "noise_relmse_est": ref_noise},
@@ -456,7 +480,7 @@ def default_time_to_relmse(args):
     import copy
     a = copy.copy(args)
     a.workload, a.arms, a.chains, a.side, a.ref_samples = "caustic", "plain,learned", 0, None, None
-    a.time_limit, a.split_epoch, a.ref_file, a.c_tilde = 20.0, -1, None, 1.0
+    a.time_limit, a.split_epoch, a.ref_file, a.c_tilde, a.batched = 20.0, -1, None, 1.0, False
     r = time_to_target(a)
     keep = ("time_to_target_s", "time_to_target_interp_s", "final_relmse", "epochs", "seconds", "clocks",
             "chain_steps", "status_word")
@@ -525,6 +549,10 @@ def main():
     ap.add_argument("--split-epoch", type=int, default=-1, help="caustic workload: time 16 extra steps per kernel class after this epoch (diagnostic)")
     ap.add_argument("--beta", type=float, default=0.15)
     ap.add_argument("--c-tilde", type=float, default=1.0, help="time-to-target harness: c~ of the Restore arms")
+    ap.add_argument("--batched", action="store_true",
+                    help="time-to-target harness: the plain and learned arms advance through a batch (batched wavefront)")
+    ap.add_argument("--batch-companions", type=int, default=0,
+                    help="with --batched: companion random-box chain sets in the batch (1 chain per pixel)")
     ap.add_argument("--mh-large-step", type=float, default=0.3, help="MH arm: large-step probability l")
     ap.add_argument("--mh-burn-in", type=int, default=10_000, help="MH arm: iterations before the estimate starts")
     ap.add_argument("--mh-chains", type=int, default=0, help="MH arm: chains (0 = the Restore arms' count)")
