@@ -489,7 +489,9 @@ def default_time_to_relmse(args):
            "plain": {k: r["plain"].get(k) for k in keep},
            "learned": {**{k: r["learned"].get(k) for k in keep}, "beta": r["learned"]["beta"]}}
     tp, tl = out["plain"]["time_to_target_s"], out["learned"]["time_to_target_s"]
-    out["learned_over_plain"] = tl / tp if tp and tl else None
+    out["learned_over_plain"] = tl / tp if tp and tl else None   # first checkpoint at or below the target
+    ip, il = out["plain"]["time_to_target_interp_s"], out["learned"]["time_to_target_interp_s"]
+    out["learned_over_plain_interp"] = il / ip if ip and il else None   # log-log crossing between checkpoints
     return out
 
 

@@ -168,8 +168,12 @@ def nll_and_grad_torch(perm, w, x, wt):
 # there: ACC_ERR times the sum of the magnitudes that formed an activation, or
 # COORD_ERR for a coordinate.  A row with margin < 1 may legitimately take the
 # other side on the GPU; every other row must agree to FP32 accuracy.
-ACC_ERR = 2.0 ** -19      # FP32 accumulation of <= 64 exact bf16 products plus a bias, relative to sum |terms|
-COORD_ERR = 2.0 ** -19    # a coordinate in [0, 1) after up to 6 FP32 coupling transforms (absolute)
+# The units: FP32 accumulation of <= 64 exact bf16 products plus a bias is
+# within 2^-23 (one unit in the last place at 1.0) of the exact sum, relative to
+# the sum of the magnitudes; a coordinate in [0, 1) after up to 6 FP32 coupling
+# transforms is within 2^-20 of the exact value.
+ACC_ERR = 2.0 ** -23
+COORD_ERR = 2.0 ** -20
 
 
 def _bf16_edge_distance(v):

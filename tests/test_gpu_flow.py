@@ -2,12 +2,26 @@
 oracle, and Jump Restore chains with a learned mixture mu (needs a GB300).
 
 Tolerance (derived from the arithmetic): the MLP operands are bf16 on both
-sides, but the GPU accumulates in FP32 and the oracle exactly, so a bf16
-rounding of an activation can land on the other side of a rounding edge
-(relative 2^-9 steps).  Per row |log q_gpu - log q_oracle| <= 2e-3 for 99.5 %
-of rows; the rest are rows where a coordinate sits within rounding of a bin
-edge (the density jumps there).
+sides, but the GPU accumulates in FP32 and runs the couplings in FP32 while the
+oracle works exactly, so the two agree to FP32 rounding -- |log q_gpu -
+log q_oracle| <= 1e-5 (1.5e-5 at D = 32, whose 96 per-coordinate log terms add
+their roundings) -- except where the rounding decides a discrete step: the bf16
+rounding of an activation (a 2^-8 relative step) or the bin of a coordinate
+(the density jumps there).  The oracle reports, per row, the distance of every
+such value to its edge in units of the GPU's FP32 error (oracle.flow's rounding
+margins); every row that differs by more than the tolerance must have a margin
+below 1, and such rows must be rare.
 """
+TOL = {2: 1e-5, 8: 1e-5, 18: 1e-5, 22: 1e-5, 26: 1e-5, 32: 1.5e-5}
+FLIP_BUDGET = 0.02   # share of rows allowed to take the other side of an edge
+
+
+def _check_rows(d, margin, tol):
+    """d: per-row disagreement; margin: the oracle's rounding margin."""
+    off = d > tol
+    assert np.all(margin[off] < 1.0), (np.sort(d[off & (margin >= 1.0)])[-5:], np.sort(margin[off])[-5:])
+    assert np.mean(off) <= FLIP_BUDGET, np.mean(off)
+    return float(np.mean(off)), float(np.mean(margin < 1.0))
 import numpy as np
 import pytest
 
@@ -45,9 +59,9 @@ def test_log_density_matches_oracle(J, D, n):
     x = np.random.default_rng(D).random((n, D)).astype(np.float32)
     lq = f.log_density(torch.from_numpy(np.ascontiguousarray(x.T)).cuda()).cpu().numpy()
     lo, _ = FL.log_density(perm, w, x.astype(np.float64))
-    d = np.abs(lq - lo)
-    assert np.mean(d <= 2e-3) >= 0.995, np.sort(d)[-5:]
+    d = np.abs(lq.astype(np.float64) - lo)
     assert np.isfinite(lq).all()
+    _check_rows(d, FL.log_density_margin(perm, w, x.astype(np.float64)), TOL[D])
 
 
 @pytest.mark.parametrize("D,n", [(8, 4099), (22, 5000)])
@@ -60,11 +74,13 @@ def test_sampling_matches_oracle_and_inverts(J, D, n):
     lq = f.sample(t).cpu().numpy()
     x = t.cpu().numpy().T
     xo, lqo = FL.sample(perm, w, z.astype(np.float64))
-    ok = np.all(np.abs(x - xo) <= 1e-4, axis=1) & (np.abs(lq - lqo) <= 2e-3)
-    assert np.mean(ok) >= 0.995
+    d = np.maximum(np.abs(x.astype(np.float64) - xo).max(axis=1), np.abs(lq.astype(np.float64) - lqo))
+    _check_rows(d, FL.sample_margin(perm, w, z.astype(np.float64)), TOL[D])
     # GPU round trip: the density direction gives back the sampling log-density
     lq2 = f.log_density(torch.from_numpy(np.ascontiguousarray(x.T)).cuda()).cpu().numpy()
-    assert np.mean(np.abs(lq2 - lq) <= 2e-3) >= 0.995
+    d2 = np.abs(lq2.astype(np.float64) - lq)
+    m2 = np.minimum(FL.log_density_margin(perm, w, x.astype(np.float64)), FL.sample_margin(perm, w, z.astype(np.float64)))
+    _check_rows(d2, m2, 2 * TOL[D])
 
 
 def test_params_round_trip(J):
@@ -102,7 +118,9 @@ def test_chains_with_flow_step_replay(J):
     u_o = FL.regen_density(perm, w, oc.x, 0.6)
     pos = fpu[3] > 0
     assert pos.sum() >= 20
-    assert np.mean(np.abs(fpu[4][pos] - u_o[pos]) <= 2e-3 * u_o[pos]) >= 0.99
+    # u = beta q + 1 - beta at each state with p > 0, to 1e-5 relative off the edges
+    du = np.abs(fpu[4][pos] - u_o[pos]) / u_o[pos]
+    _check_rows(du, FL.log_density_margin(perm, w, oc.x[pos]), 1e-5)
     assert np.all(fpu[4][~pos] == 1.0)
     oc.advance(1)
     ch.advance(1)
@@ -110,8 +128,11 @@ def test_chains_with_flow_step_replay(J):
     dx = np.abs(x2.T - oc.x)
     dx = np.minimum(dx, 1 - dx).max(axis=1)
     assert np.mean(dx <= 1e-4) >= 0.97       # decisions and flow draws agree except near ties / bin edges
-    same = (dx <= 1e-4) & (fpu2[3] > 0)
-    assert np.mean(np.abs(fpu2[4][same] - oc.u[same]) <= 3e-3 * oc.u[same]) >= 0.98
+    # u at every new state with p > 0, against the oracle's density of the GPU's own state
+    pos2 = fpu2[3] > 0
+    xs2 = x2.T[pos2].astype(np.float64)
+    u2 = FL.regen_density(perm, w, xs2, 0.6)
+    _check_rows(np.abs(fpu2[4][pos2] - u2) / u2, FL.log_density_margin(perm, w, xs2), 1e-5)
 
 
 def test_learned_mixture_image_is_unbiased(J):
@@ -212,7 +233,11 @@ def test_full_size_learned_step_sampled(J):
     dx = np.abs(x2[:, sl].T - oc.x)
     dx = np.minimum(dx, 1 - dx).max(axis=1)
     assert np.mean(dx <= 1e-4) >= 0.97, np.mean(dx <= 1e-4)
-    same = (dx <= 1e-4) & (fpu2[3, sl] > 0)   # lit states are rare here: u is checked where there are any
-    if same.any():
-        assert np.mean(np.abs(fpu2[4, sl][same] - oc.u[same]) <= 3e-3 * oc.u[same]) >= 0.98
+    # u at the new lit states (rare here: all of the 2^20 chains' are checked), against
+    # the oracle's density of the GPU's own state, to 1e-5 off the rounding edges
+    pos2 = fpu2[3] > 0
+    if pos2.any():
+        xs2 = x2.T[pos2].astype(np.float64)
+        u2 = FL.regen_density(perm, w, xs2, 0.3)
+        _check_rows(np.abs(fpu2[4][pos2] - u2) / u2, FL.log_density_margin(perm, w, xs2), 1e-5)
     assert ch.stats()["status_word"] == 0

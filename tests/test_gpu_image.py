@@ -207,13 +207,26 @@ def test_spheres_plain_path_tracer_matches_oracle_paired(J):
 
 def test_spheres_relmse_and_per_pixel_vs_converged_reference(J, spheres_reference):
     """Jump Restore on the full 40k-triangle scene at 128^2, depth 8: 32
-    independent batches of 2^16 chains x 1500 steps scatter about the
-    converged reference within 4 sigma per pixel (0.1 % budget), and the
-    pooled image reaches relMSE <= 1e-3."""
+    independent batches of 2^16 chains x 1500 steps, each stopped with every
+    tour completed (the completed-tour estimator of Section 7.4, which has no
+    open-tour bias; with 2^16 open tours against J ~ 10^8 that bias reaches
+    several standard errors in the bright pixels, where tours are long), scatter
+    about the converged reference within 4 sigma per pixel (0.1 % budget), and
+    the pooled image reaches relMSE <= 1e-3."""
+    import torch
     from scipy import stats
     sc, ref, ref_noise = spheres_reference
     assert ref_noise < 2e-4, ref_noise
-    imgs = _gpu_batches(J, sc, 32, 1 << 16, 1500, seed=31, first_chain=1 << 24)
+    g = J.Scene(sc)
+    imgs = []
+    for b in range(32):
+        c = J.Chains(g, sc.width, sc.height, sc.depth, 1 << 16, seed=31, chain_offset=(1 << 24) + b * (1 << 16))
+        c.advance(1500)
+        assert J.complete_tours(c) == 0
+        imgs.append(c.resolve())
+        assert c.stats()["status_word"] == 0
+    torch.cuda.synchronize()
+    imgs = np.array(imgs, np.float64)
     img = imgs.mean(0)
     e = relmse(img, ref)
     assert e <= 1e-3, e
@@ -221,5 +234,9 @@ def test_spheres_relmse_and_per_pixel_vs_converged_reference(J, spheres_referenc
     ok = se > 0
     t = (img - ref)[ok] / se[ok]
     z = np.sign(t) * stats.norm.isf(stats.t.sf(np.abs(t), len(imgs) - 1))
-    assert np.mean(np.abs(z) > 4) <= 1e-3, np.sort(np.abs(z))[-8:]
+    bad = np.abs(z) > 4
+    msg = dict(frac=float(np.mean(bad)), worst=np.sort(np.abs(z))[-8:].tolist(),
+               positive=float(np.mean(z[bad] > 0)) if bad.any() else None,
+               rel_dev=np.sort(np.abs((img - ref)[ok][bad]) / np.maximum(ref[ok][bad], 1e-30))[-8:].tolist())
+    assert np.mean(bad) <= 1e-3, msg
     assert 0.7 < np.mean(z ** 2) < 1.5, np.mean(z ** 2)
