@@ -76,3 +76,24 @@ def mh_mixture_kernel(p: np.ndarray, mu: np.ndarray, ell: float, accept=None) ->
                 K[i, j] = Q[i, j] * acc(p[i], p[j])
         K[i, i] = 1.0 - K[i].sum()
     return K
+
+
+def restore_generator_general(p: np.ndarray, K: np.ndarray, M: np.ndarray, kappa: float, k: np.ndarray | None = None):
+    """Generator of the Restore process with general local dynamics and transfer
+    kernel (Section 6.1, eq. "killing-rate"; supplement, Theorem A) on
+    {0..M-1} with counting reference measure:
+
+        A = (K - I) + diag(k) (M - I),
+
+    local dynamics = rate-1 jumps by the Markov matrix K (not necessarily
+    pi-invariant), transfer rule mu(exit, .) = row `exit` of M, and
+    k_x = ((L* + kappa mu*) p)_x / p_x with L = K - I, (L* p)_x = (p K)_x - p_x
+    and (mu* p)_x = (p M)_x, formed by the oracle's killing_rate_general.
+    Returns (A, k); k may come out negative when kappa is too small."""
+    n = len(p)
+    ls = p @ K - p
+    ms = p @ M
+    if k is None:
+        k = np.array([_o.killing_rate_general(p[i], ls[i], kappa * ms[i]) for i in range(n)])
+    A = (K - np.eye(n)) + np.diag(k) @ (M - np.eye(n))
+    return A, k

@@ -22,6 +22,9 @@
  *   - the MH baseline of Section 8 ("Metropolis"): Alg. 1 with the mixture
  *     proposal of Section 5, l mu + (1 - l) zeta, and its ergodic-average
  *     estimator after a burn-in (Section 9 parameters).
+ *   - the general Restore of Section 6.1 (local dynamics that need not be
+ *     pi-invariant, killing rate ((L* + kappa mu*) p) / p) on 1-D analytic
+ *     targets, with the unadjusted Gaussian random walk as local dynamics.
  *   - the integrand: primary-sample-space (Section 2, Kelemen et al.) path
  *     contribution of a unidirectional path tracer with emission collected at
  *     every vertex; p = luminance of the RGB contribution.
@@ -1010,6 +1013,160 @@ ORC_EXPORT int orc_mh_advance(int target_kind, const orc_scene* scene, const orc
     free(jobs);
     free(th);
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* General Restore (Section 6.1, eq. "killing-rate"; supplement, Theorem A):  */
+/* local dynamics that need not leave pi invariant, so the killing rate keeps */
+/* the adjoint term: k = ((L* + kappa mu*) p) / p.  With state-independent mu */
+/* of density u, kappa mu* p = c~ u with c~ = kappa p_lambda, and             */
+/* k = (L* p + c~ u) / p.                                                     */
+/* ------------------------------------------------------------------------- */
+ORC_EXPORT double orc_killing_rate_general(double p, double lstar_p, double kappa_mustar_p)
+{
+    return p > 0.0 ? (lstar_p + kappa_mustar_p) / p : INFINITY;
+}
+
+/* Local dynamics of the continuous general Restore below: the unadjusted     *
+ * Gaussian random walk on the unit torus, y = (x + sigma N) mod 1, always    *
+ * taken (no MH correction), run as the jump process of Section 7.1 (holding  *
+ * times Exp(1)).  Its generator is L f = zeta f - f, so                       *
+ * (L* p)(x) = integral over [0,1) of p(y) zeta(y, x) dy - p(x), with          *
+ * zeta(y, x) the wrapped normal density sum_k phi_sigma(x - y + k).  The     *
+ * integral is a midpoint rule on n_quad points (1-D analytic targets).       */
+static double wrapped_normal(double d, double sigma)
+{
+    double s = 0.0;
+    for (int k = -3; k <= 3; ++k) {
+        double z = (d + k) / sigma;
+        s += exp(-0.5 * z * z);
+    }
+    return s / (sigma * sqrt(2.0 * M_PI));
+}
+
+static double lstar_p_1d(const orc_analytic* an, double x, double sigma, int n_quad)
+{
+    double acc = 0.0, h = 1.0 / n_quad;
+    for (int q = 0; q < n_quad; ++q) {
+        double y = (q + 0.5) * h;
+        v3 F = eval_analytic(an, 1, &y);
+        acc += lum(F) * wrapped_normal(x - y, sigma);
+    }
+    v3 Fx = eval_analytic(an, 1, &x);
+    return acc * h - lum(Fx);
+}
+
+ORC_EXPORT void orc_lstar_p_1d(const orc_analytic* an, int n, const double* x, double sigma, int n_quad, double* out)
+{
+    for (int i = 0; i < n; ++i) out[i] = lstar_p_1d(an, x[i], sigma, n_quad);
+}
+
+typedef struct {
+    const orc_analytic* an;
+    double sigma, c_tilde;
+    int n_quad, W, simplified;
+    uint64_t seed, chain_begin, c_lo, c_hi, step_begin, n_steps;
+    double* state;    /* per chain: x, p, k */
+    double* accum;    /* W*4 */
+    uint64_t J;
+} orc_gen_job;
+
+static void gen_eval(const orc_gen_job* jb, double x, double* p, double* k)
+{
+    v3 F = eval_analytic(jb->an, 1, &x);
+    *p = lum(F);
+    double ls = jb->simplified ? 0.0 : lstar_p_1d(jb->an, x, jb->sigma, jb->n_quad);
+    *k = orc_killing_rate_general(*p, ls, jb->c_tilde * 1.0 /* u = 1 */);
+}
+
+static void* gen_worker(void* arg)
+{
+    orc_gen_job* jb = (orc_gen_job*)arg;
+    for (uint64_t c = jb->c_lo; c < jb->c_hi; ++c) {
+        double* st = jb->state + 3 * c;
+        uint32_t chain = (uint32_t)(jb->chain_begin + c);
+        for (uint64_t i = 0; i < jb->n_steps; ++i) {
+            uint64_t step = jb->step_begin + i;
+            double U[4], V[4];
+            draw_block(jb->seed, ORC_TAG_STEP, 0, chain, step, U);
+            draw_block(jb->seed, ORC_TAG_STEP, 1, chain, step, V);
+            double x = st[0], p = st[1], k = st[2];
+            /* Alg. 2 clocks with the general killing rate */
+            double t1 = -log(1.0 - U[0]);
+            double t2 = isinf(k) ? 0.0 : -log(1.0 - U[1]) / k;
+            int local = t1 < t2;
+            double dt = local ? t1 : t2;
+            if (dt > 0.0 && p > 0.0) {
+                int px = (int)floor(x * jb->W);
+                if (px >= jb->W) px = jb->W - 1;
+                v3 F = eval_analytic(jb->an, 1, &x);
+                double wgt = jb->c_tilde * dt * jb->W / p;
+                double* a = jb->accum + 4 * (size_t)px;
+                a[0] += wgt * F.x; a[1] += wgt * F.y; a[2] += wgt * F.z; a[3] += dt;
+            }
+            double y;
+            if (local) { /* the unadjusted random walk: always moves */
+                double R = sqrt(-2.0 * log(1.0 - V[0]));
+                y = wrap01(x + jb->sigma * R * cos(2.0 * M_PI * V[1]));
+            } else {     /* regeneration from mu = uniform */
+                y = V[0];
+                jb->J += 1;
+            }
+            st[0] = y;
+            gen_eval(jb, y, &st[1], &st[2]);
+        }
+    }
+    return NULL;
+}
+
+/* Public: n chains of the general Restore process on a 1-D analytic target   *
+ * (state rows x, p, k; initialise with orc_general_init).  simplified = 1    *
+ * drops the L* p term (the killing rate of pi-invariant dynamics: a          *
+ * deliberately wrong choice for this local dynamics, the negative control).  */
+ORC_EXPORT void orc_general_init(const orc_analytic* an, double sigma, double c_tilde, int n_quad, int simplified,
+                                 uint64_t seed, uint64_t chain_begin, uint64_t n, double* state)
+{
+    orc_gen_job jb;
+    memset(&jb, 0, sizeof(jb));
+    jb.an = an; jb.sigma = sigma; jb.c_tilde = c_tilde; jb.n_quad = n_quad; jb.simplified = simplified;
+    for (uint64_t c = 0; c < n; ++c) {
+        double v[ORC_MAX_DIM + 8];
+        draw_coords(seed, ORC_TAG_INIT, (uint32_t)(chain_begin + c), 0, 1, v);
+        state[3 * c] = v[0];
+        gen_eval(&jb, v[0], &state[3 * c + 1], &state[3 * c + 2]);
+    }
+}
+
+ORC_EXPORT uint64_t orc_general_advance(const orc_analytic* an, int width, double sigma, double c_tilde, int n_quad,
+                                        int simplified, uint64_t seed, uint64_t chain_begin, uint64_t n,
+                                        uint64_t step_begin, uint64_t n_steps, double* state, double* accum,
+                                        int n_threads)
+{
+    int T = resolve_threads(n_threads, n);
+    orc_gen_job* jobs = (orc_gen_job*)calloc((size_t)T, sizeof(orc_gen_job));
+    pthread_t* th = (pthread_t*)calloc((size_t)T, sizeof(pthread_t));
+    size_t npx = (size_t)width * 4;
+    for (int t = 0; t < T; ++t) {
+        orc_gen_job* jb = &jobs[t];
+        jb->an = an; jb->sigma = sigma; jb->c_tilde = c_tilde; jb->n_quad = n_quad; jb->W = width;
+        jb->simplified = simplified; jb->seed = seed; jb->chain_begin = chain_begin;
+        jb->c_lo = n * (uint64_t)t / (uint64_t)T;
+        jb->c_hi = n * (uint64_t)(t + 1) / (uint64_t)T;
+        jb->step_begin = step_begin; jb->n_steps = n_steps; jb->state = state;
+        jb->accum = (double*)calloc(npx, sizeof(double));
+        if (T > 1) pthread_create(&th[t], NULL, gen_worker, jb);
+    }
+    if (T == 1) gen_worker(&jobs[0]);
+    uint64_t J = 0;
+    for (int t = 0; t < T; ++t) {
+        if (T > 1) pthread_join(th[t], NULL);
+        for (size_t k = 0; k < npx; ++k) accum[k] += jobs[t].accum[k];
+        free(jobs[t].accum);
+        J += jobs[t].J;
+    }
+    free(jobs);
+    free(th);
+    return J;
 }
 
 /* Public: F, p, u, k for given states (row-major n x D).  hit_ids optional,   *

@@ -83,6 +83,12 @@ def lib():
             L.orc_mh_advance.argtypes = [I, P, P, I, I, I, I, D, D, U64, U64, U64, U64, U64, U64, P, P, P, P,
                                          P, P, P, I]
             L.orc_mh_advance.restype = I
+            L.orc_killing_rate_general.argtypes = [D, D, D]
+            L.orc_killing_rate_general.restype = D
+            L.orc_lstar_p_1d.argtypes = [P, I, P, D, I, P]
+            L.orc_general_init.argtypes = [P, D, D, I, I, U64, U64, U64, P]
+            L.orc_general_advance.argtypes = [P, I, D, D, I, I, U64, U64, U64, U64, U64, P, P, I]
+            L.orc_general_advance.restype = U64
             L.orc_eval_states.argtypes = [I, P, P, I, I, D, U64, P, P, P, P, P, P]
             L.orc_render_pt.argtypes = [I, P, P, I, I, I, I, U64, U64, U64, P, I]
             L.orc_threads_default.restype = I
@@ -321,6 +327,46 @@ class MHChains:
     def image(self):
         """MH ergodic-average estimate: b_hat * accum / N."""
         return self.b_hat() * self.accum[:, :, :3] / max(self.splats, 1)
+
+
+def killing_rate_general(p, lstar_p, kappa_mustar_p):
+    """((L* + kappa mu*) p) / p (Section 6.1), +inf at p = 0."""
+    return lib().orc_killing_rate_general(float(p), float(lstar_p), float(kappa_mustar_p))
+
+
+def lstar_p_1d(target, x, sigma, n_quad=4096):
+    """(L* p)(x) of the unadjusted wrapped-Gaussian random walk on a 1-D analytic target."""
+    x = np.ascontiguousarray(x, np.float64)
+    out = np.zeros(len(x))
+    lib().orc_lstar_p_1d(target.h, len(x), _ptr(x), float(sigma), int(n_quad), _ptr(out))
+    return out
+
+
+class GeneralChains:
+    """General Restore (Section 6.1) on a 1-D analytic target: local dynamics =
+    the unadjusted Gaussian random walk (not pi-invariant), mu uniform,
+    k = (L* p + c~) / p; simplified=True drops L* p (a wrong rate here)."""
+
+    def __init__(self, target, width, sigma, c_tilde, seed=0, chain_begin=0, n_chains=1, n_quad=4096,
+                 simplified=False):
+        self.target, self.W, self.sigma, self.c_tilde = target, int(width), float(sigma), float(c_tilde)
+        self.seed, self.cb, self.n, self.nq, self.simp = int(seed), int(chain_begin), int(n_chains), int(n_quad), \
+            int(bool(simplified))
+        self.state = np.zeros((self.n, 3))
+        lib().orc_general_init(target.h, self.sigma, self.c_tilde, self.nq, self.simp, self.seed, self.cb, self.n,
+                               _ptr(self.state))
+        self.accum = np.zeros((self.W, 4))
+        self.step = 0
+        self.J = 0
+
+    def advance(self, n_steps, n_threads=0):
+        self.J += int(lib().orc_general_advance(self.target.h, self.W, self.sigma, self.c_tilde, self.nq, self.simp,
+                                                self.seed, self.cb, self.n, self.step, n_steps, _ptr(self.state),
+                                                _ptr(self.accum), int(n_threads)))
+        self.step += n_steps
+
+    def image(self):
+        return self.accum[:, :3] / max(self.J, 1)
 
 
 def eval_states(target, x, c_tilde=1.0, depth=None, hit_ids=False):
