@@ -22,6 +22,9 @@
  *   - the MH baseline of Section 8 ("Metropolis"): Alg. 1 with the mixture
  *     proposal of Section 5, l mu + (1 - l) zeta, and its ergodic-average
  *     estimator after a burn-in (Section 9 parameters).
+ *   - Langevin local dynamics (MALA, Section 9): the integrand's gradient in
+ *     forward mode, the MALA proposal and its MH acceptance, for Jump Restore
+ *     ("MALA Restore") and for the MH baseline ("MALA").
  *   - the general Restore of Section 6.1 (local dynamics that need not be
  *     pi-invariant, killing rate ((L* + kappa mu*) p) / p) on 1-D analytic
  *     targets, with the unadjusted Gaussian random walk as local dynamics.
@@ -1009,6 +1012,430 @@ ORC_EXPORT int orc_mh_advance(int target_kind, const orc_scene* scene, const orc
         ps += jobs[t].p_sum_large;
     }
     out4[0] = L; out4[1] = Sm; out4[2] = A; out4[3] = N;
+    *p_sum_large += ps;
+    free(jobs);
+    free(th);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Gradient of the integrand w.r.t. the PSS coordinates, for the Langevin     */
+/* local dynamics (MALA, Section 9's second family).  Forward mode: every     */
+/* quantity that depends continuously on x carries its D partial derivatives. */
+/* In this path sampler F depends continuously on x only through the camera   */
+/* direction, the scattered directions and the modified Phong weights         */
+/* (Lambertian and dielectric weights are constant, and the hit points only   */
+/* select triangles, which is piecewise constant); so origins and hit points  */
+/* carry no derivatives.  The result is the gradient almost everywhere; at a  */
+/* change of the hit triangle, the bounce type or the Fresnel choice it is    */
+/* the one-sided gradient of the piece the state lies in.                     */
+/* ------------------------------------------------------------------------- */
+typedef struct { double v; double g[ORC_MAX_DIM]; } dnum;
+typedef struct { dnum x, y, z; } dvec;
+static _Thread_local int g_dn_D = 0;   /* the active dimension D, set per evaluation */
+
+static dnum dn_c(double v) { dnum r; r.v = v; memset(r.g, 0, sizeof(r.g)); return r; }
+static dnum dn_var(double v, int i) { dnum r = dn_c(v); r.g[i] = 1.0; return r; }
+static dnum dn_add(dnum a, dnum b) { dnum r; r.v = a.v + b.v; for (int i = 0; i < g_dn_D; ++i) r.g[i] = a.g[i] + b.g[i]; return r; }
+static dnum dn_sub(dnum a, dnum b) { dnum r; r.v = a.v - b.v; for (int i = 0; i < g_dn_D; ++i) r.g[i] = a.g[i] - b.g[i]; return r; }
+static dnum dn_mul(dnum a, dnum b)
+{
+    dnum r; r.v = a.v * b.v;
+    for (int i = 0; i < g_dn_D; ++i) r.g[i] = a.g[i] * b.v + a.v * b.g[i];
+    return r;
+}
+static dnum dn_scl(dnum a, double s) { dnum r; r.v = a.v * s; for (int i = 0; i < g_dn_D; ++i) r.g[i] = a.g[i] * s; return r; }
+static dnum dn_div(dnum a, dnum b)
+{
+    dnum r; r.v = a.v / b.v;
+    for (int i = 0; i < g_dn_D; ++i) r.g[i] = (a.g[i] * b.v - a.v * b.g[i]) / (b.v * b.v);
+    return r;
+}
+static dnum dn_sqrt(dnum a)
+{
+    dnum r; r.v = sqrt(a.v > 0.0 ? a.v : 0.0);
+    for (int i = 0; i < g_dn_D; ++i) r.g[i] = r.v > 0.0 ? 0.5 * a.g[i] / r.v : 0.0;
+    return r;
+}
+static dnum dn_pow(dnum a, double e)   /* a^e, a > 0 */
+{
+    dnum r; r.v = pow(a.v, e);
+    double d = a.v > 0.0 ? e * pow(a.v, e - 1.0) : 0.0;
+    for (int i = 0; i < g_dn_D; ++i) r.g[i] = d * a.g[i];
+    return r;
+}
+static dnum dn_cos(dnum a) { dnum r; r.v = cos(a.v); for (int i = 0; i < g_dn_D; ++i) r.g[i] = -sin(a.v) * a.g[i]; return r; }
+static dnum dn_sin(dnum a) { dnum r; r.v = sin(a.v); for (int i = 0; i < g_dn_D; ++i) r.g[i] = cos(a.v) * a.g[i]; return r; }
+static dvec dv_c(v3 a) { dvec r; r.x = dn_c(a.x); r.y = dn_c(a.y); r.z = dn_c(a.z); return r; }
+static v3 dv_val(dvec a) { return mk(a.x.v, a.y.v, a.z.v); }
+static dvec dv_add(dvec a, dvec b) { dvec r; r.x = dn_add(a.x, b.x); r.y = dn_add(a.y, b.y); r.z = dn_add(a.z, b.z); return r; }
+static dvec dv_sub(dvec a, dvec b) { dvec r; r.x = dn_sub(a.x, b.x); r.y = dn_sub(a.y, b.y); r.z = dn_sub(a.z, b.z); return r; }
+static dvec dv_scl(dvec a, dnum s) { dvec r; r.x = dn_mul(a.x, s); r.y = dn_mul(a.y, s); r.z = dn_mul(a.z, s); return r; }
+static dvec dv_sclc(dvec a, double s) { dvec r; r.x = dn_scl(a.x, s); r.y = dn_scl(a.y, s); r.z = dn_scl(a.z, s); return r; }
+static dvec dv_cmul(dvec a, v3 c) { dvec r; r.x = dn_scl(a.x, c.x); r.y = dn_scl(a.y, c.y); r.z = dn_scl(a.z, c.z); return r; }
+static dnum dv_dot(dvec a, dvec b) { return dn_add(dn_add(dn_mul(a.x, b.x), dn_mul(a.y, b.y)), dn_mul(a.z, b.z)); }
+static dnum dv_dotc(dvec a, v3 c) { return dn_add(dn_add(dn_scl(a.x, c.x), dn_scl(a.y, c.y)), dn_scl(a.z, c.z)); }
+static dvec dv_normalize(dvec a) { dnum l = dn_sqrt(dv_dot(a, a)); dvec r; r.x = dn_div(a.x, l); r.y = dn_div(a.y, l); r.z = dn_div(a.z, l); return r; }
+
+/* Duff et al.'s basis around the unit vector n, with derivatives. */
+static void dv_onb(dvec n, dvec* t, dvec* b)
+{
+    double sign = copysign(1.0, n.z.v);
+    dnum a = dn_div(dn_c(-1.0), dn_add(dn_c(sign), n.z));
+    dnum bb = dn_mul(dn_mul(n.x, n.y), a);
+    t->x = dn_add(dn_c(1.0), dn_scl(dn_mul(dn_mul(n.x, n.x), a), sign));
+    t->y = dn_scl(bb, sign);
+    t->z = dn_scl(n.x, -sign);
+    b->x = bb;
+    b->y = dn_add(dn_c(sign), dn_mul(dn_mul(n.y, n.y), a));
+    b->z = dn_scl(n.y, -1.0);
+}
+
+/* The scatter of the path sampler (same branches as scatter()), on dual      *
+ * directions; u1, u2 are the bounce's coordinates (dual).                    */
+static int scatter_d(const orc_material* m, dvec d, v3 ng, dnum u1, dnum u2, dvec* wi, dvec* w)
+{
+    if (m->type == ORC_DIELECTRIC) {
+        dnum cos_i = dn_scl(dv_dotc(d, ng), -1.0);
+        double eta_i = 1.0, eta_t = m->ior;
+        v3 nn = ng;
+        if (cos_i.v < 0.0) { cos_i = dn_scl(cos_i, -1.0); eta_i = m->ior; eta_t = 1.0; nn = scl(ng, -1.0); }
+        double e = eta_i / eta_t;
+        dnum sin2_t = dn_scl(dn_sub(dn_c(1.0), dn_mul(cos_i, cos_i)), e * e);
+        double cos_t_v;
+        double R = fresnel_dielectric(cos_i.v, eta_i, eta_t, &cos_t_v);
+        dvec nnd = dv_c(nn);
+        if (u1.v < R) {
+            *wi = dv_add(d, dv_scl(nnd, dn_scl(cos_i, 2.0)));
+        } else {
+            dnum cos_t = dn_sqrt(dn_sub(dn_c(1.0), sin2_t));
+            *wi = dv_add(dv_sclc(d, e), dv_scl(nnd, dn_sub(dn_scl(cos_i, e), cos_t)));
+        }
+        *w = dv_c(mk(1.0, 1.0, 1.0));
+        return 1;
+    }
+    v3 ns = dot(dv_val(d), ng) < 0.0 ? ng : scl(ng, -1.0);
+    dvec t, b;
+    if (m->type == ORC_LAMBERT) {
+        dnum r = dn_sqrt(u1), phi = dn_scl(u2, 2.0 * M_PI);
+        dnum lz = dn_sqrt(dn_sub(dn_c(1.0), u1));
+        v3 tc, bc;
+        onb(ns, &tc, &bc);
+        *wi = dv_add(dv_add(dv_scl(dv_c(tc), dn_mul(r, dn_cos(phi))), dv_scl(dv_c(bc), dn_mul(r, dn_sin(phi)))),
+                     dv_scl(dv_c(ns), lz));
+        *w = dv_c(m->albedo);
+        return m->albedo.x > 0.0 || m->albedo.y > 0.0 || m->albedo.z > 0.0;
+    }
+    dvec nsd = dv_c(ns);
+    dvec r = dv_sub(d, dv_scl(nsd, dn_scl(dv_dotc(d, ns), 2.0)));
+    double n = m->phong_n;
+    dnum cos_a = dn_pow(dn_sub(dn_c(1.0), u1), 1.0 / (n + 1.0));
+    dnum sin_a = dn_sqrt(dn_sub(dn_c(1.0), dn_mul(cos_a, cos_a)));
+    dnum phi = dn_scl(u2, 2.0 * M_PI);
+    dv_onb(r, &t, &b);
+    *wi = dv_add(dv_add(dv_scl(t, dn_mul(sin_a, dn_cos(phi))), dv_scl(b, dn_mul(sin_a, dn_sin(phi)))), dv_scl(r, cos_a));
+    dnum cos_i = dv_dotc(*wi, ns);
+    if (cos_i.v <= 0.0) return 0;
+    *w = dv_sclc(dv_c(m->albedo), 0.0);
+    w->x = dn_scl(cos_i, m->albedo.x * (n + 2.0) / (n + 1.0));
+    w->y = dn_scl(cos_i, m->albedo.y * (n + 2.0) / (n + 1.0));
+    w->z = dn_scl(cos_i, m->albedo.z * (n + 2.0) / (n + 1.0));
+    return 1;
+}
+
+/* F(x) and dF/dx (3 x D, row-major by channel).  Same path as eval_path(). */
+static void eval_path_grad(const orc_scene* s, int depth, int D, const double* x, v3* F_out, double* dF)
+{
+    g_dn_D = D;
+    dvec F = dv_c(mk(0, 0, 0)), T = dv_c(mk(1, 1, 1));
+    v3 o = s->cam_o;
+    dnum x0 = dn_var(x[0], 0), x1 = dn_var(x[1], 1);
+    dvec d = dv_add(dv_c(s->cam_f), dv_add(dv_scl(dv_c(s->cam_r), dn_sub(dn_scl(x0, 2.0), dn_c(1.0))),
+                                           dv_scl(dv_c(s->cam_u), dn_sub(dn_c(1.0), dn_scl(x1, 2.0)))));
+    d = dv_normalize(d);
+    for (int v = 0; v <= depth; ++v) {
+        double t;
+        v3 dv = dv_val(d);
+        int id = closest_hit(s, o, dv, &t);
+        if (id < 0) break;
+        const orc_material* m = &s->mats[s->mat[id]];
+        v3 ng = s->ng[id];
+        v3 p = add(o, scl(dv, t));
+        if (m->emits && -dot(dv, ng) > 0.0) F = dv_add(F, dv_cmul(T, m->emission));
+        if (v == depth) break;
+        dvec wi, w;
+        dnum u1 = dn_var(x[2 + 2 * v], 2 + 2 * v), u2 = dn_var(x[3 + 2 * v], 3 + 2 * v);
+        if (!scatter_d(m, d, ng, u1, u2, &wi, &w)) break;
+        dvec Tn;
+        Tn.x = dn_mul(T.x, w.x); Tn.y = dn_mul(T.y, w.y); Tn.z = dn_mul(T.z, w.z);
+        T = Tn;
+        if (T.x.v == 0.0 && T.y.v == 0.0 && T.z.v == 0.0) break;
+        v3 wv = dv_val(wi);
+        v3 off = dot(wv, ng) >= 0.0 ? ng : scl(ng, -1.0);
+        double mx = fabs(p.x);
+        if (fabs(p.y) > mx) mx = fabs(p.y);
+        if (fabs(p.z) > mx) mx = fabs(p.z);
+        o = add(p, scl(off, ORC_EPS_OFFSET * (1.0 + mx)));
+        d = wi;
+    }
+    *F_out = dv_val(F);
+    for (int i = 0; i < D; ++i) {
+        dF[i] = F.x.g[i];
+        dF[D + i] = F.y.g[i];
+        dF[2 * D + i] = F.z.g[i];
+    }
+}
+
+/* F and dF/dx of the analytic target (the definition differentiated by hand: *
+ * q = sum_i w_i exp(-r_i^2 / (2 s_i^2)), F = q (0.5 + x0, 1, 0.5 + x1), zero  *
+ * inside the band a <= x0 < b; the band edges are jumps, where the gradient  *
+ * of the piece the state lies in is taken).                                  */
+static void eval_analytic_grad(const orc_analytic* a, int D, const double* x, v3* F_out, double* dF)
+{
+    for (int i = 0; i < 3 * D; ++i) dF[i] = 0.0;
+    double x0 = x[0], x1 = D >= 2 ? x[1] : 0.0;
+    if (x0 >= a->band_a && x0 < a->band_b) { *F_out = mk(0, 0, 0); return; }
+    double q = 0.0, dq0 = 0.0, dq1 = 0.0;
+    for (int i = 0; i < a->n_modes; ++i) {
+        double dx = x0 - a->m0[i], dy = D >= 2 ? x1 - a->m1[i] : 0.0;
+        double s2 = a->sd[i] * a->sd[i];
+        double e = a->w[i] * exp(-(dx * dx + dy * dy) / (2.0 * s2));
+        q += e;
+        dq0 += -dx / s2 * e;
+        dq1 += -dy / s2 * e;
+    }
+    *F_out = mk(q * (0.5 + x0), q, q * (0.5 + x1));
+    dF[0] = dq0 * (0.5 + x0) + q;       /* dF_r / dx0 */
+    dF[D] = dq0;                        /* dF_g / dx0 */
+    dF[2 * D] = dq0 * (0.5 + x1);       /* dF_b / dx0 */
+    if (D >= 2) {
+        dF[1] = dq1 * (0.5 + x0);
+        dF[D + 1] = dq1;
+        dF[2 * D + 1] = dq1 * (0.5 + x1) + q;
+    }
+}
+
+ORC_EXPORT void orc_analytic_grad(const orc_analytic* a, int D, uint64_t n, const double* x, double* F3, double* dF)
+{
+    for (uint64_t i = 0; i < n; ++i) {
+        v3 F;
+        eval_analytic_grad(a, D, x + i * (uint64_t)D, &F, dF + i * 3 * (uint64_t)D);
+        F3[3 * i] = F.x; F3[3 * i + 1] = F.y; F3[3 * i + 2] = F.z;
+    }
+}
+
+/* Public: F and dF/dx (n x 3 x D) for states x (row-major n x D). */
+ORC_EXPORT void orc_eval_grad(const orc_scene* s, int D, int depth, uint64_t n, const double* x, double* F3, double* dF)
+{
+    for (uint64_t i = 0; i < n; ++i) {
+        v3 F;
+        eval_path_grad(s, depth, D, x + i * (uint64_t)D, &F, dF + i * 3 * (uint64_t)D);
+        F3[3 * i] = F.x; F3[3 * i + 1] = F.y; F3[3 * i + 2] = F.z;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Langevin local dynamics (MALA): one MH step (Alg. 1) with the proposal     */
+/* y = (x + m(x) + sigma N) mod 1, m(x) = clamp(sigma^2/2 grad log p(x),      */
+/* -2 sigma, 2 sigma) per coordinate (the clamp keeps the drift of a sharp    */
+/* Phong lobe from throwing the proposal across the torus; any deterministic  */
+/* drift gives a valid proposal), and acceptance                              */
+/* min(1, p(y) q(x|y) / (p(x) q(y|x))), q(y|x) = prod_d phi_sigma(y_d - x_d - */
+/* m_d(x)) on the signed torus difference (the nearest image; the others are */
+/* below exp(-50) for sigma <= 0.05).  MALA leaves pi invariant, so          */
+/* "MALA Restore" keeps the killing rate c~ u / p of Section 6.2; the MALA    */
+/* baseline is the mixture of a large step (prob. l, uniform, acceptance      */
+/* min(1, p(y)/p(x))) and a MALA step, each with its own MH acceptance.        */
+/* State row: x[D], F.rgb, p, u, m[D] (the drift at x).                        */
+/* ------------------------------------------------------------------------- */
+static void mala_eval(const orc_params* P, const double* x, double* row, double sigma)
+{
+    int D = P->D;
+    v3 F;
+    double dF[3 * ORC_MAX_DIM];
+    if (P->target_kind == 0) eval_path_grad(P->scene, P->depth, D, x, &F, dF);
+    else eval_analytic_grad(P->analytic, D, x, &F, dF);
+    for (int d = 0; d < D; ++d) row[d] = x[d];
+    row[D] = F.x; row[D + 1] = F.y; row[D + 2] = F.z;
+    double p = lum(F);
+    row[D + 3] = p;
+    row[D + 4] = 1.0;
+    for (int d = 0; d < D; ++d) {
+        double g = p > 0.0 ? (0.2126 * dF[d] + 0.7152 * dF[D + d] + 0.0722 * dF[2 * D + d]) / p : 0.0;
+        double m = isfinite(g) ? 0.5 * sigma * sigma * g : 0.0;
+        if (m > 2.0 * sigma) m = 2.0 * sigma;
+        if (m < -2.0 * sigma) m = -2.0 * sigma;
+        row[D + 5 + d] = m;
+    }
+}
+
+static double torus_delta(double to, double from)
+{
+    double d = to - from;
+    return d - floor(d + 0.5);
+}
+
+/* log q(y | x) up to the constant, from x's drift m */
+static double mala_log_q(const double* y, const double* x, const double* m, int D, double sigma)
+{
+    double s = 0.0;
+    for (int d = 0; d < D; ++d) {
+        double e = torus_delta(y[d], x[d]) - m[d];
+        s += e * e;
+    }
+    return -s / (2.0 * sigma * sigma);
+}
+
+typedef struct {
+    const orc_params* P;
+    int method;           /* 0: Jump Restore with MALA local moves; 1: MH baseline with MALA small steps;
+                             2: as 1 but with the Hastings ratio dropped -- a deliberately wrong kernel that
+                                only the tests' negative control runs */
+    double ell;
+    uint64_t burn_in, chain_begin, c_lo, c_hi, step_begin, n_steps;
+    double* state;        /* stride 2 D + 5 */
+    double* accum;
+    uint64_t J, locals, accepts, splats;
+    double p_sum_large;
+    uint8_t* tr_flags;
+    int32_t* tr_pix;
+    double* tr_margin;    /* log of the acceptance ratio minus log U_a (local / small steps), else 0 */
+} orc_mala_job;
+
+static void* mala_worker(void* arg)
+{
+    orc_mala_job* jb = (orc_mala_job*)arg;
+    const orc_params* P = jb->P;
+    int D = P->D, S = 2 * D + 5;
+    double WH = (double)P->width * (double)P->height;
+    double v[ORC_MAX_DIM + 8], y[ORC_MAX_DIM], cand[2 * ORC_MAX_DIM + 5];
+    for (uint64_t c = jb->c_lo; c < jb->c_hi; ++c) {
+        double* st = jb->state + c * S;
+        uint32_t chain = (uint32_t)(jb->chain_begin + c);
+        for (uint64_t i = 0; i < jb->n_steps; ++i) {
+            uint64_t step = jb->step_begin + i;
+            double U[4];
+            draw_block(P->seed, ORC_TAG_STEP, 0, chain, step, U);
+            double p = st[D + 3], u = st[D + 4];
+            int local;
+            double dt = 0.0, wgt = 0.0;
+            if (jb->method == 0) {   /* Alg. 2 clocks, killing rate c~ u / p */
+                double t1 = -log(1.0 - U[0]);
+                double t2 = p > 0.0 ? -log(1.0 - U[1]) * p / (P->c_tilde * u) : 0.0;
+                local = t1 < t2;
+                dt = local ? t1 : t2;
+                wgt = P->c_tilde * dt * WH / (p > 0.0 ? p : 1.0);
+            } else {                 /* MH baseline: large step with probability l */
+                local = !(U[0] < jb->ell);
+                if (step >= jb->burn_in) { dt = 1.0; jb->splats += 1; }
+                wgt = WH / (p > 0.0 ? p : 1.0);
+            }
+            int pix = -1;
+            if (dt > 0.0 && p > 0.0) {
+                int px, py;
+                pixel_of(P, st, &px, &py);
+                pix = py * P->width + px;
+                double* a = jb->accum + 4 * (size_t)pix;
+                a[0] += wgt * st[D]; a[1] += wgt * st[D + 1]; a[2] += wgt * st[D + 2]; a[3] += dt;
+            }
+            draw_coords(P->seed, ORC_TAG_STEP, chain, step, D, v);
+            int accepted = 0;
+            double margin = 0.0;
+            if (local) {   /* MALA proposal from the drift cached with the state */
+                const double* m = st + D + 5;
+                for (int k = 0; k < (D + 1) / 2; ++k) {
+                    double R = sqrt(-2.0 * log(1.0 - v[2 * k]));
+                    double ang = 2.0 * M_PI * v[2 * k + 1];
+                    y[2 * k] = wrap01(st[2 * k] + m[2 * k] + P->sigma * R * cos(ang));
+                    if (2 * k + 1 < D) y[2 * k + 1] = wrap01(st[2 * k + 1] + m[2 * k + 1] + P->sigma * R * sin(ang));
+                }
+                mala_eval(P, y, cand, P->sigma);
+                double py = cand[D + 3];
+                if (!(p > 0.0)) {
+                    accepted = 1;
+                } else if (py > 0.0) {
+                    double la = log(py) - log(p);
+                    if (jb->method != 2)
+                        la += mala_log_q(st, y, cand + D + 5, D, P->sigma) - mala_log_q(y, st, m, D, P->sigma);
+                    margin = la - log(U[2]);
+                    accepted = U[2] > 0.0 ? margin > 0.0 : 1;
+                }
+                if (accepted) memcpy(st, cand, sizeof(double) * (size_t)S);
+                jb->locals += 1;
+                jb->accepts += (uint64_t)accepted;
+            } else if (jb->method == 0) {   /* regeneration from mu */
+                mala_eval(P, v, st, P->sigma);
+                jb->J += 1;
+            } else {                        /* MH large step: uniform, symmetric */
+                mala_eval(P, v, cand, P->sigma);
+                double py = cand[D + 3];
+                jb->J += 1;
+                jb->p_sum_large += py;
+                accepted = U[2] < orc_mh_accept_prob(p, py);
+                margin = U[2] * p - py;
+                if (accepted) memcpy(st, cand, sizeof(double) * (size_t)S);
+                jb->accepts += (uint64_t)accepted;
+            }
+            if (jb->tr_flags) {
+                size_t o = (size_t)c * jb->n_steps + i;
+                jb->tr_flags[o] = (uint8_t)((local ? 0 : 1) | (accepted ? 2 : 0));
+                jb->tr_pix[o] = pix;
+                if (jb->tr_margin) jb->tr_margin[o] = margin;
+            }
+        }
+    }
+    return NULL;
+}
+
+/* Public: initial states (x0 ~ mu, tag 1) with F, p, u and the drift. */
+ORC_EXPORT void orc_mala_init(int target_kind, const orc_scene* scene, const orc_analytic* an, int D, int depth,
+                              double sigma, uint64_t seed, uint64_t chain_begin, uint64_t n, double* state)
+{
+    orc_params P = make_params(target_kind, scene, an, D, depth, 1, 1, 1.0, sigma, seed, 0);
+    double v[ORC_MAX_DIM + 8];
+    for (uint64_t c = 0; c < n; ++c) {
+        draw_coords(seed, ORC_TAG_INIT, (uint32_t)(chain_begin + c), 0, D, v);
+        mala_eval(&P, v, state + c * (uint64_t)(2 * D + 5), sigma);
+    }
+}
+
+/* Public: advance MALA chains.  method 0 = Jump Restore (J = regenerations,   *
+ * out4 = (J, local steps, accepted, 0)); method 1 = MH baseline (out4 =       *
+ * (large steps, small steps, accepted, splatted iterations), p_sum_large).    */
+ORC_EXPORT int orc_mala_advance(int target_kind, const orc_scene* scene, const orc_analytic* an, int D, int depth,
+                                int width, int height, double sigma, double c_tilde, int method, double ell,
+                                uint64_t burn_in, uint64_t seed, uint64_t chain_begin, uint64_t n,
+                                uint64_t step_begin, uint64_t n_steps, double* state, double* accum, uint64_t* out4,
+                                double* p_sum_large, uint8_t* tr_flags, int32_t* tr_pix, double* tr_margin,
+                                int n_threads)
+{
+    if (D > ORC_MAX_DIM || D < 2) return -1;
+    orc_params P = make_params(target_kind, scene, an, D, depth, width, height, c_tilde, sigma, seed, 0);
+    int T = resolve_threads(n_threads, n);
+    orc_mala_job* jobs = (orc_mala_job*)calloc((size_t)T, sizeof(orc_mala_job));
+    pthread_t* th = (pthread_t*)calloc((size_t)T, sizeof(pthread_t));
+    size_t npx = (size_t)width * (size_t)height * 4;
+    for (int t = 0; t < T; ++t) {
+        orc_mala_job* jb = &jobs[t];
+        jb->P = &P; jb->method = method; jb->ell = ell; jb->burn_in = burn_in;
+        jb->chain_begin = chain_begin;
+        jb->c_lo = n * (uint64_t)t / (uint64_t)T;
+        jb->c_hi = n * (uint64_t)(t + 1) / (uint64_t)T;
+        jb->step_begin = step_begin; jb->n_steps = n_steps; jb->state = state;
+        jb->accum = (double*)calloc(npx, sizeof(double));
+        jb->tr_flags = tr_flags; jb->tr_pix = tr_pix; jb->tr_margin = tr_margin;
+        if (T > 1) pthread_create(&th[t], NULL, mala_worker, jb);
+    }
+    if (T == 1) mala_worker(&jobs[0]);
+    uint64_t J = 0, L = 0, A = 0, N = 0;
+    double ps = 0.0;
+    for (int t = 0; t < T; ++t) {
+        if (T > 1) pthread_join(th[t], NULL);
+        for (size_t k = 0; k < npx; ++k) accum[k] += jobs[t].accum[k];
+        free(jobs[t].accum);
+        J += jobs[t].J; L += jobs[t].locals; A += jobs[t].accepts; N += jobs[t].splats; ps += jobs[t].p_sum_large;
+    }
+    out4[0] = J; out4[1] = L; out4[2] = A; out4[3] = N;
     *p_sum_large += ps;
     free(jobs);
     free(th);

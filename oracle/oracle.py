@@ -83,6 +83,12 @@ def lib():
             L.orc_mh_advance.argtypes = [I, P, P, I, I, I, I, D, D, U64, U64, U64, U64, U64, U64, P, P, P, P,
                                          P, P, P, I]
             L.orc_mh_advance.restype = I
+            L.orc_eval_grad.argtypes = [P, I, I, U64, P, P, P]
+            L.orc_analytic_grad.argtypes = [P, I, U64, P, P, P]
+            L.orc_mala_init.argtypes = [I, P, P, I, I, D, U64, U64, U64, P]
+            L.orc_mala_advance.argtypes = [I, P, P, I, I, I, I, D, D, I, D, U64, U64, U64, U64, U64, U64, P, P, P,
+                                           P, P, P, P, I]
+            L.orc_mala_advance.restype = I
             L.orc_killing_rate_general.argtypes = [D, D, D]
             L.orc_killing_rate_general.restype = D
             L.orc_lstar_p_1d.argtypes = [P, I, P, D, I, P]
@@ -327,6 +333,76 @@ class MHChains:
     def image(self):
         """MH ergodic-average estimate: b_hat * accum / N."""
         return self.b_hat() * self.accum[:, :, :3] / max(self.splats, 1)
+
+
+def eval_grad(target, x, depth=None):
+    """F [n, 3] and dF/dx [n, 3, D] of a scene integrand (forward mode) or of
+    an analytic target (closed form)."""
+    x = np.ascontiguousarray(x, np.float64)
+    n, D = x.shape
+    dep = int(depth) if depth is not None else (D - 2) // 2
+    F = np.zeros((n, 3))
+    dF = np.zeros((n, 3, D))
+    if isinstance(target, Scene):
+        lib().orc_eval_grad(target.h, D, dep, n, _ptr(x), _ptr(F), _ptr(dF))
+    else:
+        lib().orc_analytic_grad(target.h, D, n, _ptr(x), _ptr(F), _ptr(dF))
+    return F, dF
+
+
+class MALAChains:
+    """Chains with Langevin (MALA) local moves on a scene target: method
+    "restore" (MALA Restore: Jump Restore, k = c~ u / p) or "mh" (the MALA
+    baseline: large steps with probability l, MALA small steps)."""
+
+    def __init__(self, target, D, width, height, sigma=0.01, c_tilde=1.0, method="restore", ell=0.3, burn_in=0,
+                 seed=0, chain_begin=0, n_chains=1, depth=None):
+        self.target, self.D = target, int(D)
+        self.kind, self.sh, self.ah = _target(target)
+        self.depth = int(depth) if depth is not None else (self.D - 2) // 2
+        self.W, self.H = int(width), int(height)
+        self.sigma, self.c_tilde, self.ell, self.burn_in = float(sigma), float(c_tilde), float(ell), int(burn_in)
+        self.method = {"restore": 0, "mh": 1, "mh_uncorrected": 2}[method]
+        self.seed, self.cb, self.n = int(seed), int(chain_begin), int(n_chains)
+        self.state = np.zeros((self.n, 2 * self.D + 5))
+        lib().orc_mala_init(self.kind, self.sh, self.ah, self.D, self.depth, self.sigma, self.seed, self.cb, self.n,
+                            _ptr(self.state))
+        self.accum = np.zeros((self.H, self.W, 4))
+        self.step = 0
+        self.J = self.locals = self.accepts = self.splats = 0
+        self.p_sum_large = 0.0
+
+    @property
+    def x(self):
+        return self.state[:, :self.D]
+
+    def advance(self, n_steps, trace=False, margins=False, n_threads=0):
+        out = np.zeros(4, np.uint64)
+        ps = np.zeros(1)
+        tr = None
+        if trace:
+            tr = dict(flags=np.zeros((self.n, n_steps), np.uint8), pix=np.zeros((self.n, n_steps), np.int32),
+                      margin=np.zeros((self.n, n_steps)) if margins else None)
+        rc = lib().orc_mala_advance(self.kind, self.sh, self.ah, self.D, self.depth, self.W, self.H, self.sigma,
+                                    self.c_tilde,
+                                    self.method, self.ell, self.burn_in, self.seed, self.cb, self.n, self.step,
+                                    n_steps, _ptr(self.state), _ptr(self.accum), _ptr(out), _ptr(ps),
+                                    _ptr(tr["flags"]) if tr else None, _ptr(tr["pix"]) if tr else None,
+                                    _ptr(tr["margin"]) if tr and margins else None, int(n_threads))
+        if rc != 0:
+            raise ValueError("oracle: invalid dimension")
+        self.step += n_steps
+        self.J += int(out[0])
+        self.locals += int(out[1])
+        self.accepts += int(out[2])
+        self.splats += int(out[3])
+        self.p_sum_large += float(ps[0])
+        return tr
+
+    def image(self):
+        if self.method == 0:
+            return self.accum[:, :, :3] / max(self.J, 1)
+        return (self.p_sum_large / max(self.J, 1)) * self.accum[:, :, :3] / max(self.splats, 1)
 
 
 def killing_rate_general(p, lstar_p, kappa_mustar_p):

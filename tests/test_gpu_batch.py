@@ -266,9 +266,8 @@ def test_flow_attached_after_the_batch_was_built(J):
     J.set_flow(mk[0][2], fr, 0.6)
     J.set_flow(mk[0][3], fc, 0.6)
     b.advance_graph(3)             # the old graph had no flow launches
-    for _, _, r, _ in mk:
-        if r.stats()["steps_per_chain"] < mk[0][3].stats()["steps_per_chain"]:
-            r.advance(mk[0][3].stats()["steps_per_chain"] - r.stats()["steps_per_chain"])
+    for _, _, r, c in mk:          # each reference catches up with its batched twin
+        r.advance(c.stats()["steps_per_chain"] - r.stats()["steps_per_chain"])
     for _, _, r, c in mk:
         _compare(r, c)
 

@@ -230,13 +230,25 @@ def test_spheres_relmse_and_per_pixel_vs_converged_reference(J, spheres_referenc
     img = imgs.mean(0)
     e = relmse(img, ref)
     assert e <= 1e-3, e
-    se = imgs.std(0, ddof=1) / np.sqrt(len(imgs))
-    ok = se > 0
-    t = (img - ref)[ok] / se[ok]
-    z = np.sign(t) * stats.norm.isf(stats.t.sf(np.abs(t), len(imgs) - 1))
-    bad = np.abs(z) > 4
-    msg = dict(frac=float(np.mean(bad)), worst=np.sort(np.abs(z))[-8:].tolist(),
-               positive=float(np.mean(z[bad] > 0)) if bad.any() else None,
-               rel_dev=np.sort(np.abs((img - ref)[ok][bad]) / np.maximum(ref[ok][bad], 1e-30))[-8:].tolist())
+    # Per-pixel 4 sigma where the batch means are in the central-limit regime: at
+    # least 24 of the 32 batches saw light in the pixel-channel.  Pixels lit
+    # only by rare paths (glossy reflections of the 0.05-wide light) have batch
+    # values that are mostly exactly 0 with a rare large one; there the batch
+    # standard error underestimates and a z-score means nothing, so they are
+    # checked in 8x8 tiles below (and by the relMSE above).
+    def zscores(a, r):
+        se = a.std(0, ddof=1) / np.sqrt(len(a))
+        ok = se > 0
+        t = (a.mean(0) - r)[ok] / se[ok]
+        return np.sign(t) * stats.norm.isf(stats.t.sf(np.abs(t), len(a) - 1)), ok
+    z, ok = zscores(imgs, ref)
+    dense = (np.count_nonzero(imgs, axis=0) >= 24)[ok]
+    assert dense.mean() > 0.8, dense.mean()
+    zd = z[dense]
+    bad = np.abs(zd) > 4
+    msg = dict(frac=float(np.mean(bad)), worst=np.sort(np.abs(zd))[-8:].tolist())
     assert np.mean(bad) <= 1e-3, msg
-    assert 0.7 < np.mean(z ** 2) < 1.5, np.mean(z ** 2)
+    assert 0.7 < np.mean(zd ** 2) < 1.5, np.mean(zd ** 2)
+    tiles = imgs.reshape(len(imgs), 16, 8, 16, 8, 3).mean(axis=(2, 4))
+    zt, _ = zscores(tiles, ref.reshape(16, 8, 16, 8, 3).mean(axis=(1, 3)))
+    assert np.abs(zt).max() < 4.5, np.sort(np.abs(zt))[-5:]
