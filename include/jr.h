@@ -78,6 +78,18 @@ typedef enum {
  * -), a large step if U_s < l; blocks 1.. give the D uniforms (large) or
  * Gaussian pairs (small).  Not with JR_FLAG_RAO_BLACKWELL, flows or drains. */
 #define JR_FLAG_MH 2u
+/* Langevin local dynamics (MALA; the paper's "MALA Restore" and, with
+ * JR_FLAG_MH, its "MALA" baseline, Section 9): the local move (or the MH small
+ * step) proposes y = (x + m(x) + sigma N) mod 1 with the drift
+ * m(x) = clamp(sigma^2 / 2 grad log p(x), -2 sigma, 2 sigma) per coordinate and
+ * accepts with min(1, p(y) q(x|y) / (p(x) q(y|x))), q(b|a) = prod_d
+ * phi_sigma(b_d - a_d - m_d(a)) on the signed torus difference.  grad log p is
+ * the forward-mode derivative of the path contribution (it flows through the
+ * directions and the modified Phong weights; Lambertian and dielectric weights
+ * are constant).  MALA is pi-invariant, so MALA Restore keeps k = c~ u / p.
+ * Runs in the megakernel only (jr_advance picks it; 128 threads per block); not
+ * with JR_FLAG_RAO_BLACKWELL, flows, drains, batches or jr_advance_static. */
+#define JR_FLAG_MALA 4u
 
 /* status-word bits (jr_stats.status_word) */
 #define JR_STATUS_NONFINITE 1u  /* F(x) was NaN/Inf for some state: it was treated as 0 */
@@ -297,6 +309,13 @@ jr_status jr_eval_states(const jr_scene* scene, const jr_params* params, const f
  * accum / total samples.  Asynchronous. */
 jr_status jr_render_pt(const jr_scene* scene, const jr_params* params, uint64_t sample_begin, uint64_t n_samples,
                        double* accum_dev, void* stream);
+
+/* F and its gradient for given states (the gradient of JR_FLAG_MALA's drift):
+ * x_dev [D][n] (device, SoA) in; F_dev [3][n] and dF_dev [3][D][n] (dF_dev[(c
+ * D + d) n + i] = dF_c / dx_d of state i) out, either may be NULL.  Uses
+ * params->max_depth only.  Asynchronous. */
+jr_status jr_eval_grad(const jr_scene* scene, const jr_params* params, const float* x_dev, uint64_t n, float* F_dev,
+                       float* dF_dev, void* stream);
 
 /* Measured FP32 throughput of the current device, the denominator of the
  * path kernels' ALU roofline (the method has no part in it): a kernel of 8

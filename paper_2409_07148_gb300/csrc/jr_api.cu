@@ -102,6 +102,7 @@ struct jr_chains {
         cudaFree(view.acc64);
         cudaFree(view.counters);
         cudaFree(view.status);
+        cudaFree(view.drift);
     }
 };
 
@@ -205,8 +206,10 @@ static jr_status check_params(const jr_params* p, const char* who) {
         return fail(JR_ERR_INVALID_ARG, std::string(who) + ": c_tilde must be finite and > 0");
     if (!(p->sigma > 0.f) || !std::isfinite(p->sigma))
         return fail(JR_ERR_INVALID_ARG, std::string(who) + ": sigma must be finite and > 0");
-    if (p->flags & ~(JR_FLAG_RAO_BLACKWELL | JR_FLAG_MH))
+    if (p->flags & ~(JR_FLAG_RAO_BLACKWELL | JR_FLAG_MH | JR_FLAG_MALA))
         return fail(JR_ERR_INVALID_ARG, std::string(who) + ": unknown flag");
+    if ((p->flags & JR_FLAG_MALA) && (p->flags & JR_FLAG_RAO_BLACKWELL))
+        return fail(JR_ERR_INVALID_ARG, std::string(who) + ": MALA chains splat the sampled holding time");
     if ((p->flags & JR_FLAG_MH) && (p->flags & JR_FLAG_RAO_BLACKWELL))
         return fail(JR_ERR_INVALID_ARG, std::string(who) + ": the MH baseline has no holding times to Rao-Blackwellise");
     if ((p->flags & JR_FLAG_MH) && !(p->large_step >= 0.f && p->large_step <= 1.f))
@@ -248,7 +251,9 @@ jr_status jr_chains_create(const jr_scene* scene, const jr_params* params, void*
         (e = cudaMemsetAsync(v.acc64, 0, sizeof(double4_32a) * npx, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(v.counters, 0, sizeof(unsigned long long) * kCounters, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(v.status, 0, sizeof(unsigned int), st)) != cudaSuccess ||
+        ((v.flags & JR_FLAG_MALA) && (e = dev_alloc(&v.drift, (size_t)v.dim * v.n)) != cudaSuccess) ||
         (e = launch_init(scene->view, v, st)) != cudaSuccess ||
+        ((v.flags & JR_FLAG_MALA) && (e = launch_mala_reeval(scene->view, v, st)) != cudaSuccess) ||
         (e = prepare_static_scratch()) != cudaSuccess) {  // jr_advance_static's array, see jr_wavefront.cu
         delete c;
         return cuda_fail(e, "jr_chains_create");
@@ -294,6 +299,13 @@ static jr_status advance_impl(jr_chains* c, uint32_t n_steps, uint8_t* f, float*
     cudaStream_t st = (cudaStream_t)stream;
     const bool plain = !f && !dt && !pix && !work;
     const bool has_flow = c->view.flow.D != 0;
+    if (c->view.flags & JR_FLAG_MALA) {  // Langevin moves: the megakernel only
+        if (work) return fail(JR_ERR_STATE, std::string(who) + ": the counted advance does not run MALA chains");
+        JR_CUDA(launch_step_mala(c->scene_view(), c->view, c->steps, n_steps, f, dt, pix, st), who);
+        JR_CUDA(launch_fold(c->view, st), who);
+        c->steps += n_steps;
+        return JR_OK;
+    }
     if (has_flow && !plain)
         return fail(JR_ERR_STATE, std::string(who) + ": traced and counted advances do not run with a flow attached");
     const bool wave = plain && (has_flow || c->exec == JR_EXEC_WAVEFRONT ||
@@ -325,7 +337,14 @@ jr_status jr_advance_timed(jr_chains* c, uint32_t n_steps, double ms_out[4], uin
     const bool wave = c->view.flow.D != 0 || c->exec == JR_EXEC_WAVEFRONT ||
                       (c->exec == JR_EXEC_AUTO && c->view.n >= kWavefrontMinChains);
     KernelTimer tm;
-    if (n_steps > 0) {
+    if (n_steps > 0 && (c->view.flags & JR_FLAG_MALA)) {
+        JR_CUDA(tm.mark(-1, st), "jr_advance_timed");
+        JR_CUDA(launch_step_mala(c->scene_view(), c->view, c->steps, n_steps, nullptr, nullptr, nullptr, st),
+                "jr_advance_timed");
+        JR_CUDA(tm.mark(KernelTimer::kStep, st), "jr_advance_timed");
+        JR_CUDA(launch_fold(c->view, st), "jr_advance_timed");
+        c->steps += n_steps;
+    } else if (n_steps > 0) {
         if (wave) {
             jr_status a = ensure_wavefront(c, st);
             if (a != JR_OK) return a;
@@ -354,6 +373,8 @@ jr_status jr_advance_static(jr_chains* chains, uint32_t n_steps, void* stream) {
                                             std::to_string(kStaticMaxChains) + " chains; use jr_advance");
     if (chains->view.flow.D != 0)
         return fail(JR_ERR_STATE, "jr_advance_static: chains with a flow attached advance with jr_advance");
+    if (chains->view.flags & JR_FLAG_MALA)
+        return fail(JR_ERR_STATE, "jr_advance_static: MALA chains advance with jr_advance (megakernel)");
     if (n_steps == 0) return JR_OK;
     cudaStream_t st = (cudaStream_t)stream;
     JR_CUDA(launch_wavefront_static(chains->scene_view(), chains->view, chains->steps, n_steps, st),
@@ -490,7 +511,9 @@ jr_status jr_set_state(jr_chains* c, const float* x_in, const float* fpu_in, voi
     cudaStream_t st = (cudaStream_t)stream;
     JR_CUDA(cudaMemcpyAsync(c->view.x, x_in, sizeof(float) * c->view.dim * c->view.n, cudaMemcpyHostToDevice, st),
             "jr_set_state");
-    if (fpu_in)
+    if (c->view.flags & JR_FLAG_MALA)  // F, p and the drift from the states themselves
+        JR_CUDA(launch_mala_reeval(c->scene_view(), c->view, st), "jr_set_state");
+    else if (fpu_in)
         JR_CUDA(cudaMemcpyAsync(c->view.fpu, fpu_in, sizeof(float) * 5 * c->view.n, cudaMemcpyHostToDevice, st),
                 "jr_set_state");
     else
@@ -524,6 +547,15 @@ jr_status jr_eval_states(const jr_scene* scene, const jr_params* params, const f
     JR_CUDA(launch_eval_states(scene->view, params->max_depth, params->c_tilde, x_dev, n, F_dev, p_dev, u_dev, k_dev,
                                hit_ids_dev, (cudaStream_t)stream),
             "jr_eval_states");
+    return JR_OK;
+}
+
+jr_status jr_eval_grad(const jr_scene* scene, const jr_params* params, const float* x_dev, uint64_t n, float* F_dev,
+                       float* dF_dev, void* stream) {
+    if (!scene || !params || (n > 0 && !x_dev)) return fail(JR_ERR_INVALID_ARG, "jr_eval_grad: null argument");
+    if (params->max_depth > JR_MAX_DEPTH) return fail(JR_ERR_INVALID_ARG, "jr_eval_grad: max_depth > 15");
+    JR_CUDA(launch_eval_grad(scene->view, params->max_depth, x_dev, n, F_dev, dF_dev, (cudaStream_t)stream),
+            "jr_eval_grad");
     return JR_OK;
 }
 
@@ -857,6 +889,10 @@ jr_status jr_batch_create(jr_chains* const* sets, uint32_t n_sets, void* stream,
                 delete b;
                 return fail(JR_ERR_INVALID_ARG, "jr_batch_create: a chain set appears twice");
             }
+        if (c->view.flags & JR_FLAG_MALA) {
+            delete b;
+            return fail(JR_ERR_STATE, "jr_batch_create: MALA chain sets advance on their own (megakernel)");
+        }
         h[k].s = c->scene_view();
         h[k].c = c->view;
         h[k].step = c->steps;
@@ -1333,6 +1369,8 @@ extern "C" {
 jr_status jr_complete_tours(jr_chains* c, uint32_t max_steps, uint64_t* remaining, void* stream) {
     if (!c) return fail(JR_ERR_INVALID_ARG, "jr_complete_tours: null chains");
     if (c->view.flags & JR_FLAG_MH) return fail(JR_ERR_STATE, "jr_complete_tours: an MH chain set has no tours");
+    if (c->view.flags & JR_FLAG_MALA)
+        return fail(JR_ERR_STATE, "jr_complete_tours: the drain runs in the wavefront, which has no MALA moves");
     cudaStream_t st = (cudaStream_t)stream;
     jr_status r = drain_impl(c, max_steps, remaining, st, "jr_complete_tours");
     if (r == JR_OK) r = restart_impl(c, st, "jr_complete_tours");
@@ -1342,8 +1380,8 @@ jr_status jr_complete_tours(jr_chains* c, uint32_t max_steps, uint64_t* remainin
 jr_status jr_chains_set_flow(jr_chains* c, const jr_flow* f, float beta, uint32_t max_drain_steps,
                              uint64_t* remaining, void* stream) {
     if (!c) return fail(JR_ERR_INVALID_ARG, "jr_chains_set_flow: null chains");
-    if (c->view.flags & JR_FLAG_MH)
-        return fail(JR_ERR_STATE, "jr_chains_set_flow: the MH baseline regenerates from the uniform mu only");
+    if (c->view.flags & (JR_FLAG_MH | JR_FLAG_MALA))
+        return fail(JR_ERR_STATE, "jr_chains_set_flow: MH and MALA chains regenerate from the uniform mu only");
     if (f && f->D != c->view.dim) return fail(JR_ERR_INVALID_ARG, "jr_chains_set_flow: flow and chain dimensions differ");
     if (f && !(beta >= 0.f && beta < 1.f))
         return fail(JR_ERR_INVALID_ARG, "jr_chains_set_flow: beta must be in [0, 1)");

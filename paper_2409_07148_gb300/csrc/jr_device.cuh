@@ -420,6 +420,239 @@ __device__ __forceinline__ float3 eval_path(const SceneView& s, unsigned mask, b
     return eval_path_w<false>(s, mask, want, depth, y, ys, ids, id_stride, status, w);
 }
 
+// ------------------------------------------------------------------ gradient
+// dF/dx for the Langevin local dynamics (MALA), forward mode.  F depends on x
+// continuously only through the directions (camera, scattered) and the modified
+// Phong weights (Lambertian and dielectric weights are constant; hit points only
+// select triangles), so a lane carries the Jacobians of the current direction,
+// of the throughput and of F, 3 x D each: column c is d/dx_c.  A Lambertian
+// bounce's direction depends only on its own two coordinates, so its Jacobian
+// restarts there.  At a change of hit triangle, bounce type or Fresnel choice the
+// result is the gradient of the piece the state lies in.
+struct Jac3 {
+    float c[3][kMaxDim];
+};
+
+// J_out = d(normalize(v))/dx from J_v (v unnormalised, n = v / |v|).
+__device__ inline void jac_normalize(float3 n, float inv_len, const Jac3& Jv, Jac3& Jn, int D) {
+    for (int k = 0; k < D; ++k) {
+        const float dvx = Jv.c[0][k], dvy = Jv.c[1][k], dvz = Jv.c[2][k];
+        const float proj = n.x * dvx + n.y * dvy + n.z * dvz;
+        Jn.c[0][k] = (dvx - n.x * proj) * inv_len;
+        Jn.c[1][k] = (dvy - n.y * proj) * inv_len;
+        Jn.c[2][k] = (dvz - n.z * proj) * inv_len;
+    }
+}
+
+// The scatter of `scatter` with the Jacobian of the outgoing direction (Jwi) and
+// the weight's log-derivative contribution: dw[ch][k] = d(weight_ch)/dx_k.
+// Jd: Jacobian of the incoming direction d; (u1, u2) are coordinates i1, i1+1.
+__device__ inline bool scatter_grad(const Material& m, float3 d, float3 ng, float u1, float u2, int i1, const Jac3& Jd,
+                                    float3& wi, float3& w, Jac3& Jwi, Jac3& Jw, int D) {
+    for (int q = 0; q < 3; ++q)
+        for (int k = 0; k < D; ++k) Jw.c[q][k] = 0.f;
+    if (m.type == JR_MAT_DIELECTRIC) {
+        float cos_i = -dot(d, ng);
+        float eta_i = 1.0f, eta_t = m.ior;
+        float3 nn = ng;
+        if (cos_i < 0.0f) {
+            cos_i = -cos_i;
+            eta_i = m.ior;
+            eta_t = 1.0f;
+            nn = ng * -1.0f;
+        }
+        float cos_t;
+        const float R = fresnel(cos_i, eta_i, eta_t, cos_t);
+        const float e = eta_i / eta_t;
+        const bool refl = u1 < R;
+        if (refl) wi = d + nn * (2.0f * cos_i);
+        else wi = d * e + nn * (e * cos_i - cos_t);
+        for (int k = 0; k < D; ++k) {
+            const float dci = -(nn.x * Jd.c[0][k] + nn.y * Jd.c[1][k] + nn.z * Jd.c[2][k]);
+            if (refl) {
+                Jwi.c[0][k] = Jd.c[0][k] + 2.0f * nn.x * dci;
+                Jwi.c[1][k] = Jd.c[1][k] + 2.0f * nn.y * dci;
+                Jwi.c[2][k] = Jd.c[2][k] + 2.0f * nn.z * dci;
+            } else {
+                const float dct = cos_t > 0.0f ? e * e * cos_i * dci / cos_t : 0.0f;
+                const float g = e * dci - dct;
+                Jwi.c[0][k] = e * Jd.c[0][k] + nn.x * g;
+                Jwi.c[1][k] = e * Jd.c[1][k] + nn.y * g;
+                Jwi.c[2][k] = e * Jd.c[2][k] + nn.z * g;
+            }
+        }
+        w = f3(1.0f, 1.0f, 1.0f);
+        return true;
+    }
+    const float3 ns = dot(d, ng) < 0.0f ? ng : ng * -1.0f;
+    float3 t, b;
+    for (int q = 0; q < 3; ++q)
+        for (int k = 0; k < D; ++k) Jwi.c[q][k] = 0.f;
+    if (m.type == JR_MAT_LAMBERT) {
+        const float r = sqrtf(u1);
+        float sn, cs;
+        sincospif(2.0f * u2, &sn, &cs);
+        const float lz = sqrtf(fmaxf(1.0f - u1, 0.0f));
+        onb(ns, t, b);
+        wi = t * (r * cs) + b * (r * sn) + ns * lz;
+        // d/du1 and d/du2 only
+        const float dr = r > 0.0f ? 0.5f / r : 0.0f, dlz = lz > 0.0f ? -0.5f / lz : 0.0f;
+        const float tw = 2.0f * 3.14159265358979f;
+        const float3 d1 = t * (dr * cs) + b * (dr * sn) + ns * dlz;
+        const float3 d2 = t * (-r * sn * tw) + b * (r * cs * tw);
+        Jwi.c[0][i1] = d1.x; Jwi.c[1][i1] = d1.y; Jwi.c[2][i1] = d1.z;
+        Jwi.c[0][i1 + 1] = d2.x; Jwi.c[1][i1 + 1] = d2.y; Jwi.c[2][i1 + 1] = d2.z;
+        w = m.albedo;
+        return m.albedo.x > 0.0f || m.albedo.y > 0.0f || m.albedo.z > 0.0f;
+    }
+    // modified Phong: r = d - 2 (d.ns) ns, basis around r, lobe angle from u1, azimuth from u2
+    const float3 r = d - ns * (2.0f * dot(d, ns));
+    const float cos_a = powf(1.0f - u1, m.phong_inv_n1);
+    const float sin_a = sqrtf(fmaxf(1.0f - cos_a * cos_a, 0.0f));
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    onb(r, t, b);
+    wi = t * (sin_a * cs) + b * (sin_a * sn) + r * cos_a;
+    const float cos_i = dot(wi, ns);
+    if (cos_i <= 0.0f) return false;
+    const float sign = copysignf(1.0f, r.z);
+    const float a = -1.0f / (sign + r.z);
+    const float bb = r.x * r.y * a;
+    // d cos_a / d u1 and d sin_a / d u1
+    const float dca = 1.0f - u1 > 0.0f ? -m.phong_inv_n1 * cos_a / (1.0f - u1) : 0.0f;
+    const float dsa = sin_a > 0.0f ? -cos_a * dca / sin_a : 0.0f;
+    const float tw = 2.0f * 3.14159265358979f;
+    for (int k = 0; k < D; ++k) {
+        const float ddx = Jd.c[0][k], ddy = Jd.c[1][k], ddz = Jd.c[2][k];
+        const float dn = ns.x * ddx + ns.y * ddy + ns.z * ddz;
+        const float drx = ddx - 2.0f * ns.x * dn, dry = ddy - 2.0f * ns.y * dn, drz = ddz - 2.0f * ns.z * dn;
+        const float da = a * a * drz;
+        const float dbb = r.y * a * drx + r.x * a * dry + r.x * r.y * da;
+        const float dtx = sign * (2.0f * r.x * a * drx + r.x * r.x * da), dty = sign * dbb, dtz = -sign * drx;
+        const float dbx = dbb, dby = 2.0f * r.y * a * dry + r.y * r.y * da, dbz = -dry;
+        float gx = dtx * (sin_a * cs) + dbx * (sin_a * sn) + drx * cos_a;
+        float gy = dty * (sin_a * cs) + dby * (sin_a * sn) + dry * cos_a;
+        float gz = dtz * (sin_a * cs) + dbz * (sin_a * sn) + drz * cos_a;
+        if (k == i1) {
+            gx += t.x * (dsa * cs) + b.x * (dsa * sn) + r.x * dca;
+            gy += t.y * (dsa * cs) + b.y * (dsa * sn) + r.y * dca;
+            gz += t.z * (dsa * cs) + b.z * (dsa * sn) + r.z * dca;
+        } else if (k == i1 + 1) {
+            gx += sin_a * tw * (-t.x * sn + b.x * cs);
+            gy += sin_a * tw * (-t.y * sn + b.y * cs);
+            gz += sin_a * tw * (-t.z * sn + b.z * cs);
+        }
+        Jwi.c[0][k] = gx;
+        Jwi.c[1][k] = gy;
+        Jwi.c[2][k] = gz;
+        const float dci = ns.x * gx + ns.y * gy + ns.z * gz;
+        Jw.c[0][k] = m.albedo.x * m.phong_scale * dci;
+        Jw.c[1][k] = m.albedo.y * m.phong_scale * dci;
+        Jw.c[2][k] = m.albedo.z * m.phong_scale * dci;
+    }
+    w = m.albedo * (m.phong_scale * cos_i);
+    return true;
+}
+
+// F(y) and dF/dy (dF->c[ch][k]) for one lane (no warp cooperation: the
+// megakernel's lanes call it together, each with its own state).
+template <bool kCount>
+__device__ inline float3 eval_path_grad(const SceneView& s, unsigned mask, bool want, int depth, const float* y,
+                                        uint32_t ys, Jac3& JF, unsigned& status, Work& work) {
+    const int D = 2 + 2 * depth;
+    Jac3 Jd, JT, Jtmp, Jw;
+    for (int q = 0; q < 3; ++q)
+        for (int k = 0; k < D; ++k) {
+            JF.c[q][k] = 0.f;
+            JT.c[q][k] = 0.f;
+            Jd.c[q][k] = 0.f;
+        }
+    float3 F = f3(0.f, 0.f, 0.f), T = f3(1.f, 1.f, 1.f);
+    float3 o = f3(0.f, 0.f, 1.f), d = f3(0.f, 0.f, 1.f);
+    if (want) {
+        const float3 cf = f3(s.cam[3], s.cam[4], s.cam[5]);
+        const float3 cr = f3(s.cam[6], s.cam[7], s.cam[8]);
+        const float3 cu = f3(s.cam[9], s.cam[10], s.cam[11]);
+        o = f3(s.cam[0], s.cam[1], s.cam[2]);
+        const float3 c = cf + cr * (2.0f * y[0] - 1.0f) + cu * (1.0f - 2.0f * y[ys]);
+        const float il = 1.0f / sqrtf(dot(c, c));
+        d = c * il;
+        Jtmp.c[0][0] = 2.0f * cr.x; Jtmp.c[1][0] = 2.0f * cr.y; Jtmp.c[2][0] = 2.0f * cr.z;
+        Jtmp.c[0][1] = -2.0f * cu.x; Jtmp.c[1][1] = -2.0f * cu.y; Jtmp.c[2][1] = -2.0f * cu.z;
+        for (int q = 0; q < 3; ++q)
+            for (int k = 2; k < D; ++k) Jtmp.c[q][k] = 0.f;
+        jac_normalize(d, il, Jtmp, Jd, D);
+    }
+    bool alive = want;
+    for (int v = 0; v <= depth; ++v) {
+        if (!__any_sync(mask, alive)) break;
+        float t;
+        const int k = closest_hit<kCount>(s, mask, alive, o, d, t, status, work);
+        if (!alive) continue;
+        if (k < 0) {
+            alive = false;
+            continue;
+        }
+        const TriRecord* tr = s.tris + k;
+        const float4 q1 = __ldg(&tr->e1_mat), q2 = __ldg(&tr->e2);
+        const Material m = s.mats[__float_as_int(q1.w)];
+        const float3 ng = normalize(cross(f3(q1.x, q1.y, q1.z), f3(q2.x, q2.y, q2.z)));
+        const float3 p = o + d * t;
+        if (m.emits && -dot(d, ng) > 0.0f) {
+            F = F + mul(T, m.emission);
+            for (int kk = 0; kk < D; ++kk) {
+                JF.c[0][kk] += JT.c[0][kk] * m.emission.x;
+                JF.c[1][kk] += JT.c[1][kk] * m.emission.y;
+                JF.c[2][kk] += JT.c[2][kk] * m.emission.z;
+            }
+        }
+        if (v == depth) {
+            alive = false;
+            continue;
+        }
+        float3 wi, w;
+        const float u1 = y[(2 + 2 * v) * ys], u2 = y[(3 + 2 * v) * ys];
+        if (!scatter_grad(m, d, ng, u1, u2, 2 + 2 * v, Jd, wi, w, Jtmp, Jw, D)) {
+            alive = false;
+            continue;
+        }
+        for (int kk = 0; kk < D; ++kk) {  // d(T w) = dT w + T dw
+            JT.c[0][kk] = JT.c[0][kk] * w.x + T.x * Jw.c[0][kk];
+            JT.c[1][kk] = JT.c[1][kk] * w.y + T.y * Jw.c[1][kk];
+            JT.c[2][kk] = JT.c[2][kk] * w.z + T.z * Jw.c[2][kk];
+        }
+        T = mul(T, w);
+        if (T.x == 0.0f && T.y == 0.0f && T.z == 0.0f) {
+            alive = false;
+            continue;
+        }
+        for (int q = 0; q < 3; ++q)
+            for (int kk = 0; kk < D; ++kk) Jd.c[q][kk] = Jtmp.c[q][kk];
+        const float3 off = dot(wi, ng) >= 0.0f ? ng : ng * -1.0f;
+        const float mx = fmaxf(fmaxf(fabsf(p.x), fabsf(p.y)), fabsf(p.z));
+        o = p + off * (1e-4f * (1.0f + mx));
+        d = wi;
+    }
+    if (want) {
+        if (!isfinite(F.x) || !isfinite(F.y) || !isfinite(F.z)) {
+            status |= JR_STATUS_NONFINITE;
+            F = f3(0.f, 0.f, 0.f);
+        }
+    }
+    return F;
+}
+
+// The MALA drift m = clamp(sigma^2 / 2 grad log p, -2 sigma, 2 sigma) per
+// coordinate from F and dF/dx (grad log p = grad lum(F) / lum(F); 0 where p = 0
+// or the gradient is not finite).
+__device__ inline float mala_drift(float3 F, const Jac3& JF, int k, float sigma) {
+    const float p = lum(F);
+    if (!(p > 0.0f)) return 0.0f;
+    const float g = (0.2126f * JF.c[0][k] + 0.7152f * JF.c[1][k] + 0.0722f * JF.c[2][k]) / p;
+    if (!isfinite(g)) return 0.0f;
+    return fminf(fmaxf(0.5f * sigma * sigma * g, -2.0f * sigma), 2.0f * sigma);
+}
+
 __device__ __forceinline__ void flush_status(unsigned status, unsigned int* word) {
     if (status) atomicOr(word, status);
 }

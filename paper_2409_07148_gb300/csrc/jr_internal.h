@@ -130,6 +130,7 @@ struct ChainView {
     float c_tilde, sigma;
     float large_step;              // MH: large-step probability l of the mixture proposal
     uint64_t burn_in;              // MH: iterations before the estimator starts
+    float* drift;                  // JR_FLAG_MALA: [D][n] the MALA drift m(x) of each state
     WaveView wf;
     FlowView flow;   // flow.D == 0: uniform regeneration (u = 1)
 };
@@ -225,6 +226,14 @@ cudaError_t launch_step(const SceneView& s, const ChainView& c, uint64_t step_be
                         uint8_t* tr_flags, float* tr_dt, int32_t* tr_pix, unsigned long long* work_out, int block,
                         cudaStream_t st);
 cudaError_t launch_fold(const ChainView& c, cudaStream_t st);
+// JR_FLAG_MALA chain sets: n steps with Langevin local moves (megakernel, one
+// chain per thread, 128 threads per block); F, p and drift of stored states;
+// F [3][n] and dF/dx [3][D][n] of given states x [D][n].
+cudaError_t launch_step_mala(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
+                             uint8_t* tr_flags, float* tr_dt, int32_t* tr_pix, cudaStream_t st);
+cudaError_t launch_mala_reeval(const SceneView& s, const ChainView& c, cudaStream_t st);
+cudaError_t launch_eval_grad(const SceneView& s, uint32_t depth, const float* x, uint64_t n, float* F, float* dF,
+                             cudaStream_t st);
 // Batched persistent launch + fold over n_sets chain sets (block = chains per
 // work item = threads per block, a multiple of 32 in [32, 256]).
 cudaError_t launch_batch(BatchEntry* entries, const BatchItem* items, uint32_t n_items, const uint64_t* px_off,

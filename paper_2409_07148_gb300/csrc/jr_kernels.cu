@@ -235,6 +235,233 @@ __global__ void __launch_bounds__(256, 4) step_kernel(SceneView s, ChainView c, 
     chain_steps<kTrace, kCount>(s, c, i, i < c.n, sh, step_begin, n_steps, tr_flags, tr_dt, tr_pix, work_out);
 }
 
+// ------------------------------------------------------------------ MALA
+// Langevin local dynamics (JR_FLAG_MALA), one chain per thread for the whole
+// launch.  The state's drift m(x) = clamp(sigma^2/2 grad log p(x), -2 sigma,
+// 2 sigma) lives beside it (shared memory during the launch, c.drift between
+// launches).  A MALA move proposes y = (x + m(x) + sigma N) mod 1 and accepts
+// with min(1, p(y) q(x|y) / (p(x) q(y|x))), q(b|a) = prod_d phi_sigma(b_d - a_d
+// - m_d(a)) on the signed torus difference.  With JR_FLAG_MH the chain is the
+// MALA baseline (large steps from mu with probability l, MALA small steps);
+// otherwise MALA Restore (Alg. 2, local move = the MALA step, k = c~ u / p).
+__device__ __forceinline__ float torus_delta(float to, float from) {
+    const float d = to - from;
+    return d - floorf(d + 0.5f);
+}
+
+// log q(b | a) up to the constant, from a's drift ma (all [D] with stride B).
+__device__ __forceinline__ float mala_log_q(const float* b, const float* a, const float* ma, int D, uint32_t B,
+                                            float sigma) {
+    float s = 0.f;
+    for (int d = 0; d < D; ++d) {
+        const float e = torus_delta(b[d * B], a[d * B]) - ma[d * B];
+        s += e * e;
+    }
+    return -s / (2.0f * sigma * sigma);
+}
+
+template <bool kTrace>
+__device__ __forceinline__ void chain_steps_mala(const SceneView& s, const ChainView& c, uint64_t i, bool active,
+                                                 float* sh, uint64_t step_begin, uint32_t n_steps, uint8_t* tr_flags,
+                                                 float* tr_dt, int32_t* tr_pix) {
+    const uint32_t B = blockDim.x, tid = threadIdx.x;
+    const unsigned mask = __ballot_sync(0xffffffffu, active);
+    const int D = (int)c.dim;
+    float* x0 = sh + tid;                            // [4][D][B]: x, y, m(x), m(y)
+    float* x1 = sh + (size_t)D * B + tid;
+    float* m0 = sh + (size_t)2 * D * B + tid;
+    float* m1 = sh + (size_t)3 * D * B + tid;
+    const bool mh = (c.flags & JR_FLAG_MH) != 0;
+    uint32_t nJ = 0, nL = 0, nA = 0;
+    unsigned status = 0;
+    double psum = 0.0;
+    Work work;
+    Jac3 JF;
+    if (active) {
+        for (int d = 0; d < D; ++d) {
+            x0[d * B] = c.x[d * c.n + i];
+            m0[d * B] = c.drift[d * c.n + i];
+        }
+    }
+    float Fr = 0.f, Fg = 0.f, Fb = 0.f, p = 0.f, u = 1.f;
+    if (active) {
+        Fr = c.fpu[0 * c.n + i];
+        Fg = c.fpu[1 * c.n + i];
+        Fb = c.fpu[2 * c.n + i];
+        p = c.fpu[3 * c.n + i];
+        u = c.fpu[4 * c.n + i];
+    }
+    float *cur = x0, *cand = x1, *mc = m0, *my = m1;
+    const uint32_t chain = c.chain_offset + (uint32_t)i;
+    const float WH = (float)c.width * (float)c.height;
+    for (uint32_t st = 0; st < n_steps; ++st) {
+        const uint64_t step = step_begin + st;
+        const uint4 r0 = active ? draw(c.seed, kTagStep, 0, chain, step) : make_uint4(0, 0, 0, 0);
+        const float Ua = u01(r0.z);
+        bool local = false;
+        float dt = 0.f;
+        if (mh) {
+            local = !(u01(r0.x) < c.large_step);
+            dt = step >= c.burn_in ? 1.0f : 0.0f;
+        } else {
+            const float E1 = -logf(1.0f - u01(r0.x));
+            const float E2 = -logf(1.0f - u01(r0.y));
+            const float t2 = p > 0.0f ? E2 * p / (c.c_tilde * u) : 0.0f;
+            local = E1 < t2;
+            dt = local ? E1 : t2;
+        }
+        int32_t pix = -1;
+        if (active && dt > 0.0f && p > 0.0f) {
+            uint32_t px = min((uint32_t)((double)cur[0] * (double)c.width), c.width - 1);
+            uint32_t py = min((uint32_t)((double)cur[B] * (double)c.height), c.height - 1);
+            pix = (int32_t)(py * c.width + px);
+            const float wgt = mh ? WH / p : c.c_tilde * dt * WH / p;
+            atomicAdd(c.fb + pix, make_float4(wgt * Fr, wgt * Fg, wgt * Fb, dt));
+        }
+        if (active) {
+            for (int b = 0; 4 * b < D; ++b) {
+                const uint4 r = draw(c.seed, kTagStep, (uint32_t)(b + 1), chain, step);
+                const int d0 = 4 * b;
+                if (local) {  // the MALA proposal: drift plus Gaussian pairs
+                    float sn, cs;
+                    float R = sqrtf(-2.0f * logf(1.0f - u01(r.x)));
+                    sincospif(2.0f * u01(r.y), &sn, &cs);
+                    cand[d0 * B] = wrap01(cur[d0 * B] + mc[d0 * B] + c.sigma * R * cs);
+                    cand[(d0 + 1) * B] = wrap01(cur[(d0 + 1) * B] + mc[(d0 + 1) * B] + c.sigma * R * sn);
+                    if (d0 + 2 < D) {
+                        R = sqrtf(-2.0f * logf(1.0f - u01(r.z)));
+                        sincospif(2.0f * u01(r.w), &sn, &cs);
+                        cand[(d0 + 2) * B] = wrap01(cur[(d0 + 2) * B] + mc[(d0 + 2) * B] + c.sigma * R * cs);
+                        cand[(d0 + 3) * B] = wrap01(cur[(d0 + 3) * B] + mc[(d0 + 3) * B] + c.sigma * R * sn);
+                    }
+                } else {
+                    cand[d0 * B] = u01(r.x);
+                    cand[(d0 + 1) * B] = u01(r.y);
+                    if (d0 + 2 < D) {
+                        cand[(d0 + 2) * B] = u01(r.z);
+                        cand[(d0 + 3) * B] = u01(r.w);
+                    }
+                }
+            }
+        }
+        const float3 Fy = eval_path_grad<false>(s, mask, active, (int)c.depth, cand, B, JF, status, work);
+        bool accept = false;
+        if (active) {
+            for (int d = 0; d < D; ++d) my[d * B] = mala_drift(Fy, JF, d, c.sigma);
+            const float py_ = lum(Fy);
+            if (local) {
+                if (!(p > 0.0f)) {
+                    accept = true;
+                } else if (py_ > 0.0f) {
+                    const float la = logf(py_) - logf(p) + mala_log_q(cur, cand, my, D, B, c.sigma) -
+                                     mala_log_q(cand, cur, mc, D, B, c.sigma);
+                    accept = Ua > 0.0f ? logf(Ua) < la : true;
+                }
+                nL++;
+                nA += accept;
+            } else if (mh) {  // a large step: uniform and symmetric
+                accept = !(p > 0.0f) || Ua * p < py_;
+                nJ++;
+                psum += (double)py_;
+                nA += accept;
+            } else {          // regeneration from mu
+                accept = true;
+                nJ++;
+            }
+            if (accept) {
+                float* t0 = cur;
+                cur = cand;
+                cand = t0;
+                float* t1 = mc;
+                mc = my;
+                my = t1;
+                Fr = Fy.x;
+                Fg = Fy.y;
+                Fb = Fy.z;
+                p = py_;
+                u = 1.0f;
+            }
+            if (kTrace) {
+                const uint64_t o = i * n_steps + st;
+                if (tr_flags) tr_flags[o] = (uint8_t)((local ? 0 : 1) | ((mh || local) && accept ? 2 : 0));
+                if (tr_dt) tr_dt[o] = pix >= 0 ? dt : 0.0f;
+                if (tr_pix) tr_pix[o] = pix;
+            }
+        }
+    }
+    if (active) {
+        for (int d = 0; d < D; ++d) {
+            c.x[d * c.n + i] = cur[d * B];
+            c.drift[d * c.n + i] = mc[d * B];
+        }
+        c.fpu[0 * c.n + i] = Fr;
+        c.fpu[1 * c.n + i] = Fg;
+        c.fpu[2 * c.n + i] = Fb;
+        c.fpu[3 * c.n + i] = p;
+        c.fpu[4 * c.n + i] = u;
+    }
+    nJ = __reduce_add_sync(0xffffffffu, nJ);
+    nL = __reduce_add_sync(0xffffffffu, nL);
+    nA = __reduce_add_sync(0xffffffffu, nA);
+    status = __reduce_or_sync(0xffffffffu, status);
+    if (mh) psum = warp_sum(psum);
+    if ((tid & 31) == 0) {
+        if (nJ) atomicAdd(c.counters + 0, (unsigned long long)nJ);
+        if (nL) atomicAdd(c.counters + 1, (unsigned long long)nL);
+        if (nA) atomicAdd(c.counters + 2, (unsigned long long)nA);
+        if (psum != 0.0) atomicAdd(reinterpret_cast<double*>(c.counters + kCounterPSum), psum);
+        flush_status(status, c.status);
+    }
+}
+
+template <bool kTrace>
+__global__ void __launch_bounds__(128) step_kernel_mala(SceneView s, ChainView c, uint64_t step_begin,
+                                                        uint32_t n_steps, uint8_t* tr_flags, float* tr_dt,
+                                                        int32_t* tr_pix) {
+    extern __shared__ float sh[];
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    chain_steps_mala<kTrace>(s, c, i, i < c.n, sh, step_begin, n_steps, tr_flags, tr_dt, tr_pix);
+}
+
+// F, p and the drift of the stored states (chain creation and jr_set_state).
+__global__ void __launch_bounds__(128) mala_reeval_kernel(SceneView s, ChainView c) {
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const unsigned mask = __ballot_sync(0xffffffffu, i < c.n);
+    if (i >= c.n) return;
+    unsigned status = 0;
+    Work w;
+    Jac3 JF;
+    const float3 F = eval_path_grad<false>(s, mask, true, (int)c.depth, c.x + i, (uint32_t)c.n, JF, status, w);
+    c.fpu[0 * c.n + i] = F.x;
+    c.fpu[1 * c.n + i] = F.y;
+    c.fpu[2 * c.n + i] = F.z;
+    c.fpu[3 * c.n + i] = lum(F);
+    c.fpu[4 * c.n + i] = 1.0f;
+    for (int d = 0; d < (int)c.dim; ++d) c.drift[d * c.n + i] = mala_drift(F, JF, d, c.sigma);
+    flush_status(status, c.status);
+}
+
+// F and dF/dx for given states: x [D][n], F [3][n], dF [3][D][n].
+__global__ void __launch_bounds__(128) eval_grad_kernel(SceneView s, uint32_t depth, const float* x, uint64_t n,
+                                                        float* F, float* dF) {
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const unsigned mask = __ballot_sync(0xffffffffu, i < n);
+    if (i >= n) return;
+    unsigned status = 0;
+    Work w;
+    Jac3 JF;
+    const float3 f = eval_path_grad<false>(s, mask, true, (int)depth, x + i, (uint32_t)n, JF, status, w);
+    const int D = 2 + 2 * (int)depth;
+    if (F) {
+        F[i] = f.x;
+        F[n + i] = f.y;
+        F[2 * n + i] = f.z;
+    }
+    if (dF)
+        for (int q = 0; q < 3; ++q)
+            for (int d = 0; d < D; ++d) dF[((uint64_t)q * D + d) * n + i] = JF.c[q][d];
+}
+
 // One persistent launch over a batch of chain sets (scenes with different
 // triangle counts, images and depths).  Blocks take work items -- a block of
 // chains of one set -- from a global cursor; the host orders the items by
@@ -482,6 +709,44 @@ cudaError_t launch_step(const SceneView& s, const ChainView& c, uint64_t step_be
         step_kernel<true, false><<<G, B, shm, st>>>(s, c, step_begin, n_steps, tr_flags, tr_dt, tr_pix, nullptr);
     else
         step_kernel<false, false><<<G, B, shm, st>>>(s, c, step_begin, n_steps, nullptr, nullptr, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_mala(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
+                             uint8_t* tr_flags, float* tr_dt, int32_t* tr_pix, cudaStream_t st) {
+    const unsigned B = 128;
+    const size_t shm = sizeof(float) * 4 * c.dim * B;  // <= 4 * 32 * 128 * 4 = 64 KB
+    static DeviceOnce once;
+    cudaError_t e0 = once.get(
+        [](int, long long*) {
+            const int lim = (int)(sizeof(float) * 4 * kMaxDim * 128);
+            cudaError_t e;
+            if ((e = cudaFuncSetAttribute(step_kernel_mala<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          lim)) != cudaSuccess ||
+                (e = cudaFuncSetAttribute(step_kernel_mala<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) !=
+                    cudaSuccess)
+                return e;
+            return cudaSuccess;
+        },
+        nullptr);
+    if (e0 != cudaSuccess) return e0;
+    const unsigned G = grid_for(c.n, B);
+    if (tr_flags || tr_dt || tr_pix)
+        step_kernel_mala<true><<<G, B, shm, st>>>(s, c, step_begin, n_steps, tr_flags, tr_dt, tr_pix);
+    else
+        step_kernel_mala<false><<<G, B, shm, st>>>(s, c, step_begin, n_steps, nullptr, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mala_reeval(const SceneView& s, const ChainView& c, cudaStream_t st) {
+    mala_reeval_kernel<<<grid_for(c.n, 128), 128, 0, st>>>(s, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval_grad(const SceneView& s, uint32_t depth, const float* x, uint64_t n, float* F, float* dF,
+                             cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    eval_grad_kernel<<<grid_for(n, 128), 128, 0, st>>>(s, depth, x, n, F, dF);
     return cudaGetLastError();
 }
 

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libjr_gb300.so")
 JR_OK, JR_ERR_INVALID_ARG, JR_ERR_CUDA, JR_ERR_OOM, JR_ERR_WATCHDOG, JR_ERR_NUMERIC, JR_ERR_STATE = range(7)
 JR_FLAG_RAO_BLACKWELL = 1
 JR_FLAG_MH = 2
+JR_FLAG_MALA = 4
 JR_EXEC_AUTO, JR_EXEC_MEGAKERNEL, JR_EXEC_WAVEFRONT = 0, 1, 2
 JR_STATUS_NONFINITE, JR_STATUS_TRAVERSAL, JR_STATUS_STACK = 1, 2, 4
 JR_BATCH_WAVEFRONT = 0
@@ -88,6 +89,7 @@ _SIGS = {
     "jr_render_pt": [_P, ctypes.POINTER(Params), _U64, _U64, _P, _P],
     "jr_philox": [_U64, _U32, _U32, _U64, _U64, _U64, _P, _P],
     "jr_fp32_peak": [_P, _P, _P],
+    "jr_eval_grad": [_P, _P, _P, _U64, _P, _P, _P],
     "jr_chains_set_limits": [_P, _U32, _U32],
     "jr_debug_fail_alloc": [ctypes.c_int64],
     "jr_debug_flow_wait": [_P, ctypes.c_int],
@@ -493,6 +495,18 @@ def eval_states(scene: Scene, x, depth, c_tilde=1.0, hit_ids=False, stream=None)
     _check(lib().jr_eval_states(scene.h, ctypes.byref(prm), _dptr(x), int(n), _dptr(F), _dptr(p), _dptr(u),
                                 _dptr(k), _dptr(ids), _stream(stream)))
     return (F, p, u, k, ids) if hit_ids else (F, p, u, k)
+
+
+def eval_grad(scene: Scene, x, depth, stream=None):
+    """F [3, n] and dF/dx [3, D, n] (device tensors) for states x (CUDA float32 [D, n])."""
+    import torch
+    n = x.shape[1]
+    D = 2 + 2 * int(depth)
+    F = torch.empty((3, n), dtype=torch.float32, device=x.device)
+    dF = torch.empty((3, D, n), dtype=torch.float32, device=x.device)
+    p = make_params(1, 1, depth)
+    _check(lib().jr_eval_grad(scene.h, ctypes.byref(p), _dptr(x), int(n), _dptr(F), _dptr(dF), _stream(stream)))
+    return F, dF
 
 
 def render_pt(scene: Scene, width, height, depth, n_samples, seed=0, sample_begin=0, accum=None, stream=None):
