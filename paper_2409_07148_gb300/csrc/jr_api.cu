@@ -494,13 +494,24 @@ jr_status jr_get_stats(jr_chains* c, jr_stats* out, void* stream) {
 jr_status jr_get_state(jr_chains* c, float* x_out, float* fpu_out, void* stream) {
     if (!c) return fail(JR_ERR_INVALID_ARG, "jr_get_state: null chains");
     cudaStream_t st = (cudaStream_t)stream;
-    if (x_out)
-        JR_CUDA(cudaMemcpyAsync(x_out, c->view.x, sizeof(float) * c->view.dim * c->view.n, cudaMemcpyDeviceToHost, st),
+    const uint64_t n = c->view.n, D = c->view.dim;
+    std::vector<float> pairs;
+    if (x_out) {  // the device keeps coordinate pairs (xidx); the caller gets [D][n]
+        try {
+            pairs.resize((size_t)D * n);
+        } catch (const std::bad_alloc&) {
+            return fail(JR_ERR_OOM, "jr_get_state: host allocation failed");
+        }
+        JR_CUDA(cudaMemcpyAsync(pairs.data(), c->view.x, sizeof(float) * D * n, cudaMemcpyDeviceToHost, st),
                 "jr_get_state");
+    }
     if (fpu_out)
-        JR_CUDA(cudaMemcpyAsync(fpu_out, c->view.fpu, sizeof(float) * 5 * c->view.n, cudaMemcpyDeviceToHost, st),
+        JR_CUDA(cudaMemcpyAsync(fpu_out, c->view.fpu, sizeof(float) * 5 * n, cudaMemcpyDeviceToHost, st),
                 "jr_get_state");
     JR_CUDA(cudaStreamSynchronize(st), "jr_get_state");
+    if (x_out)
+        for (uint32_t d = 0; d < D; ++d)
+            for (uint64_t i = 0; i < n; ++i) x_out[d * n + i] = pairs[xidx(d, i, n)];
     return JR_OK;
 }
 
@@ -509,7 +520,16 @@ jr_status jr_set_state(jr_chains* c, const float* x_in, const float* fpu_in, voi
     for (uint64_t k = 0; k < (uint64_t)c->view.dim * c->view.n; ++k)
         if (!(x_in[k] >= 0.0f && x_in[k] < 1.0f)) return fail(JR_ERR_INVALID_ARG, "jr_set_state: x outside [0,1)");
     cudaStream_t st = (cudaStream_t)stream;
-    JR_CUDA(cudaMemcpyAsync(c->view.x, x_in, sizeof(float) * c->view.dim * c->view.n, cudaMemcpyHostToDevice, st),
+    const uint64_t n = c->view.n, D = c->view.dim;
+    std::vector<float> pairs;
+    try {
+        pairs.resize((size_t)D * n);
+    } catch (const std::bad_alloc&) {
+        return fail(JR_ERR_OOM, "jr_set_state: host allocation failed");
+    }
+    for (uint32_t d = 0; d < D; ++d)
+        for (uint64_t i = 0; i < n; ++i) pairs[xidx(d, i, n)] = x_in[d * n + i];
+    JR_CUDA(cudaMemcpyAsync(c->view.x, pairs.data(), sizeof(float) * D * n, cudaMemcpyHostToDevice, st),
             "jr_set_state");
     if (c->view.flags & JR_FLAG_MALA)  // F, p and the drift from the states themselves
         JR_CUDA(launch_mala_reeval(c->scene_view(), c->view, st), "jr_set_state");

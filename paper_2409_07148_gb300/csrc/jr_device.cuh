@@ -516,8 +516,7 @@ __device__ inline bool scatter_grad(const Material& m, float3 d, float3 ng, floa
     const float cos_i = dot(wi, ns);
     if (cos_i <= 0.0f) return false;
     const float sign = copysignf(1.0f, r.z);
-    const float a = -1.0f / (sign + r.z);
-    const float bb = r.x * r.y * a;
+    const float a = -1.0f / (sign + r.z);  // the basis's a; its bb term is differentiated in the loop
     // d cos_a / d u1 and d sin_a / d u1
     const float dca = 1.0f - u1 > 0.0f ? -m.phong_inv_n1 * cos_a / (1.0f - u1) : 0.0f;
     const float dsa = sin_a > 0.0f ? -cos_a * dca / sin_a : 0.0f;

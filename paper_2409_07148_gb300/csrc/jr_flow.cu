@@ -581,7 +581,7 @@ __global__ void pack_kernel(const float* master, __nv_bfloat16* wb, float* bias,
 __global__ void snapshot_kernel(ChainView c, float* x_out, float* w_out) {
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (i >= c.n) return;
-    for (uint32_t d = 0; d < c.dim; ++d) x_out[d * c.n + i] = c.x[d * c.n + i];
+    for (uint32_t d = 0; d < c.dim; ++d) x_out[d * c.n + i] = c.x[xidx(d, i, c.n)];
     const float p = c.fpu[3 * c.n + i], u = c.fpu[4 * c.n + i];
     w_out[i] = p > 0.f ? p / (p + c.c_tilde * u) : 0.f;
 }
@@ -603,7 +603,7 @@ __global__ void snapshot_append_kernel(ChainView c, float* x_ring, float* w_ring
     base = __shfl_sync(0xffffffffu, base, 0);
     if (!(w > 0.f)) return;
     const uint64_t slot = (base + __popc(keep & ((1u << lane) - 1u))) % cap;
-    for (uint32_t d = 0; d < c.dim; ++d) x_ring[d * cap + slot] = c.x[d * c.n + i];
+    for (uint32_t d = 0; d < c.dim; ++d) x_ring[d * cap + slot] = c.x[xidx(d, i, c.n)];
     w_ring[slot] = w;
 }
 

@@ -291,8 +291,9 @@ __device__ __forceinline__ void coupling(const unsigned char* wl, const uint8_t*
 }
 
 // Rows: chains idx[j] (or j when idx is null) for j < *count_dev (or n_rows).
-// A row lives in SoA buffer [D][n] bufA, or -- when par is given -- in bufA if
-// par[i] is 1 and bufB otherwise.  Density: u_out[i] = beta q + 1 - beta,
+// A row lives in buffer bufA, or -- when par is given -- in bufA if par[i] is
+// 1 and bufB otherwise; pairs = 1: the chain state's pair layout (xidx), else
+// SoA [D][n].  Density: u_out[i] = beta q + 1 - beta,
 // lq_out[i] = log q.  Sample: the row is replaced by T^{-1}(row), u_out and
 // lq_out as above, and start[i] (if given) = the new row's first four
 // coordinates.
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(kThreads) flow_infer_kernel(FlowView f, float*
                                                               const uint8_t* par, uint64_t n, const uint32_t* idx,
                                                               const unsigned int* count_dev, uint32_t n_rows,
                                                               float* u_out, float* lq_out, float4* start,
-                                                              unsigned int* status) {
+                                                              unsigned int* status, int pairs) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
     uint8_t* perm_s = smem + kOffPerm;
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(kThreads) flow_infer_kernel(FlowView f, float*
             for (int e = lane; e < 16 * D; e += 32) {
                 const int r = e / D, d = e % D;
                 const uint32_t i = rows[warp * 16 + r];
-                xw[r * xs + d] = i != kNoRow ? row_buf(i)[(uint64_t)d * n + i] : 0.5f;
+                xw[r * xs + d] = i != kNoRow ? row_buf(i)[pairs ? xidx(d, i, n) : (uint64_t)d * n + i] : 0.5f;
             }
             lqp = 0.f;
             __syncwarp();
@@ -375,7 +376,7 @@ __global__ void __launch_bounds__(kThreads) flow_infer_kernel(FlowView f, float*
                 for (int e = lane; e < 16 * D; e += 32) {
                     const int r = e / D, d = e % D;
                     const uint32_t i = rows[warp * 16 + r];
-                    if (i != kNoRow) row_buf(i)[(uint64_t)d * n + i] = xw[r * xs + d];
+                    if (i != kNoRow) row_buf(i)[pairs ? xidx(d, i, n) : (uint64_t)d * n + i] = xw[r * xs + d];
                 }
             if (lane < 16) {
                 const int r = lane;
@@ -444,7 +445,7 @@ cudaError_t launch_flow_pack_ws(const float* master, unsigned char* ws, uint32_t
 
 cudaError_t launch_flow(const FlowView& f, bool sample, float* bufA, float* bufB, const uint8_t* par, uint64_t n,
                         const uint32_t* idx, const unsigned int* count_dev, uint32_t n_rows, float* u_out,
-                        float* lq_out, float4* start, unsigned int* status, cudaStream_t st) {
+                        float* lq_out, float4* start, unsigned int* status, cudaStream_t st, bool pairs) {
     static DeviceOnce once;  // per device: the SM count, after opting in to the largest layout
     const size_t shm = infer_smem(f.D, f.AK);
     long long sms = 0;
@@ -473,10 +474,10 @@ cudaError_t launch_flow(const FlowView& f, bool sample, float* bufA, float* bufB
     if (g == 0) return cudaSuccess;
     if (sample)
         flow_infer_kernel<true><<<g, kThreads, shm, st>>>(f, bufA, bufB, par, n, idx, count_dev, n_rows, u_out,
-                                                          lq_out, start, status);
+                                                          lq_out, start, status, pairs ? 1 : 0);
     else
         flow_infer_kernel<false><<<g, kThreads, shm, st>>>(f, bufA, bufB, par, n, idx, count_dev, n_rows, u_out,
-                                                           lq_out, nullptr, status);
+                                                           lq_out, nullptr, status, pairs ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -94,7 +94,7 @@ struct FlowView {
 
 // Buffers of the wavefront execution mode (allocated on first use).
 struct WaveView {
-    float* y = nullptr;           // [D][n] second state buffer
+    float* y = nullptr;           // second state buffer, the pair layout of x (xidx)
     uint8_t* par = nullptr;       // [n] 1: the current state is in y, 0: in x
     float* ua = nullptr;          // [n] Ua of a local step, -1 for a regeneration step
     float4* fy = nullptr;         // [n] the candidate's (y0, y1, y2, y3) from the step launch until its path
@@ -112,8 +112,16 @@ constexpr int kQFlowDensity = 2 * (kMaxDepth + 2), kQFlowSample = kQFlowDensity 
 // ends the chain's tour and the chain; no new tours start).
 enum WaveMode { kModeStep = 0, kModeRestart = 1, kModeDrain = 2 };
 
+// The state buffers (x, and the wavefront's y) hold coordinate pairs: the pair
+// (x_{2k}, x_{2k+1}) of chain i is one float2 at pair index k n + i, so a path
+// vertex's two coordinates are one 8-byte load from one sector.  D is always
+// even (2 + 2 depth).  Coordinate d of chain i is float xidx(d, i, n).
+__host__ __device__ inline uint64_t xidx(uint32_t d, uint64_t i, uint64_t n) {
+    return ((((uint64_t)(d >> 1)) * n + i) << 1) | (uint64_t)(d & 1u);
+}
+
 struct ChainView {
-    float* x;        // [D][n] PSS coordinates
+    float* x;        // PSS coordinates, D x n floats as n float2 per coordinate pair (xidx)
     float* fpu;      // [5][n] F.r F.g F.b p u
     float4* fb;      // [H*W] RGB sum + dt, FP32 (folded into acc64 after each advance)
     double4_32a* acc64;  // [H*W]
@@ -275,9 +283,11 @@ cudaError_t prepare_static_scratch();
 // rows replaced by T^{-1}(buf), and start[i] (if not null) = the row's first
 // four coordinates (0 past D).  Rows are idx[j], j < *count_dev (device) or
 // n_rows.
+// pairs: the rows live in chain state buffers (the xidx pair layout), else in a
+// caller's SoA buffer [D][n].
 cudaError_t launch_flow(const FlowView& f, bool sample, float* bufA, float* bufB, const uint8_t* par, uint64_t n,
                         const uint32_t* idx, const unsigned int* count_dev, uint32_t n_rows, float* u_out,
-                        float* lq_out, float4* start, unsigned int* status, cudaStream_t st);
+                        float* lq_out, float4* start, unsigned int* status, cudaStream_t st, bool pairs = false);
 // FP32 master parameters [kFL][S] -> the inference layout (flow_ws_layer_bytes per layer).
 cudaError_t launch_flow_pack_ws(const float* master, unsigned char* ws, uint32_t AK, cudaStream_t st);
 // FP32 master parameters [kFL][S] -> padded bf16 weights and biases.

@@ -44,7 +44,8 @@ __global__ void init_kernel(SceneView s, ChainView c) {
     }
     unsigned status = 0;
     const float3 F = eval_path(s, mask, true, (int)c.depth, y, B, nullptr, 0, status);
-    for (int d = 0; d < D; ++d) c.x[d * c.n + i] = y[d * B];
+    float2* x2 = reinterpret_cast<float2*>(c.x);
+    for (int k = 0; 2 * k < D; ++k) x2[(uint64_t)k * c.n + i] = make_float2(y[2 * k * B], y[(2 * k + 1) * B]);
     c.fpu[0 * c.n + i] = F.x;
     c.fpu[1 * c.n + i] = F.y;
     c.fpu[2 * c.n + i] = F.z;
@@ -53,13 +54,25 @@ __global__ void init_kernel(SceneView s, ChainView c) {
     flush_status(status, c.status);
 }
 
+// Load chain i's coordinates (pair layout) into shared memory y[d * B].
+__device__ __forceinline__ void load_coords(const ChainView& c, uint64_t i, float* y, uint32_t B) {
+    const float2* x2 = reinterpret_cast<const float2*>(c.x);
+    for (int k = 0; 2 * k < (int)c.dim; ++k) {
+        const float2 v = x2[(uint64_t)k * c.n + i];
+        y[2 * k * B] = v.x;
+        y[(2 * k + 1) * B] = v.y;
+    }
+}
+
 // Re-evaluate F, p, u of the stored states (after jr_set_state).
 __global__ void reeval_kernel(SceneView s, ChainView c) {
+    extern __shared__ float sh[];
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     const unsigned mask = __ballot_sync(0xffffffffu, i < c.n);
     if (i >= c.n) return;
     unsigned status = 0;
-    const float3 F = eval_path(s, mask, true, (int)c.depth, c.x + i, (uint32_t)c.n, nullptr, 0, status);
+    load_coords(c, i, sh + threadIdx.x, blockDim.x);
+    const float3 F = eval_path(s, mask, true, (int)c.depth, sh + threadIdx.x, blockDim.x, nullptr, 0, status);
     c.fpu[0 * c.n + i] = F.x;
     c.fpu[1 * c.n + i] = F.y;
     c.fpu[2 * c.n + i] = F.z;
@@ -86,7 +99,7 @@ __device__ __forceinline__ void chain_steps(const SceneView& s, const ChainView&
     const bool mh = (c.flags & JR_FLAG_MH) != 0;
     double psum = 0.0;  // MH: sum of p over this chain's large-step proposals
     if (active) {
-        for (int d = 0; d < D; ++d) buf0[d * B] = c.x[d * c.n + i];
+        load_coords(c, i, buf0, B);
         float Fr = c.fpu[0 * c.n + i], Fg = c.fpu[1 * c.n + i], Fb = c.fpu[2 * c.n + i];
         float p = c.fpu[3 * c.n + i], u = c.fpu[4 * c.n + i];
         float* cur = buf0;
@@ -190,7 +203,8 @@ __device__ __forceinline__ void chain_steps(const SceneView& s, const ChainView&
                 if (tr_pix) tr_pix[o] = pix;
             }
         }
-        for (int d = 0; d < D; ++d) c.x[d * c.n + i] = cur[d * B];
+        float2* x2 = reinterpret_cast<float2*>(c.x);
+        for (int k = 0; 2 * k < D; ++k) x2[(uint64_t)k * c.n + i] = make_float2(cur[2 * k * B], cur[(2 * k + 1) * B]);
         c.fpu[0 * c.n + i] = Fr;
         c.fpu[1 * c.n + i] = Fg;
         c.fpu[2 * c.n + i] = Fb;
@@ -278,10 +292,8 @@ __device__ __forceinline__ void chain_steps_mala(const SceneView& s, const Chain
     Work work;
     Jac3 JF;
     if (active) {
-        for (int d = 0; d < D; ++d) {
-            x0[d * B] = c.x[d * c.n + i];
-            m0[d * B] = c.drift[d * c.n + i];
-        }
+        load_coords(c, i, x0, B);
+        for (int d = 0; d < D; ++d) m0[d * B] = c.drift[d * c.n + i];
     }
     float Fr = 0.f, Fg = 0.f, Fb = 0.f, p = 0.f, u = 1.f;
     if (active) {
@@ -390,10 +402,9 @@ __device__ __forceinline__ void chain_steps_mala(const SceneView& s, const Chain
         }
     }
     if (active) {
-        for (int d = 0; d < D; ++d) {
-            c.x[d * c.n + i] = cur[d * B];
-            c.drift[d * c.n + i] = mc[d * B];
-        }
+        float2* x2 = reinterpret_cast<float2*>(c.x);
+        for (int k = 0; 2 * k < D; ++k) x2[(uint64_t)k * c.n + i] = make_float2(cur[2 * k * B], cur[(2 * k + 1) * B]);
+        for (int d = 0; d < D; ++d) c.drift[d * c.n + i] = mc[d * B];
         c.fpu[0 * c.n + i] = Fr;
         c.fpu[1 * c.n + i] = Fg;
         c.fpu[2 * c.n + i] = Fb;
@@ -425,13 +436,16 @@ __global__ void __launch_bounds__(128) step_kernel_mala(SceneView s, ChainView c
 
 // F, p and the drift of the stored states (chain creation and jr_set_state).
 __global__ void __launch_bounds__(128) mala_reeval_kernel(SceneView s, ChainView c) {
+    extern __shared__ float sh[];
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     const unsigned mask = __ballot_sync(0xffffffffu, i < c.n);
     if (i >= c.n) return;
     unsigned status = 0;
     Work w;
     Jac3 JF;
-    const float3 F = eval_path_grad<false>(s, mask, true, (int)c.depth, c.x + i, (uint32_t)c.n, JF, status, w);
+    load_coords(c, i, sh + threadIdx.x, blockDim.x);
+    const float3 F =
+        eval_path_grad<false>(s, mask, true, (int)c.depth, sh + threadIdx.x, blockDim.x, JF, status, w);
     c.fpu[0 * c.n + i] = F.x;
     c.fpu[1 * c.n + i] = F.y;
     c.fpu[2 * c.n + i] = F.z;
@@ -677,7 +691,7 @@ cudaError_t launch_init(const SceneView& s, const ChainView& c, cudaStream_t st)
 
 cudaError_t launch_reeval(const SceneView& s, const ChainView& c, cudaStream_t st) {
     const unsigned B = 128;
-    reeval_kernel<<<grid_for(c.n, B), B, 0, st>>>(s, c);
+    reeval_kernel<<<grid_for(c.n, B), B, sizeof(float) * c.dim * B, st>>>(s, c);
     return cudaGetLastError();
 }
 
@@ -739,7 +753,7 @@ cudaError_t launch_step_mala(const SceneView& s, const ChainView& c, uint64_t st
 }
 
 cudaError_t launch_mala_reeval(const SceneView& s, const ChainView& c, cudaStream_t st) {
-    mala_reeval_kernel<<<grid_for(c.n, 128), 128, 0, st>>>(s, c);
+    mala_reeval_kernel<<<grid_for(c.n, 128), 128, sizeof(float) * c.dim * 128, st>>>(s, c);
     return cudaGetLastError();
 }
 

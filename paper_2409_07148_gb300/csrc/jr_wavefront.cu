@@ -46,18 +46,28 @@ __device__ __forceinline__ void enqueue(bool live, uint32_t i, uint32_t* q, unsi
     if (live) q[base + __popc(m & ((1u << lane) - 1u))] = i;
 }
 
-__device__ __forceinline__ void count_and_flush(uint32_t nJ, uint32_t nL, uint32_t nA, unsigned status,
-                                                const ChainView& c) {
-    nJ = __reduce_add_sync(kFull, nJ);
-    nL = __reduce_add_sync(kFull, nL);
-    nA = __reduce_add_sync(kFull, nA);
-    status = __reduce_or_sync(kFull, status);
-    if ((threadIdx.x & 31) == 0) {
-        if (nJ) atomicAdd(c.counters + 0, (unsigned long long)nJ);
-        if (nL) atomicAdd(c.counters + 1, (unsigned long long)nL);
-        if (nA) atomicAdd(c.counters + 2, (unsigned long long)nA);
-        if (status) atomicOr(c.status, status);
+// The splat of a step, aggregated per warp: the lanes that splat into the same
+// pixel (pix >= 0) are grouped with __match_any_sync and one lane of each group
+// adds the group's sum with one vector atomic.  All 32 lanes call.
+__device__ __forceinline__ void splat_warp(float4* fb, int32_t pix, float4 v) {
+    const unsigned want = __ballot_sync(kFull, pix >= 0);
+    if (!want) return;
+    const unsigned peers = __match_any_sync(kFull, pix);
+    if (pix < 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    if (peers != (1u << lane)) {  // more than one lane in the pixel: the leader gathers
+        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (unsigned m = peers; m; m &= m - 1) {
+            const int j = __ffs(m) - 1;
+            sum.x += __shfl_sync(peers, v.x, j);
+            sum.y += __shfl_sync(peers, v.y, j);
+            sum.z += __shfl_sync(peers, v.z, j);
+            sum.w += __shfl_sync(peers, v.w, j);
+        }
+        v = sum;
     }
+    if (lane == leader) atomicAdd(fb + pix, v);
 }
 
 // count_and_flush for a whole block of the step kernel (4 warps): one atomic
@@ -131,9 +141,12 @@ __device__ __forceinline__ void count_and_flush_block(uint32_t nJ, uint32_t nL, 
 // (weight W H F / p, count 1) once the step index reaches the burn-in.  The
 // stored Ua carries the large-step flag in its sign bit (-Ua, -0 included), so
 // the acceptance sees the exact Ua.  ps collects p of the large-step proposals.
+// The splat is returned (splat_pix >= 0, splat_val), not added: the caller adds
+// it for the whole warp (splat_warp).
 __device__ __forceinline__ void step_chain(const ChainView& c, uint64_t i, uint64_t step, bool finish, bool begin,
                                            int mode, uint32_t& nJ, uint32_t& nL, uint32_t& nA, unsigned& status,
-                                           double& ps, bool& traced, bool& to_sample, bool& active) {
+                                           double& ps, bool& traced, bool& to_sample, bool& active,
+                                           int32_t& splat_pix, float4& splat_val) {
     const int D = (int)c.dim;
     const uint64_t n = c.n;
     const WaveView& w = c.wf;
@@ -148,12 +161,10 @@ __device__ __forceinline__ void step_chain(const ChainView& c, uint64_t i, uint6
     float p = c.fpu[3 * n + i], u = c.fpu[4 * n + i];
     const float ua = finish ? w.ua[i] : 0.0f;
     const float4 pf = finish ? w.fy[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float xs0 = 0.f, xs1 = 0.f, ys0 = 0.f, ys1 = 0.f;
-    if (begin) {
-        xs0 = c.x[i];
-        xs1 = c.x[n + i];
-        ys0 = w.y[i];
-        ys1 = w.y[n + i];
+    float2 xs = make_float2(0.f, 0.f), ys = make_float2(0.f, 0.f);
+    if (begin) {  // coordinate pair 0 (the film point) of both buffers
+        xs = reinterpret_cast<const float2*>(c.x)[i];
+        ys = reinterpret_cast<const float2*>(w.y)[i];
     }
     const bool was_done = drain && w.done[i];
     if (finish && !(drain && ua == -2.0f)) {
@@ -195,8 +206,8 @@ __device__ __forceinline__ void step_chain(const ChainView& c, uint64_t i, uint6
             c.fpu[4 * n + i] = u;
         }
     }
-    float* cur = par ? w.y : c.x;
-    float* cand = par ? c.x : w.y;
+    float2* cur = reinterpret_cast<float2*>(par ? w.y : c.x);  // pair layout: pair k of chain i at k n + i
+    float2* cand = reinterpret_cast<float2*>(par ? c.x : w.y);
     if (begin && was_done) {  // finished its tour during this drain
         w.ua[i] = -2.0f;
         traced = false;
@@ -221,13 +232,14 @@ __device__ __forceinline__ void step_chain(const ChainView& c, uint64_t i, uint6
         }
         const bool use_flow = has_flow && !local && u01(r0.w) < c.flow.beta;
         to_sample = use_flow;
-        const float x0 = par ? ys0 : xs0, x1 = par ? ys1 : xs1;  // = cur[i], cur[n + i]
+        const float x0 = par ? ys.x : xs.x, x1 = par ? ys.y : xs.y;  // = cur[i]
         if (dt > 0.0f && p > 0.0f) {
             uint32_t px = min((uint32_t)((double)x0 * (double)c.width), c.width - 1);
             uint32_t py = min((uint32_t)((double)x1 * (double)c.height), c.height - 1);
             const float WH = (float)c.width * (float)c.height;
             const float wgt = mh ? WH / p : c.c_tilde * dt * WH / p;
-            atomicAdd(c.fb + py * c.width + px, make_float4(wgt * Fr, wgt * Fg, wgt * Fb, dt));
+            splat_pix = (int32_t)(py * c.width + px);
+            splat_val = make_float4(wgt * Fr, wgt * Fg, wgt * Fb, dt);
         }
         w.ua[i] = mh ? (local ? Ua : -Ua) : local ? Ua : use_flow ? -3.0f : -1.0f;
         if (drain && !local) {  // the tour ends here; no new tour in a drain
@@ -240,20 +252,22 @@ __device__ __forceinline__ void step_chain(const ChainView& c, uint64_t i, uint6
         active = drain && local;
         for (int b = 0; traced && 4 * b < D; ++b) {
             const uint4 r = draw(c.seed, tag, (uint32_t)(b + 1), chain, step);
-            const uint64_t o0 = (uint64_t)(4 * b) * n + i;
+            const uint64_t q0 = (uint64_t)(2 * b) * n + i;  // pairs 2b and 2b + 1: coordinates 4b .. 4b + 3
             float v0, v1, v2 = 0.f, v3 = 0.f;
             const bool two = 4 * b + 2 < D;
             if (local) {
                 float sn, cs;
                 float R = sqrtf(-2.0f * logf(1.0f - u01(r.x)));
                 sincospif(2.0f * u01(r.y), &sn, &cs);
-                v0 = wrap01((b == 0 ? x0 : cur[o0]) + c.sigma * R * cs);
-                v1 = wrap01((b == 0 ? x1 : cur[o0 + n]) + c.sigma * R * sn);
+                const float2 c0 = b == 0 ? make_float2(x0, x1) : cur[q0];
+                v0 = wrap01(c0.x + c.sigma * R * cs);
+                v1 = wrap01(c0.y + c.sigma * R * sn);
                 if (two) {
                     R = sqrtf(-2.0f * logf(1.0f - u01(r.z)));
                     sincospif(2.0f * u01(r.w), &sn, &cs);
-                    v2 = wrap01(cur[o0 + 2 * n] + c.sigma * R * cs);
-                    v3 = wrap01(cur[o0 + 3 * n] + c.sigma * R * sn);
+                    const float2 c1 = cur[q0 + n];
+                    v2 = wrap01(c1.x + c.sigma * R * cs);
+                    v3 = wrap01(c1.y + c.sigma * R * sn);
                 }
             } else {
                 v0 = u01(r.x);
@@ -261,12 +275,8 @@ __device__ __forceinline__ void step_chain(const ChainView& c, uint64_t i, uint6
                 v2 = u01(r.z);
                 v3 = u01(r.w);
             }
-            cand[o0] = v0;
-            cand[o0 + n] = v1;
-            if (two) {
-                cand[o0 + 2 * n] = v2;
-                cand[o0 + 3 * n] = v3;
-            }
+            cand[q0] = make_float2(v0, v1);
+            if (two) cand[q0 + n] = make_float2(v2, v3);
             if (b == 0) {  // the path's start record
                 float2* f = reinterpret_cast<float2*>(w.fy + i);
                 f[0] = make_float2(v0, v1);
@@ -274,13 +284,15 @@ __device__ __forceinline__ void step_chain(const ChainView& c, uint64_t i, uint6
             }
         }
     } else if (par) {
-        for (int dd = 0; dd < D; ++dd) c.x[(uint64_t)dd * n + i] = w.y[(uint64_t)dd * n + i];
+        float2* x2 = reinterpret_cast<float2*>(c.x);
+        const float2* y2 = reinterpret_cast<const float2*>(w.y);
+        for (int k = 0; 2 * k < D; ++k) x2[(uint64_t)k * n + i] = y2[(uint64_t)k * n + i];
         par = 0;
     }
     w.par[i] = par;
 }
 
-__global__ void __launch_bounds__(128, 12) wf_step_kernel(ChainView c, uint64_t step, int finish, int begin,
+__global__ void __launch_bounds__(128, 10) wf_step_kernel(ChainView c, uint64_t step, int finish, int begin,
                                                           int mode) {
     const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     const bool valid = i < c.n;
@@ -292,7 +304,11 @@ __global__ void __launch_bounds__(128, 12) wf_step_kernel(ChainView c, uint64_t 
     unsigned status = 0;
     double ps = 0.0;
     bool to_sample = false, traced = valid, active = false;
-    if (valid) step_chain(c, i, step, finish, begin, mode, nJ, nL, nA, status, ps, traced, to_sample, active);
+    int32_t spix = -1;
+    float4 sval = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid)
+        step_chain(c, i, step, finish, begin, mode, nJ, nL, nA, status, ps, traced, to_sample, active, spix, sval);
+    if (begin) splat_warp(c.fb, spix, sval);
     if (begin) {
         if (drain) enqueue(traced, (uint32_t)i, w.queue, w.qcount + 0);
         if (has_flow) enqueue(to_sample, (uint32_t)i, w.fq + n, w.qcount + kQFlowSample);
@@ -370,10 +386,10 @@ __global__ void __launch_bounds__(128) wf_path_kernel(SceneView s, ChainView c, 
                         ++v;
                         trav_begin(s, r, o, d);
                         state = kTraverse;
-                        if (v < depth) {
-                            const float* cand = cx ? c.x : w.y;
-                            u1 = cand[(uint64_t)(2 + 2 * v) * n + i];
-                            u2 = cand[(uint64_t)(3 + 2 * v) * n + i];
+                        if (v < depth) {  // vertex v's coordinate pair, one 8-byte load
+                            const float2 uv = reinterpret_cast<const float2*>(cx ? c.x : w.y)[(uint64_t)(1 + v) * n + i];
+                            u1 = uv.x;
+                            u2 = uv.y;
                         }
                     }
                 }
@@ -487,8 +503,12 @@ __global__ void __launch_bounds__(128) wf_batch_step_kernel(const BatchEntry* en
     unsigned status = 0;
     double ps = 0.0;
     bool traced = true, to_sample = false, active = false;
+    int32_t spix = -1;
+    float4 sval = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i < it.end)
-        step_chain(e.c, i, e.step + k, finish, begin, kModeStep, nJ, nL, nA, status, ps, traced, to_sample, active);
+        step_chain(e.c, i, e.step + k, finish, begin, kModeStep, nJ, nL, nA, status, ps, traced, to_sample, active,
+                   spix, sval);
+    if (begin) splat_warp(e.c.fb, spix, sval);
     // a set with a flow: its flow draws go to the set's sampling queue (a
     // block's chains are one set's, so the warp's enqueue has one queue)
     if (begin && e.c.flow.D != 0)
@@ -520,7 +540,7 @@ __global__ void __launch_bounds__(128, 7) wf_batch_path_kernel(SceneView m, cons
     bool failed = false, drained = false;
     float3 T = f3(1.f, 1.f, 1.f), F = f3(0.f, 0.f, 0.f);
     float u1 = 0.f, u2 = 0.f;       // the coordinates of vertex v
-    const float* cand = nullptr;     // the candidate's buffer ([D][nst])
+    const float* cand = nullptr;     // the candidate's buffer (pair layout, nst chains)
     while (true) {
         // shade the waiting lanes as a batch
         const unsigned waiting = __ballot_sync(kFull, state == kWaitShade);
@@ -537,9 +557,10 @@ __global__ void __launch_bounds__(128, 7) wf_batch_path_kernel(SceneView m, cons
                         ++v;
                         trav_begin_at(r, o, d, roots[set]);
                         state = kTraverse;
-                        if (v < depth) {
-                            u1 = cand[(uint64_t)(2 + 2 * v) * nst + i];
-                            u2 = cand[(uint64_t)(3 + 2 * v) * nst + i];
+                        if (v < depth) {  // vertex v's coordinate pair, one 8-byte load
+                            const float2 uv = reinterpret_cast<const float2*>(cand)[(uint64_t)(1 + v) * nst + i];
+                            u1 = uv.x;
+                            u2 = uv.y;
                         }
                     }
                 }
@@ -653,11 +674,11 @@ inline unsigned grid_for(uint64_t n, unsigned b) { return (unsigned)((n + b - 1)
 // the flow draws.  After it: u(y) of the rows the path kernel queued.
 cudaError_t launch_flow_draws(const ChainView& c, cudaStream_t st) {
     return launch_flow(c.flow, true, c.x, c.wf.y, c.wf.par, c.n, c.wf.fq + c.n, c.wf.qcount + kQFlowSample, 0,
-                       c.wf.uy, nullptr, c.wf.fy, c.status, st);
+                       c.wf.uy, nullptr, c.wf.fy, c.status, st, true);
 }
 cudaError_t launch_flow_densities(const ChainView& c, cudaStream_t st) {
     return launch_flow(c.flow, false, c.x, c.wf.y, c.wf.par, c.n, c.wf.fq, c.wf.qcount + kQFlowDensity, 0,
-                       c.wf.uy, nullptr, nullptr, c.status, st);
+                       c.wf.uy, nullptr, nullptr, c.status, st, true);
 }
 
 }  // namespace
