@@ -299,6 +299,51 @@ def time_to_target(args):
         ref = 0.5 * (halves[0] + halves[1])
         ref_noise = relmse(halves[0], halves[1]) / 4.0   # relMSE of the mean of two halves vs truth, roughly
 
+        def run_mala(mh):
+            """MALA Restore (mh=False) or the MALA baseline (mh=True, large steps
+            l = --mh-large-step, burn-in --mh-burn-in), sigma = --mala-sigma,
+            --mala-chains chains, in the MALA megakernel.  It has no drain, so a
+            MALA Restore checkpoint resolves with the chains' open tours."""
+            Cm = args.mala_chains or C
+            flags = jr.JR_FLAG_MALA | (jr.JR_FLAG_MH if mh else 0)
+            ch = jr.Chains(g, side, side, sc.depth, Cm, seed=8, sigma=args.mala_sigma, flags=flags,
+                           large_step=args.mh_large_step, burn_in=args.mh_burn_in if mh else 0, stream=stream)
+            sampler = ClockSampler(torch.cuda.current_device())
+            sampler.start()
+            clock, curve, e, done = 0.0, [], 0, 0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            while mh and done < args.mh_burn_in:
+                k = min(args.epoch_max, args.mh_burn_in - done)
+                ch.advance(k, stream=stream)
+                done += k
+            torch.cuda.synchronize()
+            clock = time.perf_counter() - t0
+            t_burn = clock
+            while clock < tmax:
+                n_ep = min(int(round(epoch * args.epoch_growth ** e)), args.epoch_max)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ch.advance(n_ep, stream=stream)
+                torch.cuda.synchronize()
+                clock += time.perf_counter() - t0
+                img = torch.zeros((side, side, 3), dtype=torch.float32, device="cuda")
+                ch.resolve(out=img, stream=stream)
+                stream.synchronize()
+                curve.append((clock, relmse(img.double(), ref)))
+                e += 1
+                if curve[-1][1] <= target:
+                    break
+            clocks = sampler.stop()
+            st = ch.stats(stream=stream, check=False)
+            hit = next((t for t, r in curve if r <= target), None)
+            return {"time_to_target_s": hit, "final_relmse": curve[-1][1] if curve else None, "chains": Cm,
+                    "sigma": args.mala_sigma, "burn_in_s": round(t_burn, 3) if mh else None,
+                    "curve": [[round(t, 3), r] for t, r in curve[:: max(1, len(curve) // 40)]],
+                    "regenerations_or_large_steps": st["regenerations"], "local_steps": st["local_steps"],
+                    "accepted": st["accepted"], "chain_steps": int(st["steps_per_chain"]) * Cm,
+                    "status_word": st["status_word"], "clocks": clocks}
+
         def run_mh():
             """The MH baseline (Section 8): l = --mh-large-step, burn-in --mh-burn-in
             (Section 9: 0.3 and 10^4), --mh-chains chains; the burn-in runs on
@@ -455,7 +500,9 @@ def time_to_target(args):
 
         plain = run(False) if "plain" in args.arms else None
         learned = run(True) if "learned" in args.arms else {}
-        mh = run_mh() if "mh" in args.arms else None
+        mh = run_mh() if "mh" in args.arms.split(",") else None
+        mala = run_mala(False) if "mala" in args.arms.split(",") else None
+        mala_mh = run_mala(True) if "mala_mh" in args.arms.split(",") else None
     line = {"metric": METRIC, "workload": wname, "unit": "s to relMSE 1e-2",
             "relmse_eps": 1e-2, "target": target, "time_limit_s": tmax, "chains": C, "c_tilde": args.c_tilde,
             "batched": ({"companions": len(companions),
@@ -464,7 +511,7 @@ def time_to_target(args):
             "epoch_steps": epoch,
             "epoch_growth": args.epoch_growth, "epoch_max": args.epoch_max,
             "reference": {"samples": args.ref_samples, "seconds": round(t_ref, 2), "noise_relmse_est": ref_noise},
-            "plain": plain, "mh": mh, "learned": {**learned, "beta": args.beta, "train_iters_per_epoch": args.train_iters,
+            "plain": plain, "mh": mh, "mala": mala, "mala_mh": mala_mh, "learned": {**learned, "beta": args.beta, "train_iters_per_epoch": args.train_iters,
                                         "train_iters_first": args.train_iters0, "warm_epochs": args.warm_epochs,
                                         "batch": args.batch, "snap_every": args.snap_every, "replay": args.replay,
                                         "lr": args.lr, "flow": "6 coupling layers, MLP 2x64, 16 bins, bf16/FP32"},
@@ -558,6 +605,8 @@ def main():
     ap.add_argument("--mh-large-step", type=float, default=0.3, help="MH arm: large-step probability l")
     ap.add_argument("--mh-burn-in", type=int, default=10_000, help="MH arm: iterations before the estimate starts")
     ap.add_argument("--mh-chains", type=int, default=0, help="MH arm: chains (0 = the Restore arms' count)")
+    ap.add_argument("--mala-chains", type=int, default=0, help="MALA arms: chains (0 = the Restore arms' count)")
+    ap.add_argument("--mala-sigma", type=float, default=0.01, help="MALA arms: sigma of the Langevin proposal")
     args = ap.parse_args()
     if args.workload == "batched64" and args.impl == "ours":
         run_batched(args)
