@@ -69,7 +69,11 @@ def test_gradient_matches_oracle(J, which):
     gid = J.eval_states(J.Scene(sc), torch.from_numpy(np.ascontiguousarray(x.T)).cuda(), sc.depth, hit_ids=True)[4]
     same = np.all(gid.cpu().numpy().T == io, axis=1)
     assert np.mean(same) > 0.99
-    assert np.count_nonzero(dFo[same]) > 0.1 * dFo[same].size
+    # diffuse bounces make F piecewise constant in x (cosine sampling cancels the
+    # BSDF's cosine), so only paths through a Phong surface carry a gradient: most
+    # entries on the glossy box, a few percent on the spheres scene (one glossy sphere)
+    floor = 0.1 if which == "glossy_box" else 0.01
+    assert np.count_nonzero(dFo[same]) > floor * dFo[same].size
     scale = np.abs(dFo[same]) + 1e-2 * np.abs(Fo[same])[:, :, None] + 1e-6
     err = np.abs(dFg[same] - dFo[same]) / scale
     assert np.mean(err > 1e-4) < 1e-3, np.sort(err.ravel())[-5:]
