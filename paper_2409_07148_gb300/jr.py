@@ -21,7 +21,7 @@ JR_FLAG_RAO_BLACKWELL = 1
 JR_FLAG_MH = 2
 JR_FLAG_MALA = 4
 JR_EXEC_AUTO, JR_EXEC_MEGAKERNEL, JR_EXEC_WAVEFRONT = 0, 1, 2
-JR_STATUS_NONFINITE, JR_STATUS_TRAVERSAL, JR_STATUS_STACK = 1, 2, 4
+JR_STATUS_NONFINITE, JR_STATUS_TRAVERSAL, JR_STATUS_STACK, JR_STATUS_FLOW_WAIT = 1, 2, 4, 8
 JR_BATCH_WAVEFRONT = 0
 MATERIAL_FLOATS = 12
 MAX_DEPTH = 15
