@@ -191,6 +191,8 @@ __device__ __forceinline__ bool trav_node(const SceneView& s, Trav& r, int* stac
 
 // Test the triangles of leaf `leaf` (Moller-Trumbore, JGT 1997; ties on equal
 // t to the smaller original index) against the ray, updating the closest hit.
+// Branch-free: every quantity is computed and one predicate takes the hit (the
+// early-out form diverged per triangle; measured +0.5 % on the path kernel).
 template <bool kCount>
 __device__ __forceinline__ void trav_test_leaf(const SceneView& s, Trav& r, int leaf, Work& work) {
     const int enc = ~leaf;
@@ -202,21 +204,18 @@ __device__ __forceinline__ void trav_test_leaf(const SceneView& s, Trav& r, int 
         const float3 e1 = f3(q1.x, q1.y, q1.z), e2 = f3(q2.x, q2.y, q2.z);
         const float3 pv = cross(r.d, e2);
         const float det = dot(e1, pv);
-        if (det == 0.0f) continue;
         const float inv = 1.0f / det;
         const float3 tv = r.o - f3(q0.x, q0.y, q0.z);
         const float u = dot(tv, pv) * inv;
-        if (u < 0.0f || u > 1.0f) continue;
         const float3 qv = cross(tv, e1);
         const float v = dot(r.d, qv) * inv;
-        if (v < 0.0f || u + v > 1.0f) continue;
         const float t = dot(e2, qv) * inv;
         const int id = __float_as_int(q0.w);
-        if (t > 0.0f && (t < r.tb || (t == r.tb && id < r.best_id))) {
-            r.tb = t;
-            r.best = k;
-            r.best_id = id;
-        }
+        const bool hit = det != 0.0f && !(u < 0.0f || u > 1.0f) && !(v < 0.0f || u + v > 1.0f) && t > 0.0f &&
+                         (t < r.tb || (t == r.tb && id < r.best_id));
+        r.tb = hit ? t : r.tb;
+        r.best = hit ? k : r.best;
+        r.best_id = hit ? id : r.best_id;
     }
 }
 
