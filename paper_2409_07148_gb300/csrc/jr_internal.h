@@ -74,7 +74,7 @@ constexpr int kFL = 6, kFH = 64, kFK = 16, kFAP = 16, kFS1 = 24, kFS2 = 72, kFMa
 constexpr float kFE = 1e-3f;  // bin-mass floor: Q = (1 - E) softmax + E / K
 
 // Inference layout of one flow layer (bytes, 16-byte multiples): W1 [64][16],
-// W2 [64][64], W3 [AK][64] bf16, then b1 [64], b2 [64], b3 [AK] FP32.  Row n of
+// W2 [64][64], W3 [AK][64] bf16, then b1 [64], b2 [64], log2(e) b3 [AK] FP32.  Row n of
 // a bf16 matrix is stored in 16-byte chunks; chunk c sits at position c ^ (n & 7)
 // (W2, W3) or c ^ ((n >> 2) & 1) (W1), so the 8 rows of an mma B fragment hit
 // 8 different bank groups.
