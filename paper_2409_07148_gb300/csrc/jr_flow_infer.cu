@@ -19,12 +19,17 @@
 //     shared tile, so that each lane owns one (row, coordinate) pair with all
 //     16 bins in registers: softmax, cumulative masses and bin search run
 //     sequentially in the lane, with no shuffles.
-//   * Weights stream through shared memory one layer at a time, double
-//     buffered: one elected thread copies a layer's block (bf16 weights in a
-//     bank-conflict-free XOR-swizzled layout, then the FP32 biases) with one
-//     cp.async.bulk into the buffer freed two layers earlier; an mbarrier
-//     counts the bytes in.  Every wait is bounded; a wait that runs out sets
-//     JR_STATUS_FLOW_WAIT and the kernel stops after its copies have landed.
+//   * Weights stream through shared memory one layer at a time, in one
+//     buffer: once every warp is done with a layer, one elected thread copies
+//     the next layer's block (bf16 weights in a bank-conflict-free
+//     XOR-swizzled layout, then the FP32 biases) with one cp.async.bulk; an
+//     mbarrier counts the bytes in.  One buffer (about 65 KB per CTA at D = 22)
+//     lets three CTAs share an SM, 24 warps to hide the softmax chains'
+//     latency, where two buffers allowed two CTAs; the other CTAs run while
+//     one waits for its copy (measured at D = 22 and 26: -5 to -8 % per row
+//     from 2^16 rows up, within +3 % below).  Every wait is bounded; a wait
+//     that runs out sets JR_STATUS_FLOW_WAIT and the kernel stops after its
+//     copy has landed.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -45,7 +50,8 @@ constexpr uint32_t kWaitIters = 1u << 26;
 
 // Shared-memory layout (bytes): two mbarriers, perm [kFL][D], row ids
 // [kTile], the rows' states [kTile][D + 1] FP32, per warp a logits tile
-// [16][kLgStride] FP32 (two coordinates' 32 logits per row), two layer buffers.
+// [16][kLgStride] FP32 (two coordinates' 32 logits per row), one layer buffer
+// (bar[0] counts its copies).
 constexpr int kLgStride = 36;  // conflict-free 16-byte row reads by quarter warps
 constexpr size_t kOffBar = 0, kOffPerm = 64, kOffRows = 256, kOffX = kOffRows + 4 * kTile;
 constexpr size_t kLgBytes = sizeof(float) * kWarps * 16 * kLgStride;
@@ -53,7 +59,7 @@ __host__ __device__ constexpr size_t round128(size_t b) { return (b + 127) & ~(s
 __host__ __device__ constexpr size_t x_bytes(uint32_t D) { return round128(sizeof(float) * kTile * (D + 1)); }
 __host__ __device__ constexpr size_t buf_bytes(uint32_t AK) { return round128(flow_ws_layer_bytes(AK)); }
 __host__ __device__ constexpr size_t infer_smem(uint32_t D, uint32_t AK) {
-    return round128(kOffX) + x_bytes(D) + round128(kLgBytes) + 2 * buf_bytes(AK);
+    return round128(kOffX) + x_bytes(D) + round128(kLgBytes) + buf_bytes(AK);
 }
 static_assert(kOffPerm + kFL * kMaxDim <= kOffRows, "perm table overlaps the row ids");
 
@@ -324,7 +330,6 @@ __global__ void __launch_bounds__(kThreads) flow_infer_kernel(FlowView f, float*
     const int D = (int)f.D, A = (int)f.A, AK = (int)f.AK, xs = D + 1;
     float* lgt = reinterpret_cast<float*>(smem + round128(kOffX) + x_bytes(f.D));
     unsigned char* wbuf0 = smem + round128(kOffX) + x_bytes(f.D) + round128(kLgBytes);
-    const size_t bb = buf_bytes(f.AK);
     const uint32_t lbytes = (uint32_t)flow_ws_layer_bytes(f.AK);
 
     const uint32_t count = count_dev ? *count_dev : n_rows;
@@ -337,16 +342,14 @@ __global__ void __launch_bounds__(kThreads) flow_infer_kernel(FlowView f, float*
 
     if (threadIdx.x == 0) {
         mbar_init(&bar[0]);
-        mbar_init(&bar[1]);
         mbar_fence_init();
     }
     for (int e = threadIdx.x; e < kFL * D; e += blockDim.x) perm_s[e] = f.perm[e];
     __syncthreads();
-    if (threadIdx.x == 0)
-        for (uint32_t st = 0; st < 2 && st < total; ++st) {
-            mbar_expect(&bar[st], lbytes + (st == 0 ? f.extra_tx : 0u));
-            bulk_load(wbuf0 + st * bb, f.ws + (size_t)layer_of(st) * lbytes, lbytes, &bar[st]);
-        }
+    if (threadIdx.x == 0 && total > 0) {  // the first layer's weights
+        mbar_expect(&bar[0], lbytes + f.extra_tx);
+        bulk_load(wbuf0, f.ws + (size_t)layer_of(0) * lbytes, lbytes, &bar[0]);
+    }
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* xw = xt + warp * 16 * xs;
@@ -372,16 +375,15 @@ __global__ void __launch_bounds__(kThreads) flow_infer_kernel(FlowView f, float*
             lqp = 0.f;
             __syncwarp();
         }
-        const int b = st & 1;
-        failed = !mbar_wait(&bar[b], (st >> 1) & 1);
+        failed = !mbar_wait(&bar[0], st & 1);  // layer application st: the barrier's phase st
         if (!failed) {
             const int l = layer_of(st);
-            coupling<kSample>(wbuf0 + b * bb, perm_s + l * D, A, AK, xw, xs, lg, lqp);
+            coupling<kSample>(wbuf0, perm_s + l * D, A, AK, xw, xs, lg, lqp);
         }
-        if (__syncthreads_or(failed)) break;  // every warp is done with buffer b
-        if (threadIdx.x == 0 && st + 2 < total) {
-            mbar_expect(&bar[b], lbytes);
-            bulk_load(wbuf0 + b * bb, f.ws + (size_t)layer_of(st + 2) * lbytes, lbytes, &bar[b]);
+        if (__syncthreads_or(failed)) break;  // every warp is done with the buffer
+        if (threadIdx.x == 0 && st + 1 < total) {
+            mbar_expect(&bar[0], lbytes);
+            bulk_load(wbuf0, f.ws + (size_t)layer_of(st + 1) * lbytes, lbytes, &bar[0]);
         }
         if (st % kFL == kFL - 1) {  // write the warp's rows
             const float lq = lqp + __shfl_xor_sync(0xffffffffu, lqp, 16);  // row lane & 15
@@ -407,10 +409,10 @@ __global__ void __launch_bounds__(kThreads) flow_infer_kernel(FlowView f, float*
         }
     }
     if (st < total && threadIdx.x == 0) {
-        // A wait ran out: flag it, then let the copies already issued land
+        // A wait ran out: flag it, then let the copy already issued land
         // (bounded) before the CTA's shared memory goes away.
         if (status) atomicOr(status, JR_STATUS_FLOW_WAIT);
-        for (uint32_t k = st; k < st + 2 && k < total; ++k) (void)mbar_wait(&bar[k & 1], (k >> 1) & 1);
+        (void)mbar_wait(&bar[0], st & 1);
     }
 }
 
