@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(128, 7) wf_batch_path_kernel(SceneView m, cons
                         trav_begin_at(r, o, d, roots[set]);
                         state = kTraverse;
                         if (v < depth) {  // vertex v's coordinate pair, one 8-byte load
-                            const float2 uv = reinterpret_cast<const float2*>(cand)[(uint64_t)(1 + v) * nst + i];
+                            const float2 uv = __ldcs(reinterpret_cast<const float2*>(cand) + (uint64_t)(1 + v) * nst + i);
                             u1 = uv.x;
                             u2 = uv.y;
                         }
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(128, 7) wf_batch_path_kernel(SceneView m, cons
                 }
                 if (!live) {
                     const ChainView& c = entries[set].c;
-                    c.wf.fy[i] = make_float4(F.x, F.y, F.z, 0.f);
+                    __stcs(c.wf.fy + i, make_float4(F.x, F.y, F.z, 0.f));
                     if (status) {
                         atomicOr(c.status, status);
                         status = 0;
@@ -616,8 +616,8 @@ __global__ void __launch_bounds__(128, 7) wf_batch_path_kernel(SceneView m, cons
                     set = lo;
                     i = j - (uint32_t)off_s[lo];
                     const BatchEntry& e = entries[set];
-                    const float4 y = e.c.wf.fy[i];
-                    cand = e.c.wf.par[i] ? e.c.x : e.c.wf.y;
+                    const float4 y = __ldcs(e.c.wf.fy + i);
+                    cand = __ldcs(e.c.wf.par + i) ? e.c.x : e.c.wf.y;
                     nst = (uint32_t)e.c.n;
                     depth = (int)e.c.depth;
                     u1 = y.z;
