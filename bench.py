@@ -555,7 +555,9 @@ def run_reference(args, sc, wl):
         rates.append(r)
     v = float(np.mean(rates))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": 1e3 * wl["chains"] * wl["chain_steps"] / v,
+            "ms_per_step_basis": "the sample's rate projected to one full step of the workload",
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{args.workload}_{sc.width}x{sc.height}_depth{sc.depth}",
                        "image": [sc.width, sc.height], "depth": sc.depth, "n_tris": sc.n_tris,
