@@ -44,8 +44,8 @@ FP32_LANES = 128   # FP32 lanes per SM on sm_103a (the nominal-peak cross-check 
 # 2^18-chain case, scaled by 4 to the 2^20-chain workload (the paths of a
 # launch grow with the chains).  It stands only while the kernel sources still
 # hash to the values it was taken on (27.085 MB read + 0.218 MB written).
-PATH_TRAFFIC = {"bytes_per_launch": 4 * (25.712e6 + 0.191e6),
-                "sources": {"jr_wavefront.cu": "8c87be517a9caba5", "jr_device.cuh": "fe26fff844d2d218"},
+PATH_TRAFFIC = {"bytes_per_launch": 4 * (25.717e6 + 0.195e6),
+                "sources": {"jr_wavefront.cu": "736fe2193d64844d", "jr_device.cuh": "fe26fff844d2d218"},
                 "summary": "profiles/path_kernel_cornell_spheres_512x512.md"}
 
 
