@@ -70,45 +70,50 @@ __device__ __forceinline__ void splat_warp(float4* fb, int32_t pix, float4 v) {
     if (lane == leader) atomicAdd(fb + pix, v);
 }
 
-// count_and_flush for a whole block of the step kernel (4 warps): one atomic
-// per block and counter instead of one per warp (the counters are three
-// addresses that every block of a launch updates).  All threads call.
-// With JR_FLAG_MH, ps (the sum of p over large-step proposals) is summed too.
-__device__ __forceinline__ void count_and_flush_block(uint32_t nJ, uint32_t nL, uint32_t nA, unsigned status,
-                                                      double ps, const ChainView& c) {
-    __shared__ unsigned red_s[4][4];
-    __shared__ double ps_s[4];
+// The step kernels' counters (J, local steps, acceptances, status, and with
+// JR_FLAG_MH the sum of p over large steps), flushed once per block: each warp
+// adds its counts into the block's shared totals, and the block's last warp to
+// arrive issues the global atomics, so no warp waits at a closing barrier for
+// the others (measured: the step kernel about 6 % faster than with one) and the
+// three counter addresses see one atomic per block.  The totals are zeroed
+// behind the block's first barrier.  All 32 lanes of every warp call.
+struct BlockCounts {
+    unsigned J, L, A, status, arrived;
+    double ps;
+};
+__device__ __forceinline__ void block_counts_init(BlockCounts& b) {
+    if (threadIdx.x == 0) {
+        b.J = b.L = b.A = b.status = b.arrived = 0;
+        b.ps = 0.0;
+    }
+    __syncthreads();
+}
+__device__ __forceinline__ void count_and_flush_last(BlockCounts& b, uint32_t nJ, uint32_t nL, uint32_t nA,
+                                                     unsigned status, double ps, const ChainView& c) {
     const bool mh = (c.flags & JR_FLAG_MH) != 0;
     nJ = __reduce_add_sync(kFull, nJ);
     nL = __reduce_add_sync(kFull, nL);
     nA = __reduce_add_sync(kFull, nA);
     status = __reduce_or_sync(kFull, status);
     if (mh) ps = warp_sum(ps);
-    const int wq = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
-        red_s[wq][0] = nJ;
-        red_s[wq][1] = nL;
-        red_s[wq][2] = nA;
-        red_s[wq][3] = status;
-        ps_s[wq] = ps;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long sJ = 0, sL = 0, sA = 0;
-        unsigned st = 0;
-        double sp = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-            sJ += red_s[q][0];
-            sL += red_s[q][1];
-            sA += red_s[q][2];
-            st |= red_s[q][3];
-            sp += ps_s[q];
+        if (nJ) atomicAdd(&b.J, nJ);
+        if (nL) atomicAdd(&b.L, nL);
+        if (nA) atomicAdd(&b.A, nA);
+        if (status) atomicOr(&b.status, status);
+        if (mh && ps != 0.0) atomicAdd(&b.ps, ps);
+        __threadfence_block();
+        if (atomicAdd(&b.arrived, 1u) == (blockDim.x >> 5) - 1) {
+            __threadfence_block();
+            const unsigned sJ = *(volatile unsigned*)&b.J, sL = *(volatile unsigned*)&b.L,
+                           sA = *(volatile unsigned*)&b.A, st = *(volatile unsigned*)&b.status;
+            const double sp = *(volatile double*)&b.ps;
+            if (sJ) atomicAdd(c.counters + 0, (unsigned long long)sJ);
+            if (sL) atomicAdd(c.counters + 1, (unsigned long long)sL);
+            if (sA) atomicAdd(c.counters + 2, (unsigned long long)sA);
+            if (st) atomicOr(c.status, st);
+            if (mh && sp != 0.0) atomicAdd(reinterpret_cast<double*>(c.counters + kCounterPSum), sp);
         }
-        if (sJ) atomicAdd(c.counters + 0, sJ);
-        if (sL) atomicAdd(c.counters + 1, sL);
-        if (sA) atomicAdd(c.counters + 2, sA);
-        if (st) atomicOr(c.status, st);
-        if (mh && sp != 0.0) atomicAdd(reinterpret_cast<double*>(c.counters + kCounterPSum), sp);
     }
 }
 
@@ -300,6 +305,8 @@ __global__ void __launch_bounds__(128, 10) wf_step_kernel(ChainView c, uint64_t 
     const WaveView& w = c.wf;
     const bool has_flow = c.flow.D != 0;
     const bool drain = mode == kModeDrain;
+    __shared__ BlockCounts bc;
+    block_counts_init(bc);
     uint32_t nJ = 0, nL = 0, nA = 0;
     unsigned status = 0;
     double ps = 0.0;
@@ -320,7 +327,7 @@ __global__ void __launch_bounds__(128, 10) wf_step_kernel(ChainView c, uint64_t 
             }
         }
     }
-    count_and_flush_block(nJ, nL, nA, status, ps, c);  // launched with 128 threads
+    count_and_flush_last(bc, nJ, nL, nA, status, ps, c);
 }
 
 // Whole paths of every queued chain in one persistent launch.  A lane keeps
@@ -503,6 +510,8 @@ __global__ void __launch_bounds__(128) wf_batch_step_kernel(const BatchEntry* en
     const BatchItem it = items[blockIdx.x];
     const BatchEntry& e = entries[it.set];
     const uint64_t i = it.begin + threadIdx.x;
+    __shared__ BlockCounts bc;
+    block_counts_init(bc);
     uint32_t nJ = 0, nL = 0, nA = 0;
     unsigned status = 0;
     double ps = 0.0;
@@ -517,7 +526,7 @@ __global__ void __launch_bounds__(128) wf_batch_step_kernel(const BatchEntry* en
     // block's chains are one set's, so the warp's enqueue has one queue)
     if (begin && e.c.flow.D != 0)
         enqueue(to_sample && i < it.end, (uint32_t)i, e.c.wf.fq + e.c.n, e.c.wf.qcount + kQFlowSample);
-    count_and_flush_block(nJ, nL, nA, status, ps, e.c);  // a block's chains are one set's
+    count_and_flush_last(bc, nJ, nL, nA, status, ps, e.c);  // a block's chains are one set's
 }
 
 // The path kernel over every set's candidates: item j of the launch is chain
