@@ -10,8 +10,10 @@ Two kinds of comparison:
   batches' degrees of freedom do not inflate the tails); the 4-sigma budget is
   0.1 % of pixel-channels (Bonferroni-style; ~0.006 % expected).
 
-The converged reference is plain path tracing on the GPU (2^32 samples),
-itself checked against the oracle's path tracer on identical samples.
+The converged references are plain path tracing on the GPU (2^32 to 2^35
+samples; for the Cornell box, the 40k-triangle Cornell + spheres scene and the
+glass slit caustic), each path tracer checked against the oracle's on
+identical samples.
 relMSE = mean over pixels and channels of (I - R)^2 / (R^2 + 1e-2).
 """
 import numpy as np
@@ -251,4 +253,92 @@ def test_spheres_relmse_and_per_pixel_vs_converged_reference(J, spheres_referenc
     assert 0.7 < np.mean(zd ** 2) < 1.5, np.mean(zd ** 2)
     tiles = imgs.reshape(len(imgs), 16, 8, 16, 8, 3).mean(axis=(2, 4))
     zt, _ = zscores(tiles, ref.reshape(16, 8, 16, 8, 3).mean(axis=(1, 3)))
+    assert np.abs(zt).max() < 4.5, np.sort(np.abs(zt))[-5:]
+
+
+@pytest.fixture(scope="module")
+def caustic_reference(J):
+    """Converged plain path tracing of the slit caustic (a glass sphere of 80k
+    triangles, IOR 1.5, lit only through a 0.02-wide slit; depth 10, D = 22) at
+    64^2: 16 independent chunks of 2^30 samples, so that a test can carry the
+    reference's own per-pixel error."""
+    import torch
+    sc = scenes.caustic_slit(width=64, height=64, depth=10)
+    g = J.Scene(sc)
+    chunks = []
+    n, chunk = 1 << 30, 1 << 28
+    for h in range(16):
+        acc = torch.zeros((sc.height, sc.width, 4), dtype=torch.float64, device="cuda")
+        for s0 in range(0, n, chunk):
+            J.render_pt(g, sc.width, sc.height, sc.depth, chunk, seed=700 + h, sample_begin=s0, accum=acc)
+        chunks.append((acc[..., :3] / n).cpu().numpy())
+    torch.cuda.synchronize()
+    return sc, np.array(chunks)
+
+
+def test_caustic_plain_path_tracer_matches_oracle_paired(J):
+    """The caustic's GPU path tracer (dielectric Fresnel choices, refraction
+    through the sphere) against the oracle's, with its own BVH, on identical
+    samples: pixel sums agree to FP32 rounding except for rare FP32-vs-FP64
+    topology flips."""
+    import torch
+    sc = scenes.caustic_slit(width=64, height=64, depth=10)
+    n = 1 << 21
+    acc = J.render_pt(J.Scene(sc), sc.width, sc.height, sc.depth, n, seed=9)
+    torch.cuda.synchronize()
+    g = (acc[..., :3] / n).cpu().numpy()
+    o, _ = O.render_pt(O.Scene(sc, bvh=True), sc.D, sc.width, sc.height, n, seed=9)
+    nz = o != 0
+    assert nz.sum() > 1000            # enough light reaches the film for the comparison to mean something
+    rel = np.abs(g - o)[nz] / o[nz]
+    assert np.mean(rel > 1e-4) < 1e-2, np.sort(rel)[-5:]
+    assert relmse(g, o) < 1e-5
+
+
+def test_caustic_relmse_and_per_pixel_vs_converged_reference(J, caustic_reference):
+    """Jump Restore on the slit caustic at 64^2, depth 10: 32 independent
+    batches of 2^16 chains x 1500 steps, each stopped with every tour completed,
+    against the 16 reference chunks.  The pooled image reaches relMSE <= 1e-3;
+    per pixel-channel, Welch's t between the batches and the chunks (so the
+    reference's own error is carried) stays within 4 sigma (0.1 % budget) where
+    both are in the central-limit regime (lit in at least 24 of 32 batches and
+    12 of 16 chunks); the rest, caustic pixels lit by rare paths, is checked in
+    8x8 tiles and by the relMSE."""
+    import torch
+    from scipy import stats
+    sc, chunks = caustic_reference
+    ref = chunks.mean(0)
+    g = J.Scene(sc)
+    imgs = []
+    for b in range(32):
+        c = J.Chains(g, sc.width, sc.height, sc.depth, 1 << 16, seed=41, chain_offset=(1 << 24) + b * (1 << 16))
+        c.advance(1500)
+        assert J.complete_tours(c) == 0
+        imgs.append(c.resolve())
+        assert c.stats()["status_word"] == 0
+    torch.cuda.synchronize()
+    imgs = np.array(imgs, np.float64)
+    e = relmse(imgs.mean(0), ref)
+    assert e <= 1e-3, e
+
+    def welch(a, b):
+        na, nb = len(a), len(b)
+        va, vb = a.var(0, ddof=1) / na, b.var(0, ddof=1) / nb
+        se2 = va + vb
+        ok = se2 > 0
+        t = (a.mean(0) - b.mean(0))[ok] / np.sqrt(se2[ok])
+        df = se2[ok] ** 2 / (va[ok] ** 2 / (na - 1) + vb[ok] ** 2 / (nb - 1))
+        p = 2 * stats.t.sf(np.abs(t), df)
+        return np.sign(t) * stats.norm.isf(np.maximum(p, 1e-300) / 2), ok
+
+    z, ok = welch(imgs, chunks)
+    dense = ((np.count_nonzero(imgs, axis=0) >= 24) & (np.count_nonzero(chunks, axis=0) >= 12))[ok]
+    assert dense.mean() > 0.5, dense.mean()
+    zd = z[dense]
+    msg = dict(frac=float(np.mean(np.abs(zd) > 4)), worst=np.sort(np.abs(zd))[-8:].tolist())
+    assert np.mean(np.abs(zd) > 4) <= 1e-3, msg
+    assert 0.7 < np.mean(zd ** 2) < 1.5, np.mean(zd ** 2)
+    tiles = imgs.reshape(32, 8, 8, 8, 8, 3).mean(axis=(2, 4))
+    rtiles = chunks.reshape(16, 8, 8, 8, 8, 3).mean(axis=(2, 4))
+    zt, _ = welch(tiles, rtiles)
     assert np.abs(zt).max() < 4.5, np.sort(np.abs(zt))[-5:]
