@@ -158,6 +158,15 @@ __device__ __forceinline__ void step_chain(const ChainView& c, uint64_t i, uint6
     const bool has_flow = c.flow.D != 0;
     const bool mh = (c.flags & JR_FLAG_MH) != 0;
     const bool restart = mode == kModeRestart, drain = mode == kModeDrain;
+    // A chain whose tour ended earlier in a drain has nothing to finish and
+    // nothing to begin: it leaves after one byte (late in a drain nearly every
+    // chain is such a chain, and the full loads below cost the drain's steps
+    // most of their time).  The closing launch (begin = 0) still visits it, to
+    // move its state back into x.
+    if (drain && begin && w.done[i]) {
+        traced = false;
+        return;
+    }
     // Every load the step needs is issued here, before any store: the film
     // point of the current state is read from both buffers, so that no
     // load waits for the parity byte.
