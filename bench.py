@@ -575,7 +575,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cornell_spheres")
     ap.add_argument("--block", type=int, default=0, help="step-kernel block size (0 = library default)")
-    ap.add_argument("--exec", default="auto", choices=["auto", "mega", "wave"], help="execution mode")
+    ap.add_argument("--exec", default="auto", choices=["auto", "mega", "wave", "warp"], help="execution mode")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-t2t", action="store_true", help="skip the time-to-relMSE object of the default line")
     ap.add_argument("--ref-budget", type=float, default=12.0)
@@ -696,6 +696,10 @@ def main():
         alu_peak = fma_tflops
         split_total = sum(v["ms"] for v in split.values())
         dom = max(split, key=lambda k: split[k]["ms"])
+        # the library's rule for the single-launch modes: one warp per chain when asked for, or
+        # (auto) below the wavefront's 2^16 chains for a scene of at most 128 triangles
+        warp = args.exec == "warp" or (args.exec == "auto" and C < (1 << 16) and sc.n_tris <= 128)
+        step_kernel_name = "step_kernel_warp" if warp else "step_kernel"
         if dom == "path":    # the traversal work runs in the path kernel
             achieved = flop / 1e12 / (split["path"]["ms"] / 1e3)
         else:                # one launch does everything (megakernel)
@@ -742,7 +746,7 @@ def main():
                    "c_tilde": 1.0, "sigma": 0.01, "regen": "uniform", "global_batch": ws * C, "seq_len": K,
                    "parallelism": f"chains sharded over {ws} GPU(s)", "l2": "flushed by a 512 MB write between timed launches",
                    "block": args.block or 128, "exec": args.exec},
-        "roofline": {"bound": "alu", "kernel": "wf_path_kernel" if dom == "path" else "step_kernel",
+        "roofline": {"bound": "alu", "kernel": "wf_path_kernel" if dom == "path" else step_kernel_name,
                      "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved / alu_peak,
                      "traffic": path_traffic(args.workload, C) if dom == "path" else None,

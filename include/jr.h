@@ -217,11 +217,24 @@ jr_status jr_set_block_size(jr_chains* chains, uint32_t block);
  *                       (better SIMD use for many chains with uneven path
  *                       lengths; its buffers, about (4 D + 38) bytes per
  *                       chain, are allocated by the first wavefront advance);
- *   JR_EXEC_AUTO        wavefront from 2^16 chains up, else the megakernel.
- * Both modes run the same per-chain arithmetic on the same Philox streams. */
+ *   JR_EXEC_WARP        one warp per chain for the whole launch: a lane holds
+ *                       one coordinate and draws its own random numbers, and a
+ *                       ray tests every triangle of the scene in parallel
+ *                       (triangle k in lane k mod 32) before a warp reduction
+ *                       picks the closest hit; for scenes of a few dozen
+ *                       triangles and few chains, where one thread per chain is
+ *                       bound by the latency of its serial steps; chain sets
+ *                       with a flow run in the wavefront instead;
+ *   JR_EXEC_AUTO        wavefront from 2^16 chains up; below that, one warp per
+ *                       chain for scenes of at most 128 triangles, else the
+ *                       megakernel.
+ * All modes run the same per-chain arithmetic on the same Philox streams and
+ * give the same closest hits (the least (t, original triangle index) with
+ * t > 0). */
 #define JR_EXEC_AUTO 0u
 #define JR_EXEC_MEGAKERNEL 1u
 #define JR_EXEC_WAVEFRONT 2u
+#define JR_EXEC_WARP 3u
 jr_status jr_set_execution(jr_chains* chains, uint32_t mode);
 
 /* jr_advance without any device allocation -- the paper has no counterpart;

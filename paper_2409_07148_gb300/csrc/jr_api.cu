@@ -176,6 +176,7 @@ jr_status jr_scene_create(const jr_scene_desc* desc, void* stream, jr_scene** ou
     s->view.mats = s->mats;
     s->view.root = bvh.root;
     s->view.n_nodes = (int)bvh.nodes.size();
+    s->view.n_tris = (uint32_t)bvh.tris.size();
     s->view.visit_budget = kNodeVisitBudget;
     s->view.stack_limit = kStackSize;
     std::memcpy(s->view.cam, desc->camera, sizeof(float) * 12);
@@ -292,6 +293,14 @@ static jr_status ensure_wavefront(jr_chains* c, cudaStream_t st) {
     return JR_OK;
 }
 
+// One warp per chain: asked for, or (auto) a small scene below the wavefront's
+// chain count.  Only for sets without a flow (the wavefront takes those).
+static bool warp_per_chain(const jr_chains* c) {
+    if (c->view.flow.D != 0) return false;
+    return c->exec == JR_EXEC_WARP ||
+           (c->exec == JR_EXEC_AUTO && c->view.n < kWavefrontMinChains && c->scene->view.n_tris <= kWarpChainMaxTris);
+}
+
 static jr_status advance_impl(jr_chains* c, uint32_t n_steps, uint8_t* f, float* dt, int32_t* pix,
                               unsigned long long* work, void* stream, const char* who) {
     if (!c) return fail(JR_ERR_INVALID_ARG, std::string(who) + ": null chains");
@@ -314,6 +323,8 @@ static jr_status advance_impl(jr_chains* c, uint32_t n_steps, uint8_t* f, float*
         jr_status a = ensure_wavefront(c, st);
         if (a != JR_OK) return a;
         JR_CUDA(launch_wavefront(c->scene_view(), c->view, c->steps, n_steps, st), who);
+    } else if (plain && warp_per_chain(c)) {
+        JR_CUDA(launch_step_warp(c->scene_view(), c->view, c->steps, n_steps, st), who);
     } else {
         JR_CUDA(launch_step(c->scene_view(), c->view, c->steps, n_steps, f, dt, pix, work, c->block, st), who);
     }
@@ -352,9 +363,12 @@ jr_status jr_advance_timed(jr_chains* c, uint32_t n_steps, double ms_out[4], uin
                     "jr_advance_timed");
         } else {
             JR_CUDA(tm.mark(-1, st), "jr_advance_timed");
-            JR_CUDA(launch_step(c->scene_view(), c->view, c->steps, n_steps, nullptr, nullptr, nullptr, nullptr,
-                                c->block, st),
-                    "jr_advance_timed");
+            if (warp_per_chain(c))
+                JR_CUDA(launch_step_warp(c->scene_view(), c->view, c->steps, n_steps, st), "jr_advance_timed");
+            else
+                JR_CUDA(launch_step(c->scene_view(), c->view, c->steps, n_steps, nullptr, nullptr, nullptr, nullptr,
+                                    c->block, st),
+                        "jr_advance_timed");
             JR_CUDA(tm.mark(KernelTimer::kStep, st), "jr_advance_timed");
         }
         JR_CUDA(launch_fold(c->view, st), "jr_advance_timed");
@@ -386,7 +400,7 @@ jr_status jr_advance_static(jr_chains* chains, uint32_t n_steps, void* stream) {
 
 jr_status jr_set_execution(jr_chains* chains, uint32_t mode) {
     if (!chains) return fail(JR_ERR_INVALID_ARG, "jr_set_execution: null chains");
-    if (mode > JR_EXEC_WAVEFRONT) return fail(JR_ERR_INVALID_ARG, "jr_set_execution: unknown mode");
+    if (mode > JR_EXEC_WARP) return fail(JR_ERR_INVALID_ARG, "jr_set_execution: unknown mode");
     chains->exec = mode;
     return JR_OK;
 }
@@ -847,6 +861,7 @@ jr_status prepare_wave(jr_batch* b, cudaStream_t st) {
     bw.merged.mats = b->m_mats;
     bw.merged.root = kNoChild;
     bw.merged.n_nodes = (int)nn;
+    bw.merged.n_tris = (uint32_t)nt;
     bw.merged.visit_budget = kNodeVisitBudget;
     bw.merged.stack_limit = kStackSize;
     bw.roots = b->roots;

@@ -62,6 +62,7 @@ struct SceneView {
     const Material* mats;
     int root;       // child ref of the root, or INT32_MIN when the scene is empty
     int n_nodes;
+    uint32_t n_tris;  // triangle records (leaf order)
     float cam[12];
     uint32_t visit_budget;  // node visits per ray before the watchdog stops it (kNodeVisitBudget)
     int stack_limit;        // traversal stack entries a ray may use (<= kStackSize)
@@ -230,6 +231,12 @@ bool build_bvh(const float* verts, uint32_t n_verts, const uint32_t* tris, uint3
 
 // jr_kernels.cu -- launch wrappers; all return the cudaGetLastError() of the launch.
 cudaError_t launch_init(const SceneView& s, const ChainView& c, cudaStream_t st);
+// One chain per warp (JR_EXEC_WARP): brute-force intersection over every
+// triangle, for small scenes; auto mode takes it for at most kWarpChainMaxTris
+// triangles below the wavefront's chain count.
+constexpr uint32_t kWarpChainMaxTris = 128;
+cudaError_t launch_step_warp(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
+                             cudaStream_t st);
 cudaError_t launch_step(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
                         uint8_t* tr_flags, float* tr_dt, int32_t* tr_pix, unsigned long long* work_out, int block,
                         cudaStream_t st);

@@ -249,6 +249,179 @@ __global__ void __launch_bounds__(256, 4) step_kernel(SceneView s, ChainView c, 
     chain_steps<kTrace, kCount>(s, c, i, i < c.n, sh, step_begin, n_steps, tr_flags, tr_dt, tr_pix, work_out);
 }
 
+// ------------------------------------------------------------------ one chain per warp
+// For scenes of at most kWarpChainMaxTris triangles with few chains (the
+// megakernel's case), one warp carries one chain: lane d holds coordinate d,
+// draws its own Philox block and Box-Muller pair, and a ray tests every
+// triangle, triangle k in lane k mod 32, before a butterfly reduction picks the
+// closest hit.  A step's latency then shrinks to a few triangle tests and one
+// shading per vertex, and a few hundred chains spread over as many SMs as
+// their warps fill.  The per-chain arithmetic is chain_steps': the same draws,
+// the same Box-Muller expressions and acceptance, the same camera_ray and
+// shade_vertex; the closest hit is the least (t, original index) over all
+// triangles with t > 0, which is what the BVH traversal returns too.
+
+// Closest hit of the ray (o, d) over all n triangle records, for the whole
+// warp (every lane calls with the same ray).  Returns the record index or -1.
+__device__ __forceinline__ int closest_hit_warp(const SceneView& s, float3 o, float3 d, float& t_out) {
+    const int lane = threadIdx.x & 31;
+    float tb = INFINITY;
+    int best = -1, bid = INT32_MAX;
+    for (uint32_t k = lane; k < s.n_tris; k += 32) {
+        const TriRecord* tr = s.tris + k;
+        const float4 q0 = __ldg(&tr->v0_id), q1 = __ldg(&tr->e1_mat), q2 = __ldg(&tr->e2);
+        const float3 e1 = f3(q1.x, q1.y, q1.z), e2 = f3(q2.x, q2.y, q2.z);
+        const float3 pv = cross(d, e2);
+        const float det = dot(e1, pv);
+        const float inv = 1.0f / det;
+        const float3 tv = o - f3(q0.x, q0.y, q0.z);
+        const float u = dot(tv, pv) * inv;
+        const float3 qv = cross(tv, e1);
+        const float v = dot(d, qv) * inv;
+        const float t = dot(e2, qv) * inv;
+        const int id = __float_as_int(q0.w);
+        const bool hit = det != 0.0f && !(u < 0.0f || u > 1.0f) && !(v < 0.0f || u + v > 1.0f) && t > 0.0f &&
+                         (t < tb || (t == tb && id < bid));
+        tb = hit ? t : tb;
+        best = hit ? (int)k : best;
+        bid = hit ? id : bid;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float t2 = __shfl_xor_sync(0xffffffffu, tb, off);
+        const int b2 = __shfl_xor_sync(0xffffffffu, best, off);
+        const int i2 = __shfl_xor_sync(0xffffffffu, bid, off);
+        if (t2 < tb || (t2 == tb && i2 < bid)) {
+            tb = t2;
+            best = b2;
+            bid = i2;
+        }
+    }
+    t_out = best >= 0 ? tb : INFINITY;
+    return best;
+}
+
+// The integrand F(y) for the warp's chain, y[d] in lane d (eval_path_w's steps).
+__device__ __forceinline__ float3 eval_path_warp(const SceneView& s, int depth, float yd, unsigned& status) {
+    float3 F = f3(0.f, 0.f, 0.f), T = f3(1.f, 1.f, 1.f);
+    float3 o, d;
+    camera_ray(s, __shfl_sync(0xffffffffu, yd, 0), __shfl_sync(0xffffffffu, yd, 1), o, d);
+    for (int v = 0; v <= depth; ++v) {
+        float t;
+        const int k = closest_hit_warp(s, o, d, t);
+        if (k < 0) break;
+        const float u1 = __shfl_sync(0xffffffffu, yd, (2 + 2 * v) & 31);
+        const float u2 = __shfl_sync(0xffffffffu, yd, (3 + 2 * v) & 31);
+        if (!shade_vertex(s, k, t, v, depth, v < depth ? u1 : 0.0f, v < depth ? u2 : 0.0f, o, d, T, F)) break;
+    }
+    return finite_or_zero(F, status);
+}
+
+constexpr int kWarpChainThreads = 128;  // four chains per block
+
+__global__ void __launch_bounds__(kWarpChainThreads) step_kernel_warp(SceneView s, ChainView c, uint64_t step_begin,
+                                                                      uint32_t n_steps) {
+    const uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    if (i >= c.n) return;  // a whole warp
+    const int lane = threadIdx.x & 31;
+    const int D = (int)c.dim;
+    const bool mine = lane < D;  // this lane holds coordinate `lane`
+    const uint32_t chain = c.chain_offset + (uint32_t)i;
+    const bool mh = (c.flags & JR_FLAG_MH) != 0, rb = (c.flags & JR_FLAG_RAO_BLACKWELL) != 0;
+    const float c_tilde = c.c_tilde, sigma = c.sigma;
+    const float WH = (float)c.width * (float)c.height;
+    uint32_t nJ = 0, nL = 0, nA = 0;
+    unsigned status = 0;
+    double psum = 0.0;
+    float xd = mine ? c.x[xidx((uint32_t)lane, i, c.n)] : 0.0f;
+    float Fr = c.fpu[0 * c.n + i], Fg = c.fpu[1 * c.n + i], Fb = c.fpu[2 * c.n + i];
+    float p = c.fpu[3 * c.n + i], u = c.fpu[4 * c.n + i];
+    for (uint32_t st = 0; st < n_steps; ++st) {
+        const uint64_t step = step_begin + st;
+        const uint4 r0 = draw(c.seed, kTagStep, 0, chain, step);
+        const float Ua = u01(r0.z);
+        bool local;
+        float dt;
+        if (mh) {
+            local = !(u01(r0.x) < c.large_step);
+            dt = step >= c.burn_in ? 1.0f : 0.0f;
+        } else {
+            const float E1 = -logf(1.0f - u01(r0.x));
+            const float E2 = -logf(1.0f - u01(r0.y));
+            const float t2 = p > 0.0f ? E2 * p / (c_tilde * u) : 0.0f;
+            local = E1 < t2;  // a tie goes to the killing branch
+            dt = local ? E1 : t2;
+            if (rb) dt = p > 0.0f ? p / (p + c_tilde * u) : 0.0f;
+        }
+        const float x0 = __shfl_sync(0xffffffffu, xd, 0), x1 = __shfl_sync(0xffffffffu, xd, 1);
+        if (lane == 0 && dt > 0.0f && p > 0.0f) {
+            uint32_t px = (uint32_t)((double)x0 * (double)c.width);
+            uint32_t py = (uint32_t)((double)x1 * (double)c.height);
+            px = min(px, c.width - 1);
+            py = min(py, c.height - 1);
+            const float wgt = mh ? WH / p : c_tilde * dt * WH / p;
+            atomicAdd(c.fb + (py * c.width + px), make_float4(wgt * Fr, wgt * Fg, wgt * Fb, dt));
+        }
+        // candidate coordinate `lane`: Philox block lane / 4 + 1; a local move's
+        // Box-Muller pair is (r.x, r.y) for the block's first two coordinates
+        // and (r.z, r.w) for the last two
+        float yd = 0.0f;
+        if (mine) {
+            const uint4 r = draw(c.seed, kTagStep, (uint32_t)(lane >> 2) + 1u, chain, step);
+            const bool second = (lane & 2) != 0;
+            if (local) {
+                float sn, cs;
+                const float R = sqrtf(-2.0f * logf(1.0f - u01(second ? r.z : r.x)));
+                sincospif(2.0f * u01(second ? r.w : r.y), &sn, &cs);
+                yd = wrap01(xd + sigma * R * ((lane & 1) ? sn : cs));
+            } else {
+                yd = u01(second ? ((lane & 1) ? r.w : r.z) : ((lane & 1) ? r.y : r.x));
+            }
+        }
+        const float3 Fy = eval_path_warp(s, (int)c.depth, yd, status);
+        const float py_ = lum(Fy);
+        bool accept;
+        if (mh) {
+            accept = !(p > 0.0f) || Ua * p < py_;
+            if (local) {
+                nL++;
+            } else {
+                nJ++;
+                psum += (double)py_;
+            }
+            nA += accept;
+        } else if (local) {
+            accept = Ua * p < py_;
+            nL++;
+            nA += accept;
+        } else {
+            accept = true;
+            nJ++;
+        }
+        if (accept) {
+            xd = yd;
+            Fr = Fy.x;
+            Fg = Fy.y;
+            Fb = Fy.z;
+            p = py_;
+            u = 1.0f;
+        }
+    }
+    if (mine) c.x[xidx((uint32_t)lane, i, c.n)] = xd;
+    if (lane == 0) {
+        c.fpu[0 * c.n + i] = Fr;
+        c.fpu[1 * c.n + i] = Fg;
+        c.fpu[2 * c.n + i] = Fb;
+        c.fpu[3 * c.n + i] = p;
+        c.fpu[4 * c.n + i] = u;
+        if (nJ) atomicAdd(c.counters + 0, (unsigned long long)nJ);
+        if (nL) atomicAdd(c.counters + 1, (unsigned long long)nL);
+        if (nA) atomicAdd(c.counters + 2, (unsigned long long)nA);
+        if (psum != 0.0) atomicAdd(reinterpret_cast<double*>(c.counters + kCounterPSum), psum);
+        flush_status(status, c.status);
+    }
+}
+
 // ------------------------------------------------------------------ MALA
 // Langevin local dynamics (JR_FLAG_MALA), one chain per thread for the whole
 // launch.  The state's drift m(x) = clamp(sigma^2/2 grad log p(x), -2 sigma,
@@ -692,6 +865,14 @@ cudaError_t launch_init(const SceneView& s, const ChainView& c, cudaStream_t st)
 cudaError_t launch_reeval(const SceneView& s, const ChainView& c, cudaStream_t st) {
     const unsigned B = 128;
     reeval_kernel<<<grid_for(c.n, B), B, sizeof(float) * c.dim * B, st>>>(s, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_warp(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
+                             cudaStream_t st) {
+    if (c.n == 0 || n_steps == 0) return cudaSuccess;
+    const uint64_t threads = 32 * c.n;
+    step_kernel_warp<<<grid_for(threads, kWarpChainThreads), kWarpChainThreads, 0, st>>>(s, c, step_begin, n_steps);
     return cudaGetLastError();
 }
 

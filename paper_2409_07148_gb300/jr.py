@@ -20,7 +20,7 @@ JR_OK, JR_ERR_INVALID_ARG, JR_ERR_CUDA, JR_ERR_OOM, JR_ERR_WATCHDOG, JR_ERR_NUME
 JR_FLAG_RAO_BLACKWELL = 1
 JR_FLAG_MH = 2
 JR_FLAG_MALA = 4
-JR_EXEC_AUTO, JR_EXEC_MEGAKERNEL, JR_EXEC_WAVEFRONT = 0, 1, 2
+JR_EXEC_AUTO, JR_EXEC_MEGAKERNEL, JR_EXEC_WAVEFRONT, JR_EXEC_WARP = 0, 1, 2, 3
 JR_STATUS_NONFINITE, JR_STATUS_TRAVERSAL, JR_STATUS_STACK, JR_STATUS_FLOW_WAIT = 1, 2, 4, 8
 JR_BATCH_WAVEFRONT = 0
 MATERIAL_FLOATS = 12
@@ -252,8 +252,8 @@ class Chains:
         _check(lib().jr_set_block_size(self.h, int(block)))
 
     def set_execution(self, mode):
-        """JR_EXEC_AUTO, JR_EXEC_MEGAKERNEL or JR_EXEC_WAVEFRONT (or 'auto'/'mega'/'wave')."""
-        m = {"auto": 0, "mega": 1, "megakernel": 1, "wave": 2, "wavefront": 2}.get(mode, mode)
+        """JR_EXEC_AUTO, _MEGAKERNEL, _WAVEFRONT or _WARP (or 'auto'/'mega'/'wave'/'warp')."""
+        m = {"auto": 0, "mega": 1, "megakernel": 1, "wave": 2, "wavefront": 2, "warp": 3}.get(mode, mode)
         _check(lib().jr_set_execution(self.h, int(m)))
 
     def resolve(self, out=None, stream=None):

@@ -276,6 +276,36 @@ def test_wavefront_equals_megakernel(J, torch_cuda, name, kw, n):
     assert np.allclose(aa.sum(axis=(0, 1)), ab.sum(axis=(0, 1)), rtol=1e-3)
 
 
+@pytest.mark.parametrize("name,kw,n,flags", [("cornell", {}, 257, 0), ("cornell", {}, 300, 1), ("cornell", {}, 256, 2),
+                                             ("glass_furnace", {}, 129, 0), ("furnace", dict(depth=0), 64, 0),
+                                             ("furnace", dict(depth=15), 96, 0), ("empty", {}, 33, 0)])
+def test_warp_per_chain_equals_megakernel(J, torch_cuda, name, kw, n, flags):
+    """One chain per warp (brute-force intersection, the auto mode's choice
+    for small scenes) against one chain per thread: the same draws, decisions
+    and closest hits on the same Philox streams, over advance boundaries, for
+    plain Restore, Rao-Blackwell and the MH baseline; D from 2 to 32 (the glass
+    furnace's 588 triangles are above the auto mode's bound, 19 per lane when the
+    warp mode is asked for)."""
+    sc = scenes.by_name(name, **kw)
+    g = J.Scene(sc)
+    out = []
+    for mode in ("mega", "warp", "auto"):
+        ch = J.Chains(g, sc.width, sc.height, sc.depth, n, seed=17, sigma=0.02, flags=flags, burn_in=4)
+        ch.set_execution(mode)
+        ch.advance(7)
+        ch.advance(6)
+        out.append((ch.get_state(), ch.stats(), ch.accumulator()))
+    (xa, fa), sa, aa = out[0]
+    for (xb, fb), sb, ab in out[1:]:
+        same = np.all(xa == xb, axis=0)
+        assert np.mean(same) >= 0.995, np.mean(same)
+        assert np.allclose(fa[:, same], fb[:, same], rtol=1e-6, atol=0)
+        for k in ("regenerations", "local_steps", "accepted"):
+            assert abs(sa[k] - sb[k]) <= max(2, int(2e-3 * n * 13)), (k, sa[k], sb[k])
+        assert sa["status_word"] == sb["status_word"] == 0
+        assert np.allclose(aa.sum(axis=(0, 1)), ab.sum(axis=(0, 1)), rtol=1e-3, atol=1e-9)
+
+
 def test_full_size_wavefront_step_sampled(J, torch_cuda):
     """The bench workload in the bench's launch configuration: the full
     40k-triangle scene (512^2, depth 8), 2^20 chains, wavefront execution.
