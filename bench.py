@@ -172,6 +172,27 @@ def cpu_oracle_config1():
     return 256 * 10_000 / dt, O.threads_default(), dt
 
 
+def gpu_config1(stream):
+    """The same whole 64x64 Cornell workload on this GPU (auto execution: one
+    chain per warp for this 24-triangle scene), after a warm-up set, timed with
+    CUDA events on its stream: chain steps/s and seconds."""
+    import torch
+    from paper_2409_07148_gb300 import jr, scenes
+    sc = scenes.cornell()
+    g = jr.Scene(sc, stream=stream)
+    warm = jr.Chains(g, sc.width, sc.height, sc.depth, 256, seed=1, stream=stream)
+    warm.advance(1000, stream=stream)
+    ch = jr.Chains(g, sc.width, sc.height, sc.depth, 256, seed=0, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    e0.record(stream)
+    ch.advance(10_000, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3
+    return 256 * 10_000 / dt, dt
+
+
 def run_batched(args):
     """The 64-scene batch: one persistent launch per advance, replayed from a
     CUDA graph, work-item size picked by the library's autotuner (outside the
@@ -727,6 +748,11 @@ def main():
     t2t = None
     if not args.no_t2t and ws == 1:
         t2t = default_time_to_relmse(args)
+    small = None
+    if ws == 1:
+        rg1, tg1 = gpu_config1(stream)
+        small = {"workload": "cornell_64x64_depth3: the whole 256 chains x 10^4 steps", "value": rg1, "unit": UNIT,
+                 "seconds": round(tg1, 4), "kernel": "step_kernel_warp"}
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         r, cores, sample = cpu_oracle_rate(sc, wl)
@@ -768,6 +794,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": args.steps * (sum(v["launches"] for v in split.values()) + 1),  # + the fold
         "cpu_baseline": cpu,
+        "small_case": small,
         "time_to_relmse": t2t,
     }
     print(json.dumps(line), flush=True)
