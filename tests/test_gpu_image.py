@@ -11,9 +11,9 @@ Two kinds of comparison:
   0.1 % of pixel-channels (Bonferroni-style; ~0.006 % expected).
 
 The converged references are plain path tracing on the GPU (2^32 to 2^35
-samples; for the Cornell box, the 40k-triangle Cornell + spheres scene and the
-glass slit caustic), each path tracer checked against the oracle's on
-identical samples.
+samples; for the Cornell box, the 40k-triangle Cornell + spheres scene, the
+glass slit caustic and the many-emitter fBm terrain), each path tracer checked
+against the oracle's on identical samples.
 relMSE = mean over pixels and channels of (I - R)^2 / (R^2 + 1e-2).
 """
 import numpy as np
@@ -256,14 +256,23 @@ def test_spheres_relmse_and_per_pixel_vs_converged_reference(J, spheres_referenc
     assert np.abs(zt).max() < 4.5, np.sort(np.abs(zt))[-5:]
 
 
-@pytest.fixture(scope="module")
-def caustic_reference(J):
-    """Converged plain path tracing of the slit caustic (a glass sphere of 80k
-    triangles, IOR 1.5, lit only through a 0.02-wide slit; depth 10, D = 22) at
-    64^2: 16 independent chunks of 2^30 samples, so that a test can carry the
-    reference's own per-pixel error."""
+def _big_scene(name):
+    """64^2 versions of the two large benchmark scenes: the slit caustic (a glass
+    sphere of 80k triangles, IOR 1.5, lit only through a 0.02-wide slit;
+    depth 10, D = 22) and the fBm terrain (79k triangles, lit only by 256 small
+    emitters with L_e log-uniform in [1, 100], open sky; depth 12, D = 26)."""
+    if name == "caustic":
+        return scenes.caustic_slit(width=64, height=64, depth=10)
+    return scenes.terrain(width=64, height=64, n_grid=200)
+
+
+@pytest.fixture(scope="module", params=["caustic", "terrain"])
+def big_reference(J, request):
+    """Converged plain path tracing of a large scene at 64^2: 16 independent
+    chunks of 2^30 samples, so that a test can carry the reference's own
+    per-pixel error."""
     import torch
-    sc = scenes.caustic_slit(width=64, height=64, depth=10)
+    sc = _big_scene(request.param)
     g = J.Scene(sc)
     chunks = []
     n, chunk = 1 << 30, 1 << 28
@@ -273,16 +282,17 @@ def caustic_reference(J):
             J.render_pt(g, sc.width, sc.height, sc.depth, chunk, seed=700 + h, sample_begin=s0, accum=acc)
         chunks.append((acc[..., :3] / n).cpu().numpy())
     torch.cuda.synchronize()
-    return sc, np.array(chunks)
+    return request.param, sc, np.array(chunks)
 
 
-def test_caustic_plain_path_tracer_matches_oracle_paired(J):
-    """The caustic's GPU path tracer (dielectric Fresnel choices, refraction
-    through the sphere) against the oracle's, with its own BVH, on identical
-    samples: pixel sums agree to FP32 rounding except for rare FP32-vs-FP64
-    topology flips."""
+@pytest.mark.parametrize("name", ["caustic", "terrain"])
+def test_big_scene_plain_path_tracer_matches_oracle_paired(J, name):
+    """The GPU path tracer against the oracle's, with its own BVH, on
+    identical samples (the caustic's dielectric Fresnel choices and
+    refractions; the terrain's 256 emitters and open sky): pixel sums agree to
+    FP32 rounding except for rare FP32-vs-FP64 topology flips."""
     import torch
-    sc = scenes.caustic_slit(width=64, height=64, depth=10)
+    sc = _big_scene(name)
     n = 1 << 21
     acc = J.render_pt(J.Scene(sc), sc.width, sc.height, sc.depth, n, seed=9)
     torch.cuda.synchronize()
@@ -295,18 +305,18 @@ def test_caustic_plain_path_tracer_matches_oracle_paired(J):
     assert relmse(g, o) < 1e-5
 
 
-def test_caustic_relmse_and_per_pixel_vs_converged_reference(J, caustic_reference):
-    """Jump Restore on the slit caustic at 64^2, depth 10: 32 independent
-    batches of 2^16 chains x 1500 steps, each stopped with every tour completed,
-    against the 16 reference chunks.  The pooled image reaches relMSE <= 1e-3;
-    per pixel-channel, Welch's t between the batches and the chunks (so the
+def test_big_scene_relmse_and_per_pixel_vs_converged_reference(J, big_reference):
+    """Jump Restore on a large scene at 64^2: 32 independent batches of 2^16
+    chains x 1500 steps, each stopped with every tour completed, against the
+    16 reference chunks.  The pooled image reaches relMSE <= 1e-3; per
+    pixel-channel, Welch's t between the batches and the chunks (so the
     reference's own error is carried) stays within 4 sigma (0.1 % budget) where
     both are in the central-limit regime (lit in at least 24 of 32 batches and
-    12 of 16 chunks); the rest, caustic pixels lit by rare paths, is checked in
-    8x8 tiles and by the relMSE."""
+    12 of 16 chunks); the rest, pixels lit by rare paths, is checked in 8x8
+    tiles and by the relMSE."""
     import torch
     from scipy import stats
-    sc, chunks = caustic_reference
+    name, sc, chunks = big_reference
     ref = chunks.mean(0)
     g = J.Scene(sc)
     imgs = []
@@ -319,7 +329,7 @@ def test_caustic_relmse_and_per_pixel_vs_converged_reference(J, caustic_referenc
     torch.cuda.synchronize()
     imgs = np.array(imgs, np.float64)
     e = relmse(imgs.mean(0), ref)
-    assert e <= 1e-3, e
+    assert e <= 1e-3, (name, e)
 
     def welch(a, b):
         na, nb = len(a), len(b)
@@ -333,12 +343,12 @@ def test_caustic_relmse_and_per_pixel_vs_converged_reference(J, caustic_referenc
 
     z, ok = welch(imgs, chunks)
     dense = ((np.count_nonzero(imgs, axis=0) >= 24) & (np.count_nonzero(chunks, axis=0) >= 12))[ok]
-    assert dense.mean() > 0.5, dense.mean()
+    assert dense.mean() > 0.5, (name, dense.mean())
     zd = z[dense]
-    msg = dict(frac=float(np.mean(np.abs(zd) > 4)), worst=np.sort(np.abs(zd))[-8:].tolist())
+    msg = dict(scene=name, frac=float(np.mean(np.abs(zd) > 4)), worst=np.sort(np.abs(zd))[-8:].tolist())
     assert np.mean(np.abs(zd) > 4) <= 1e-3, msg
-    assert 0.7 < np.mean(zd ** 2) < 1.5, np.mean(zd ** 2)
+    assert 0.7 < np.mean(zd ** 2) < 1.5, (name, np.mean(zd ** 2))
     tiles = imgs.reshape(32, 8, 8, 8, 8, 3).mean(axis=(2, 4))
     rtiles = chunks.reshape(16, 8, 8, 8, 8, 3).mean(axis=(2, 4))
     zt, _ = welch(tiles, rtiles)
-    assert np.abs(zt).max() < 4.5, np.sort(np.abs(zt))[-5:]
+    assert np.abs(zt).max() < 4.5, (name, np.sort(np.abs(zt))[-5:])
