@@ -718,8 +718,9 @@ def main():
         split_total = sum(v["ms"] for v in split.values())
         dom = max(split, key=lambda k: split[k]["ms"])
         # the library's rule for the single-launch modes: one warp per chain when asked for, or
-        # (auto) below the wavefront's 2^16 chains for a scene of at most 128 triangles
-        warp = args.exec == "warp" or (args.exec == "auto" and C < (1 << 16) and sc.n_tris <= 128)
+        # (auto) for a scene of at most 128 triangles with fewer than 32 chains per SM
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        warp = args.exec == "warp" or (args.exec == "auto" and C < 32 * n_sm and sc.n_tris <= 128)
         step_kernel_name = "step_kernel_warp" if warp else "step_kernel"
         if dom == "path":    # the traversal work runs in the path kernel
             achieved = flop / 1e12 / (split["path"]["ms"] / 1e3)

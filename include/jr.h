@@ -226,8 +226,9 @@ jr_status jr_set_block_size(jr_chains* chains, uint32_t block);
  *                       bound by the latency of its serial steps; chain sets
  *                       with a flow run in the wavefront instead;
  *   JR_EXEC_AUTO        wavefront from 2^16 chains up; below that, one warp per
- *                       chain for scenes of at most 128 triangles, else the
- *                       megakernel.
+ *                       chain for scenes of at most 128 triangles and fewer
+ *                       than 32 chains per SM (4 864 on a 152-SM GB300), else
+ *                       the megakernel.
  * All modes run the same per-chain arithmetic on the same Philox streams and
  * give the same closest hits (the least (t, original triangle index) with
  * t > 0). */

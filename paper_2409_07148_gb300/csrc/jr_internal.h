@@ -233,7 +233,7 @@ bool build_bvh(const float* verts, uint32_t n_verts, const uint32_t* tris, uint3
 cudaError_t launch_init(const SceneView& s, const ChainView& c, cudaStream_t st);
 // One chain per warp (JR_EXEC_WARP): brute-force intersection over every
 // triangle, for small scenes; auto mode takes it for at most kWarpChainMaxTris
-// triangles below the wavefront's chain count.
+// triangles and fewer than 32 chains per SM.
 constexpr uint32_t kWarpChainMaxTris = 128;
 cudaError_t launch_step_warp(const SceneView& s, const ChainView& c, uint64_t step_begin, uint32_t n_steps,
                              cudaStream_t st);
