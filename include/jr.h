@@ -225,7 +225,7 @@ jr_status jr_set_block_size(jr_chains* chains, uint32_t block);
  *                       triangles and few chains, where one thread per chain is
  *                       bound by the latency of its serial steps; chain sets
  *                       with a flow run in the wavefront instead;
- *   JR_EXEC_AUTO        wavefront from 2^16 chains up; below that, one warp per
+ *   JR_EXEC_AUTO        wavefront from 2^18 chains up; below that, one warp per
  *                       chain for scenes of at most 128 triangles and fewer
  *                       than 32 chains per SM (4 864 on a 152-SM GB300), else
  *                       the megakernel.

@@ -21,7 +21,7 @@ constexpr uint32_t kNodeVisitBudget = 1u << 16;  // per ray; exceeding it is a w
 constexpr uint32_t kTagStep = 0, kTagInit = 1, kTagPt = 2, kTagRestart = 3;
 constexpr int kCounters = 8;   // ChainView::counters entries
 constexpr int kCounterPSum = 5;  // MH: sum of p over the large-step proposals (double)
-constexpr uint64_t kWavefrontMinChains = 1u << 16;  // JR_EXEC_AUTO picks the wavefront from here up
+constexpr uint64_t kWavefrontMinChains = 1u << 18;  // JR_EXEC_AUTO picks the wavefront from here up
 
 // 4-wide BVH node, 128 bytes (one L2 line): the boxes of up to 4 children,
 // one float4 per plane with child j in component j, then the child refs:
