@@ -153,8 +153,8 @@ typedef struct {
 /* Upload a scene and build its BVH (binned SAH, host, native code).  The
  * triangle arrays are copied; the call synchronises `stream` before it
  * returns.  n_tris may be 0 (every ray misses).  Errors: JR_ERR_INVALID_ARG
- * (index out of range, unknown material type, n_tris >= 2^27), JR_ERR_OOM,
- * JR_ERR_CUDA. */
+ * (index out of range, a triangle's vertex coordinate not finite, unknown
+ * material type, n_tris >= 2^27), JR_ERR_OOM, JR_ERR_CUDA. */
 jr_status jr_scene_create(const jr_scene_desc* desc, void* stream, jr_scene** out);
 jr_status jr_scene_get_info(const jr_scene* scene, jr_scene_info* out);
 void jr_scene_destroy(jr_scene* scene);

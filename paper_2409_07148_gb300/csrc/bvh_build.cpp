@@ -10,6 +10,7 @@
 #include <cstring>
 #include <future>
 #include <system_error>
+#include <thread>
 
 #include "jr_internal.h"
 
@@ -53,39 +54,73 @@ struct BinNode {
     int ref[2];
 };
 
-// The output of a (sub)tree build: binary nodes and leaf triangle records in
-// depth-first order, refs relative to these arrays.
-struct Part {
-    std::vector<BinNode> bin;
-    std::vector<TriRecord> tris;
-    int max_depth = 0;
-};
-
-// Append part q after part p, moving q's refs by p's sizes; returns ref moved.
-// Appending a node's left and then its right part reproduces the order a
-// sequential depth-first build would give.
-int append_part(Part& p, Part& q, int ref) {
-    const int node_off = (int)p.bin.size(), tri_off = (int)p.tris.size();
-    for (BinNode& nd : q.bin)
-        for (int j = 0; j < 2; ++j) nd.ref[j] = rebase_ref(nd.ref[j], node_off, tri_off);
-    p.bin.insert(p.bin.end(), q.bin.begin(), q.bin.end());
-    p.tris.insert(p.tris.end(), q.tris.begin(), q.tris.end());
-    p.max_depth = std::max(p.max_depth, q.max_depth);
-    return rebase_ref(ref, node_off, tri_off);
-}
-
 // Subtrees of at least this many triangles, this close to the root, are
 // built on their own thread (the left one; the right one on the caller's).
-constexpr uint32_t kParallelMin = 8192;
-constexpr int kParallelDepth = 4;
+constexpr uint32_t kParallelMin = 1024;
+constexpr int kParallelDepth = 8;
+
+// A range of at least two chunks of this many prims is binned, and the prims
+// of the whole scene set up, by several threads, one chunk range each; the
+// chunks' results are merged in order.  Bins and boxes are minima, maxima and
+// counts, which do not depend on the order, so the tree is the same.
+constexpr uint32_t kChunk = 8192;
+
+constexpr int kBins = 16;
+
+// The bins of a range on the three axes: boxes, counts, and a mask per axis of
+// the bins that hold prims.
+struct Bins {
+    Box bb[3][kBins];
+    uint32_t cnt[3][kBins] = {};
+    uint32_t used[3] = {0u, 0u, 0u};
+    void merge(const Bins& o) {
+        for (int ax = 0; ax < 3; ++ax) {
+            for (int k = 0; k < kBins; ++k) {
+                bb[ax][k].grow(o.bb[ax][k]);
+                cnt[ax][k] += o.cnt[ax][k];
+            }
+            used[ax] |= o.used[ax];
+        }
+    }
+};
+
+uint32_t worker_count(uint32_t n) {
+    if (n < 2 * kChunk) return 1u;  // before the query, which may read a file
+    return std::min(std::max(1u, std::thread::hardware_concurrency()), n / kChunk);
+}
+
+// Runs body(0, chunks) .. body(chunks - 1, chunks): all but the first on
+// threads of their own where one can be had, the rest on the caller's.
+template <class F>
+void run_chunks(uint32_t chunks, F&& body) {
+    std::vector<std::future<void>> fut;
+    fut.reserve(chunks);
+    for (uint32_t c = 1; c < chunks; ++c) {
+        try {
+            fut.push_back(std::async(std::launch::async, [&body, c, chunks] { body(c, chunks); }));
+        } catch (const std::system_error&) {  // no thread to be had: run it here
+            body(c, chunks);
+        }
+    }
+    body(0, chunks);
+    for (auto& f : fut) f.get();
+}
 
 struct Builder {
     const float* verts;
     const uint32_t* tris;
     const uint32_t* tri_mat;
     std::vector<Prim> prims;
-    std::vector<BinNode> bin;  // the binary tree, for collapse()
-    HostBvh* out;              // collapse() writes the 4-wide nodes here
+    // The binary tree.  The inner node that splits [b, e) at mid is bin[mid - 1]:
+    // a split position separates two neighbouring prims for good, so no two
+    // nodes share one, and threads building disjoint ranges write disjoint
+    // slots.  Positions inside leaves stay unused; collapse() follows refs.
+    std::vector<BinNode> bin;
+    // Leaf records.  A depth-first build emits the leaves of [b, e) after
+    // those of every range left of b, which hold exactly b prims, so the leaf
+    // of [b, e) owns records [b, e): the order a single thread would give.
+    std::vector<TriRecord> recs;
+    HostBvh* out;  // collapse() writes the 4-wide nodes here
 
     // Widen a box so that a FP32 slab test never rejects a box whose triangle
     // the ray/triangle test accepts (coordinates are rounded outward by a
@@ -103,8 +138,7 @@ struct Builder {
         return r;
     }
 
-    int make_leaf(uint32_t b, uint32_t e, Part& out) {
-        uint32_t first = (uint32_t)out.tris.size();
+    int make_leaf(uint32_t b, uint32_t e) {
         for (uint32_t i = b; i < e; ++i) {
             uint32_t t = prims[i].id;
             const float* v0 = verts + 3 * tris[3 * t];
@@ -118,25 +152,39 @@ struct Builder {
             r.v0_id = make_float4(v0[0], v0[1], v0[2], fid);
             r.e1_mat = make_float4(v1[0] - v0[0], v1[1] - v0[1], v1[2] - v0[2], fmat);
             r.e2 = make_float4(v2[0] - v0[0], v2[1] - v0[1], v2[2] - v0[2], 0.0f);
-            out.tris.push_back(r);
+            recs[i] = r;
         }
-        return ~(int)((first << 3) | (e - b - 1));
+        return ~(int)((b << 3) | (e - b - 1));
     }
 
-    // Returns the child ref of range [b, e); bounds is the range's box and cb
-    // the box of its centroids.  One pass bins all three axes; the partition
-    // pass also gathers the two sides' centroid boxes, and the sides' boxes
-    // come from the chosen split's bins (min and max are exact, so these are
-    // the boxes a pass over each side would give).
-    int build(uint32_t b, uint32_t e, int depth, const Box& bounds, const Box& cb, Part& out) {
+    // Returns the child ref of range [b, e); bounds is the range's box, cb the
+    // box of its centroids, and max_depth gets the deepest level reached.  One
+    // pass bins all three axes; the partition pass also gathers the two sides'
+    // centroid boxes, and the sides' boxes come from the chosen split's bins
+    // (min and max are exact, so these are the boxes a pass over each side
+    // would give).
+    void bin_range(uint32_t b, uint32_t e, const float* lo, const float* scale, const bool* live, Bins& out) const {
+        for (uint32_t i = b; i < e; ++i) {
+            const Prim& p = prims[i];
+            for (int ax = 0; ax < 3; ++ax) {
+                if (!live[ax]) continue;
+                const int k = std::min(kBins - 1, (int)((p.c[ax] - lo[ax]) * scale[ax]));
+                out.bb[ax][k].grow(p.box);
+                out.cnt[ax][k]++;
+                out.used[ax] |= 1u << k;
+            }
+        }
+    }
+
+    int build(uint32_t b, uint32_t e, int depth, const Box& bounds, const Box& cb, int& max_depth) {
         const uint32_t n = e - b;
-        out.max_depth = std::max(out.max_depth, depth);
+        max_depth = std::max(max_depth, depth);
         const double leaf_cost = (double)n;
         int best_axis = -1, best_bin = -1;
         double best_cost = INFINITY;
-        constexpr int kBins = 16;
-        Box bb[3][kBins];
-        uint32_t cnt[3][kBins] = {};
+        Bins bins;
+        Box (&bb)[3][kBins] = bins.bb;
+        uint32_t (&cnt)[3][kBins] = bins.cnt;
         float scale[3] = {0.f, 0.f, 0.f};
         bool live[3] = {false, false, false};
         if (n > 1) {
@@ -145,55 +193,57 @@ struct Builder {
                 live[ax] = ext > 0.0f;
                 if (live[ax]) scale[ax] = kBins / ext;
             }
-            for (uint32_t i = b; i < e; ++i) {
-                const Prim& p = prims[i];
-                for (int ax = 0; ax < 3; ++ax) {
-                    if (!live[ax]) continue;
-                    const int k = std::min(kBins - 1, (int)((p.c[ax] - cb.lo[ax]) * scale[ax]));
-                    bb[ax][k].grow(p.box);
-                    cnt[ax][k]++;
-                }
+            const uint32_t chunks = worker_count(n);
+            if (chunks == 1) {
+                bin_range(b, e, cb.lo, scale, live, bins);
+            } else {
+                std::vector<Bins> part(chunks);
+                run_chunks(chunks, [&](uint32_t c, uint32_t m) {
+                    Bins local;  // the chunks' bins in one array would share cache lines at their edges
+                    bin_range(b + (uint32_t)((uint64_t)n * c / m), b + (uint32_t)((uint64_t)n * (c + 1) / m), cb.lo,
+                              scale, live, local);
+                    part[c] = local;
+                });
+                for (const Bins& q : part) bins.merge(q);
             }
             const double inv_area = 1.0 / std::max(bounds.area(), 1e-30);
             for (int ax = 0; ax < 3; ++ax) {
                 if (!live[ax]) continue;
-                // An empty bin changes neither side's box nor its count: the
-                // candidate after it equals the one before, so it is skipped
-                // (costs are compared strictly, so the choice is unchanged).
+                // Only the bins that hold prims are visited: an empty bin
+                // changes neither side's box nor its count, so the candidate
+                // after it equals the one before (costs are compared
+                // strictly, so the choice is unchanged).  ra[j], rc[j]: area
+                // and count of the bins from kept[j] up.
+                int kept[kBins], m = 0;
+                for (uint32_t u = bins.used[ax]; u; u &= u - 1) kept[m++] = __builtin_ctz(u);
                 double ra[kBins];
                 uint32_t rc[kBins];
                 Box acc;
                 uint32_t c = 0;
-                double a = 0.0;
-                for (int k = kBins - 1; k > 0; --k) {
-                    if (cnt[ax][k]) {
-                        acc.grow(bb[ax][k]);
-                        c += cnt[ax][k];
-                        a = acc.area();
-                    }
-                    ra[k] = a;
-                    rc[k] = c;
+                for (int j = m - 1; j > 0; --j) {
+                    acc.grow(bb[ax][kept[j]]);
+                    c += cnt[ax][kept[j]];
+                    ra[j] = acc.area();
+                    rc[j] = c;
                 }
                 Box la;
                 uint32_t lc = 0;
-                for (int k = 0; k < kBins - 1; ++k) {
-                    if (!cnt[ax][k]) continue;
-                    la.grow(bb[ax][k]);
-                    lc += cnt[ax][k];
-                    if (rc[k + 1] == 0) continue;
-                    const double cost = 1.0 + (la.area() * lc + ra[k + 1] * rc[k + 1]) * inv_area;
+                for (int j = 0; j + 1 < m; ++j) {
+                    la.grow(bb[ax][kept[j]]);
+                    lc += cnt[ax][kept[j]];
+                    const double cost = 1.0 + (la.area() * lc + ra[j + 1] * rc[j + 1]) * inv_area;
                     if (cost < best_cost) {
                         best_cost = cost;
                         best_axis = ax;
-                        best_bin = k;
+                        best_bin = kept[j];
                     }
                 }
             }
         }
         const bool must_split = n > (uint32_t)kLeafMax;
-        if (!must_split && (best_axis < 0 || best_cost >= leaf_cost)) return make_leaf(b, e, out);
+        if (!must_split && (best_axis < 0 || best_cost >= leaf_cost)) return make_leaf(b, e);
         if (depth >= kMaxBvhDepth - 1) {
-            if (!must_split) return make_leaf(b, e, out);
+            if (!must_split) return make_leaf(b, e);
         }
         uint32_t mid = b;
         Box lb, rb, lcb, rcb;
@@ -224,29 +274,28 @@ struct Builder {
             for (uint32_t i = b; i < mid; ++i) lcb.grow(prims[i].c);
             for (uint32_t i = mid; i < e; ++i) rcb.grow(prims[i].c);
         }
-        const int me = (int)out.bin.size();
-        out.bin.push_back(BinNode{});
         int l, r;
-        Part pl, pr;
         std::future<int> left;
-        if (n >= kParallelMin && depth < kParallelDepth) {  // the two sides touch disjoint prims
+        int left_depth = 0;
+        if (n >= kParallelMin && depth < kParallelDepth) {  // the two sides touch disjoint prims and slots
             try {
-                left = std::async(std::launch::async, [&] { return build(b, mid, depth + 1, lb, lcb, pl); });
+                left = std::async(std::launch::async,
+                                  [&] { return build(b, mid, depth + 1, lb, lcb, left_depth); });
             } catch (const std::system_error&) {  // no thread to be had: both sides here
             }
         }
         if (left.valid()) {
-            const int rr = build(mid, e, depth + 1, rb, rcb, pr);
-            const int lr = left.get();
-            l = append_part(out, pl, lr);
-            r = append_part(out, pr, rr);
+            r = build(mid, e, depth + 1, rb, rcb, max_depth);
+            l = left.get();
+            max_depth = std::max(max_depth, left_depth);
         } else {
-            l = build(b, mid, depth + 1, lb, lcb, out);
-            r = build(mid, e, depth + 1, rb, rcb, out);
+            l = build(b, mid, depth + 1, lb, lcb, max_depth);
+            r = build(mid, e, depth + 1, rb, rcb, max_depth);
         }
         widen(lb);
         widen(rb);
-        BinNode& nd = out.bin[me];
+        const int me = (int)mid - 1;
+        BinNode& nd = bin[me];
         nd.box[0] = lb;
         nd.box[1] = rb;
         nd.ref[0] = l;
@@ -336,31 +385,55 @@ bool build_bvh(const float* verts, uint32_t n_verts, const uint32_t* tris, uint3
     B.tri_mat = tri_mat;
     B.out = out;
     B.prims.resize(n_tris);
-    for (uint32_t t = 0; t < n_tris; ++t) {
-        Prim& p = B.prims[t];
-        for (int j = 0; j < 3; ++j) {
-            uint32_t vi = tris[3 * t + j];
-            if (vi >= n_verts) {
-                *err = "triangle vertex index out of range";
-                return false;
+    B.bin.resize(n_tris - 1);
+    B.recs.resize(n_tris);
+    // Each chunk of triangles gets its prims, the box of their boxes and of
+    // their centroids, and its first error (1: vertex index out of range, 2:
+    // a coordinate not finite); the first chunk with an error names it.
+    struct Setup {
+        Box box, c;
+        int error = 0;
+    };
+    const uint32_t chunks = worker_count(n_tris);
+    std::vector<Setup> part(chunks);
+    run_chunks(chunks, [&](uint32_t c, uint32_t m) {
+        Setup r;  // local: the chunks' results share cache lines
+        const uint32_t t0 = (uint32_t)((uint64_t)n_tris * c / m), t1 = (uint32_t)((uint64_t)n_tris * (c + 1) / m);
+        for (uint32_t t = t0; t < t1 && !r.error; ++t) {
+            Prim& p = B.prims[t];
+            for (int j = 0; j < 3; ++j) {
+                const uint32_t vi = tris[3 * t + j];
+                if (vi >= n_verts) {
+                    r.error = 1;
+                    break;
+                }
+                const float* q = verts + 3 * (size_t)vi;
+                if (!std::isfinite(q[0]) || !std::isfinite(q[1]) || !std::isfinite(q[2])) {
+                    r.error = 2;
+                    break;
+                }
+                p.box.grow(q);
             }
-            p.box.grow(verts + 3 * vi);
+            for (int k = 0; k < 3; ++k) p.c[k] = 0.5f * (p.box.lo[k] + p.box.hi[k]);
+            p.id = t;
+            r.box.grow(p.box);
+            r.c.grow(p.c);
         }
-        for (int k = 0; k < 3; ++k) p.c[k] = 0.5f * (p.box.lo[k] + p.box.hi[k]);
-        p.id = t;
-    }
-    Part root;
-    root.bin.reserve(n_tris);
-    root.tris.reserve(n_tris);
+        part[c] = r;
+    });
     Box all_box, all_c;
-    for (uint32_t t = 0; t < n_tris; ++t) {
-        all_box.grow(B.prims[t].box);
-        all_c.grow(B.prims[t].c);
+    for (const Setup& r : part) {
+        if (r.error) {
+            *err = r.error == 1 ? "triangle vertex index out of range" : "triangle vertex coordinate not finite";
+            return false;
+        }
+        all_box.grow(r.box);
+        all_c.grow(r.c);
     }
-    const int root2 = B.build(0, n_tris, 0, all_box, all_c, root);
-    B.bin = std::move(root.bin);
-    out->tris = std::move(root.tris);
-    if (root.max_depth >= kMaxBvhDepth) {
+    int max_depth = 0;
+    const int root2 = B.build(0, n_tris, 0, all_box, all_c, max_depth);
+    out->tris = std::move(B.recs);
+    if (max_depth >= kMaxBvhDepth) {
         *err = "BVH too deep for the traversal stack";
         return false;
     }

@@ -73,6 +73,13 @@ def test_invalid_scene_arguments(L):
     d, keep = _desc(L, sc2)
     assert lib.jr_scene_create(ctypes.byref(d), None, ctypes.byref(h)) == L.JR_ERR_INVALID_ARG
     assert b"out of range" in lib.jr_last_error()
+    for bad_value in (np.nan, np.inf, -np.inf):  # a triangle's vertex must be finite
+        v = sc.verts.copy()
+        v[sc.tris[5, 1], 2] = bad_value
+        sc3 = scenes.SceneArrays("bad", v, sc.tris, sc.tri_mat, sc.mats, sc.camera, 8, 8, 1)
+        d, keep = _desc(L, sc3)
+        assert lib.jr_scene_create(ctypes.byref(d), None, ctypes.byref(h)) == L.JR_ERR_INVALID_ARG
+        assert b"not finite" in lib.jr_last_error()
 
 
 def test_invalid_chain_arguments(L):
