@@ -440,9 +440,10 @@ def time_to_target(args):
             clock = 0.0
             trainer = render = None
             if learned:
-                perm, w = init_flow_params(sc.D, 0)
-                trainer = jr.Flow(sc.D, perm, w, stream=stream)
-                render = [jr.Flow(sc.D, perm, w, stream=stream), jr.Flow(sc.D, perm, w, stream=stream)]
+                Df = min(args.flow_dim, sc.D) if args.flow_dim else sc.D
+                perm, w = init_flow_params(Df, 0)
+                trainer = jr.Flow(Df, perm, w, stream=stream)
+                render = [jr.Flow(Df, perm, w, stream=stream), jr.Flow(Df, perm, w, stream=stream)]
                 buf = jr.ReplayBuffer(sc.D, args.replay)
             e = 0
             parts = {"advance": 0.0, "train": 0.0, "drain_switch": 0.0}
@@ -532,7 +533,8 @@ def time_to_target(args):
             "epoch_steps": epoch,
             "epoch_growth": args.epoch_growth, "epoch_max": args.epoch_max,
             "reference": {"samples": args.ref_samples, "seconds": round(t_ref, 2), "noise_relmse_est": ref_noise},
-            "plain": plain, "mh": mh, "mala": mala, "mala_mh": mala_mh, "learned": {**learned, "beta": args.beta, "train_iters_per_epoch": args.train_iters,
+            "plain": plain, "mh": mh, "mala": mala, "mala_mh": mala_mh, "learned": {**learned, "beta": args.beta, "flow_dim": min(args.flow_dim, sc.D) if args.flow_dim else sc.D,
+                                        "train_iters_per_epoch": args.train_iters,
                                         "train_iters_first": args.train_iters0, "warm_epochs": args.warm_epochs,
                                         "batch": args.batch, "snap_every": args.snap_every, "replay": args.replay,
                                         "lr": args.lr, "flow": "6 coupling layers, MLP 2x64, 16 bins, bf16/FP32"},
@@ -555,7 +557,8 @@ def default_time_to_relmse(args):
     out = {"workload": r["workload"], "unit": r["unit"], "target": r["target"], "relmse_eps": r["relmse_eps"],
            "chains": r["chains"], "reference": r["reference"],
            "plain": {k: r["plain"].get(k) for k in keep},
-           "learned": {**{k: r["learned"].get(k) for k in keep}, "beta": r["learned"]["beta"]}}
+           "learned": {**{k: r["learned"].get(k) for k in keep}, "beta": r["learned"]["beta"],
+                       "flow_dim": r["learned"]["flow_dim"]}}
     tp, tl = out["plain"]["time_to_target_s"], out["learned"]["time_to_target_s"]
     out["learned_over_plain"] = tl / tp if tp and tl else None   # first checkpoint at or below the target
     ip, il = out["plain"]["time_to_target_interp_s"], out["learned"]["time_to_target_interp_s"]
@@ -620,6 +623,9 @@ def main():
     ap.add_argument("--arms", default="plain,learned", help="caustic workload: arms to run")
     ap.add_argument("--split-epoch", type=int, default=-1, help="caustic workload: time 16 extra steps per kernel class after this epoch (diagnostic)")
     ap.add_argument("--beta", type=float, default=0.15)
+    ap.add_argument("--flow-dim", type=int, default=8,
+                    help="time-to-target harness: the flow models the first flow-dim coordinates, the rest "
+                         "uniform (0 or >= D: all D)")
     ap.add_argument("--c-tilde", type=float, default=1.0, help="time-to-target harness: c~ of the Restore arms")
     ap.add_argument("--batched", action="store_true",
                     help="time-to-target harness: the plain and learned arms advance through a batch (batched wavefront)")

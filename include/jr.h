@@ -511,8 +511,13 @@ jr_status jr_complete_tours(jr_chains* chains, uint32_t max_steps, uint64_t* rem
  * [0, 1): first the current tours are completed under the old mu (as in
  * jr_complete_tours, at most max_drain_steps steps), then every chain starts a
  * new tour from the new mu.  So no tour mixes two regeneration densities.  The
+ * flow's dimension D' is the chains' D, or 4 <= D' < D: the flow then models
+ * the leading D' coordinates and the others stay uniform, mu_flow(x) =
+ * q(x[0 .. D')) and u = beta q(x[0 .. D')) + 1 - beta (a flow draw maps the
+ * first D' of the step's uniforms through the flow and keeps the rest).  The
  * flow must outlive its use; chains with a flow advance in the wavefront mode
- * (jr_advance only). */
+ * (jr_advance only).  Errors: JR_ERR_INVALID_ARG (null chains, D' not D and
+ * not in 4 .. D - 1, beta outside [0, 1)), JR_ERR_STATE (MH or MALA chains). */
 jr_status jr_chains_set_flow(jr_chains* chains, const jr_flow* flow, float beta, uint32_t max_drain_steps,
                              uint64_t* remaining, void* stream);
 

@@ -10,6 +10,11 @@ path integrand or an analytic target) and q from oracle/flow.py.
 Random numbers: the Philox layout of the C oracle.  Block 0 of a step gives
 (U1, U2, Ua, Ub); a regeneration draws from the flow when Ub < beta (then
 y = T^{-1}(v) for the step's D uniforms v), else y = v.
+
+A flow of dimension D' < D (perm [L][D']) models the leading D' coordinates
+only: mu_flow = q on [0,1)^D' times the uniform density on the other D - D'
+coordinates, so u(x) = beta q(x[:D']) + (1 - beta), and a flow draw maps the
+first D' uniforms through T^{-1} and keeps the rest.
 """
 from __future__ import annotations
 
@@ -41,10 +46,21 @@ class LearnedChains:
         x = _coords(self.seed, TAG_INIT, self.cb, self.n, 0, self.D)   # x0 ~ uniform (tag 1)
         self._set(x, self.u_of(x))
 
+    def flow_dim(self):
+        return len(self.perm[0]) if self.w is not None else self.D
+
     def u_of(self, x):
         if self.w is None or self.beta == 0.0:
             return np.ones(len(x))
-        return FL.regen_density(self.perm, self.w, x, self.beta)
+        return FL.regen_density(self.perm, self.w, x[:, :self.flow_dim()], self.beta)
+
+    def _flow_draw(self, v):
+        """y = (T^{-1}(v[:, :D']), v[:, D':]) and u(y)."""
+        Df = self.flow_dim()
+        y = v.copy()
+        xf, lq = FL.sample(self.perm, self.w, v[:, :Df])
+        y[:, :Df] = xf
+        return y, self.beta * np.exp(lq) + (1.0 - self.beta)
 
     def _set(self, x, u):
         self.x = x
@@ -86,9 +102,7 @@ class LearnedChains:
             uni = regen & ~use_flow
             y[uni] = v[uni]
             if use_flow.any():
-                xf, lq = FL.sample(self.perm, self.w, v[use_flow])
-                y[use_flow] = xf
-                uy[use_flow] = self.beta * np.exp(lq) + (1.0 - self.beta)
+                y[use_flow], uy[use_flow] = self._flow_draw(v[use_flow])
             dens = ~use_flow
             if dens.any():
                 uy[dens] = self.u_of(y[dens])
@@ -111,9 +125,7 @@ class LearnedChains:
         uy = np.ones(len(v))
         use_flow = regen_mask & (U[:, 3] < self.beta) & (self.w is not None)
         if use_flow.any():
-            xf, lq = FL.sample(self.perm, self.w, v[use_flow])
-            y[use_flow] = xf
-            uy[use_flow] = self.beta * np.exp(lq) + (1.0 - self.beta)
+            y[use_flow], uy[use_flow] = self._flow_draw(v[use_flow])
         dens = ~use_flow
         if dens.any():
             uy[dens] = self.u_of(y[dens])

@@ -1433,7 +1433,10 @@ jr_status jr_chains_set_flow(jr_chains* c, const jr_flow* f, float beta, uint32_
     if (!c) return fail(JR_ERR_INVALID_ARG, "jr_chains_set_flow: null chains");
     if (c->view.flags & (JR_FLAG_MH | JR_FLAG_MALA))
         return fail(JR_ERR_STATE, "jr_chains_set_flow: MH and MALA chains regenerate from the uniform mu only");
-    if (f && f->D != c->view.dim) return fail(JR_ERR_INVALID_ARG, "jr_chains_set_flow: flow and chain dimensions differ");
+    // A flow of lower dimension models the leading coordinates only (the rest
+    // stay uniform); it must cover the path's start record, coordinates 0..3.
+    if (f && !(f->D == c->view.dim || (f->D >= 4 && f->D < c->view.dim)))
+        return fail(JR_ERR_INVALID_ARG, "jr_chains_set_flow: the flow's dimension must equal the chains' or lie in 4 .. D - 1");
     if (f && !(beta >= 0.f && beta < 1.f))
         return fail(JR_ERR_INVALID_ARG, "jr_chains_set_flow: beta must be in [0, 1)");
     cudaStream_t st = (cudaStream_t)stream;

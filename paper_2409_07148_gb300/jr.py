@@ -398,6 +398,7 @@ def set_flow(chains, flow, beta, max_drain_steps=1 << 20, stream=None):
     rem = ctypes.c_uint64(0)
     _check(lib().jr_chains_set_flow(chains.h, None if flow is None else flow.h, float(beta), int(max_drain_steps),
                                     ctypes.byref(rem), _stream(stream)))
+    chains._flow = flow   # the device keeps using the flow's weights: hold it as long as the chains
     return int(rem.value)
 
 

@@ -201,23 +201,26 @@ def _flow_params(D, seed, sd=0.1):
     return perm, w
 
 
-FLOW_SETS = [("cornell", dict(width=16, height=16), 3000, 1, 0.6),
-             ("random_boxes", dict(seed=4, n_tris=2500, width=48, height=48, depth=6), 2047, 4, None),
-             ("cornell_spheres", dict(width=32, height=24, depth=5, n_lon=30, n_lat=16), 2500, 2, 0.3),
-             ("furnace", dict(depth=2), 700, 5, None)]
+# (scene, arguments, chains, seed, beta, flow dimension: None = all D; the
+# spheres set's flow models the leading 6 of its 12 coordinates)
+FLOW_SETS = [("cornell", dict(width=16, height=16), 3000, 1, 0.6, None),
+             ("random_boxes", dict(seed=4, n_tris=2500, width=48, height=48, depth=6), 2047, 4, None, None),
+             ("cornell_spheres", dict(width=32, height=24, depth=5, n_lon=30, n_lat=16), 2500, 2, 0.3, 6),
+             ("furnace", dict(depth=2), 700, 5, None, None)]
 
 
 def _make_flow_sets(J):
     out = []
-    for name, kw, n, seed, beta in FLOW_SETS:
+    for name, kw, n, seed, beta, flow_dim in FLOW_SETS:
         sc = scenes.by_name(name, **kw)
         g = J.Scene(sc)
         c = J.Chains(g, sc.width, sc.height, sc.depth, n, seed=seed, sigma=0.03)
         c.set_execution("wave")
         f = None
         if beta is not None:
-            perm, w = _flow_params(sc.D, seed)
-            f = J.Flow(sc.D, perm, w)
+            Df = flow_dim or sc.D
+            perm, w = _flow_params(Df, seed)
+            f = J.Flow(Df, perm, w)
             J.set_flow(c, f, beta)
         out.append((sc, g, c, f))
     return out

@@ -92,13 +92,17 @@ def test_params_round_trip(J):
     assert np.array_equal(f.get_params(), w2.ravel())
 
 
-def test_chains_with_flow_step_replay(J):
+@pytest.mark.parametrize("flow_dim", [None, 4])
+def test_chains_with_flow_step_replay(J, flow_dim):
     """One step of chains with u = beta q + 1 - beta, replayed by the oracle's
-    Alg. 2 with the FP64 flow from the GPU's own state."""
+    Alg. 2 with the FP64 flow from the GPU's own state.  flow_dim = 4: the flow
+    models coordinates 0..3 of the 8 (the rest uniform), u = beta q(x[:4]) +
+    1 - beta."""
     sc = scenes.cornell(width=16, height=16, depth=3)
-    perm, w = _flow(sc.D, 5, 0.1)
+    Df = flow_dim or sc.D
+    perm, w = _flow(Df, 5, 0.1)
     g = J.Scene(sc)
-    f = J.Flow(sc.D, perm, w)
+    f = J.Flow(Df, perm, w)
     ch = J.Chains(g, 16, 16, sc.depth, 512, seed=3, sigma=0.02)
     J.set_flow(ch, f, 0.6)
     ch.advance(4)
@@ -115,12 +119,12 @@ def test_chains_with_flow_step_replay(J):
     # u of the GPU state is the flow's density (up to the tolerance above)
     # wherever p > 0; at p = 0 the killing rate is +inf whatever u is, and the
     # chains keep u = 1 there without evaluating the flow
-    u_o = FL.regen_density(perm, w, oc.x, 0.6)
+    u_o = FL.regen_density(perm, w, oc.x[:, :Df], 0.6)
     pos = fpu[3] > 0
     assert pos.sum() >= 20
     # u = beta q + 1 - beta at each state with p > 0, to 1e-5 relative off the edges
     du = np.abs(fpu[4][pos] - u_o[pos]) / u_o[pos]
-    _check_rows(du, FL.log_density_margin(perm, w, oc.x[pos]), 1e-5)
+    _check_rows(du, FL.log_density_margin(perm, w, oc.x[pos][:, :Df]), 1e-5)
     assert np.all(fpu[4][~pos] == 1.0)
     oc.advance(1)
     ch.advance(1)
@@ -130,20 +134,23 @@ def test_chains_with_flow_step_replay(J):
     assert np.mean(dx <= 1e-4) >= 0.97       # decisions and flow draws agree except near ties / bin edges
     # u at every new state with p > 0, against the oracle's density of the GPU's own state
     pos2 = fpu2[3] > 0
-    xs2 = x2.T[pos2].astype(np.float64)
+    xs2 = x2.T[pos2].astype(np.float64)[:, :Df]
     u2 = FL.regen_density(perm, w, xs2, 0.6)
     _check_rows(np.abs(fpu2[4][pos2] - u2) / u2, FL.log_density_margin(perm, w, xs2), 1e-5)
 
 
-def test_learned_mixture_image_is_unbiased(J):
+@pytest.mark.parametrize("flow_dim", [None, 4])
+def test_learned_mixture_image_is_unbiased(J, flow_dim):
     """With a non-trivial flow (beta = 0.7) the Jump Restore image converges to
-    the same pixels as with uniform regeneration (per-pixel z over batches)."""
+    the same pixels as with uniform regeneration (per-pixel z over batches);
+    flow_dim = 4: a flow over the leading 4 of the 8 coordinates."""
     from scipy import stats
     import torch
     sc = scenes.cornell(width=32, height=32, depth=3)
-    perm, w = _flow(sc.D, 9, 0.1)
+    Df = flow_dim or sc.D
+    perm, w = _flow(Df, 9, 0.1)
     g = J.Scene(sc)
-    f = J.Flow(sc.D, perm, w)
+    f = J.Flow(Df, perm, w)
     a, b = [], []
     for k in range(16):
         c1 = J.Chains(g, 32, 32, sc.depth, 16384, seed=1, chain_offset=16384 * k)
@@ -166,13 +173,14 @@ def test_learned_mixture_image_is_unbiased(J):
     assert 0.6 < np.mean(z ** 2) < 1.6
 
 
-@pytest.mark.parametrize("beta", [0.0, 0.6])
-def test_complete_tours_paired_with_oracle(J, beta):
+@pytest.mark.parametrize("beta,flow_dim", [(0.0, None), (0.6, None), (0.6, 4)])
+def test_complete_tours_paired_with_oracle(J, beta, flow_dim):
     """Identical Philox streams: GPU chains (wavefront, learned mixture or
     uniform) advanced, drained until every tour ends, and restarted, against
     the oracle's Alg. 2 doing the same from the same initial states."""
     sc = scenes.cornell(width=8, height=8, depth=3)
-    perm, w = _flow(sc.D, 13, 0.1)
+    Df = flow_dim or sc.D
+    perm, w = _flow(Df, 13, 0.1)
     g = J.Scene(sc)
     ch = J.Chains(g, 8, 8, sc.depth, 2048, seed=4, sigma=0.02)
     ch.set_execution("wave")
@@ -180,7 +188,7 @@ def test_complete_tours_paired_with_oracle(J, beta):
     F_of = lambda xx: O.eval_states(osc, xx)[0]
     oc = LR.LearnedChains(F_of, sc.D, 8, 8, beta=0.0, sigma=0.02, seed=4, n_chains=2048)
     if beta:
-        f = J.Flow(sc.D, perm, w)
+        f = J.Flow(Df, perm, w)
         J.set_flow(ch, f, beta)
         oc.set_flow(perm, w, beta)
     ch.advance(6)
@@ -200,17 +208,20 @@ def test_complete_tours_paired_with_oracle(J, beta):
     assert np.mean(same) >= 0.98
 
 
-def test_full_size_learned_step_sampled(J):
+@pytest.mark.parametrize("flow_dim", [None, 8])
+def test_full_size_learned_step_sampled(J, flow_dim):
     """The learned-regeneration workload at full size: the slit caustic
     (80k triangles, glass, 1024^2, depth 10, D = 22), 2^20 chains in the
     wavefront with a non-trivial flow (beta = 0.3).  A contiguous sample of
     2048 chains is handed to the oracle's Alg. 2 with the same flow before a
     step; the next states agree except near ties and bin edges (the
-    tolerance of the small replay above)."""
+    tolerance of the small replay above).  flow_dim = 8: the flow over the
+    leading 8 of the 22 coordinates that the time-to-relMSE harness uses."""
     sc = scenes.caustic_slit()
-    perm, w = _flow(sc.D, 17, 0.1)
+    Df = flow_dim or sc.D
+    perm, w = _flow(Df, 17, 0.1)
     g = J.Scene(sc)
-    f = J.Flow(sc.D, perm, w)
+    f = J.Flow(Df, perm, w)
     n, first, m = 1 << 20, 700_000, 2048
     ch = J.Chains(g, sc.width, sc.height, sc.depth, n, seed=2)
     J.set_flow(ch, f, 0.3)
@@ -237,7 +248,26 @@ def test_full_size_learned_step_sampled(J):
     # the oracle's density of the GPU's own state, to 1e-5 off the rounding edges
     pos2 = fpu2[3] > 0
     if pos2.any():
-        xs2 = x2.T[pos2].astype(np.float64)
+        xs2 = x2.T[pos2].astype(np.float64)[:, :Df]
         u2 = FL.regen_density(perm, w, xs2, 0.3)
         _check_rows(np.abs(fpu2[4][pos2] - u2) / u2, FL.log_density_margin(perm, w, xs2), 1e-5)
+    assert ch.stats()["status_word"] == 0
+
+
+def test_flow_dimension_is_checked(J):
+    """A flow covers all D coordinates or a leading block of at least 4 (the
+    path's start record); anything else is an argument error."""
+    sc = scenes.cornell(width=8, height=8, depth=3)     # D = 8
+    g = J.Scene(sc)
+    ch = J.Chains(g, 8, 8, sc.depth, 64, seed=1)
+    for Df in (2, 10):
+        perm, w = _flow(Df, 3, 0.1)
+        f = J.Flow(Df, perm, w)
+        with pytest.raises(J.JRError) as e:
+            J.set_flow(ch, f, 0.5)
+        assert "dimension" in str(e.value)
+    perm, w = _flow(6, 3, 0.1)
+    f6 = J.Flow(6, perm, w)
+    J.set_flow(ch, f6, 0.5)
+    ch.advance(2)
     assert ch.stats()["status_word"] == 0

@@ -164,3 +164,51 @@ def test_completed_tours_remove_the_finite_run_bias():
         open_ = np.array(open_)
         zo = (open_.mean(0) - pix) / (open_.std(0, ddof=1) / np.sqrt(len(open_)))
         assert np.abs(zo).max() > 4.5     # the open-tour bias is real at this run length
+
+
+def _product_target(an):
+    """F(x) = F_an(x0, x1) g(x2, x3) h(x4, x5) on [0,1)^6 with g and h of
+    integral 1, so the pixel means are the 2-D target's."""
+    def F_of(x):
+        g = (1.0 + 0.6 * np.cos(2 * np.pi * x[:, 2])) * (1.0 + 0.5 * np.sin(2 * np.pi * x[:, 3]))
+        h = (1.0 + 0.6 * np.cos(2 * np.pi * x[:, 4])) * (1.0 + 0.5 * np.sin(2 * np.pi * x[:, 5]))
+        return an.eval(x[:, :2]) * (g * h)[:, None]
+    return F_of
+
+
+def _prefix_run(F_of, perm, w, planted=False):
+    imgs = []
+    for b in range(10):
+        ch = LR.LearnedChains(F_of, 6, 4, 4, perm, w, beta=0.7, sigma=0.05, seed=31, chain_begin=512 * b,
+                              n_chains=512)
+        if planted:   # a flow draw that forgets its density: u = 1 whatever T^{-1} did
+            draw = ch._flow_draw
+            ch._flow_draw = lambda v, draw=draw: (draw(v)[0], np.ones(len(v)))
+        ch.advance(200)
+        imgs.append(ch.image())
+    return np.array(imgs)
+
+
+def test_prefix_flow_mixture_keeps_the_estimator_exact():
+    """A flow over the leading 4 of 6 coordinates (the rest uniform):
+    mu = beta (q x uniform) + (1 - beta) uniform has density
+    u = beta q(x[:4]) + 1 - beta, and Alg. 2 with k = c~ u / p stays exact
+    (Section 6.2) on a target that varies in all six coordinates.  Planted
+    mistake: flow draws that keep u = 1 bias the image, so the check is not
+    vacuous."""
+    an = O.Analytic([(1.0, 0.3, 0.4, 0.08), (0.5, 0.7, 0.6, 0.1)], (0.45, 0.5))
+    F_of = _product_target(an)
+    n = 1024
+    g = (np.arange(n) + 0.5) / n
+    X0, X1 = np.meshgrid(g, g)
+    F = an.eval(np.stack([X0.ravel(), X1.ravel()], 1)).reshape(n, n, 3)
+    pix = F.reshape(4, n // 4, 4, n // 4, 3).mean(axis=(1, 3))
+    perm, w = _flow(4, 41, 0.3)
+    q = np.exp(FL.log_density(perm, w, np.random.default_rng(5).random((4096, 4)))[0])
+    assert q.max() / q.min() > 5            # the flow is far from uniform
+    imgs = _prefix_run(F_of, perm, w)
+    z = (imgs.mean(0) - pix) / (imgs.std(0, ddof=1) / np.sqrt(len(imgs)))
+    assert np.abs(z).max() < 4.5, z
+    bad = _prefix_run(F_of, perm, w, planted=True)
+    zb = (bad.mean(0) - pix) / (bad.std(0, ddof=1) / np.sqrt(len(bad)))
+    assert np.abs(zb).max() > 4.5
