@@ -178,13 +178,13 @@ def _product_target(an):
 
 def _prefix_run(F_of, perm, w, planted=False):
     imgs = []
-    for b in range(10):
-        ch = LR.LearnedChains(F_of, 6, 4, 4, perm, w, beta=0.7, sigma=0.05, seed=31, chain_begin=512 * b,
-                              n_chains=512)
+    for b in range(8):
+        ch = LR.LearnedChains(F_of, 6, 4, 4, perm, w, beta=0.7, sigma=0.05, seed=31, chain_begin=256 * b,
+                              n_chains=256)
         if planted:   # a flow draw that forgets its density: u = 1 whatever T^{-1} did
             draw = ch._flow_draw
             ch._flow_draw = lambda v, draw=draw: (draw(v)[0], np.ones(len(v)))
-        ch.advance(200)
+        ch.advance(150)
         imgs.append(ch.image())
     return np.array(imgs)
 
