@@ -416,7 +416,7 @@ def time_to_target(args):
                 cg = jr.Scene(csc, stream=stream)
                 companions.append((cg, csc))
 
-        def run(learned):
+        def run(learned, flow_dim=None):
             ch = jr.Chains(g, side, side, sc.depth, C, seed=5 if learned else 6, c_tilde=args.c_tilde, stream=stream)
             ch.set_execution("wave")
             batch, comp_sets = None, []
@@ -440,7 +440,7 @@ def time_to_target(args):
             clock = 0.0
             trainer = render = None
             if learned:
-                Df = min(args.flow_dim, sc.D) if args.flow_dim else sc.D
+                Df = flow_dim or (min(args.flow_dim, sc.D) if args.flow_dim else sc.D)
                 perm, w = init_flow_params(Df, 0)
                 trainer = jr.Flow(Df, perm, w, stream=stream)
                 render = [jr.Flow(Df, perm, w, stream=stream), jr.Flow(Df, perm, w, stream=stream)]
@@ -521,7 +521,9 @@ def time_to_target(args):
                     "status_word": st["status_word"], "clocks": clocks}
 
         plain = run(False) if "plain" in args.arms else None
-        learned = run(True) if "learned" in args.arms else {}
+        learned = run(True) if "learned" in args.arms.split(",") else {}
+        # the flow's couplings over all D coordinates (configuration 4's statement)
+        learned_full = run(True, flow_dim=sc.D) if "learned_full" in args.arms.split(",") else None
         mh = run_mh() if "mh" in args.arms.split(",") else None
         mala = run_mala(False) if "mala" in args.arms.split(",") else None
         mala_mh = run_mala(True) if "mala_mh" in args.arms.split(",") else None
@@ -533,7 +535,9 @@ def time_to_target(args):
             "epoch_steps": epoch,
             "epoch_growth": args.epoch_growth, "epoch_max": args.epoch_max,
             "reference": {"samples": args.ref_samples, "seconds": round(t_ref, 2), "noise_relmse_est": ref_noise},
-            "plain": plain, "mh": mh, "mala": mala, "mala_mh": mala_mh, "learned": {**learned, "beta": args.beta, "flow_dim": min(args.flow_dim, sc.D) if args.flow_dim else sc.D,
+            "plain": plain, "mh": mh, "mala": mala, "mala_mh": mala_mh,
+            "learned_full_dim": None if learned_full is None else {**learned_full, "flow_dim": sc.D},
+            "learned": {**learned, "beta": args.beta, "flow_dim": min(args.flow_dim, sc.D) if args.flow_dim else sc.D,
                                         "train_iters_per_epoch": args.train_iters,
                                         "train_iters_first": args.train_iters0, "warm_epochs": args.warm_epochs,
                                         "batch": args.batch, "snap_every": args.snap_every, "replay": args.replay,
@@ -546,10 +550,12 @@ def default_time_to_relmse(args):
     """Metric 2 for the default line: time to relMSE 1e-2 on the slit caustic
     (1024^2, depth 10, 2^20 chains), plain against learned regeneration, with
     the harness defaults (a 2^36-sample reference, 20 s at most per arm) and a
-    clock record per arm; the curves are left out of the line."""
+    clock record per arm; the curves are left out of the line.  Two learned
+    arms: the flow over the leading --flow-dim coordinates (the rest uniform),
+    and the flow whose couplings transform all 22."""
     import copy
     a = copy.copy(args)
-    a.workload, a.arms, a.chains, a.side, a.ref_samples = "caustic", "plain,learned", 0, None, None
+    a.workload, a.arms, a.chains, a.side, a.ref_samples = "caustic", "plain,learned,learned_full", 0, None, None
     a.time_limit, a.split_epoch, a.ref_file, a.c_tilde, a.batched = 20.0, -1, None, 1.0, False
     r = time_to_target(a)
     keep = ("time_to_target_s", "time_to_target_interp_s", "final_relmse", "epochs", "seconds", "clocks",
@@ -563,6 +569,11 @@ def default_time_to_relmse(args):
     out["learned_over_plain"] = tl / tp if tp and tl else None   # first checkpoint at or below the target
     ip, il = out["plain"]["time_to_target_interp_s"], out["learned"]["time_to_target_interp_s"]
     out["learned_over_plain_interp"] = il / ip if ip and il else None   # log-log crossing between checkpoints
+    lf = r["learned_full_dim"]
+    out["learned_full_dim"] = {**{k: lf.get(k) for k in keep}, "beta": r["learned"]["beta"], "flow_dim": lf["flow_dim"]}
+    tf, jf = lf["time_to_target_s"], lf["time_to_target_interp_s"]
+    out["learned_full_dim_over_plain"] = tf / tp if tp and tf else None
+    out["learned_full_dim_over_plain_interp"] = jf / ip if ip and jf else None
     return out
 
 
