@@ -416,7 +416,8 @@ jr_status jr_batch_autotune(jr_batch* batch, uint32_t probe_steps, void* stream,
  * may regenerate from the mixture mu = beta mu_flow + (1 - beta) uniform, whose
  * density u = beta q + (1 - beta) enters the killing rate k = c~ u / p of
  * Section 6.2 exactly: q is the change-of-variables density of a normalizing
- * flow on [0,1)^D.  The flow: JR_FLOW_LAYERS coupling layers; layer l
+ * flow on [0,1)^D (or on the leading D' < D coordinates, the rest uniform: see
+ * jr_chains_set_flow).  The flow: JR_FLOW_LAYERS coupling layers; layer l
  * conditions on x[perm[l][0 .. D/2)] and maps each x[perm[l][D/2 + j]] through
  * a piecewise-linear CDF of JR_FLOW_BINS bins (Mueller et al., "Neural
  * Importance Sampling", 2019) with bin masses Q = (1 - 1e-3) softmax(o) +
