@@ -97,3 +97,23 @@ def test_bvh_merge_as_in_a_batch(checker, tmp_path):
         assert res["merge_a"] == "1" and res["merge_b"] == "1", res
     res = _run(checker, pa, "merge_off_by_one", pb)
     assert res["merge_a"] == "1" and res["merge_b"] == "0", res
+
+
+@pytest.mark.parametrize("bad", ["index", "nan", "inf", "both"])
+def test_bvh_rejects_a_bad_triangle_in_a_late_chunk(checker, tmp_path, bad):
+    """The 40k-triangle scene is set up in chunks on several threads; a bad
+    triangle deep in the last chunk is still found, and with two bad triangles
+    the error of the earlier one (in triangle order) is the one reported."""
+    sc = scenes.cornell_spheres()
+    verts, tris = sc.verts.copy(), sc.tris.copy()
+    late = 37_000
+    if bad in ("index", "both"):
+        tris[late if bad == "index" else 100, 2] = len(verts)
+    if bad in ("nan", "inf", "both"):
+        verts[tris[late, 1], 0] = np.inf if bad == "inf" else np.nan
+    path = str(tmp_path / f"bad_{bad}.bin")
+    _write(path, verts, tris, sc.tri_mat)
+    r = subprocess.run([checker, path], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert r.stdout.startswith("ok=0"), r.stdout
+    assert ("out of range" if bad in ("index", "both") else "not finite") in r.stdout, r.stdout
