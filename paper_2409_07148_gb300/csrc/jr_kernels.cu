@@ -286,18 +286,21 @@ __device__ __forceinline__ int closest_hit_warp(const SceneView& s, float3 o, fl
         best = hit ? (int)k : best;
         bid = hit ? id : bid;
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const float t2 = __shfl_xor_sync(0xffffffffu, tb, off);
-        const int b2 = __shfl_xor_sync(0xffffffffu, best, off);
-        const int i2 = __shfl_xor_sync(0xffffffffu, bid, off);
-        if (t2 < tb || (t2 == tb && i2 < bid)) {
-            tb = t2;
-            best = b2;
-            bid = i2;
-        }
+    // The warp's closest hit, ties to the smaller original index.  Every tb is
+    // a hit distance t > 0 or +inf, and for such floats the bit patterns order
+    // as the values do, so two warp-wide integer minima find it: the nearest
+    // distance, then the smallest index among the lanes at that distance (the
+    // indices are distinct); the lane holding it hands over its record.
+    const unsigned tbits = __float_as_uint(tb);
+    const unsigned tmin = __reduce_min_sync(0xffffffffu, tbits);
+    if (tmin == __float_as_uint(INFINITY)) {  // no lane has a hit
+        t_out = INFINITY;
+        return -1;
     }
-    t_out = best >= 0 ? tb : INFINITY;
+    const unsigned imin = __reduce_min_sync(0xffffffffu, tbits == tmin ? (unsigned)bid : 0xffffffffu);
+    const int src = __ffs(__ballot_sync(0xffffffffu, tbits == tmin && (unsigned)bid == imin)) - 1;
+    best = __shfl_sync(0xffffffffu, best, src);
+    t_out = __uint_as_float(tmin);
     return best;
 }
 
