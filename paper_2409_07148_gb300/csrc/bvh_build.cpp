@@ -157,12 +157,8 @@ struct Builder {
         return ~(int)((b << 3) | (e - b - 1));
     }
 
-    // Returns the child ref of range [b, e); bounds is the range's box, cb the
-    // box of its centroids, and max_depth gets the deepest level reached.  One
-    // pass bins all three axes; the partition pass also gathers the two sides'
-    // centroid boxes, and the sides' boxes come from the chosen split's bins
-    // (min and max are exact, so these are the boxes a pass over each side
-    // would give).
+    // Adds prims [b, e) to the bins of every live axis (centroid box lower
+    // corner lo, bins per unit length scale).
     void bin_range(uint32_t b, uint32_t e, const float* lo, const float* scale, const bool* live, Bins& out) const {
         for (uint32_t i = b; i < e; ++i) {
             const Prim& p = prims[i];
@@ -176,6 +172,12 @@ struct Builder {
         }
     }
 
+    // Returns the child ref of range [b, e); bounds is the range's box, cb the
+    // box of its centroids, and max_depth gets the deepest level reached.  One
+    // pass bins all three axes; the partition pass also gathers the two sides'
+    // centroid boxes, and the sides' boxes come from the chosen split's bins
+    // (min and max are exact, so these are the boxes a pass over each side
+    // would give).
     int build(uint32_t b, uint32_t e, int depth, const Box& bounds, const Box& cb, int& max_depth) {
         const uint32_t n = e - b;
         max_depth = std::max(max_depth, depth);
